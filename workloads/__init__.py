@@ -1,0 +1,245 @@
+"""Seeded synthetic inputs for the C-PCM (ISWIG) hot path.
+
+This module is shared by the CUDA path's tests and benchmark and by the
+CPU oracle's tests.  It holds NO arithmetic of the method itself: it only
+draws molecules (element, position, nuclear charge, cavity radius), basis
+sets (shell angular momenta, exponents, raw contraction coefficients) and
+density matrices.  Surface points, switching functions, integrals, the
+linear system and the energy are computed separately by each side.
+
+The paper's own inputs (PDB proteins, the SI test molecules, Lebedev
+tables and real basis sets) are not available; these generators stand in
+for them with the shapes the paper describes (Section 3: proteins of
+about 100-500 atoms, 6-31G-like basis sets, 110 points per atom, radii of
+1.2 x Bondi).
+
+Units: bohr for lengths, atomic units throughout.
+
+Conventions fixed here and assumed by both sides:
+  * shell_l: 0 = s, 1 = p, 2 = d, -1 = sp (an s and a p shell sharing one
+    set of exponents; its coefficients are given s first, then p).
+  * basis-function order: shells in order; within an sp shell s, px, py,
+    pz; p: x, y, z; d (6 Cartesian): xx, xy, xz, yy, yz, zz.
+  * the density is a full symmetric nbf x nbf matrix, row-major.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+ANGSTROM = 1.0 / 0.529177210903          # bohr per angstrom
+
+# Bondi (1964) van der Waals radii in angstrom.
+BONDI_ANGSTROM = {"H": 1.20, "C": 1.70, "N": 1.55, "O": 1.52, "S": 1.80}
+ATOMIC_NUMBER = {"H": 1, "C": 6, "N": 7, "O": 8, "S": 16}
+RADIUS_SCALE = 1.2                       # cavity radii are 1.2 x Bondi (Section 3)
+
+# Paper defaults (Section 3 and Eq. 1): water, C-PCM k = 0, 110 points per atom.
+EPSILON = 78.39
+K_COSMO = 0.0
+ZETA_110 = 4.9                           # optimized exponent used for 110-point spheres
+POINTS_PER_SPHERE = 110
+SWITCH_DROP = 1e-8                       # ISWIG screening threshold (Section 3)
+
+
+@dataclasses.dataclass
+class Molecule:
+    symbols: list
+    xyz: np.ndarray          # (natom, 3) bohr
+    Z: np.ndarray            # (natom,) nuclear charges
+    radius: np.ndarray       # (natom,) cavity radii in bohr (already 1.2 x Bondi)
+
+    @property
+    def natom(self) -> int:
+        return len(self.symbols)
+
+
+@dataclasses.dataclass
+class Basis:
+    shell_atom: np.ndarray   # (nshell,) int32
+    shell_l: np.ndarray      # (nshell,) int32, -1 = sp
+    shell_nprim: np.ndarray  # (nshell,) int32
+    exps: np.ndarray         # (sum nprim,) exponents, shell after shell
+    coefs: np.ndarray        # raw contraction coefficients; sp shells store
+                             # nprim s coefficients then nprim p coefficients
+
+    @property
+    def nshell(self) -> int:
+        return len(self.shell_l)
+
+    @property
+    def nbf(self) -> int:
+        per = {0: 1, 1: 3, 2: 6, -1: 4}
+        return int(sum(per[int(l)] for l in self.shell_l))
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    mol: Molecule
+    basis: Basis
+    P: np.ndarray            # (nbf, nbf) symmetric density
+    nocc: int
+    seed: int
+
+
+def _mol(symbols, xyz_bohr):
+    symbols = list(symbols)
+    xyz = np.asarray(xyz_bohr, dtype=np.float64).reshape(-1, 3)
+    Z = np.array([ATOMIC_NUMBER[s] for s in symbols], dtype=np.float64)
+    radius = np.array([RADIUS_SCALE * BONDI_ANGSTROM[s] * ANGSTROM for s in symbols])
+    return Molecule(symbols, xyz, Z, radius)
+
+
+def _loguniform(rng, lo, hi, n):
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n))
+
+
+# Per-element shell recipes: (shell_l, nprim, exponent range).  The ranges
+# sit inside the overall [0.1, 5000] span, a core shell tight and the outer
+# shells diffuse, as in 6-31G-like sets.
+_SHELLS_631G = {
+    "H": [(0, 3, (0.3, 30.0)), (0, 1, (0.1, 0.4))],
+    "C": [(0, 6, (3.0, 5000.0)), (-1, 3, (0.3, 30.0)), (-1, 1, (0.1, 0.4))],
+    "N": [(0, 6, (3.0, 5000.0)), (-1, 3, (0.3, 30.0)), (-1, 1, (0.1, 0.4))],
+    "O": [(0, 6, (3.0, 5000.0)), (-1, 3, (0.3, 30.0)), (-1, 1, (0.1, 0.4))],
+    "S": [(0, 6, (10.0, 5000.0)), (-1, 6, (1.0, 500.0)), (-1, 3, (0.2, 5.0)), (-1, 1, (0.1, 0.4))],
+}
+_D_SHELL = (2, 1, (0.3, 1.5))            # one polarisation d shell per heavy atom (6-31G*-like)
+
+
+def make_basis(mol: Molecule, recipe: dict, rng, d_on_heavy: bool = False) -> Basis:
+    sa, sl, sn, ex, co = [], [], [], [], []
+    for ia, s in enumerate(mol.symbols):
+        shells = list(recipe[s])
+        if d_on_heavy and s != "H":
+            shells.append(_D_SHELL)
+        for (l, n, (lo, hi)) in shells:
+            e = np.sort(_loguniform(rng, lo, hi, n))[::-1]
+            sa.append(ia); sl.append(l); sn.append(n); ex.extend(e)
+            ncoef = 2 * n if l == -1 else n
+            co.extend(rng.uniform(0.1, 1.0, size=ncoef))
+    return Basis(np.array(sa, np.int32), np.array(sl, np.int32), np.array(sn, np.int32),
+                 np.array(ex, np.float64), np.array(co, np.float64))
+
+
+def make_density(nbf: int, nocc: int, rng) -> np.ndarray:
+    """P = 2 C C^T with C the Euclidean-orthonormalised columns of a seeded
+    Gaussian nbf x nocc matrix (QR)."""
+    G = rng.standard_normal((nbf, nocc))
+    C, _ = np.linalg.qr(G)
+    P = 2.0 * C @ C.T
+    return 0.5 * (P + P.T)
+
+
+def water(seed: int = 150507851 + 0) -> Workload:
+    """3-atom O,H,H molecule: O at the origin, H at (+-1.43, 1.11, 0) bohr.
+    H: one s shell of 3 primitives; O: one s and one sp shell of 3
+    primitives; exponents log-uniform in [0.1, 130]; nbf = 7; 5 occupied."""
+    rng = np.random.default_rng(seed)
+    mol = _mol(["O", "H", "H"], [[0, 0, 0], [1.43, 1.11, 0], [-1.43, 1.11, 0]])
+    recipe = {"O": [(0, 3, (0.1, 130.0)), (-1, 3, (0.1, 130.0))],
+              "H": [(0, 3, (0.1, 130.0))]}
+    basis = make_basis(mol, recipe, rng)
+    P = make_density(basis.nbf, 5, rng)
+    return Workload("water", mol, basis, P, 5, seed)
+
+
+def _composition(natom: int, ratios=(("H", 50), ("C", 31), ("N", 9), ("O", 9), ("S", 1))):
+    tot = sum(r for _, r in ratios)
+    counts = [int(round(natom * r / tot)) for _, r in ratios]
+    counts[0] += natom - sum(counts)
+    out = []
+    for (s, _), c in zip(ratios, counts):
+        out += [s] * c
+    return out
+
+
+def random_walk_cluster(natom: int, rng, globule_radius_A: float,
+                        bond=(1.0, 1.5), nonbond=2.0, max_tries=20000) -> np.ndarray:
+    """Positions (angstrom) of a seeded branching random walk: each new atom
+    sits 1.0-1.5 A from a parent (mostly the previous atom) and at least
+    2.0 A from every other atom, inside a sphere of the given radius."""
+    pos = np.zeros((natom, 3))
+    n = 1
+    tries = 0
+    while n < natom:
+        tries += 1
+        if tries > max_tries * natom:
+            raise RuntimeError("random walk could not place all atoms; enlarge the globule")
+        parent = n - 1 if rng.random() < 0.7 else int(rng.integers(0, n))
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        cand = pos[parent] + rng.uniform(*bond) * d
+        if np.linalg.norm(cand) > globule_radius_A:
+            continue
+        dist = np.linalg.norm(pos[:n] - cand, axis=1)
+        dist[parent] = np.inf
+        if np.all(dist >= nonbond):
+            pos[n] = cand
+            n += 1
+    return pos
+
+
+def cluster(natom: int, seed: int, globule_radius_A: float, d_shells: bool = False,
+            nocc: int | None = None, name: str = "cluster") -> Workload:
+    """Protein-shaped cluster with H:C:N:O:S = 50:31:9:9:1, s/sp (and
+    optionally d) shells, and nocc = 2 * natom occupied orbitals unless given."""
+    rng = np.random.default_rng(seed)
+    symbols = _composition(natom)
+    rng.shuffle(symbols)
+    pos = random_walk_cluster(natom, rng, globule_radius_A)
+    mol = _mol(symbols, pos * ANGSTROM)
+    basis = make_basis(mol, _SHELLS_631G, rng, d_on_heavy=d_shells)
+    nocc = 2 * natom if nocc is None else nocc
+    nocc = min(nocc, basis.nbf)
+    P = make_density(basis.nbf, nocc, rng)
+    return Workload(name, mol, basis, P, nocc, seed)
+
+
+# Globule radii (angstrom) chosen so that the 110-point ISWIG surface of the
+# cluster has roughly the number of kept points the workloads call for.
+GLOBULE_RADIUS_A = {300: 9.0, 1000: 13.5}
+
+
+def config(i: int) -> Workload:
+    """The five workloads, by number:
+    0: water, nbf 7, M ~ 250.
+    1: 300-atom s/sp cluster, nbf ~ 1.6k, 600 occupied, M ~ 12k.
+    2: 1000-atom s/sp/d cluster, nbf ~ 9.5k, M ~ 45k.
+    3: the 300-atom cluster of 1 with d shells, nbf ~ 2.8k.
+    4: (batched conformations; see conformations()).
+    """
+    seed = 150507851 + i
+    if i == 0:
+        return water(seed)
+    if i == 1:
+        return cluster(300, seed, GLOBULE_RADIUS_A[300], nocc=600, name="cluster300_sp")
+    if i == 2:
+        return cluster(1000, seed, GLOBULE_RADIUS_A[1000], d_shells=True, nocc=2000,
+                       name="cluster1000_spd")
+    if i == 3:
+        w = cluster(300, 150507851 + 1, GLOBULE_RADIUS_A[300], d_shells=True, nocc=600,
+                    name="cluster300_spd")
+        return w
+    raise ValueError("config %d is a batch; use conformations()" % i)
+
+
+def small_cluster(natom: int, seed: int, d_shells: bool = False, radius_A: float | None = None,
+                  nocc: int | None = None) -> Workload:
+    """Small clusters for parity tests (sizes the oracle finishes in seconds)."""
+    if radius_A is None:
+        radius_A = max(3.0, 9.0 * (natom / 300.0) ** (1.0 / 3.0))
+    return cluster(natom, seed, radius_A, d_shells=d_shells, nocc=nocc,
+                   name="cluster%d%s" % (natom, "_spd" if d_shells else "_sp"))
+
+
+def conformations(n: int = 64, seed: int = 150507851 + 4, lo: int = 150, hi: int = 600):
+    """Seeded batch of peptide-like clusters with uniform-random sizes."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(lo, hi + 1, size=n)
+    out = []
+    for j, na in enumerate(sizes):
+        r = 9.0 * (na / 300.0) ** (1.0 / 3.0)
+        out.append(cluster(int(na), seed * 1000 + j, r, name="conf%d" % j))
+    return out
