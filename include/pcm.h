@@ -1,0 +1,184 @@
+/*
+ * pcm.h -- C ABI of the GB300 (sm_103a) C-PCM / ISWIG solvation hot path.
+ *
+ * The library computes, on one GPU, the quantities of the conductor-like
+ * polarizable continuum model with ISWIG switching/Gaussian discretization
+ * of Liu, Luehr, Kulik & Martinez (arXiv 1505.07851):
+ *
+ *   A q = -f (B z + c)                                   (Eq. 1)
+ *   A_kl = erf(zeta'_kl r_kl) / r_kl                      (Eq. 2, Eq. 8)
+ *   A_kk = zeta_k sqrt(2/pi) / S_k                        (Eq. 3, read as the r -> 0 limit of Eq. 2)
+ *   (B z)_k = sum_J Z_J erf(zeta_k r_kJ) / r_kJ           (Eq. 4)
+ *   c_k = sum_{mu nu} P_{mu nu} L^k_{mu nu}               (Eq. 5)
+ *   L^k_{mu nu} = -(mu | erf(zeta_k |r - r_k|)/|r - r_k| | nu)   (Eq. 6, Eq. 12)
+ *   dF_{mu nu} = sum_k q_k L^k_{mu nu}                    (Eq. 10)
+ *   dG = (Bz)^T q + c^T q + q^T A q / (2 f)               (Eq. 13)
+ *
+ * Units: atomic units (bohr, hartree).
+ *
+ * Conventions
+ *   - Every function returns a pcm_status; PCM_OK is 0.  pcm_strerror()
+ *     gives a message.  On an error nothing is written to the outputs
+ *     unless stated.
+ *   - A context (pcm_ctx) owns every device buffer it allocates (surface,
+ *     pair lists, the stored A, preconditioner, scratch).  Arrays passed
+ *     to a call are borrowed for the duration of that call only.
+ *   - By default pointers are HOST pointers; the library copies them to
+ *     and from the device.  With PCM_PTR_DEVICE in `flags` they are CUDA
+ *     device pointers on the context's device (e.g. from PyTorch).
+ *   - All GPU work is enqueued on the context's CUDA stream.  A call
+ *     returns after that work has finished unless PCM_ASYNC is given
+ *     (then only for device pointers; host pointers always synchronise).
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Surface points are numbered in the library's order: grouped by
+ *     Gaussian exponent class (points of equal zeta_k together, classes in
+ *     increasing zeta), and within a class by candidate index I*n + i
+ *     (atom I, sphere point i).  pcm_get_surface() returns each point's
+ *     candidate index.  c, Bz, rhs and q use this order.
+ *   - Basis functions are Cartesian; shells in input order; within an sp
+ *     shell s, px, py, pz; p: x, y, z; d: xx, xy, xz, yy, yz, zz.  Each
+ *     Cartesian primitive component is normalised to unit self-overlap and
+ *     multiplied by the raw contraction coefficient (no renormalisation of
+ *     the contracted function).
+ */
+#ifndef PCM_H
+#define PCM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pcm_status {
+    PCM_OK = 0,
+    PCM_ERR_ARG = 1,            /* invalid argument (size, pointer, NaN input, call order) */
+    PCM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    PCM_ERR_OOM = 3,            /* device or host allocation failed */
+    PCM_ERR_UNSUPPORTED = 4,    /* e.g. shell angular momentum above d */
+    PCM_ERR_NOT_CONVERGED = 5,  /* solver hit its iteration cap; q holds the last iterate */
+    PCM_ERR_TIMEOUT = 6         /* a bounded device wait gave up */
+} pcm_status;
+
+/* flags */
+#define PCM_PTR_DEVICE 1        /* array arguments are device pointers */
+#define PCM_ASYNC 2             /* do not synchronise the stream before returning */
+#define PCM_WARM 4              /* pcm_solve: q holds the initial guess */
+
+/* precision modes */
+#define PCM_FP64 0              /* every step in FP64 */
+#define PCM_MIXED 1             /* FP32 integrals and inner solver, FP64 accumulation and refinement */
+
+/* preconditioners (Section 4b-ii) */
+#define PCM_PRECOND_AUTO 0      /* Jacobi below `jacobi_below` points, else RBJ */
+#define PCM_PRECOND_NONE 1
+#define PCM_PRECOND_JACOBI 2
+#define PCM_PRECOND_RBJ 3
+
+typedef struct pcm_options {
+    double eps;                 /* dielectric constant, default 78.39 (Section 3) */
+    double k;                   /* f = (eps - 1) / (eps + k); default 0 (Eq. 1) */
+    double zeta;                /* sphere exponent of Eq. 7, default 4.9 (110 points) */
+    double switch_drop;         /* drop points with S_k below this, default 1e-8 (Section 3) */
+    double schwarz;             /* primitive-pair screening cutoff of Eq. 15 / Eq. 18, default 1e-12; 0 disables */
+    int rbj_block;              /* RBJ block size l, default 100 (Section 3) */
+    int precond;                /* PCM_PRECOND_*, default AUTO */
+    int jacobi_below;           /* AUTO uses Jacobi when M is below this, default 1000 (Section 4b-ii) */
+    int precision;              /* PCM_FP64 or PCM_MIXED */
+    int max_iter;               /* PCG iteration cap, default 5000 */
+    int device;                 /* CUDA device ordinal, default 0 */
+    unsigned long long seed;    /* RBJ pivot stream seed (splitmix64), default 0 */
+    void *stream;               /* cudaStream_t to use; NULL: the context creates its own */
+} pcm_options;
+
+typedef struct pcm_stats {
+    int iterations;             /* PCG iterations of the last solve */
+    int converged;              /* 1 if ||A q - rhs||_2 < delta was reached */
+    double delta;               /* threshold used by the last solve */
+    double rnorm;               /* final residual norm (recursively updated) */
+    int refinements;            /* outer FP64 refinement steps (PCM_MIXED) */
+    int M;                      /* surface points */
+    int nbf;                    /* basis functions */
+    long long pairs_candidate;  /* primitive pairs before screening */
+    long long pairs_kept;       /* primitive pairs surviving Eq. 15 */
+    long long pairs_esp;        /* pairs surviving the density-weighted test of Eq. 18 in the last pcm_esp */
+    double integrals_esp;       /* equivalent Cartesian primitive integrals of the last pcm_esp */
+    double integrals_fock;      /* equivalent Cartesian primitive integrals of the last pcm_fock */
+} pcm_stats;
+
+typedef struct pcm_ctx pcm_ctx;
+
+/* Fill `opt` with the paper's defaults (Section 3). */
+int pcm_default_options(pcm_options *opt);
+
+/* Create a context on opt->device (NULL opt: defaults).  *ctx receives the
+ * handle; destroy it with pcm_destroy. */
+int pcm_create(pcm_ctx **ctx, const pcm_options *opt);
+int pcm_destroy(pcm_ctx *ctx);
+
+/* Message for a status code (static storage). */
+const char *pcm_strerror(int status);
+
+/* Details of the last error raised on the calling host thread (empty if
+ * none); valid until the next failing call on that thread. */
+const char *pcm_last_error(void);
+
+/* Build the ISWIG cavity surface (Eq. 7, Eq. 9, Section 3).
+ * xyz: natom*3 nuclear positions (bohr); Z: natom nuclear charges;
+ * radius: natom sphere radii (bohr, already scaled, e.g. 1.2 x Bondi);
+ * pts_per_sphere: points per atom (Fibonacci sphere, equal weights
+ * w = 4 pi / n, used in place of Lebedev points).  Host pointers.
+ * Points with S_k < switch_drop are dropped; *M_out receives M.  Also
+ * stores A (Eq. 2, Eq. 3) and B z (Eq. 4) for the new surface.  Invalidates
+ * any preconditioner of a previous surface. */
+int pcm_build_surface(pcm_ctx *ctx, int natom, const double *xyz, const double *Z,
+                      const double *radius, int pts_per_sphere, int *M_out);
+
+/* Copy the surface out: xyzzs (M*5: x, y, z, zeta_k, S_k) and index (M:
+ * candidate index I*n + i).  Either may be NULL.  flags: PCM_PTR_DEVICE. */
+int pcm_get_surface(pcm_ctx *ctx, double *xyzzs, int *index, int flags);
+
+/* Set the basis (Eq. 11).  shell_atom/shell_l/shell_nprim: nshell entries,
+ * shell_l in {0, 1, 2, -1 (sp)}; exps: sum(nprim) exponents; coefs: raw
+ * contraction coefficients, shell after shell, an sp shell giving its
+ * nprim s coefficients then its nprim p coefficients.  Host pointers.
+ * Needs pcm_build_surface first (uses the atom positions).  Builds the
+ * primitive-pair list with the Schwarz-type screening of Eq. 15.
+ * *nbf_out receives the number of basis functions.  PCM_ERR_UNSUPPORTED
+ * for l > 2. */
+int pcm_set_basis(pcm_ctx *ctx, int nshell, const int *shell_atom, const int *shell_l,
+                  const int *shell_nprim, const double *exps, const double *coefs, int *nbf_out);
+
+/* Electrostatic potential of the electrons at the points, c (Eq. 5, Eq. 6):
+ * c_k = -sum_{mu nu} P_{mu nu} (mu|J_k|nu).  P: nbf*nbf symmetric,
+ * row-major.  c: M outputs.  Bz: optional (may be NULL) M outputs of
+ * (B z)_k.  Primitive pairs are screened with |P_{mu nu}| [ij|ij]^{1/2}
+ * (Eq. 18).  The context keeps c for pcm_solve(rhs = NULL). */
+int pcm_esp(pcm_ctx *ctx, const double *P, double *c, double *Bz, int flags);
+
+/* Solve A q = rhs (Eq. 1) by preconditioned CG to ||A q - rhs||_2 < delta
+ * (Eq. 20).  rhs: M entries, or NULL for -f (B z + c) with c from the last
+ * pcm_esp.  delta > 0: fixed threshold; delta <= 0: dynamic threshold of
+ * Eq. 21 from prev_diis_error (delta = (1e-3 prev / 0.01)^(1/1.07) clamped
+ * to [1e-10, 1]; prev_diis_error < 0 means first SCF step, delta = 1).
+ * q: M outputs (and the initial guess with PCM_WARM).  st: optional stats.
+ * Returns PCM_ERR_NOT_CONVERGED when max_iter is reached (q is the last
+ * iterate). */
+int pcm_solve(pcm_ctx *ctx, const double *rhs, double delta, double prev_diis_error, double *q,
+              pcm_stats *st, int flags);
+
+/* Solvation correction to the Fock matrix (Eq. 10, Eq. 16, Eq. 17):
+ * dF_{mu nu} = -sum_k q_k (mu|J_k|nu).  q: M inputs; dF: nbf*nbf outputs,
+ * symmetric, row-major. */
+int pcm_fock(pcm_ctx *ctx, const double *q, double *dF, int flags);
+
+/* Electrostatic solvation energy (Eq. 13) in hartree:
+ * E = (Bz)^T q + c^T q + q^T A q / (2 f).  q, c: M inputs (c may be NULL
+ * for the last pcm_esp result).  E: one host double. */
+int pcm_energy(pcm_ctx *ctx, const double *q, const double *c, double *E, int flags);
+
+/* Statistics of the context's last calls. */
+int pcm_get_stats(pcm_ctx *ctx, pcm_stats *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCM_H */

@@ -1,0 +1,252 @@
+"""Python binding of the GB300 C-PCM / ISWIG library (libpcm.so).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in include/pcm.h.  Arrays may be NumPy
+arrays (host memory; the library copies them) or CUDA torch tensors (device
+pointers, passed with PCM_PTR_DEVICE).  There is no CPU fallback: importing
+this package fails if the compiled library is missing.
+
+    from paper_1505_07851_gb300 import Context
+    ctx = Context()
+    M = ctx.build_surface(xyz, Z, radius)           # pcm_build_surface
+    nbf = ctx.set_basis(atom, l, nprim, exps, coefs) # pcm_set_basis
+    c = ctx.esp(P)                                   # pcm_esp
+    q, st = ctx.solve(prev_diis_error=-1)            # pcm_solve
+    dF = ctx.fock(q)                                 # pcm_fock
+    E = ctx.energy(q)                                # pcm_energy
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libpcm.so")
+
+PCM_OK = 0
+PCM_ERR_ARG = 1
+PCM_ERR_CUDA = 2
+PCM_ERR_OOM = 3
+PCM_ERR_UNSUPPORTED = 4
+PCM_ERR_NOT_CONVERGED = 5
+PCM_ERR_TIMEOUT = 6
+PCM_PTR_DEVICE = 1
+PCM_ASYNC = 2
+PCM_WARM = 4
+PCM_FP64 = 0
+PCM_MIXED = 1
+PRECOND = {"auto": 0, "none": 1, "jacobi": 2, "rbj": 3}
+
+
+class pcm_options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("k", ctypes.c_double), ("zeta", ctypes.c_double),
+                ("switch_drop", ctypes.c_double), ("schwarz", ctypes.c_double),
+                ("rbj_block", ctypes.c_int), ("precond", ctypes.c_int), ("jacobi_below", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("device", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p)]
+
+
+class pcm_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("delta", ctypes.c_double),
+                ("rnorm", ctypes.c_double), ("refinements", ctypes.c_int), ("M", ctypes.c_int),
+                ("nbf", ctypes.c_int), ("pairs_candidate", ctypes.c_longlong),
+                ("pairs_kept", ctypes.c_longlong), ("pairs_esp", ctypes.c_longlong),
+                ("integrals_esp", ctypes.c_double), ("integrals_fock", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PCMError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__("%s failed: %s (%d)%s" % (where, _lib.pcm_strerror(status).decode(), status,
+                                                   (": " + detail) if detail else ""))
+
+
+def _load():
+    if not os.path.exists(LIBPATH):
+        raise ImportError("libpcm.so is not built (run __graft_entry__.build() or "
+                          "python -m paper_1505_07851_gb300.build); there is no fallback")
+    L = ctypes.CDLL(LIBPATH)
+    vp = ctypes.c_void_p
+    i = ctypes.c_int
+    d = ctypes.c_double
+    sig = {
+        "pcm_default_options": (i, [ctypes.POINTER(pcm_options)]),
+        "pcm_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(pcm_options)]),
+        "pcm_destroy": (i, [vp]),
+        "pcm_strerror": (ctypes.c_char_p, [i]),
+        "pcm_last_error": (ctypes.c_char_p, []),
+        "pcm_build_surface": (i, [vp, i, vp, vp, vp, i, ctypes.POINTER(i)]),
+        "pcm_get_surface": (i, [vp, vp, vp, i]),
+        "pcm_set_basis": (i, [vp, i, vp, vp, vp, vp, vp, ctypes.POINTER(i)]),
+        "pcm_esp": (i, [vp, vp, vp, vp, i]),
+        "pcm_solve": (i, [vp, vp, d, d, vp, ctypes.POINTER(pcm_stats), i]),
+        "pcm_fock": (i, [vp, vp, vp, i]),
+        "pcm_energy": (i, [vp, vp, vp, ctypes.POINTER(d), i]),
+        "pcm_get_stats": (i, [vp, ctypes.POINTER(pcm_stats)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L, sorted(sig)
+
+
+_lib, EXPORTS = _load()
+globals().update({n: getattr(_lib, n) for n in EXPORTS})   # raw C entry points, same names
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, flags, keepalive) for a NumPy array or a CUDA torch tensor."""
+    if a is None:
+        return None, 0, None
+    if _is_torch(a):
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.int32
+        if not a.is_cuda or a.dtype != want or not a.is_contiguous():
+            raise TypeError("torch arguments must be contiguous CUDA tensors of dtype %s" % want)
+        return a.data_ptr(), PCM_PTR_DEVICE, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, 0, arr
+
+
+class Context:
+    """One pcm_ctx: surface, basis, stored A and preconditioner on one GPU."""
+
+    def __init__(self, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
+                 precond="auto", jacobi_below=1000, precision="fp64", max_iter=5000, device=0, seed=0,
+                 stream=None):
+        o = pcm_options()
+        _lib.pcm_default_options(ctypes.byref(o))
+        o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
+        o.rbj_block, o.precond, o.jacobi_below = rbj_block, PRECOND[precond], jacobi_below
+        o.precision = {"fp64": PCM_FP64, "mixed": PCM_MIXED}[precision]
+        o.max_iter, o.device, o.seed = max_iter, device, seed
+        o.stream = stream
+        h = ctypes.c_void_p()
+        self._check(_lib.pcm_create(ctypes.byref(h), ctypes.byref(o)), "pcm_create")
+        self._h = h
+        self.options = o
+        self.M = 0
+        self.nbf = 0
+
+    def _check(self, st, where, ok=(PCM_OK,)):
+        if st not in ok:
+            raise PCMError(st, where, _lib.pcm_last_error().decode())
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pcm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls -------------------------------------------------------------
+    def build_surface(self, xyz, Z, radius, pts_per_sphere=110):
+        xyz = np.ascontiguousarray(xyz, np.float64)
+        Z = np.ascontiguousarray(Z, np.float64)
+        radius = np.ascontiguousarray(radius, np.float64)
+        M = ctypes.c_int()
+        self._check(_lib.pcm_build_surface(self._h, len(Z), xyz.ctypes.data, Z.ctypes.data, radius.ctypes.data,
+                                           int(pts_per_sphere), ctypes.byref(M)), "pcm_build_surface")
+        self.M = M.value
+        self.nbf = 0
+        return self.M
+
+    def get_surface(self):
+        xyzzs = np.zeros((self.M, 5))
+        index = np.zeros(self.M, np.int32)
+        self._check(_lib.pcm_get_surface(self._h, xyzzs.ctypes.data, index.ctypes.data, 0), "pcm_get_surface")
+        return xyzzs, index
+
+    def set_basis(self, shell_atom, shell_l, shell_nprim, exps, coefs):
+        a = np.ascontiguousarray(shell_atom, np.int32)
+        l = np.ascontiguousarray(shell_l, np.int32)
+        n = np.ascontiguousarray(shell_nprim, np.int32)
+        e = np.ascontiguousarray(exps, np.float64)
+        c = np.ascontiguousarray(coefs, np.float64)
+        nbf = ctypes.c_int()
+        self._check(_lib.pcm_set_basis(self._h, len(l), a.ctypes.data, l.ctypes.data, n.ctypes.data,
+                                       e.ctypes.data, c.ctypes.data, ctypes.byref(nbf)), "pcm_set_basis")
+        self.nbf = nbf.value
+        return self.nbf
+
+    def _out(self, like, shape):
+        if like is not None and _is_torch(like):
+            import torch
+            return torch.empty(shape, dtype=torch.float64, device=like.device)
+        return np.zeros(shape)
+
+    def esp(self, P, out=None, bz_out=None, async_=False):
+        pP, fl, keep = _ptr(P, np.float64)
+        c = out if out is not None else self._out(P, (self.M,))
+        pc, flc, keepc = _ptr(c, np.float64)
+        pb, flb, keepb = _ptr(bz_out, np.float64)
+        if flc != fl or (bz_out is not None and flb != fl):
+            raise TypeError("all array arguments must live on the same side (host or device)")
+        flags = fl | (PCM_ASYNC if async_ else 0)
+        self._check(_lib.pcm_esp(self._h, pP, pc, pb, flags), "pcm_esp")
+        return c
+
+    def solve(self, rhs=None, delta=-1.0, prev_diis_error=-1.0, q=None, warm=False, like=None):
+        """Returns (q, stats dict).  delta <= 0 selects the dynamic threshold of Eq. 21."""
+        pr, flr, keepr = _ptr(rhs, np.float64)
+        if q is None:
+            q = self._out(rhs if rhs is not None else like, (self.M,))
+        pq, flq, keepq = _ptr(q, np.float64)
+        if rhs is not None and flr != flq:
+            raise TypeError("rhs and q must live on the same side (host or device)")
+        st = pcm_stats()
+        flags = flq | (PCM_WARM if warm else 0)
+        self._check(_lib.pcm_solve(self._h, pr, float(delta), float(prev_diis_error), pq, ctypes.byref(st),
+                                   flags), "pcm_solve", ok=(PCM_OK, PCM_ERR_NOT_CONVERGED))
+        return q, st.as_dict()
+
+    def fock(self, q, out=None, async_=False):
+        pq, fl, keep = _ptr(q, np.float64)
+        dF = out if out is not None else self._out(q, (self.nbf, self.nbf))
+        pF, flF, keepF = _ptr(dF, np.float64)
+        if flF != fl:
+            raise TypeError("q and dF must live on the same side (host or device)")
+        self._check(_lib.pcm_fock(self._h, pq, pF, fl | (PCM_ASYNC if async_ else 0)), "pcm_fock")
+        return dF
+
+    def energy(self, q, c=None):
+        pq, fl, keep = _ptr(q, np.float64)
+        pc, flc, keepc = _ptr(c, np.float64)
+        if c is not None and flc != fl:
+            raise TypeError("q and c must live on the same side (host or device)")
+        E = ctypes.c_double()
+        self._check(_lib.pcm_energy(self._h, pq, pc, ctypes.byref(E), fl), "pcm_energy")
+        return E.value
+
+    def stats(self):
+        st = pcm_stats()
+        self._check(_lib.pcm_get_stats(self._h, ctypes.byref(st)), "pcm_get_stats")
+        return st.as_dict()
+
+    # -- convenience -------------------------------------------------------
+    def setup(self, mol, basis, pts_per_sphere=110):
+        """build_surface + set_basis from workload-style objects."""
+        M = self.build_surface(mol.xyz, mol.Z, mol.radius, pts_per_sphere)
+        nbf = self.set_basis(basis.shell_atom, basis.shell_l, basis.shell_nprim, basis.exps, basis.coefs)
+        return M, nbf

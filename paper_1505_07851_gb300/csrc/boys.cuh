@@ -1,0 +1,80 @@
+// Boys function F_m(T) = \int_0^1 u^{2m} exp(-T u^2) du on the device.
+//
+// T < BOYS_TMAX: tabulated values at T_i = i * BOYS_DT and a Taylor expansion
+// in d = T - T_i, using dF_m/dT = -F_{m+1}:
+//     F_m(T) = sum_k F_{m+k}(T_i) (-d)^k / k!
+// (7 terms in FP64, 4 in FP32; |d| <= BOYS_DT / 2).
+// T >= BOYS_TMAX: F_0 = sqrt(pi / T) / 2 and F_m = F_{m-1} (2m - 1) / (2T);
+// the neglected exp(-T) terms are below 1e-14 relative for m <= 6 there.
+#pragma once
+#include "common.cuh"
+
+namespace pcm {
+
+constexpr double BOYS_TMAX = 48.0;
+constexpr double BOYS_DT = 1.0 / 32.0;
+constexpr double BOYS_INV_DT = 32.0;
+constexpr int BOYS_NROW = 1540;            // rows 0 .. 48*32 (+ margin)
+constexpr int BOYS_STRIDE64 = 16;          // doubles per row: m = 0 .. 15
+constexpr int BOYS_STRIDE32 = 8;           // floats per row:  m = 0 .. 7
+constexpr int BOYS_MCOL = 16;              // columns generated
+
+template <int MM>
+__device__ __forceinline__ void boys_eval(double T, const double *__restrict__ tab, double (&F)[MM + 1])
+{
+    static_assert(MM + 6 < BOYS_STRIDE64, "Boys table too narrow");
+    if (T < BOYS_TMAX) {
+        const int i = min(max(__double2int_rn(T * BOYS_INV_DT), 0), BOYS_NROW - 1);
+        const double d = T - (double)i * BOYS_DT;      // exact: BOYS_DT is a power of two
+        const double *row = tab + (size_t)i * BOYS_STRIDE64;
+        double r[MM + 7];
+#pragma unroll
+        for (int k = 0; k < MM + 7; ++k) r[k] = __ldg(row + k);
+        const double e1 = -d, e2 = -d * 0.5, e3 = -d * (1.0 / 3.0), e4 = -d * 0.25, e5 = -d * 0.2,
+                     e6 = -d * (1.0 / 6.0);
+#pragma unroll
+        for (int m = 0; m <= MM; ++m) {
+            double s = fma(r[m + 6], e6, r[m + 5]);
+            s = fma(s, e5, r[m + 4]);
+            s = fma(s, e4, r[m + 3]);
+            s = fma(s, e3, r[m + 2]);
+            s = fma(s, e2, r[m + 1]);
+            F[m] = fma(s, e1, r[m]);
+        }
+    } else {
+        const double rs = rsqrt(T);
+        const double half_inv_T = 0.5 * rs * rs;
+        F[0] = 0.88622692545275801365 * rs;           // sqrt(pi) / 2
+#pragma unroll
+        for (int m = 1; m <= MM; ++m) F[m] = F[m - 1] * (double)(2 * m - 1) * half_inv_T;
+    }
+}
+
+template <int MM>
+__device__ __forceinline__ void boys_eval(float T, const float *__restrict__ tab, float (&F)[MM + 1])
+{
+    static_assert(MM + 3 < BOYS_STRIDE32, "Boys table too narrow");
+    if (T < (float)BOYS_TMAX) {
+        const int i = min(max(__float2int_rn(T * (float)BOYS_INV_DT), 0), BOYS_NROW - 1);
+        const float d = fmaf((float)i, -(float)BOYS_DT, T);
+        const float *row = tab + (size_t)i * BOYS_STRIDE32;
+        float r[MM + 4];
+#pragma unroll
+        for (int k = 0; k < MM + 4; ++k) r[k] = __ldg(row + k);
+        const float e1 = -d, e2 = -d * 0.5f, e3 = -d * (1.0f / 3.0f);
+#pragma unroll
+        for (int m = 0; m <= MM; ++m) {
+            float s = fmaf(r[m + 3], e3, r[m + 2]);
+            s = fmaf(s, e2, r[m + 1]);
+            F[m] = fmaf(s, e1, r[m]);
+        }
+    } else {
+        const float rs = rsqrtf(T);
+        const float half_inv_T = 0.5f * rs * rs;
+        F[0] = 0.886226925f * rs;
+#pragma unroll
+        for (int m = 1; m <= MM; ++m) F[m] = F[m - 1] * (float)(2 * m - 1) * half_inv_T;
+    }
+}
+
+}  // namespace pcm

@@ -1,0 +1,182 @@
+// Host-side context of the C-PCM library: device buffers, the surface, the
+// basis and primitive-pair lists, the stored A and the preconditioner.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pcm.h"
+
+namespace pcm {
+
+// error plumbing -------------------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+void set_last_error(const char *fmt, ...);
+
+#define PCM_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            pcm::set_last_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? PCM_ERR_OOM : PCM_ERR_CUDA;               \
+        }                                                                                     \
+    } while (0)
+
+#define PCM_TRY(call)                  \
+    do {                               \
+        int s_ = (call);               \
+        if (s_ != PCM_OK) return s_;   \
+    } while (0)
+
+// A device buffer that frees itself.
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    int alloc(size_t count)
+    {
+        if (count <= n && p) return PCM_OK;
+        release();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_last_error("cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? PCM_ERR_OOM : PCM_ERR_CUDA;
+        }
+        n = count;
+        return PCM_OK;
+    }
+};
+
+// One angular-momentum class of primitive pairs (la >= lb), SoA.
+struct PairClass {
+    int la = 0, lb = 0;
+    // shell pairs of this class (host and device)
+    std::vector<int> h_spA, h_spB;          // expanded shell indices, l(A) = la, l(B) = lb
+    DBuf<int> spA, spB;                    // shell pair -> shells
+    DBuf<int> sp_start;                    // nsp + 1: range of kept primitive pairs per shell pair
+    DBuf<long long> sp_cand;               // nsp + 1: candidate offsets
+    int nsp = 0;
+    long long ncand = 0;
+    int npair = 0;                         // kept primitive pairs
+    // kept primitive pairs
+    DBuf<int> sp, ia, ib;                  // shell pair id, primitive index in A and in B
+    DBuf<double> Px, Py, Pz, p, pref, Q;   // centre, exponent sum, (2 pi / p) K_AB, Schwarz bound
+    // per-call ESP pairs (after the density test of Eq. 18), SoA; D has nherm(L) rows
+    int nesp = 0;
+    DBuf<double> eP, eD;                   // eP: 4 x nesp (Px, Py, Pz, p); eD: nherm x nesp
+    DBuf<float> eP32, eD32;                // FP32 copies for PCM_MIXED
+    DBuf<float> Pxyz32;                    // 4 x npair (Px, Py, Pz, p) FP32 for the Fock kernel
+};
+
+struct pcm_ctx_impl;
+
+}  // namespace pcm
+
+struct pcm_ctx {
+    pcm_options opt;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    // Boys tables
+    pcm::DBuf<double> boys64;
+    pcm::DBuf<float> boys32;
+
+    // molecule
+    int natom = 0;
+    std::vector<double> h_xyz, h_Z, h_radius;
+    pcm::DBuf<double> xyz, Z, radius;
+
+    // surface in library order (grouped by exponent class)
+    int npts_sphere = 0;
+    int M = 0;
+    int ncls = 0;
+    std::vector<double> h_cls_zeta;        // exponent of each class (ascending)
+    std::vector<int> h_cls_off;            // ncls + 1 offsets into the point list
+    pcm::DBuf<double> cls_zeta;            // ncls
+    pcm::DBuf<int> cls_off;                // ncls + 1
+    pcm::DBuf<double> px, py, pz, pzeta, pS, Bz;
+    pcm::DBuf<int> pindex, pcls;
+    pcm::DBuf<float> p32;                  // 4 x M: x, y, z (split high parts) and unused
+    pcm::DBuf<float> p32lo;                // 3 x M: low parts of the split coordinates
+
+    // stored A (FP64), leading dimension lda
+    int lda = 0;
+    pcm::DBuf<double> A;
+    pcm::DBuf<float> A32;                  // Jacobi-scaled FP32 copy for PCM_MIXED
+    pcm::DBuf<double> dinv;                // 1 / A_kk
+
+    // basis (expanded: sp shells split into an s and a p shell)
+    int nbf = 0;
+    int nshell = 0;
+    std::vector<int> h_sh_atom, h_sh_l, h_sh_nprim, h_sh_off, h_sh_bf;
+    pcm::DBuf<int> sh_atom, sh_l, sh_nprim, sh_off, sh_bf;
+    pcm::DBuf<double> exps, cnorm;         // exponent and coefficient x base normalisation per primitive
+    pcm::PairClass cls[6];                 // (0,0) (1,0) (1,1) (2,0) (2,1) (2,2)
+    long long pairs_candidate = 0, pairs_kept = 0;
+
+    // last results
+    pcm::DBuf<double> c_last;
+    bool have_c = false;
+
+    // preconditioner
+    int pc_kind = 0;                       // resolved PCM_PRECOND_*
+    bool pc_ready = false;
+    int rbj_l = 0, rbj_nblk = 0;
+    pcm::DBuf<int> rbj_perm;               // M: block-ordered point indices
+    pcm::DBuf<double> rbj_inv;             // nblk x l x l inverses (padded)
+
+    // solver work vectors and scalars
+    pcm::DBuf<double> vx, vr, vz, vp, vAp, vrhs, vtmp;
+    pcm::DBuf<double> red;                 // partial sums
+    pcm::DBuf<double> scal;                // device scalars
+    pcm::DBuf<int> iscal;                  // device ints (done flag, iteration count)
+    pcm::DBuf<unsigned int> counter;       // last-block counters
+    double *h_pinned = nullptr;            // pinned host scratch for scalars
+
+    // integral scratch
+    pcm::DBuf<double> esp_part;            // nseg x M partial potentials
+    pcm::DBuf<double> fock_W;              // nsplit x nherm x npair accumulators
+    pcm::DBuf<double> dP, dF;              // device copies of P and dF for host-pointer calls
+    pcm::DBuf<double> vin, vout;           // device copies of M-vectors for host-pointer calls
+    pcm::DBuf<unsigned char> flags8;
+    pcm::DBuf<int> idx32, scan32;
+    pcm::DBuf<long long> scan64;
+
+    pcm_stats stats;
+};
+
+namespace pcm {
+// launchers implemented in the .cu files ------------------------------------
+int boys_build_tables(pcm_ctx *c);
+int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, const double *radius, int n);
+int basis_build(pcm_ctx *c, int nshell, const int *shell_atom, const int *shell_l, const int *shell_nprim,
+                const double *exps, const double *coefs);
+int esp_compute(pcm_ctx *c, const double *dP, double *dc);
+int fock_compute(pcm_ctx *c, const double *dq, double *ddF);
+int solver_prepare(pcm_ctx *c);
+int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st);
+int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E);
+
+// stable compaction of n byte flags: out[j] = i of the j-th nonzero flag (if
+// out != nullptr), pos[i] = number of nonzero flags before i (n + 1 entries,
+// if pos != nullptr); *count_dev = total.  Scratch is taken from the context.
+int compact_flags(pcm_ctx *c, const unsigned char *flags, long long n, int *out, int *pos, int *count_dev);
+}  // namespace pcm

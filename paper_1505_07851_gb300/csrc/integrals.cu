@@ -1,0 +1,576 @@
+// The two contractions of the erf-screened one-electron integrals:
+//   c_k        = -sum_{mu nu} P_{mu nu} (mu|J_k|nu)       (Eq. 5, Eq. 6, Eq. 19)
+//   dF_{mu nu} = -sum_k q_k (mu|J_k|nu)                   (Eq. 10, Eq. 16, Eq. 17)
+// with (mu|J_k|nu) contracted from primitives (Eq. 12).
+//
+// Integrals are evaluated in the McMurchie-Davidson (Hermite) form.  For a
+// primitive pair with exponents a, b, p = a + b, centre P and
+// K = exp(-ab/p |A-B|^2), and a point with exponent zeta:
+//   rho = p zeta^2 / (p + zeta^2),  U = sqrt(zeta^2 / (p + zeta^2))
+//   [a|J|b] = (2 pi / p) K U sum_tuv E^{ab}_tuv R_tuv(rho, P - C)
+//   R^(n)_000 = (-2 rho)^n F_n(rho |P - C|^2)
+// (the erf operator is the Coulomb operator between the pair's Gaussian
+// charge and a Gaussian charge of exponent zeta^2).  The ESP kernel dots each
+// pair's density-weighted Hermite coefficients D_tuv into R_tuv; the Fock
+// kernel accumulates W_tuv = sum_k q_k U R_tuv per pair and contracts with
+// E^{ab}_tuv at the end.  Both contractions are reduced on the device in a
+// fixed order, so results are bit-reproducible.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "boys.cuh"
+#include "common.cuh"
+#include "context.h"
+
+namespace pcm {
+
+__device__ inline double comp_factor_i(int l, int c)
+{
+    if (l < 2) return 1.0;
+    return (c == 1 || c == 2 || c == 4) ? 1.7320508075688772935 : 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// ESP prologue: density test of Eq. 18 and Hermite density coefficients
+//   D_tuv = -(2 pi / p) K sum_{a in A, b in B} W_ab c_a c_b E^{ab}_tuv
+// with W_ab = P_ab + P_ba for off-diagonal primitive pairs (a pair stands for
+// itself and its mirror image) and W_ab = P_ab for i = j in a diagonal shell pair.
+// ---------------------------------------------------------------------------
+template <int LA, int LB>
+__global__ void esp_flag_kernel(int npair, const int *__restrict__ sp, const int *__restrict__ ia,
+                                const int *__restrict__ ib, const int *__restrict__ spA, const int *__restrict__ spB,
+                                const int *__restrict__ sh_bf, const double *__restrict__ Q,
+                                const double *__restrict__ Pm, int nbf, double thresh, unsigned char *__restrict__ flag)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= npair) return;
+    const int s = sp[r];
+    const int A = spA[s], B = spB[s];
+    const bool mirror = (A != B) || (ia[r] != ib[r]);
+    const int fa = sh_bf[A], fb = sh_bf[B];
+    double wmax = 0.0;
+    for (int a = 0; a < ncart(LA); ++a)
+        for (int b = 0; b < ncart(LB); ++b) {
+            double w = Pm[(size_t)(fa + a) * nbf + fb + b];
+            if (mirror) w += Pm[(size_t)(fb + b) * nbf + fa + a];
+            wmax = fmax(wmax, fabs(w));
+        }
+    flag[r] = (thresh <= 0.0 || wmax * Q[r] >= thresh) ? 1 : 0;
+}
+
+template <int LA, int LB>
+__global__ void esp_coef_kernel(int nesp, const int *__restrict__ list, const int *__restrict__ sp,
+                                const int *__restrict__ ia, const int *__restrict__ ib, const int *__restrict__ spA,
+                                const int *__restrict__ spB, const int *__restrict__ sh_atom,
+                                const int *__restrict__ sh_off, const int *__restrict__ sh_bf,
+                                const double *__restrict__ cnorm, const double *__restrict__ xyz,
+                                const double *__restrict__ Px, const double *__restrict__ Py,
+                                const double *__restrict__ Pz, const double *__restrict__ pp,
+                                const double *__restrict__ pref, const double *__restrict__ Pm, int nbf,
+                                double *__restrict__ eP, double *__restrict__ eD, float *__restrict__ eP32,
+                                float *__restrict__ eD32)
+{
+    constexpr int L = LA + LB;
+    constexpr int NH = nherm(L);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nesp) return;
+    const int r = list[j];
+    const int s = sp[r];
+    const int A = spA[s], B = spB[s];
+    const int i1 = ia[r], i2 = ib[r];
+    const bool mirror = (A != B) || (i1 != i2);
+    const double p = pp[r];
+    const double P[3] = {Px[r], Py[r], Pz[r]};
+    const double *RA = xyz + 3 * sh_atom[A], *RB = xyz + 3 * sh_atom[B];
+    E1D Ex, Ey, Ez;
+    const double inv2p = 0.5 / p;
+    hermite_E1D(LA, LB, P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
+    hermite_E1D(LA, LB, P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
+    hermite_E1D(LA, LB, P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
+    const double cc = cnorm[sh_off[A] + i1] * cnorm[sh_off[B] + i2];
+    const int fa = sh_bf[A], fb = sh_bf[B];
+    double D[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) D[h] = 0.0;
+    for (int a = 0; a < ncart(LA); ++a) {
+        int ax, ay, az;
+        cart_xyz(LA, a, ax, ay, az);
+        for (int b = 0; b < ncart(LB); ++b) {
+            int bx, by, bz;
+            cart_xyz(LB, b, bx, by, bz);
+            double w = Pm[(size_t)(fa + a) * nbf + fb + b];
+            if (mirror) w += Pm[(size_t)(fb + b) * nbf + fa + a];
+            w *= cc * comp_factor_i(LA, a) * comp_factor_i(LB, b);
+#pragma unroll
+            for (int t = 0; t <= L; ++t)
+#pragma unroll
+                for (int u = 0; u <= L - t; ++u)
+#pragma unroll
+                    for (int v = 0; v <= L - t - u; ++v) {
+                        if (t > ax + bx || u > ay + by || v > az + bz) continue;
+                        D[hidx(t, u, v)] += w * Ex.e[ax][bx][t] * Ey.e[ay][by][u] * Ez.e[az][bz][v];
+                    }
+        }
+    }
+    const double scale = -pref[r];
+    eP[0 * (size_t)nesp + j] = P[0];
+    eP[1 * (size_t)nesp + j] = P[1];
+    eP[2 * (size_t)nesp + j] = P[2];
+    eP[3 * (size_t)nesp + j] = p;
+    eP32[0 * (size_t)nesp + j] = (float)P[0];
+    eP32[1 * (size_t)nesp + j] = (float)P[1];
+    eP32[2 * (size_t)nesp + j] = (float)P[2];
+    eP32[3 * (size_t)nesp + j] = (float)p;
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+        eD[(size_t)h * nesp + j] = scale * D[h];
+        eD32[(size_t)h * nesp + j] = (float)(scale * D[h]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ESP main kernel: one thread per surface point (PPT points per thread),
+// looping over tiles of TP primitive pairs staged in shared memory.  The
+// per-(pair, exponent class) factors rho and U are computed once per tile for
+// the classes present in the block (at most MAXCB).
+// grid.x: point blocks (ranges from blk_off), grid.y: pair segments.
+// ---------------------------------------------------------------------------
+constexpr int ESP_NT = 128;
+constexpr int ESP_PPT = 2;
+constexpr int ESP_TP = 32;
+constexpr int ESP_MAXCB = 8;
+
+template <int L>
+__global__ void __launch_bounds__(ESP_NT) esp_kernel_f64(int nesp, int seglen, const double *__restrict__ eP,
+                                                         const double *__restrict__ eD, const int *__restrict__ blk_off,
+                                                         const double *__restrict__ px, const double *__restrict__ py,
+                                                         const double *__restrict__ pz, const int *__restrict__ pcls,
+                                                         const double *__restrict__ cls_zeta,
+                                                         const double *__restrict__ boys, int M,
+                                                         double *__restrict__ part)
+{
+    constexpr int NH = nherm(L);
+    __shared__ double sP[4][ESP_TP];
+    __shared__ double sD[NH][ESP_TP];
+    __shared__ double sRho[ESP_MAXCB][ESP_TP];
+    __shared__ double sU[ESP_MAXCB][ESP_TP];
+
+    const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
+    const int cmin = pcls[k0];
+    const int ncb = pcls[k1 - 1] - cmin + 1;  // <= ESP_MAXCB by construction of blk_off
+    const int j0 = blockIdx.y * seglen;
+    const int j1 = min(nesp, j0 + seglen);
+
+    double x[ESP_PPT], y[ESP_PPT], z[ESP_PPT], acc[ESP_PPT];
+    int e[ESP_PPT];
+    bool on[ESP_PPT];
+#pragma unroll
+    for (int q = 0; q < ESP_PPT; ++q) {
+        const int k = k0 + threadIdx.x + q * ESP_NT;
+        on[q] = k < k1;
+        const int kk = on[q] ? k : k0;
+        x[q] = px[kk];
+        y[q] = py[kk];
+        z[q] = pz[kk];
+        e[q] = pcls[kk] - cmin;
+        acc[q] = 0.0;
+    }
+
+    for (int jt = j0; jt < j1; jt += ESP_TP) {
+        const int nt = min(ESP_TP, j1 - jt);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 4 * ESP_TP; t += ESP_NT) {
+            const int f = t / ESP_TP, jj = t % ESP_TP;
+            sP[f][jj] = jj < nt ? eP[(size_t)f * nesp + jt + jj] : 1.0;
+        }
+        for (int t = threadIdx.x; t < NH * ESP_TP; t += ESP_NT) {
+            const int h = t / ESP_TP, jj = t % ESP_TP;
+            sD[h][jj] = jj < nt ? eD[(size_t)h * nesp + jt + jj] : 0.0;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ncb * ESP_TP; t += ESP_NT) {
+            const int ec = t / ESP_TP, jj = t % ESP_TP;
+            const double zz = cls_zeta[cmin + ec];
+            const double z2 = zz * zz;
+            const double p = sP[3][jj];
+            const double inv = 1.0 / (p + z2);
+            sRho[ec][jj] = p * z2 * inv;
+            sU[ec][jj] = sqrt(z2 * inv);
+        }
+        __syncthreads();
+        for (int jj = 0; jj < nt; ++jj) {
+            const double Px = sP[0][jj], Py = sP[1][jj], Pz = sP[2][jj];
+#pragma unroll
+            for (int q = 0; q < ESP_PPT; ++q) {
+                const double rho = sRho[e[q]][jj];
+                const double X = Px - x[q], Y = Py - y[q], Z = Pz - z[q];
+                const double T = rho * (X * X + Y * Y + Z * Z);
+                double F[L + 1];
+                boys_eval<L>(T, boys, F);
+                double dot;
+                if constexpr (L == 0) {
+                    dot = sD[0][jj] * F[0];
+                } else {
+                    double Rn[L + 1];
+                    double m2r = -2.0 * rho, f = 1.0;
+#pragma unroll
+                    for (int n = 0; n <= L; ++n) {
+                        Rn[n] = f * F[n];
+                        f *= m2r;
+                    }
+                    double R[NH];
+                    hermite_R<L, double>(X, Y, Z, Rn, R);
+                    dot = 0.0;
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) dot = fma(sD[h][jj], R[h], dot);
+                }
+                acc[q] = fma(sU[e[q]][jj], dot, acc[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < ESP_PPT; ++q) {
+        const int k = k0 + threadIdx.x + q * ESP_NT;
+        if (on[q]) part[(size_t)blockIdx.y * M + k] = acc[q];
+    }
+}
+
+// c_k = sum over segments of the partial sums, in segment order.
+__global__ void esp_reduce_kernel(int M, int nseg, const double *__restrict__ part, double *__restrict__ c)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    double s = 0.0;
+    for (int g = 0; g < nseg; ++g) s += part[(size_t)g * M + k];
+    c[k] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Fock main kernel: one thread per primitive pair, looping over the points of
+// its split in exponent-class order, staged in shared memory tiles of TQ.
+// W[split][h][pair] = sum_k q_k U_k R_h(rho_k, P - C_k)
+// ---------------------------------------------------------------------------
+constexpr int FOCK_NT = 128;
+constexpr int FOCK_TQ = 128;
+
+template <int L>
+__global__ void __launch_bounds__(FOCK_NT) fock_kernel_f64(int npair, const double *__restrict__ gPx,
+                                                           const double *__restrict__ gPy,
+                                                           const double *__restrict__ gPz,
+                                                           const double *__restrict__ gp, int ksplit,
+                                                           const double *__restrict__ px, const double *__restrict__ py,
+                                                           const double *__restrict__ pz, const double *__restrict__ q,
+                                                           int M, int ncls, const int *__restrict__ cls_off,
+                                                           const double *__restrict__ cls_zeta,
+                                                           const double *__restrict__ boys, double *__restrict__ W)
+{
+    constexpr int NH = nherm(L);
+    __shared__ double sx[FOCK_TQ], sy[FOCK_TQ], sz[FOCK_TQ], sq[FOCK_TQ];
+    const int r = blockIdx.x * FOCK_NT + threadIdx.x;
+    const bool active = r < npair;
+    const int rr = active ? r : 0;
+    const double Px = gPx[rr], Py = gPy[rr], Pz = gPz[rr], p = gp[rr];
+    const int ka = blockIdx.y * ksplit;
+    const int kb = min(M, ka + ksplit);
+    double w[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) w[h] = 0.0;
+    for (int ec = 0; ec < ncls; ++ec) {
+        const int a = max(ka, cls_off[ec]), b = min(kb, cls_off[ec + 1]);
+        if (a >= b) continue;
+        const double zz = cls_zeta[ec];
+        const double z2 = zz * zz;
+        const double inv = 1.0 / (p + z2);
+        const double rho = p * z2 * inv;
+        const double U = sqrt(z2 * inv);
+        const double m2r = -2.0 * rho;
+        for (int t0 = a; t0 < b; t0 += FOCK_TQ) {
+            const int nt = min(FOCK_TQ, b - t0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < nt; t += FOCK_NT) {
+                sx[t] = px[t0 + t];
+                sy[t] = py[t0 + t];
+                sz[t] = pz[t0 + t];
+                sq[t] = q[t0 + t];
+            }
+            __syncthreads();
+            for (int kk = 0; kk < nt; ++kk) {
+                const double X = Px - sx[kk], Y = Py - sy[kk], Z = Pz - sz[kk];
+                const double T = rho * (X * X + Y * Y + Z * Z);
+                double F[L + 1];
+                boys_eval<L>(T, boys, F);
+                const double sc = sq[kk] * U;
+                if constexpr (L == 0) {
+                    w[0] = fma(sc, F[0], w[0]);
+                } else {
+                    double Rn[L + 1];
+                    double f = sc;
+#pragma unroll
+                    for (int n = 0; n <= L; ++n) {
+                        Rn[n] = f * F[n];
+                        f *= m2r;
+                    }
+                    double R[NH];
+                    hermite_R<L, double>(X, Y, Z, Rn, R);
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) w[h] += R[h];
+                }
+            }
+        }
+    }
+    if (active) {
+#pragma unroll
+        for (int h = 0; h < NH; ++h) W[((size_t)blockIdx.y * NH + h) * npair + r] = w[h];
+    }
+}
+
+// Fock epilogue: one thread per shell pair.  For each kept primitive pair of
+// the shell pair, L_ab = -(2 pi/p) K sum_tuv E^{ab}_tuv W_tuv is contracted
+// with c_a c_b (Eq. 16) and summed in pair order (Eq. 17).  A diagonal shell
+// pair's off-diagonal primitive pair also adds its mirror image.  Both dF
+// blocks (A,B) and (B,A) are written; every element of dF is written.
+template <int LA, int LB>
+__global__ void fock_epilogue_kernel(int nsp, int npair, int nsplit, const int *__restrict__ spA,
+                                     const int *__restrict__ spB, const int *__restrict__ sp_start,
+                                     const int *__restrict__ ia, const int *__restrict__ ib,
+                                     const int *__restrict__ sh_atom, const int *__restrict__ sh_off,
+                                     const int *__restrict__ sh_bf, const double *__restrict__ cnorm,
+                                     const double *__restrict__ xyz, const double *__restrict__ Px,
+                                     const double *__restrict__ Py, const double *__restrict__ Pz,
+                                     const double *__restrict__ pp, const double *__restrict__ pref,
+                                     const double *__restrict__ W, int nbf, double *__restrict__ dF)
+{
+    constexpr int L = LA + LB;
+    constexpr int NH = nherm(L);
+    constexpr int NA = ncart(LA), NB = ncart(LB);
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsp) return;
+    const int A = spA[s], B = spB[s];
+    const double *RA = xyz + 3 * sh_atom[A], *RB = xyz + 3 * sh_atom[B];
+    double G[NA * NB];
+#pragma unroll
+    for (int t = 0; t < NA * NB; ++t) G[t] = 0.0;
+    for (int r = sp_start[s]; r < sp_start[s + 1]; ++r) {
+        double w[NH];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            double acc = 0.0;
+            for (int g = 0; g < nsplit; ++g) acc += W[((size_t)g * NH + h) * npair + r];
+            w[h] = acc;
+        }
+        const double p = pp[r];
+        const double P[3] = {Px[r], Py[r], Pz[r]};
+        E1D Ex, Ey, Ez;
+        const double inv2p = 0.5 / p;
+        hermite_E1D(LA, LB, P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
+        hermite_E1D(LA, LB, P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
+        hermite_E1D(LA, LB, P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
+        const int i1 = ia[r], i2 = ib[r];
+        const double cc = -pref[r] * cnorm[sh_off[A] + i1] * cnorm[sh_off[B] + i2];
+        const bool mirror = (A == B) && (i1 != i2);
+        for (int a = 0; a < NA; ++a) {
+            int ax, ay, az;
+            cart_xyz(LA, a, ax, ay, az);
+            for (int b = 0; b < NB; ++b) {
+                int bx, by, bz;
+                cart_xyz(LB, b, bx, by, bz);
+                double v = 0.0;
+#pragma unroll
+                for (int t = 0; t <= L; ++t)
+#pragma unroll
+                    for (int u = 0; u <= L - t; ++u)
+#pragma unroll
+                        for (int vv = 0; vv <= L - t - u; ++vv) {
+                            if (t > ax + bx || u > ay + by || vv > az + bz) continue;
+                            v += Ex.e[ax][bx][t] * Ey.e[ay][by][u] * Ez.e[az][bz][vv] * w[hidx(t, u, vv)];
+                        }
+                v *= cc * comp_factor_i(LA, a) * comp_factor_i(LB, b);
+                G[a * NB + b] += v;
+                if (mirror) G[b * NB + a] += v;
+            }
+        }
+    }
+    const int fa = sh_bf[A], fb = sh_bf[B];
+    for (int a = 0; a < NA; ++a)
+        for (int b = 0; b < NB; ++b) {
+            dF[(size_t)(fa + a) * nbf + fb + b] = G[a * NB + b];
+            dF[(size_t)(fb + b) * nbf + fa + a] = G[a * NB + b];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int target_ctas(pcm_ctx *) { return 152 * 8; }
+
+// point blocks of at most ESP_NT*ESP_PPT points spanning at most ESP_MAXCB classes
+static void esp_blocks(pcm_ctx *c, std::vector<int> &off)
+{
+    off.clear();
+    const int cap = ESP_NT * ESP_PPT;
+    int k = 0;
+    // class of point k from the class offsets
+    auto cls_of = [&](int kk) {
+        return (int)(std::upper_bound(c->h_cls_off.begin(), c->h_cls_off.end(), kk) - c->h_cls_off.begin()) - 1;
+    };
+    off.push_back(0);
+    while (k < c->M) {
+        int end = std::min(c->M, k + cap);
+        const int c0 = cls_of(k);
+        if (cls_of(end - 1) - c0 + 1 > ESP_MAXCB) end = c->h_cls_off[c0 + ESP_MAXCB];
+        off.push_back(end);
+        k = end;
+    }
+}
+
+template <int L>
+static int launch_esp_class(pcm_ctx *c, PairClass &pc, const int *blk, int nblk, int seg_base, int nseg_cls,
+                            int seglen)
+{
+    if (pc.nesp == 0) return PCM_OK;
+    dim3 grid(nblk, nseg_cls);
+    esp_kernel_f64<L><<<grid, ESP_NT, 0, c->stream>>>(pc.nesp, seglen, pc.eP.p, pc.eD.p, blk, c->px.p, c->py.p,
+                                                       c->pz.p, c->pcls.p, c->cls_zeta.p, c->boys64.p, c->M,
+                                                       c->esp_part.p + (size_t)seg_base * c->M);
+    PCM_CUDA(cudaGetLastError());
+    return PCM_OK;
+}
+
+template <int LA, int LB>
+static int esp_prepare_class(pcm_ctx *c, PairClass &pc, const double *dP)
+{
+    pc.nesp = 0;
+    if (pc.npair == 0) return PCM_OK;
+    PCM_TRY(c->flags8.alloc(pc.npair));
+    PCM_TRY(c->idx32.alloc(pc.npair));
+    esp_flag_kernel<LA, LB><<<(pc.npair + 127) / 128, 128, 0, c->stream>>>(
+        pc.npair, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_bf.p, pc.Q.p, dP, c->nbf, c->opt.schwarz,
+        c->flags8.p);
+    PCM_CUDA(cudaGetLastError());
+    PCM_TRY(compact_flags(c, c->flags8.p, pc.npair, c->idx32.p, nullptr, c->iscal.p));
+    int n = 0;
+    PCM_CUDA(cudaMemcpyAsync(&n, c->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PCM_CUDA(cudaStreamSynchronize(c->stream));
+    pc.nesp = n;
+    if (n == 0) return PCM_OK;
+    constexpr int NH = nherm(LA + LB);
+    PCM_TRY(pc.eP.alloc(4 * (size_t)n));
+    PCM_TRY(pc.eD.alloc((size_t)NH * n));
+    PCM_TRY(pc.eP32.alloc(4 * (size_t)n));
+    PCM_TRY(pc.eD32.alloc((size_t)NH * n));
+    esp_coef_kernel<LA, LB><<<(n + 127) / 128, 128, 0, c->stream>>>(
+        n, c->idx32.p, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_off.p, c->sh_bf.p,
+        c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, dP, c->nbf, pc.eP.p, pc.eD.p, pc.eP32.p,
+        pc.eD32.p);
+    PCM_CUDA(cudaGetLastError());
+    return PCM_OK;
+}
+
+int esp_compute(pcm_ctx *c, const double *dP, double *dc)
+{
+    PCM_TRY((esp_prepare_class<0, 0>(c, c->cls[0], dP)));
+    PCM_TRY((esp_prepare_class<1, 0>(c, c->cls[1], dP)));
+    PCM_TRY((esp_prepare_class<1, 1>(c, c->cls[2], dP)));
+    PCM_TRY((esp_prepare_class<2, 0>(c, c->cls[3], dP)));
+    PCM_TRY((esp_prepare_class<2, 1>(c, c->cls[4], dP)));
+    PCM_TRY((esp_prepare_class<2, 2>(c, c->cls[5], dP)));
+
+    std::vector<int> off;
+    esp_blocks(c, off);
+    const int nblk = (int)off.size() - 1;
+    DBuf<int> blk;
+    PCM_TRY(blk.alloc(off.size()));
+    PCM_CUDA(cudaMemcpyAsync(blk.p, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+
+    // pair segments per class
+    int nseg[6], seglen[6], total = 0;
+    long long pesp = 0;
+    double ints = 0.0;
+    for (int k = 0; k < 6; ++k) {
+        PairClass &pc = c->cls[k];
+        pesp += pc.nesp;
+        ints += (double)pc.nesp * ncart(pc.la) * ncart(pc.lb) * c->M;
+        if (pc.nesp == 0) {
+            nseg[k] = 0;
+            seglen[k] = 0;
+            continue;
+        }
+        const int maxseg = (pc.nesp + ESP_TP - 1) / ESP_TP;
+        int ns = std::max(1, std::min(maxseg, (target_ctas(c) + nblk - 1) / nblk));
+        int sl = (pc.nesp + ns - 1) / ns;
+        sl = (sl + ESP_TP - 1) / ESP_TP * ESP_TP;
+        ns = (pc.nesp + sl - 1) / sl;
+        nseg[k] = ns;
+        seglen[k] = sl;
+        total += ns;
+    }
+    c->stats.pairs_esp = pesp;
+    c->stats.integrals_esp = ints;
+    if (total == 0) {
+        PCM_CUDA(cudaMemsetAsync(dc, 0, c->M * sizeof(double), c->stream));
+        return PCM_OK;
+    }
+    PCM_TRY(c->esp_part.alloc((size_t)total * c->M));
+    int base = 0;
+    PCM_TRY((launch_esp_class<0>(c, c->cls[0], blk.p, nblk, base, nseg[0], seglen[0])));
+    base += nseg[0];
+    PCM_TRY((launch_esp_class<1>(c, c->cls[1], blk.p, nblk, base, nseg[1], seglen[1])));
+    base += nseg[1];
+    PCM_TRY((launch_esp_class<2>(c, c->cls[2], blk.p, nblk, base, nseg[2], seglen[2])));
+    base += nseg[2];
+    PCM_TRY((launch_esp_class<2>(c, c->cls[3], blk.p, nblk, base, nseg[3], seglen[3])));
+    base += nseg[3];
+    PCM_TRY((launch_esp_class<3>(c, c->cls[4], blk.p, nblk, base, nseg[4], seglen[4])));
+    base += nseg[4];
+    PCM_TRY((launch_esp_class<4>(c, c->cls[5], blk.p, nblk, base, nseg[5], seglen[5])));
+    base += nseg[5];
+    esp_reduce_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
+    PCM_CUDA(cudaGetLastError());
+    PCM_CUDA(cudaStreamSynchronize(c->stream));  // blk is freed on return
+    return PCM_OK;
+}
+
+template <int LA, int LB>
+static int fock_class(pcm_ctx *c, PairClass &pc, const double *dq, double *ddF)
+{
+    constexpr int L = LA + LB;
+    constexpr int NH = nherm(L);
+    if (pc.nsp == 0) return PCM_OK;
+    int nsplit = 1;
+    if (pc.npair > 0) {
+        const int nb = (pc.npair + FOCK_NT - 1) / FOCK_NT;
+        const int maxsplit = std::max(1, (c->M + FOCK_TQ - 1) / FOCK_TQ);
+        nsplit = std::max(1, std::min(maxsplit, (target_ctas(c) + nb - 1) / nb));
+        int ks = (c->M + nsplit - 1) / nsplit;
+        ks = (ks + FOCK_TQ - 1) / FOCK_TQ * FOCK_TQ;
+        nsplit = (c->M + ks - 1) / ks;
+        PCM_TRY(c->fock_W.alloc((size_t)nsplit * NH * pc.npair));
+        dim3 grid(nb, nsplit);
+        fock_kernel_f64<L><<<grid, FOCK_NT, 0, c->stream>>>(pc.npair, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, ks, c->px.p,
+                                                             c->py.p, c->pz.p, dq, c->M, c->ncls, c->cls_off.p,
+                                                             c->cls_zeta.p, c->boys64.p, c->fock_W.p);
+        PCM_CUDA(cudaGetLastError());
+    }
+    fock_epilogue_kernel<LA, LB><<<(pc.nsp + 127) / 128, 128, 0, c->stream>>>(
+        pc.nsp, pc.npair, nsplit, pc.spA.p, pc.spB.p, pc.sp_start.p, pc.ia.p, pc.ib.p, c->sh_atom.p, c->sh_off.p,
+        c->sh_bf.p, c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, c->fock_W.p, c->nbf, ddF);
+    PCM_CUDA(cudaGetLastError());
+    c->stats.integrals_fock += (double)pc.npair * ncart(LA) * ncart(LB) * c->M;
+    return PCM_OK;
+}
+
+int fock_compute(pcm_ctx *c, const double *dq, double *ddF)
+{
+    c->stats.integrals_fock = 0.0;
+    PCM_TRY((fock_class<0, 0>(c, c->cls[0], dq, ddF)));
+    PCM_TRY((fock_class<1, 0>(c, c->cls[1], dq, ddF)));
+    PCM_TRY((fock_class<1, 1>(c, c->cls[2], dq, ddF)));
+    PCM_TRY((fock_class<2, 0>(c, c->cls[3], dq, ddF)));
+    PCM_TRY((fock_class<2, 1>(c, c->cls[4], dq, ddF)));
+    PCM_TRY((fock_class<2, 2>(c, c->cls[5], dq, ddF)));
+    return PCM_OK;
+}
+
+}  // namespace pcm

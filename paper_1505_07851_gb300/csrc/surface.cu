@@ -1,0 +1,339 @@
+// ISWIG cavity surface (Eq. 7, Eq. 9, Section 3), the stored A (Eq. 2, Eq. 3,
+// Eq. 8) and B z (Eq. 4).
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+#include "context.h"
+
+namespace pcm {
+
+constexpr int SURF_T = 128;
+constexpr int SURF_ATOM_TILE = 512;
+
+// Per-atom exponent of Eq. 7 with equal weights w = 4 pi / n.
+__global__ void atom_zeta_kernel(int natom, const double *__restrict__ radius, double zeta, int n,
+                                 double *__restrict__ azeta)
+{
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= natom) return;
+    const double w = 4.0 * PCM_PI / n;
+    azeta[I] = zeta / (radius[I] * sqrt(w));
+}
+
+// One thread per candidate point (atom I, Fibonacci index i):
+//   u_i: z_i = 1 - (2i+1)/n, phi_i = i pi (3 - sqrt 5)
+//   r_k = X_I + R_I u_i,  zeta_k = zeta_I
+//   S_k = prod_{J != I} (erfc(zeta_k (R_J - d)) + erfc(zeta_k (R_J + d))) / 2
+// (Eq. 9 with erf written as 1 - erfc).  An atom with zeta_k (d - R_J) > 6
+// contributes a factor that rounds to exactly 1 in FP64 and is skipped.
+__global__ void surface_candidates_kernel(int natom, int n, const double *__restrict__ xyz,
+                                          const double *__restrict__ radius, const double *__restrict__ azeta,
+                                          double drop, double *__restrict__ cx, double *__restrict__ cy,
+                                          double *__restrict__ cz, double *__restrict__ cS,
+                                          unsigned char *__restrict__ keep)
+{
+    __shared__ double sx[SURF_ATOM_TILE], sy[SURF_ATOM_TILE], sz[SURF_ATOM_TILE], sr[SURF_ATOM_TILE];
+    const long long ncand = (long long)natom * n;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = k < ncand;
+    int I = 0, i = 0;
+    double rx = 0, ry = 0, rz = 0, zk = 1.0;
+    if (active) {
+        I = (int)(k / n);
+        i = (int)(k - (long long)I * n);
+        const double zc = 1.0 - (2.0 * i + 1.0) / n;
+        const double phi = i * (PCM_PI * (3.0 - sqrt(5.0)));
+        const double s = sqrt(1.0 - zc * zc);
+        double sphi, cphi;
+        sincos(phi, &sphi, &cphi);
+        const double R = radius[I];
+        rx = xyz[3 * I + 0] + R * (s * cphi);
+        ry = xyz[3 * I + 1] + R * (s * sphi);
+        rz = xyz[3 * I + 2] + R * zc;
+        zk = azeta[I];
+    }
+    const double reach = 6.0 / zk;
+    double S = 1.0;
+    for (int J0 = 0; J0 < natom; J0 += SURF_ATOM_TILE) {
+        const int nj = min(SURF_ATOM_TILE, natom - J0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+            sx[j] = xyz[3 * (J0 + j) + 0];
+            sy[j] = xyz[3 * (J0 + j) + 1];
+            sz[j] = xyz[3 * (J0 + j) + 2];
+            sr[j] = radius[J0 + j];
+        }
+        __syncthreads();
+        if (active) {
+            for (int j = 0; j < nj; ++j) {
+                if (J0 + j == I) continue;
+                const double dx = rx - sx[j], dy = ry - sy[j], dz = rz - sz[j];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                const double lim = sr[j] + reach;
+                if (d2 > lim * lim) continue;
+                const double d = sqrt(d2);
+                S *= 0.5 * (erfc(zk * (sr[j] - d)) + erfc(zk * (sr[j] + d)));
+            }
+        }
+    }
+    if (active) {
+        cx[k] = rx;
+        cy[k] = ry;
+        cz[k] = rz;
+        cS[k] = S;
+        keep[k] = S >= drop ? 1 : 0;
+    }
+}
+
+// flags of the kept candidates of one exponent class
+__global__ void class_flags_kernel(long long ncand, int n, const unsigned char *__restrict__ keep,
+                                   const int *__restrict__ atom_cls, int e, unsigned char *__restrict__ f)
+{
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncand) return;
+    f[k] = (keep[k] && atom_cls[k / n] == e) ? 1 : 0;
+}
+
+__global__ void gather_points_kernel(int M, int n, const int *__restrict__ idx, const double *__restrict__ cx,
+                                     const double *__restrict__ cy, const double *__restrict__ cz,
+                                     const double *__restrict__ cS, const double *__restrict__ azeta,
+                                     const int *__restrict__ atom_cls, double *px, double *py, double *pz,
+                                     double *pzeta, double *pS, int *pindex, int *pcls)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int k = idx[j];
+    const int I = k / n;
+    px[j] = cx[k];
+    py[j] = cy[k];
+    pz[j] = cz[k];
+    pS[j] = cS[k];
+    pzeta[j] = azeta[I];
+    pindex[j] = k;
+    pcls[j] = atom_cls[I];
+}
+
+// (B z)_k = sum_J Z_J erf(zeta_k r_kJ) / r_kJ (Eq. 4); erf(x) rounds to 1 in
+// FP64 for x > 6, where the plain Z_J / r_kJ is used.
+__global__ void bz_kernel(int M, int natom, const double *__restrict__ px, const double *__restrict__ py,
+                          const double *__restrict__ pz, const double *__restrict__ pzeta,
+                          const double *__restrict__ xyz, const double *__restrict__ Z, double *__restrict__ Bz)
+{
+    __shared__ double sx[SURF_ATOM_TILE], sy[SURF_ATOM_TILE], sz[SURF_ATOM_TILE], sq[SURF_ATOM_TILE];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = k < M;
+    double x = 0, y = 0, z = 0, zk = 1;
+    if (active) {
+        x = px[k];
+        y = py[k];
+        z = pz[k];
+        zk = pzeta[k];
+    }
+    double s = 0.0;
+    for (int J0 = 0; J0 < natom; J0 += SURF_ATOM_TILE) {
+        const int nj = min(SURF_ATOM_TILE, natom - J0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+            sx[j] = xyz[3 * (J0 + j) + 0];
+            sy[j] = xyz[3 * (J0 + j) + 1];
+            sz[j] = xyz[3 * (J0 + j) + 2];
+            sq[j] = Z[J0 + j];
+        }
+        __syncthreads();
+        if (active) {
+            for (int j = 0; j < nj; ++j) {
+                const double dx = x - sx[j], dy = y - sy[j], dz = z - sz[j];
+                const double r = sqrt(dx * dx + dy * dy + dz * dz);
+                const double a = zk * r;
+                s += sq[j] * (a > 6.0 ? 1.0 : erf(a)) / r;
+            }
+        }
+    }
+    if (active) Bz[k] = s;
+}
+
+// Stored A in FP64 (Eq. 2, Eq. 3 read as zeta_k sqrt(2/pi) / S_k, Eq. 8).
+// Tiles (bi, bj) with bi <= bj are computed once and written to both halves.
+constexpr int AT = 32;
+__global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, const double *__restrict__ py,
+                               const double *__restrict__ pz, const double *__restrict__ pzeta,
+                               const double *__restrict__ pS, double *__restrict__ A)
+{
+    // map the linear block id onto the upper triangle of tiles
+    const int nt = (M + AT - 1) / AT;
+    long long t = blockIdx.x;
+    int bi = 0;
+    {
+        // row bi holds nt - bi tiles
+        long long rem = t;
+        while (rem >= nt - bi) {
+            rem -= nt - bi;
+            ++bi;
+        }
+        t = rem;
+    }
+    const int bj = bi + (int)t;
+    __shared__ double tile[AT][AT + 1];
+    const int tx = threadIdx.x & (AT - 1);
+    const int ty = threadIdx.x / AT;  // 0 .. 7
+    const int l = bj * AT + tx;
+    double lx = 0, ly = 0, lz = 0, lzeta = 1;
+    if (l < M) {
+        lx = px[l];
+        ly = py[l];
+        lz = pz[l];
+        lzeta = pzeta[l];
+    }
+    for (int r = ty; r < AT; r += 8) {
+        const int k = bi * AT + r;
+        double v = 0.0;
+        if (k < M && l < M) {
+            if (k == l) {
+                v = pzeta[k] * 0.79788456080286535588 / pS[k];  // sqrt(2/pi)
+            } else {
+                const double dx = px[k] - lx, dy = py[k] - ly, dz = pz[k] - lz;
+                const double d = sqrt(dx * dx + dy * dy + dz * dz);
+                const double zk = pzeta[k];
+                const double zp = zk * lzeta / sqrt(zk * zk + lzeta * lzeta);
+                const double a = zp * d;
+                v = (a > 6.0 ? 1.0 : erf(a)) / d;
+            }
+            A[(size_t)k * lda + l] = v;
+        }
+        tile[r][tx] = v;
+    }
+    if (bi == bj) return;
+    __syncthreads();
+    // transposed write: rows of tile bj, columns of tile bi
+    for (int r = ty; r < AT; r += 8) {
+        const int k = bj * AT + r;
+        const int ll = bi * AT + tx;
+        if (k < M && ll < M) A[(size_t)k * lda + ll] = tile[tx][r];
+    }
+}
+
+__global__ void dinv_kernel(int M, int lda, const double *__restrict__ A, double *__restrict__ dinv)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < M) dinv[k] = 1.0 / A[(size_t)k * lda + k];
+}
+
+int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, const double *radius, int n)
+{
+    c->natom = natom;
+    c->npts_sphere = n;
+    c->h_xyz.assign(xyz, xyz + 3 * natom);
+    c->h_Z.assign(Z, Z + natom);
+    c->h_radius.assign(radius, radius + natom);
+    PCM_TRY(c->xyz.alloc(3 * natom));
+    PCM_TRY(c->Z.alloc(natom));
+    PCM_TRY(c->radius.alloc(natom));
+    PCM_CUDA(cudaMemcpyAsync(c->xyz.p, xyz, 3 * natom * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    PCM_CUDA(cudaMemcpyAsync(c->Z.p, Z, natom * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    PCM_CUDA(cudaMemcpyAsync(c->radius.p, radius, natom * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+
+    // exponent classes: atoms with equal zeta (Eq. 7) share a class; classes in increasing zeta
+    DBuf<double> azeta;
+    PCM_TRY(azeta.alloc(natom));
+    atom_zeta_kernel<<<(natom + 127) / 128, 128, 0, c->stream>>>(natom, c->radius.p, c->opt.zeta, n, azeta.p);
+    PCM_CUDA(cudaGetLastError());
+    std::vector<double> h_azeta(natom);
+    PCM_CUDA(cudaMemcpyAsync(h_azeta.data(), azeta.p, natom * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PCM_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<double> uz(h_azeta);
+    std::sort(uz.begin(), uz.end());
+    uz.erase(std::unique(uz.begin(), uz.end()), uz.end());
+    c->ncls = (int)uz.size();
+    c->h_cls_zeta = uz;
+    std::vector<int> h_acls(natom);
+    for (int I = 0; I < natom; ++I)
+        h_acls[I] = (int)(std::lower_bound(uz.begin(), uz.end(), h_azeta[I]) - uz.begin());
+    DBuf<int> acls;
+    PCM_TRY(acls.alloc(natom));
+    PCM_CUDA(cudaMemcpyAsync(acls.p, h_acls.data(), natom * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+
+    // candidates
+    const long long ncand = (long long)natom * n;
+    DBuf<double> cx, cy, cz, cS;
+    DBuf<unsigned char> keep;
+    PCM_TRY(cx.alloc(ncand));
+    PCM_TRY(cy.alloc(ncand));
+    PCM_TRY(cz.alloc(ncand));
+    PCM_TRY(cS.alloc(ncand));
+    PCM_TRY(keep.alloc(ncand));
+    surface_candidates_kernel<<<(unsigned)((ncand + SURF_T - 1) / SURF_T), SURF_T, 0, c->stream>>>(
+        natom, n, c->xyz.p, c->radius.p, azeta.p, c->opt.switch_drop, cx.p, cy.p, cz.p, cS.p, keep.p);
+    PCM_CUDA(cudaGetLastError());
+
+    // compaction class by class into library order
+    PCM_TRY(c->flags8.alloc(ncand));
+    PCM_TRY(c->idx32.alloc(ncand));
+    PCM_TRY(c->iscal.alloc(64));
+    std::vector<int> counts(c->ncls);
+    DBuf<int> order;
+    PCM_TRY(order.alloc(ncand));
+    int M = 0;
+    c->h_cls_off.assign(c->ncls + 1, 0);
+    for (int e = 0; e < c->ncls; ++e) {
+        class_flags_kernel<<<(unsigned)((ncand + 255) / 256), 256, 0, c->stream>>>(ncand, n, keep.p, acls.p, e,
+                                                                                  c->flags8.p);
+        PCM_CUDA(cudaGetLastError());
+        PCM_TRY(compact_flags(c, c->flags8.p, ncand, order.p + M, nullptr, c->iscal.p));
+        int cnt = 0;
+        PCM_CUDA(cudaMemcpyAsync(&cnt, c->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PCM_CUDA(cudaStreamSynchronize(c->stream));
+        M += cnt;
+        c->h_cls_off[e + 1] = M;
+    }
+    c->M = M;
+    if (M == 0) {
+        set_last_error("no surface point survives the switching threshold");
+        return PCM_ERR_ARG;
+    }
+    PCM_TRY(c->px.alloc(M));
+    PCM_TRY(c->py.alloc(M));
+    PCM_TRY(c->pz.alloc(M));
+    PCM_TRY(c->pzeta.alloc(M));
+    PCM_TRY(c->pS.alloc(M));
+    PCM_TRY(c->pindex.alloc(M));
+    PCM_TRY(c->pcls.alloc(M));
+    PCM_TRY(c->Bz.alloc(M));
+    gather_points_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, n, order.p, cx.p, cy.p, cz.p, cS.p, azeta.p,
+                                                                acls.p, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
+                                                                c->pS.p, c->pindex.p, c->pcls.p);
+    PCM_CUDA(cudaGetLastError());
+    PCM_TRY(c->cls_zeta.alloc(c->ncls));
+    PCM_TRY(c->cls_off.alloc(c->ncls + 1));
+    PCM_CUDA(cudaMemcpyAsync(c->cls_zeta.p, c->h_cls_zeta.data(), c->ncls * sizeof(double),
+                             cudaMemcpyHostToDevice, c->stream));
+    PCM_CUDA(cudaMemcpyAsync(c->cls_off.p, c->h_cls_off.data(), (c->ncls + 1) * sizeof(int),
+                             cudaMemcpyHostToDevice, c->stream));
+
+    bz_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, natom, c->px.p, c->py.p, c->pz.p, c->pzeta.p, c->xyz.p,
+                                                     c->Z.p, c->Bz.p);
+    PCM_CUDA(cudaGetLastError());
+
+    // stored A
+    c->lda = (M + 31) / 32 * 32;
+    PCM_TRY(c->A.alloc((size_t)M * c->lda));
+    {
+        const long long nt = (M + AT - 1) / AT;
+        const long long ntiles = nt * (nt + 1) / 2;
+        a_build_kernel<<<(unsigned)ntiles, 256, 0, c->stream>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
+                                                               c->pS.p, c->A.p);
+        PCM_CUDA(cudaGetLastError());
+    }
+    PCM_TRY(c->dinv.alloc(M));
+    dinv_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, c->lda, c->A.p, c->dinv.p);
+    PCM_CUDA(cudaGetLastError());
+    PCM_CUDA(cudaStreamSynchronize(c->stream));  // local scratch buffers are freed on return
+    c->pc_ready = false;
+    c->have_c = false;
+    return PCM_OK;
+}
+
+}  // namespace pcm

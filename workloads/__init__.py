@@ -199,7 +199,7 @@ def cluster(natom: int, seed: int, globule_radius_A: float, d_shells: bool = Fal
 
 # Globule radii (angstrom) chosen so that the 110-point ISWIG surface of the
 # cluster has roughly the number of kept points the workloads call for.
-GLOBULE_RADIUS_A = {300: 9.0, 1000: 13.5}
+GLOBULE_RADIUS_A = {300: 8.0, 1000: 13.5}
 
 
 def config(i: int) -> Workload:
@@ -229,7 +229,7 @@ def small_cluster(natom: int, seed: int, d_shells: bool = False, radius_A: float
                   nocc: int | None = None) -> Workload:
     """Small clusters for parity tests (sizes the oracle finishes in seconds)."""
     if radius_A is None:
-        radius_A = max(3.0, 9.0 * (natom / 300.0) ** (1.0 / 3.0))
+        radius_A = max(3.0, 8.0 * (natom / 300.0) ** (1.0 / 3.0))
     return cluster(natom, seed, radius_A, d_shells=d_shells, nocc=nocc,
                    name="cluster%d%s" % (natom, "_spd" if d_shells else "_sp"))
 
@@ -240,6 +240,6 @@ def conformations(n: int = 64, seed: int = 150507851 + 4, lo: int = 150, hi: int
     sizes = rng.integers(lo, hi + 1, size=n)
     out = []
     for j, na in enumerate(sizes):
-        r = 9.0 * (na / 300.0) ** (1.0 / 3.0)
+        r = 8.0 * (na / 300.0) ** (1.0 / 3.0)
         out.append(cluster(int(na), seed * 1000 + j, r, name="conf%d" % j))
     return out
