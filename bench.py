@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the C-PCM / ISWIG hot path on one GB300 (or N, as replicas).
+
+One step is one pass of the whole path over one synthetic molecule:
+surface build (points, switching, stored A, Bz), basis and primitive-pair
+list with screening, ESP c, rhs, PCG solve (RBJ, threshold of Eq. 21 for a
+1e-6 Eh energy error), Fock correction dF and the Eq. 13 energy.
+
+Metric: ESP + Fock equivalent Cartesian primitive integrals per second
+(kept primitive pairs x ncart(a) ncart(b) x M, summed over the ESP and the
+Fock call of a step) divided by the step time; the PCG solve time is
+reported beside it.  Workload: the 300-atom H:C:N:O:S = 50:31:9:9:1 cluster
+with 6-31G-like s/sp shells (nbf ~ 1.66k), 600 occupied orbitals, 110
+points per sphere at 1.2 x Bondi (M ~ 12k), FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs its own conformation (seed offset by
+rank): independent problems, no data-path collective (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "ESP+Fock integrals/s & PCG solve ms: mixed/batched vs FP64, at 1e-6 Eh"
+UNIT = "integrals/s"
+# Eq. 21: Err(delta) = 0.01 delta^1.07 = 1e-6 Eh
+DELTA_1E6 = (1e-6 / 0.01) ** (1.0 / 1.07)
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
+
+
+# --------------------------------------------------------------------------
+# algorithmic FP64 operation counts per pair-point interaction
+# --------------------------------------------------------------------------
+def _nherm(L):
+    return (L + 1) * (L + 2) * (L + 3) // 6
+
+
+def _hermite_ops(L):
+    ops = 0
+    for n in range(L, -1, -1):
+        D = L - n
+        for d in range(1, D + 1):
+            for t in range(d, -1, -1):
+                for u in range(d - t, -1, -1):
+                    v = d - t - u
+                    k = t if t > 0 else (u if u > 0 else v)
+                    ops += 1 + (2 if k > 1 else 0)
+    return ops
+
+
+def flops_per_interaction(L, kind):
+    """Operations of the algorithm (an FMA counts 2): distance and T (9),
+    Boys F_0..F_L by 7-term Taylor (7 + 12 (L+1)), (-2 rho)^n scaling (2L),
+    Hermite recurrence, then the ESP dot (2 nherm + 2) or the Fock
+    accumulation (1 + nherm)."""
+    base = 9 + 7 + 12 * (L + 1) + 2 * L + _hermite_ops(L)
+    if kind == "esp":
+        return base + 2 * _nherm(L) + 2
+    return base + 1 + _nherm(L)
+
+
+CLASS_L = [0, 1, 2, 2, 3, 4]
+CLASS_NAME = ["ss", "ps", "pp", "ds", "dp", "dd"]
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (one process per GPU)
+# --------------------------------------------------------------------------
+def dist_init(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def dist_max(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload_for(config, rank):
+    if rank == 0:
+        return workloads.config(config)
+    w0 = workloads.config(config)
+    seed = w0.seed + 1000 * rank
+    return workloads.cluster(w0.mol.natom, seed, workloads.GLOBULE_RADIUS_A[w0.mol.natom],
+                             d_shells=(config in (2, 3)), nocc=w0.nocc, name=w0.name + "_r%d" % rank)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_init("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1505_07851_gb300 as pcm
+
+    w = workload_for(args.config, rank)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pcm.Context(precision=args.precision, device=local, stream=stream.cuda_stream, timing=True,
+                      seed=args.seed)
+    b = w.basis
+    Pd = torch.tensor(w.P, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    delta = args.delta if args.delta else DELTA_1E6
+    bufs = {}
+
+    def step():
+        M = ctx.build_surface(w.mol.xyz, w.mol.Z, w.mol.radius, 110)
+        nbf = ctx.set_basis(b.shell_atom, b.shell_l, b.shell_nprim, b.exps, b.coefs)
+        if "c" not in bufs or bufs["c"].numel() != M:
+            bufs["c"] = torch.empty(M, dtype=torch.float64, device=dev)
+            bufs["q"] = torch.empty(M, dtype=torch.float64, device=dev)
+            bufs["dF"] = torch.empty((nbf, nbf), dtype=torch.float64, device=dev)
+        ctx.esp(Pd, out=bufs["c"])
+        q, st = ctx.solve(delta=delta, q=bufs["q"])
+        ctx.fock(q, out=bufs["dF"])
+        E = ctx.energy(q)
+        return E, st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    launches0 = st0["launches"]
+    times, solve_ms, iters, energies = [], [], [], []
+    ints = 0.0
+    esp_cls = np.zeros(6)
+    fock_cls = np.zeros(6)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()                       # evict L2 between steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            E, st = step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            s = ctx.stats()
+            solve_ms.append(s["ms_solve"])
+            iters.append(st["iterations"])
+            energies.append(E)
+            ints += s["integrals_esp"] + s["integrals_fock"]
+            esp_cls += np.array(s["ms_esp_class"])
+            fock_cls += np.array(s["ms_fock_class"])
+    torch.cuda.synchronize()
+    barrier(world)
+    s = ctx.stats()
+    launches = s["launches"] - launches0
+    total_ms = sum(times)
+    total_ms_max = dist_max(total_ms, world, dev)
+    ints_all = ints * world                      # every rank ran a molecule of the same size class
+    value = ints_all / (total_ms_max * 1e-3)
+
+    # dominant kernel and its roofline (FP64 ALU bound)
+    M = s["M"]
+    cand = []
+    for k in range(6):
+        if esp_cls[k] > 0:
+            cand.append(("esp_kernel_f64<L=%d> (%s)" % (CLASS_L[k], CLASS_NAME[k]), esp_cls[k] / args.steps,
+                         s["esp_class_pairs"][k] * M * flops_per_interaction(CLASS_L[k], "esp")))
+        if fock_cls[k] > 0:
+            cand.append(("fock_kernel_f64<L=%d> (%s)" % (CLASS_L[k], CLASS_NAME[k]), fock_cls[k] / args.steps,
+                         s["fock_class_pairs"][k] * M * flops_per_interaction(CLASS_L[k], "fock")))
+    name, ms_k, flops_k = max(cand, key=lambda t: t[1])
+    achieved = flops_k / (ms_k * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
+                "kernel_ms": ms_k}
+
+    # end-to-end through the public API with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        Ph = np.ascontiguousarray(w.P)
+        h2d = Ph.nbytes + w.mol.xyz.nbytes + w.mol.Z.nbytes + w.mol.radius.nbytes + \
+            b.shell_atom.nbytes + b.shell_l.nbytes + b.shell_nprim.nbytes + b.exps.nbytes + b.coefs.nbytes
+        et = []
+        for it in range(max(1, args.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Mh = ctx.build_surface(w.mol.xyz, w.mol.Z, w.mol.radius, 110)
+            nbfh = ctx.set_basis(b.shell_atom, b.shell_l, b.shell_nprim, b.exps, b.coefs)
+            ch = ctx.esp(Ph)
+            qh, _ = ctx.solve(delta=delta)
+            Fh = ctx.fock(qh)
+            Eh = ctx.energy(qh)
+            et.append(time.perf_counter() - t0)
+        d2h = ch.nbytes + qh.nbytes + Fh.nbytes + 8
+        e_ms = dist_max(sum(et) * 1e3, world, dev)
+        e2e = {"value": ints_all / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms / len(et)}
+
+    # accuracy of the timed solve: energy against a tight solve (not timed)
+    ctx.build_surface(w.mol.xyz, w.mol.Z, w.mol.radius, 110)
+    ctx.set_basis(b.shell_atom, b.shell_l, b.shell_nprim, b.exps, b.coefs)
+    ctx.esp(Pd, out=bufs["c"])
+    qt, stt = ctx.solve(delta=1e-10, q=bufs["q"])
+    E_tight = ctx.energy(qt)
+    energy_err = abs(energies[-1] - E_tight)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(w, args.cpu_points)
+    ctx.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (seeded protein-shaped cluster; no PDB/basis data in this container)",
+            "config": {"workload": w.name, "natom": w.mol.natom, "nbf": s["nbf"], "M": M,
+                       "pts_per_sphere": 110, "precision": args.precision, "delta": delta,
+                       "precond": "rbj-100" if M >= 1000 else "jacobi",
+                       "l2": "flushed between timed steps (512 MB write, not timed)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "pcg_solve_ms": statistics.mean(solve_ms), "pcg_iterations": statistics.mean(iters),
+            "energy_Eh": energies[-1], "energy_err_Eh": energy_err,
+            "esp_kernel_ms": float(esp_cls.sum() / args.steps), "fock_kernel_ms": float(fock_cls.sum() / args.steps),
+            "integrals_per_step": ints / args.steps, "pairs_kept": s["pairs_kept"],
+            "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# the oracle, timed on the host cores
+# --------------------------------------------------------------------------
+def _oracle_sample(w, npts, seed=0):
+    import oracle
+    s = oracle.surface(w.mol.xyz, w.mol.radius)
+    eb = oracle.ExpandedBasis(w.basis, w.mol.xyz)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(len(s["zeta"]), size=min(npts, len(s["zeta"])), replace=False))
+    # equivalent Cartesian primitive integrals the oracle evaluates per point
+    nc = (eb.sh_l + 1) * (eb.sh_l + 2) // 2
+    w_sh = eb.sh_nprim * nc
+    tot = float(w_sh.sum())
+    per_point = 0.5 * (tot * tot + float((w_sh * w_sh).sum()))     # shell pairs A <= B
+    return oracle, s, eb, idx, per_point
+
+
+def cpu_baseline(w, npts):
+    oracle, s, eb, idx, per_point = _oracle_sample(w, npts)
+    t0 = time.perf_counter()
+    oracle.esp(eb, w.P, s["r"][idx], s["zeta"][idx])
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": per_point * len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle ESP (Obara-Saika, no screening) at %d of %d surface points over all "
+                      "%d shell pairs; %.1f s" % (len(idx), len(s["zeta"]), eb.nshell * (eb.nshell + 1) // 2, dt)}
+
+
+def run_reference(args):
+    rank, world, local = dist_init("gloo")
+    if rank != 0:
+        return
+    w = workloads.config(args.config)
+    oracle, s, eb, idx_all, per_point = _oracle_sample(w, 10 ** 9)
+    rng = np.random.default_rng(1)
+    times = []
+    ints = 0.0
+    for it in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(len(s["zeta"]), size=args.ref_points, replace=False))
+        t0 = time.perf_counter()
+        oracle.esp(eb, w.P, s["r"][idx], s["zeta"][idx])
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            ints += per_point * len(idx)
+    total = sum(times)
+    value = ints / total
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = ("oracle ESP at %d random surface points per step over all %d shell pairs (the full "
+              "step would need %d points)" % (args.ref_points, eb.nshell * (eb.nshell + 1) // 2, len(s["zeta"])))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w.name, "natom": w.mol.natom, "nbf": w.basis.nbf, "M": len(s["zeta"])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--delta", type=float, default=None)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-points", type=int, default=32)
+    ap.add_argument("--ref-points", type=int, default=16)
+    ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch of the dominant kernel (ncu)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

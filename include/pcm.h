@@ -87,6 +87,7 @@ typedef struct pcm_options {
     int device;                 /* CUDA device ordinal, default 0 */
     unsigned long long seed;    /* RBJ pivot stream seed (splitmix64), default 0 */
     void *stream;               /* cudaStream_t to use; NULL: the context creates its own */
+    int timing;                 /* 1: time the integral kernels and the solve with CUDA events (stats) */
 } pcm_options;
 
 typedef struct pcm_stats {
@@ -102,6 +103,12 @@ typedef struct pcm_stats {
     long long pairs_esp;        /* pairs surviving the density-weighted test of Eq. 18 in the last pcm_esp */
     double integrals_esp;       /* equivalent Cartesian primitive integrals of the last pcm_esp */
     double integrals_fock;      /* equivalent Cartesian primitive integrals of the last pcm_fock */
+    long long esp_class_pairs[6];   /* pairs per class (ss, ps, pp, ds, dp, dd) in the last pcm_esp */
+    long long fock_class_pairs[6];  /* pairs per class in the last pcm_fock */
+    double ms_esp_class[6];     /* with timing: main ESP kernel time per class (ms) */
+    double ms_fock_class[6];    /* with timing: main Fock kernel time per class (ms) */
+    double ms_solve;            /* with timing: device time of the last pcm_solve (ms) */
+    long long launches;         /* kernels launched by this context since its creation */
 } pcm_stats;
 
 typedef struct pcm_ctx pcm_ctx;

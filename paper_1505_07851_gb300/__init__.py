@@ -45,7 +45,7 @@ class pcm_options(ctypes.Structure):
                 ("switch_drop", ctypes.c_double), ("schwarz", ctypes.c_double),
                 ("rbj_block", ctypes.c_int), ("precond", ctypes.c_int), ("jacobi_below", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("device", ctypes.c_int),
-                ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p)]
+                ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int)]
 
 
 class pcm_stats(ctypes.Structure):
@@ -53,10 +53,17 @@ class pcm_stats(ctypes.Structure):
                 ("rnorm", ctypes.c_double), ("refinements", ctypes.c_int), ("M", ctypes.c_int),
                 ("nbf", ctypes.c_int), ("pairs_candidate", ctypes.c_longlong),
                 ("pairs_kept", ctypes.c_longlong), ("pairs_esp", ctypes.c_longlong),
-                ("integrals_esp", ctypes.c_double), ("integrals_fock", ctypes.c_double)]
+                ("integrals_esp", ctypes.c_double), ("integrals_fock", ctypes.c_double),
+                ("esp_class_pairs", ctypes.c_longlong * 6), ("fock_class_pairs", ctypes.c_longlong * 6),
+                ("ms_esp_class", ctypes.c_double * 6), ("ms_fock_class", ctypes.c_double * 6),
+                ("ms_solve", ctypes.c_double), ("launches", ctypes.c_longlong)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        out = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            out[f] = list(v) if hasattr(v, "__len__") else v
+        return out
 
 
 class PCMError(RuntimeError):
@@ -123,7 +130,7 @@ class Context:
 
     def __init__(self, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
                  precond="auto", jacobi_below=1000, precision="fp64", max_iter=5000, device=0, seed=0,
-                 stream=None):
+                 stream=None, timing=False):
         o = pcm_options()
         _lib.pcm_default_options(ctypes.byref(o))
         o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
@@ -131,6 +138,7 @@ class Context:
         o.precision = {"fp64": PCM_FP64, "mixed": PCM_MIXED}[precision]
         o.max_iter, o.device, o.seed = max_iter, device, seed
         o.stream = stream
+        o.timing = 1 if timing else 0
         h = ctypes.c_void_p()
         self._check(_lib.pcm_create(ctypes.byref(h), ctypes.byref(o)), "pcm_create")
         self._h = h

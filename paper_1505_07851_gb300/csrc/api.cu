@@ -167,6 +167,13 @@ int pcm_create(pcm_ctx **out, const pcm_options *opt)
         }
         c->own_stream = true;
     }
+    if (o.timing) {
+        for (int i = 0; i < 13; ++i) {
+            cudaEventCreate(&c->ev_a[i]);
+            cudaEventCreate(&c->ev_b[i]);
+        }
+        c->have_events = true;
+    }
     int st = boys_build_tables(c);
     if (st != PCM_OK) {
         if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -182,6 +189,11 @@ int pcm_destroy(pcm_ctx *c)
     if (!c) return PCM_OK;
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->have_events)
+        for (int i = 0; i < 13; ++i) {
+            cudaEventDestroy(c->ev_a[i]);
+            cudaEventDestroy(c->ev_b[i]);
+        }
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;  // device buffers free themselves
     return PCM_OK;
@@ -234,7 +246,7 @@ int pcm_get_surface(pcm_ctx *c, double *xyzzs, int *index, int flags)
         }
         pack_surface_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
                                                                    c->pS.p, dst);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
         if (!(flags & PCM_PTR_DEVICE))
             PCM_CUDA(cudaMemcpyAsync(xyzzs, dst, 5 * (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         PCM_CUDA(cudaStreamSynchronize(c->stream));
@@ -325,7 +337,7 @@ int pcm_solve(pcm_ctx *c, const double *rhs, double delta, double prev_diis_erro
         PCM_TRY(to_device(c, rhs, M, c->vin, &drhs, flags));
     } else {
         rhs_kernel<<<(M + 255) / 256, 256, 0, c->stream>>>(M, f, c->Bz.p, c->c_last.p, c->vrhs.p);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
         drhs = c->vrhs.p;
     }
     const bool warm = (flags & PCM_WARM) != 0;
@@ -341,7 +353,16 @@ int pcm_solve(pcm_ctx *c, const double *rhs, double delta, double prev_diis_erro
         }
         dq = c->vx.p;
     }
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[12], c->stream));
     int status = solver_run(c, drhs, d, dq, warm, st);
+    if (c->have_events) {
+        PCM_CUDA(cudaEventRecord(c->ev_b[12], c->stream));
+        PCM_CUDA(cudaEventSynchronize(c->ev_b[12]));
+        float ms = 0.f;
+        PCM_CUDA(cudaEventElapsedTime(&ms, c->ev_a[12], c->ev_b[12]));
+        c->stats.ms_solve = ms;
+        if (st) st->ms_solve = ms;
+    }
     if (status != PCM_OK && status != PCM_ERR_NOT_CONVERGED) return status;
     if (!(flags & PCM_PTR_DEVICE))
         PCM_CUDA(cudaMemcpyAsync(q, dq, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

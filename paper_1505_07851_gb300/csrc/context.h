@@ -27,6 +27,13 @@ void set_last_error(const char *fmt, ...);
         }                                                                                     \
     } while (0)
 
+// check a kernel launch and count it
+#define PCM_LAUNCHED(ctx)                                                                      \
+    do {                                                                                       \
+        ++(ctx)->stats.launches;                                                               \
+        PCM_CUDA(cudaGetLastError());                                                          \
+    } while (0)
+
 #define PCM_TRY(call)                  \
     do {                               \
         int s_ = (call);               \
@@ -161,6 +168,8 @@ struct pcm_ctx {
     pcm::DBuf<long long> scan64;
 
     pcm_stats stats;
+    cudaEvent_t ev_a[13], ev_b[13];         // timing events: 0-5 ESP classes, 6-11 Fock classes, 12 solve
+    bool have_events = false;
 };
 
 namespace pcm {

@@ -430,11 +430,14 @@ static int launch_esp_class(pcm_ctx *c, PairClass &pc, const int *blk, int nblk,
                             int seglen)
 {
     if (pc.nesp == 0) return PCM_OK;
+    const int k = (int)(&pc - c->cls);
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[k], c->stream));
     dim3 grid(nblk, nseg_cls);
     esp_kernel_f64<L><<<grid, ESP_NT, 0, c->stream>>>(pc.nesp, seglen, pc.eP.p, pc.eD.p, blk, c->px.p, c->py.p,
                                                        c->pz.p, c->pcls.p, c->cls_zeta.p, c->boys64.p, c->M,
                                                        c->esp_part.p + (size_t)seg_base * c->M);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[k], c->stream));
     return PCM_OK;
 }
 
@@ -448,7 +451,7 @@ static int esp_prepare_class(pcm_ctx *c, PairClass &pc, const double *dP)
     esp_flag_kernel<LA, LB><<<(pc.npair + 127) / 128, 128, 0, c->stream>>>(
         pc.npair, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_bf.p, pc.Q.p, dP, c->nbf, c->opt.schwarz,
         c->flags8.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     PCM_TRY(compact_flags(c, c->flags8.p, pc.npair, c->idx32.p, nullptr, c->iscal.p));
     int n = 0;
     PCM_CUDA(cudaMemcpyAsync(&n, c->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -464,7 +467,7 @@ static int esp_prepare_class(pcm_ctx *c, PairClass &pc, const double *dP)
         n, c->idx32.p, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_off.p, c->sh_bf.p,
         c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, dP, c->nbf, pc.eP.p, pc.eD.p, pc.eP32.p,
         pc.eD32.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     return PCM_OK;
 }
 
@@ -527,8 +530,17 @@ int esp_compute(pcm_ctx *c, const double *dP, double *dc)
     PCM_TRY((launch_esp_class<4>(c, c->cls[5], blk.p, nblk, base, nseg[5], seglen[5])));
     base += nseg[5];
     esp_reduce_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     PCM_CUDA(cudaStreamSynchronize(c->stream));  // blk is freed on return
+    for (int k = 0; k < 6; ++k) {
+        c->stats.esp_class_pairs[k] = c->cls[k].nesp;
+        c->stats.ms_esp_class[k] = 0.0;
+        if (c->have_events && c->cls[k].nesp > 0) {
+            float ms = 0.f;
+            PCM_CUDA(cudaEventElapsedTime(&ms, c->ev_a[k], c->ev_b[k]));
+            c->stats.ms_esp_class[k] = ms;
+        }
+    }
     return PCM_OK;
 }
 
@@ -548,15 +560,17 @@ static int fock_class(pcm_ctx *c, PairClass &pc, const double *dq, double *ddF)
         nsplit = (c->M + ks - 1) / ks;
         PCM_TRY(c->fock_W.alloc((size_t)nsplit * NH * pc.npair));
         dim3 grid(nb, nsplit);
+        if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[6 + (int)(&pc - c->cls)], c->stream));
         fock_kernel_f64<L><<<grid, FOCK_NT, 0, c->stream>>>(pc.npair, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, ks, c->px.p,
                                                              c->py.p, c->pz.p, dq, c->M, c->ncls, c->cls_off.p,
                                                              c->cls_zeta.p, c->boys64.p, c->fock_W.p);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
+        if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[6 + (int)(&pc - c->cls)], c->stream));
     }
     fock_epilogue_kernel<LA, LB><<<(pc.nsp + 127) / 128, 128, 0, c->stream>>>(
         pc.nsp, pc.npair, nsplit, pc.spA.p, pc.spB.p, pc.sp_start.p, pc.ia.p, pc.ib.p, c->sh_atom.p, c->sh_off.p,
         c->sh_bf.p, c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, c->fock_W.p, c->nbf, ddF);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     c->stats.integrals_fock += (double)pc.npair * ncart(LA) * ncart(LB) * c->M;
     return PCM_OK;
 }
@@ -570,6 +584,16 @@ int fock_compute(pcm_ctx *c, const double *dq, double *ddF)
     PCM_TRY((fock_class<2, 0>(c, c->cls[3], dq, ddF)));
     PCM_TRY((fock_class<2, 1>(c, c->cls[4], dq, ddF)));
     PCM_TRY((fock_class<2, 2>(c, c->cls[5], dq, ddF)));
+    if (c->have_events) PCM_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 6; ++k) {
+        c->stats.fock_class_pairs[k] = c->cls[k].npair;
+        c->stats.ms_fock_class[k] = 0.0;
+        if (c->have_events && c->cls[k].npair > 0) {
+            float ms = 0.f;
+            PCM_CUDA(cudaEventElapsedTime(&ms, c->ev_a[6 + k], c->ev_b[6 + k]));
+            c->stats.ms_fock_class[k] = ms;
+        }
+    }
     return PCM_OK;
 }
 

@@ -198,7 +198,7 @@ static int screen_class(pcm_ctx *c, PairClass &pc)
         pair_screen_kernel<LA, LB><<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(
             n, pc.nsp, pc.sp_cand.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_nprim.p, c->sh_off.p, c->exps.p,
             c->cnorm.p, c->xyz.p, c->opt.schwarz, c_sp.p, c_i.p, c_j.p, c_P.p, c_p.p, c_pref.p, c_Q.p, flag.p);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
     }
     DBuf<int> idx;
     PCM_TRY(idx.alloc(n));
@@ -221,11 +221,11 @@ static int screen_class(pcm_ctx *c, PairClass &pc)
         pair_gather_kernel<<<(kept + 127) / 128, 128, 0, c->stream>>>(
             kept, idx.p, c_sp.p, c_i.p, c_j.p, c_P.p, c_p.p, c_pref.p, c_Q.p, pc.sp.p, pc.ia.p, pc.ib.p, pc.Px.p,
             pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, pc.Q.p, pc.Pxyz32.p);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
     }
     PCM_TRY(pc.sp_start.alloc(pc.nsp + 1));
     sp_start_kernel<<<(pc.nsp + 1 + 127) / 128, 128, 0, c->stream>>>(pc.nsp, pc.sp_cand.p, pos.p, pc.sp_start.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     PCM_CUDA(cudaStreamSynchronize(c->stream));  // candidate scratch is freed on return
     return PCM_OK;
 }
@@ -299,7 +299,7 @@ int basis_build(pcm_ctx *c, int nshell, const int *shell_atom, const int *shell_
     PCM_CUDA(cudaMemcpyAsync(dco.p, co.data(), co.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     cnorm_kernel<<<(ns + 127) / 128, 128, 0, c->stream>>>(ns, c->sh_l.p, c->sh_nprim.p, c->sh_off.p, c->exps.p, dco.p,
                                                          c->cnorm.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
 
     // shell pairs by class (la >= lb); the higher-l shell (ties: lower index) comes first
     for (int k = 0; k < 6; ++k) {

@@ -592,14 +592,14 @@ int solver_prepare(pcm_ctx *c)
         PCM_CUDA(cudaMemsetAsync(c->iscal.p, 0, 64 * sizeof(int), c->stream));
         rbj_perm_kernel<<<1, RBJ_NT, 0, c->stream>>>(M, c->lda, c->A.p, l, c->opt.seed, U.p, U2.p, c->rbj_perm.p,
                                                      c->iscal.p + 16);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
         PCM_TRY(c->rbj_inv.alloc((size_t)c->rbj_nblk * l * l));
         DBuf<double> work;
         PCM_TRY(work.alloc((size_t)c->rbj_nblk * l * l));
         const int nt = std::min(1024, std::max(32, (l + 31) / 32 * 32));
         rbj_invert_kernel<<<c->rbj_nblk, nt, 0, c->stream>>>(M, c->lda, c->A.p, l, c->rbj_perm.p, work.p,
                                                              c->rbj_inv.p, c->iscal.p + 16);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
         int st = 0;
         PCM_CUDA(cudaMemcpyAsync(&st, c->iscal.p + 16, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         PCM_CUDA(cudaStreamSynchronize(c->stream));
@@ -639,10 +639,10 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
     const int ub = std::min(MAX_PART, (M + UP_NT - 1) / UP_NT);
     if (warm) {
         gemv_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, x, Ap, c->red.p);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
     }
     pcg_init_kernel<<<std::min(1024, (M + 255) / 256), 256, 0, c->stream>>>(M, drhs, Ap, warm ? 1 : 0, x, r);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     const double *dinv = (c->pc_kind == PCM_PRECOND_JACOBI) ? c->dinv.p : nullptr;
     const bool rbj = c->pc_kind == PCM_PRECOND_RBJ;
     const int rbj_nt = std::min(1024, std::max(32, (c->rbj_l + 31) / 32 * 32));
@@ -657,9 +657,9 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
         pcg_init_diag_kernel<<<ub, UP_NT, 0, c->stream>>>(M, dinv, r, z, c->red.p, c->scal.p, c->iscal.p,
                                                           c->counter.p);
     }
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     copy_kernel<<<std::min(1024, (M + 255) / 256), 256, 0, c->stream>>>(M, z, p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
 
     const int batch = 8;
     int h_i[I_NINT] = {0, 0, 0, 0};
@@ -675,6 +675,7 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
                 pcg_update_diag_kernel<<<ub, UP_NT, 0, c->stream>>>(M, dinv, x, r, z, p, Ap, c->red.p, c->scal.p,
                                                                     c->iscal.p, c->counter.p);
             pcg_dir_kernel<<<std::min(1024, (M + 255) / 256), 256, 0, c->stream>>>(M, z, p, c->scal.p, c->iscal.p);
+            c->stats.launches += 3;
         }
         PCM_CUDA(cudaGetLastError());
         PCM_CUDA(cudaMemcpyAsync(h_i, c->iscal.p, sizeof(h_i), cudaMemcpyDeviceToHost, c->stream));
@@ -736,9 +737,9 @@ int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E)
     const int nb = std::min(1024, (M + 255) / 256);
     PCM_TRY(part2.alloc(2 * nb));
     gemv_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, dq, c->vtmp.p, c->red.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     dot2_kernel<<<nb, 256, 0, c->stream>>>(M, c->Bz.p, dcv, dq, part2.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     std::vector<double> h1(gv), h2(2 * nb);
     PCM_CUDA(cudaMemcpyAsync(h1.data(), c->red.p, gv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaMemcpyAsync(h2.data(), part2.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -240,7 +240,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     DBuf<double> azeta;
     PCM_TRY(azeta.alloc(natom));
     atom_zeta_kernel<<<(natom + 127) / 128, 128, 0, c->stream>>>(natom, c->radius.p, c->opt.zeta, n, azeta.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     std::vector<double> h_azeta(natom);
     PCM_CUDA(cudaMemcpyAsync(h_azeta.data(), azeta.p, natom * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
@@ -267,7 +267,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     PCM_TRY(keep.alloc(ncand));
     surface_candidates_kernel<<<(unsigned)((ncand + SURF_T - 1) / SURF_T), SURF_T, 0, c->stream>>>(
         natom, n, c->xyz.p, c->radius.p, azeta.p, c->opt.switch_drop, cx.p, cy.p, cz.p, cS.p, keep.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
 
     // compaction class by class into library order
     PCM_TRY(c->flags8.alloc(ncand));
@@ -281,7 +281,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     for (int e = 0; e < c->ncls; ++e) {
         class_flags_kernel<<<(unsigned)((ncand + 255) / 256), 256, 0, c->stream>>>(ncand, n, keep.p, acls.p, e,
                                                                                   c->flags8.p);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
         PCM_TRY(compact_flags(c, c->flags8.p, ncand, order.p + M, nullptr, c->iscal.p));
         int cnt = 0;
         PCM_CUDA(cudaMemcpyAsync(&cnt, c->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -305,7 +305,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     gather_points_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, n, order.p, cx.p, cy.p, cz.p, cS.p, azeta.p,
                                                                 acls.p, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
                                                                 c->pS.p, c->pindex.p, c->pcls.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     PCM_TRY(c->cls_zeta.alloc(c->ncls));
     PCM_TRY(c->cls_off.alloc(c->ncls + 1));
     PCM_CUDA(cudaMemcpyAsync(c->cls_zeta.p, c->h_cls_zeta.data(), c->ncls * sizeof(double),
@@ -315,7 +315,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
 
     bz_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, natom, c->px.p, c->py.p, c->pz.p, c->pzeta.p, c->xyz.p,
                                                      c->Z.p, c->Bz.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
 
     // stored A
     c->lda = (M + 31) / 32 * 32;
@@ -325,11 +325,11 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
         const long long ntiles = nt * (nt + 1) / 2;
         a_build_kernel<<<(unsigned)ntiles, 256, 0, c->stream>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
                                                                c->pS.p, c->A.p);
-        PCM_CUDA(cudaGetLastError());
+        PCM_LAUNCHED(c);
     }
     PCM_TRY(c->dinv.alloc(M));
     dinv_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, c->lda, c->A.p, c->dinv.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     PCM_CUDA(cudaStreamSynchronize(c->stream));  // local scratch buffers are freed on return
     c->pc_ready = false;
     c->have_c = false;

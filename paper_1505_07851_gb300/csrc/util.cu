@@ -90,7 +90,7 @@ int boys_build_tables(pcm_ctx *c)
     PCM_TRY(c->boys32.alloc((size_t)BOYS_NROW * BOYS_STRIDE32));
     PCM_CUDA(cudaMemsetAsync(c->boys64.p, 0, (size_t)BOYS_NROW * BOYS_STRIDE64 * sizeof(double), c->stream));
     boys_table_kernel<<<BOYS_NROW, BOYS_MCOL, 0, c->stream>>>(gx.p, gw.p, c->boys64.p, c->boys32.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     PCM_CUDA(cudaStreamSynchronize(c->stream));  // gx, gw are freed on return
     return PCM_OK;
 }
@@ -192,11 +192,11 @@ int compact_flags(pcm_ctx *c, const unsigned char *flags, long long n, int *out,
     if (nb < 1) nb = 1;
     PCM_TRY(c->scan32.alloc((size_t)nb + 1));
     compact_count<<<(unsigned)nb, CT, 0, c->stream>>>(flags, n, c->scan32.p);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     compact_scan<<<1, CT, 0, c->stream>>>(c->scan32.p, (int)nb, count_dev);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     compact_scatter<<<(unsigned)nb, CT, 0, c->stream>>>(flags, n, c->scan32.p, out, pos, count_dev);
-    PCM_CUDA(cudaGetLastError());
+    PCM_LAUNCHED(c);
     return PCM_OK;
 }
 
