@@ -185,6 +185,34 @@ int pcm_energy(pcm_ctx *ctx, const double *q, const double *c, double *E, int fl
 /* Statistics of the context's last calls. */
 int pcm_get_stats(pcm_ctx *ctx, pcm_stats *st);
 
+/* The energy of pcm_energy for callers that cannot allocate device memory
+ * (the paper has no counterpart; this is a library service).  A program
+ * whose GPU memory belongs to its own allocator -- a framework pool that has
+ * reserved the device, or an embedded solver with a fixed memory budget --
+ * cannot let a library call cudaMalloc: the call may fail while the pool
+ * holds the memory, and cudaMalloc/cudaFree may synchronise the device in
+ * the middle of the caller's work.  This entry point allocates nothing.
+ *
+ *   E = (Bz)^T q + c^T q + q^T A q / (2 f)
+ *
+ * All pointers are DEVICE pointers on the current CUDA device, owned by the
+ * caller: A (M rows, leading dimension lda >= M, row-major, e.g. the matrix
+ * of Eq. 2 and Eq. 3), Bz, c, q (M each) and the output E (one double).
+ * f = (eps - 1) / (eps + k).  stream: cudaStream_t (NULL: legacy default
+ * stream).  The work is only enqueued: E is valid once the stream reaches it.
+ *
+ * Scratch (A q and per-block partial sums) lives in a fixed device array of
+ * 536 KiB inside the library, held by every GPU that loads the library until
+ * the process exits.  M above 65536 is rejected with PCM_ERR_ARG.  The first
+ * call on a device looks up the array's device address (with that device
+ * current) and may load the library's device code; make that first call
+ * before any stream capture.  Every call shares the array: calls whose
+ * kernels overlap on the GPU (other streams, other host threads) race and
+ * give wrong results; serialise them.  Nothing in the array needs clearing
+ * between calls. */
+int pcm_energy_noalloc(int M, const double *A, int lda, const double *Bz, const double *c,
+                       const double *q, double f, double *E, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,7 @@ def _load():
         "pcm_fock": (i, [vp, vp, vp, i]),
         "pcm_energy": (i, [vp, vp, vp, ctypes.POINTER(d), i]),
         "pcm_get_stats": (i, [vp, ctypes.POINTER(pcm_stats)]),
+        "pcm_energy_noalloc": (i, [i, vp, i, vp, vp, vp, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -123,6 +124,23 @@ def _ptr(a, dtype):
         return a.data_ptr(), PCM_PTR_DEVICE, a
     arr = np.ascontiguousarray(a, dtype=dtype)
     return arr.ctypes.data, 0, arr
+
+
+def energy_noalloc(A, Bz, c, q, f, E, stream=None):
+    """pcm_energy_noalloc on CUDA torch tensors: A (M, lda >= M) row-major,
+    Bz, c, q (M,), E (1,) output; nothing is allocated by the library.  The
+    result is ready once `stream` (default: torch's current stream) reaches it."""
+    import torch
+    for t in (A, Bz, c, q, E):
+        _ptr(t, np.float64)
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device).cuda_stream
+    M = q.numel()
+    st = _lib.pcm_energy_noalloc(M, A.data_ptr(), A.stride(0), Bz.data_ptr(), c.data_ptr(), q.data_ptr(),
+                                 float(f), E.data_ptr(), stream)
+    if st != PCM_OK:
+        raise PCMError(st, "pcm_energy_noalloc", _lib.pcm_last_error().decode())
+    return E
 
 
 class Context:
