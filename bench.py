@@ -11,7 +11,10 @@ Metric: ESP + Fock equivalent Cartesian primitive integrals per second
 Fock call of a step) divided by the step time; the PCG solve time is
 reported beside it.  Workload: the 300-atom H:C:N:O:S = 50:31:9:9:1 cluster
 with 6-31G-like s/sp shells (nbf ~ 1.66k), 600 occupied orbitals, 110
-points per sphere at 1.2 x Bondi (M ~ 12k), FP64.
+points per sphere at 1.2 x Bondi (M ~ 12k).  The timed path is PCM_MIXED
+(FP32 integrals, FP64 accumulation and solve) unless --precision fp64; the
+FP64 path is timed beside it, and the energy of the timed solve is compared
+with an FP64 solve at delta = 1e-10.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -74,6 +77,19 @@ def flops_per_interaction(L, kind):
         return base + 2 * _nherm(L) + 2
     return base + 1 + _nherm(L)
 
+
+def flops_per_interaction_f32(L, kind):
+    """The FP32 kernels' operations: split-coordinate distance (9), R^2 (5),
+    T from split rho (3), Boys by 4-term Taylor (5 + 6 (L+1)), (-2 rho)^n
+    with the first-order rho_lo correction (4L + 1), Hermite recurrence, then
+    the split-D dot (4 nherm + 1) or the accumulation (nherm + 1)."""
+    base = 9 + 5 + 3 + 5 + 6 * (L + 1) + (4 * L + 1 if L else 0) + _hermite_ops(L)
+    if kind == "esp":
+        return base + (4 * _nherm(L) if L else 3) + 1
+    return base + _nherm(L) + 1
+
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
 
 CLASS_L = [0, 1, 2, 2, 3, 4]
 CLASS_NAME = ["ss", "ps", "pp", "ds", "dp", "dd"]
@@ -178,21 +194,14 @@ def workload_for(config, rank):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
-def run_ours(args):
+def _timed_steps(pcm, w, precision, args, dev, stream, flush, delta, steps, warmup):
+    """Warm up, then time `steps` whole-path steps with CUDA events on the
+    library's stream; L2 is flushed between steps outside the events."""
     import torch
-    rank, world, local = dist_init("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    import paper_1505_07851_gb300 as pcm
-
-    w = workload_for(args.config, rank)
-    stream = torch.cuda.current_stream(dev)
-    ctx = pcm.Context(precision=args.precision, device=local, stream=stream.cuda_stream, timing=True,
+    ctx = pcm.Context(precision=precision, device=dev.index, stream=stream.cuda_stream, timing=True,
                       seed=args.seed)
     b = w.basis
     Pd = torch.tensor(w.P, dtype=torch.float64, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    delta = args.delta if args.delta else DELTA_1E6
     bufs = {}
 
     def step():
@@ -205,62 +214,98 @@ def run_ours(args):
         ctx.esp(Pd, out=bufs["c"])
         q, st = ctx.solve(delta=delta, q=bufs["q"])
         ctx.fock(q, out=bufs["dF"])
-        E = ctx.energy(q)
-        return E, st
+        return ctx.energy(q), st
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    st0 = ctx.stats()
-    launches0 = st0["launches"]
-    times, solve_ms, iters, energies = [], [], [], []
-    ints = 0.0
-    esp_cls = np.zeros(6)
-    fock_cls = np.zeros(6)
-    barrier(world)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()                       # evict L2 between steps (not timed)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            E, st = step()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            s = ctx.stats()
-            solve_ms.append(s["ms_solve"])
-            iters.append(st["iterations"])
-            energies.append(E)
-            ints += s["integrals_esp"] + s["integrals_fock"]
-            esp_cls += np.array(s["ms_esp_class"])
-            fock_cls += np.array(s["ms_fock_class"])
-    torch.cuda.synchronize()
-    barrier(world)
+    launches0 = ctx.stats()["launches"]
+    out = {"times": [], "solve_ms": [], "iters": [], "E": [], "ints": 0.0, "esp_cls": np.zeros(6),
+           "fock_cls": np.zeros(6)}
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        E, st = step()
+        e1.record(stream)
+        e1.synchronize()
+        out["times"].append(e0.elapsed_time(e1))
+        s = ctx.stats()
+        out["solve_ms"].append(s["ms_solve"])
+        out["iters"].append(st["iterations"])
+        out["E"].append(E)
+        out["ints"] += s["integrals_esp"] + s["integrals_fock"]
+        out["esp_cls"] += np.array(s["ms_esp_class"])
+        out["fock_cls"] += np.array(s["ms_fock_class"])
     s = ctx.stats()
-    launches = s["launches"] - launches0
-    total_ms = sum(times)
-    total_ms_max = dist_max(total_ms, world, dev)
-    ints_all = ints * world                      # every rank ran a molecule of the same size class
-    value = ints_all / (total_ms_max * 1e-3)
+    out["launches"] = s["launches"] - launches0
+    out["stats"] = s
+    out["ctx"] = ctx
+    out["bufs"] = bufs
+    out["Pd"] = Pd
+    return out
 
-    # dominant kernel and its roofline (FP64 ALU bound)
+
+def _dominant(res, precision, steps):
+    s = res["stats"]
     M = s["M"]
+    fl = flops_per_interaction if precision == "fp64" else flops_per_interaction_f32
+    tag = "f64" if precision == "fp64" else "f32"
     cand = []
     for k in range(6):
-        if esp_cls[k] > 0:
-            cand.append(("esp_kernel_f64<L=%d> (%s)" % (CLASS_L[k], CLASS_NAME[k]), esp_cls[k] / args.steps,
-                         s["esp_class_pairs"][k] * M * flops_per_interaction(CLASS_L[k], "esp")))
-        if fock_cls[k] > 0:
-            cand.append(("fock_kernel_f64<L=%d> (%s)" % (CLASS_L[k], CLASS_NAME[k]), fock_cls[k] / args.steps,
-                         s["fock_class_pairs"][k] * M * flops_per_interaction(CLASS_L[k], "fock")))
+        if res["esp_cls"][k] > 0:
+            cand.append(("esp_kernel_%s<L=%d> (%s)" % (tag, CLASS_L[k], CLASS_NAME[k]), res["esp_cls"][k] / steps,
+                         s["esp_class_pairs"][k] * M * fl(CLASS_L[k], "esp")))
+        if res["fock_cls"][k] > 0:
+            cand.append(("fock_kernel_%s<L=%d> (%s)" % (tag, CLASS_L[k], CLASS_NAME[k]), res["fock_cls"][k] / steps,
+                         s["fock_class_pairs"][k] * M * fl(CLASS_L[k], "fock")))
     name, ms_k, flops_k = max(cand, key=lambda t: t[1])
+    peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
     achieved = flops_k / (ms_k * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
-                "kernel_ms": ms_k}
+    src = ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (nominal 1.25 TFLOP/s)" if precision == "fp64" else
+           "FP32 pipe: 152 SMs x 128 FFMA/clk x 2070 MHz")
+    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_source": src, "kernel_ms": ms_k}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_init("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1505_07851_gb300 as pcm
+
+    w = workload_for(args.config, rank)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    delta = args.delta if args.delta else DELTA_1E6
+    b = w.basis
+
+    # reference energy: FP64 path with a tight solve (not timed)
+    with pcm.Context(precision="fp64", device=local, stream=stream.cuda_stream) as ref:
+        ref.setup(w.mol, w.basis)
+        ref.esp(w.P)
+        qr, _ = ref.solve(delta=1e-10)
+        E_ref = ref.energy(qr)
+
+    barrier(world)
+    with ClockSampler(local) as clk:
+        main = _timed_steps(pcm, w, args.precision, args, dev, stream, flush, delta, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    other = None
+    if args.precision == "mixed" and not args.no_fp64:
+        other = _timed_steps(pcm, w, "fp64", args, dev, stream, flush, delta, max(1, args.steps // 2), 1)
+
+    total_ms = sum(main["times"])
+    total_ms_max = dist_max(total_ms, world, dev)
+    ints_all = main["ints"] * world                 # every rank ran a molecule of the same size class
+    value = ints_all / (total_ms_max * 1e-3)
+    roofline = _dominant(main, args.precision, args.steps)
+    roofline["traffic"] = args.traffic
+    s = main["stats"]
+    ctx = main["ctx"]
 
     # end-to-end through the public API with host buffers (copies inside the timed region)
     e2e = None
@@ -273,49 +318,55 @@ def run_ours(args):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Mh = ctx.build_surface(w.mol.xyz, w.mol.Z, w.mol.radius, 110)
-            nbfh = ctx.set_basis(b.shell_atom, b.shell_l, b.shell_nprim, b.exps, b.coefs)
+            ctx.build_surface(w.mol.xyz, w.mol.Z, w.mol.radius, 110)
+            ctx.set_basis(b.shell_atom, b.shell_l, b.shell_nprim, b.exps, b.coefs)
             ch = ctx.esp(Ph)
             qh, _ = ctx.solve(delta=delta)
             Fh = ctx.fock(qh)
-            Eh = ctx.energy(qh)
+            ctx.energy(qh)
             et.append(time.perf_counter() - t0)
         d2h = ch.nbytes + qh.nbytes + Fh.nbytes + 8
         e_ms = dist_max(sum(et) * 1e3, world, dev)
         e2e = {"value": ints_all / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms / len(et)}
 
-    # accuracy of the timed solve: energy against a tight solve (not timed)
-    ctx.build_surface(w.mol.xyz, w.mol.Z, w.mol.radius, 110)
-    ctx.set_basis(b.shell_atom, b.shell_l, b.shell_nprim, b.exps, b.coefs)
-    ctx.esp(Pd, out=bufs["c"])
-    qt, stt = ctx.solve(delta=1e-10, q=bufs["q"])
-    E_tight = ctx.energy(qt)
-    energy_err = abs(energies[-1] - E_tight)
-
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_points)
-    ctx.close()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64",
             "data": "synthetic (seeded protein-shaped cluster; no PDB/basis data in this container)",
-            "config": {"workload": w.name, "natom": w.mol.natom, "nbf": s["nbf"], "M": M,
+            "config": {"workload": w.name, "natom": w.mol.natom, "nbf": s["nbf"], "M": s["M"],
                        "pts_per_sphere": 110, "precision": args.precision, "delta": delta,
-                       "precond": "rbj-100" if M >= 1000 else "jacobi",
+                       "precond": "rbj-100" if s["M"] >= 1000 else "jacobi",
                        "l2": "flushed between timed steps (512 MB write, not timed)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "pcg_solve_ms": statistics.mean(solve_ms), "pcg_iterations": statistics.mean(iters),
-            "energy_Eh": energies[-1], "energy_err_Eh": energy_err,
-            "esp_kernel_ms": float(esp_cls.sum() / args.steps), "fock_kernel_ms": float(fock_cls.sum() / args.steps),
-            "integrals_per_step": ints / args.steps, "pairs_kept": s["pairs_kept"],
-            "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
+            "pcg_solve_ms": statistics.mean(main["solve_ms"]), "pcg_iterations": statistics.mean(main["iters"]),
+            "energy_Eh": main["E"][-1], "energy_ref_fp64_Eh": E_ref,
+            "energy_err_Eh": abs(main["E"][-1] - E_ref),
+            "esp_kernel_ms": float(main["esp_cls"].sum() / args.steps),
+            "fock_kernel_ms": float(main["fock_cls"].sum() / args.steps),
+            "integrals_per_step": main["ints"] / args.steps, "pairs_kept": s["pairs_kept"],
+            "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": main["launches"],
             "cpu_baseline": cpu,
         }
+        if other is not None:
+            n = len(other["times"])
+            line["fp64"] = {"value": other["ints"] * world / (sum(other["times"]) * 1e-3), "unit": UNIT,
+                            "ms_per_step": sum(other["times"]) / n,
+                            "pcg_solve_ms": statistics.mean(other["solve_ms"]),
+                            "esp_kernel_ms": float(other["esp_cls"].sum() / n),
+                            "fock_kernel_ms": float(other["fock_cls"].sum() / n),
+                            "energy_err_Eh": abs(other["E"][-1] - E_ref),
+                            "roofline": _dominant(other, "fp64", n)}
+            line["speedup_vs_fp64"] = line["fp64"]["ms_per_step"] / line["ms_per_step"]
         print(json.dumps(line))
+    main["ctx"].close()
+    if other is not None:
+        other["ctx"].close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -388,7 +439,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=1)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--delta", type=float, default=None)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-points", type=int, default=32)

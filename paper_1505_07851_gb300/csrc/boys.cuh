@@ -3,7 +3,7 @@
 // T < BOYS_TMAX: tabulated values at T_i = i * BOYS_DT and a Taylor expansion
 // in d = T - T_i, using dF_m/dT = -F_{m+1}:
 //     F_m(T) = sum_k F_{m+k}(T_i) (-d)^k / k!
-// (7 terms in FP64, 4 in FP32; |d| <= BOYS_DT / 2).
+// (7 terms in FP64, 5 in FP32 with F_m(T_i) split as hi + lo; |d| <= BOYS_DT / 2).
 // T >= BOYS_TMAX: F_0 = sqrt(pi / T) / 2 and F_m = F_{m-1} (2m - 1) / (2T);
 // the neglected exp(-T) terms are below 1e-14 relative for m <= 6 there.
 #pragma once
@@ -16,7 +16,8 @@ constexpr double BOYS_DT = 1.0 / 32.0;
 constexpr double BOYS_INV_DT = 32.0;
 constexpr int BOYS_NROW = 1540;            // rows 0 .. 48*32 (+ margin)
 constexpr int BOYS_STRIDE64 = 16;          // doubles per row: m = 0 .. 15
-constexpr int BOYS_STRIDE32 = 8;           // floats per row:  m = 0 .. 7
+constexpr int BOYS_STRIDE32 = 16;          // floats per row: F_0..F_9 (hi) then the lo parts of F_0..F_5
+constexpr int BOYS_LO32 = 10;              // offset of the lo parts
 constexpr int BOYS_MCOL = 16;              // columns generated
 
 template <int MM>
@@ -53,25 +54,40 @@ __device__ __forceinline__ void boys_eval(double T, const double *__restrict__ t
 template <int MM>
 __device__ __forceinline__ void boys_eval(float T, const float *__restrict__ tab, float (&F)[MM + 1])
 {
-    static_assert(MM + 3 < BOYS_STRIDE32, "Boys table too narrow");
+    // 5-term Taylor from F_m(T_i) stored as hi + lo: the table's FP32 rounding
+    // and the truncation (whose d^4 remainder has one sign) would otherwise
+    // both bias the result in the same direction for every interaction
+    static_assert(MM + 4 < BOYS_LO32 && MM <= 5, "Boys table too narrow");
     if (T < (float)BOYS_TMAX) {
         const int i = min(max(__float2int_rn(T * (float)BOYS_INV_DT), 0), BOYS_NROW - 1);
         const float d = fmaf((float)i, -(float)BOYS_DT, T);
         const float *row = tab + (size_t)i * BOYS_STRIDE32;
-        float r[MM + 4];
+        float r[MM + 5], lo[MM + 1];
 #pragma unroll
-        for (int k = 0; k < MM + 4; ++k) r[k] = __ldg(row + k);
-        const float e1 = -d, e2 = -d * 0.5f, e3 = -d * (1.0f / 3.0f);
+        for (int k = 0; k < MM + 5; ++k) r[k] = __ldg(row + k);
+#pragma unroll
+        for (int k = 0; k <= MM; ++k) lo[k] = __ldg(row + BOYS_LO32 + k);
+        const float e1 = -d, e2 = -d * 0.5f, e3 = -d * (1.0f / 3.0f), e4 = -d * 0.25f;
 #pragma unroll
         for (int m = 0; m <= MM; ++m) {
-            float s = fmaf(r[m + 3], e3, r[m + 2]);
+            float s = fmaf(r[m + 4], e4, r[m + 3]);
+            s = fmaf(s, e3, r[m + 2]);
             s = fmaf(s, e2, r[m + 1]);
-            F[m] = fmaf(s, e1, r[m]);
+            F[m] = fmaf(s, e1, lo[m]) + r[m];  // the small terms first, one rounding of the sum
         }
     } else {
-        const float rs = rsqrtf(T);
+        // sqrt(pi)/2 carried as hi + lo so that its FP32 rounding does not bias
+        // every far-field interaction the same way
+        constexpr float C_HI = 0.88622692545275801365f;
+        constexpr float C_LO = (float)(0.88622692545275801365 - (double)C_HI);
+        // hardware reciprocal square root, then one Newton step: the rounding
+        // error left is that of the last FMA, without the approximation's
+        // structured (input-correlated) error
+        const float r0 = rsqrtf(T);
+        const float e = fmaf(-T * r0, r0, 1.0f);
+        const float rs = fmaf(0.5f * r0, e, r0);
         const float half_inv_T = 0.5f * rs * rs;
-        F[0] = 0.886226925f * rs;
+        F[0] = fmaf(C_HI, rs, C_LO * rs);
 #pragma unroll
         for (int m = 1; m <= MM; ++m) F[m] = F[m - 1] * (float)(2 * m - 1) * half_inv_T;
     }

@@ -88,8 +88,8 @@ struct PairClass {
     // per-call ESP pairs (after the density test of Eq. 18), SoA; D has nherm(L) rows
     int nesp = 0;
     DBuf<double> eP, eD;                   // eP: 4 x nesp (Px, Py, Pz, p); eD: nherm x nesp
-    DBuf<float> eP32, eD32;                // FP32 copies for PCM_MIXED
-    DBuf<float> Pxyz32;                    // 4 x npair (Px, Py, Pz, p) FP32 for the Fock kernel
+    DBuf<float> eX32, eC32;                // PCM_MIXED ESP: 6 x nesp split centres; ncls x (3 + 2 nherm) x nesp constants
+    DBuf<float> Pxyz32;                    // 6 x npair: hi (3) and lo (3) FP32 parts of the centre (Fock, PCM_MIXED)
 };
 
 struct pcm_ctx_impl;
@@ -121,8 +121,8 @@ struct pcm_ctx {
     pcm::DBuf<int> cls_off;                // ncls + 1
     pcm::DBuf<double> px, py, pz, pzeta, pS, Bz;
     pcm::DBuf<int> pindex, pcls;
-    pcm::DBuf<float> p32;                  // 4 x M: x, y, z (split high parts) and unused
-    pcm::DBuf<float> p32lo;                // 3 x M: low parts of the split coordinates
+    pcm::DBuf<float> p32;                  // 3 x M: FP32 high parts of x, y, z (2^-10 grid)
+    pcm::DBuf<float> p32lo;                // 3 x M: FP32 low parts
 
     // stored A (FP64), leading dimension lda
     int lda = 0;
@@ -180,6 +180,10 @@ int basis_build(pcm_ctx *c, int nshell, const int *shell_atom, const int *shell_
                 const double *exps, const double *coefs);
 int esp_compute(pcm_ctx *c, const double *dP, double *dc);
 int fock_compute(pcm_ctx *c, const double *dq, double *ddF);
+// PCM_MIXED (integrals_mixed.cu)
+int points_split(pcm_ctx *c);
+int esp_compute_mixed(pcm_ctx *c, double *dc);
+int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W);
 int solver_prepare(pcm_ctx *c);
 int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st);
 int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E);

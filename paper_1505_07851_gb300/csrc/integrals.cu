@@ -69,8 +69,7 @@ __global__ void esp_coef_kernel(int nesp, const int *__restrict__ list, const in
                                 const double *__restrict__ Px, const double *__restrict__ Py,
                                 const double *__restrict__ Pz, const double *__restrict__ pp,
                                 const double *__restrict__ pref, const double *__restrict__ Pm, int nbf,
-                                double *__restrict__ eP, double *__restrict__ eD, float *__restrict__ eP32,
-                                float *__restrict__ eD32)
+                                double *__restrict__ eP, double *__restrict__ eD)
 {
     constexpr int L = LA + LB;
     constexpr int NH = nherm(L);
@@ -119,15 +118,8 @@ __global__ void esp_coef_kernel(int nesp, const int *__restrict__ list, const in
     eP[1 * (size_t)nesp + j] = P[1];
     eP[2 * (size_t)nesp + j] = P[2];
     eP[3 * (size_t)nesp + j] = p;
-    eP32[0 * (size_t)nesp + j] = (float)P[0];
-    eP32[1 * (size_t)nesp + j] = (float)P[1];
-    eP32[2 * (size_t)nesp + j] = (float)P[2];
-    eP32[3 * (size_t)nesp + j] = (float)p;
 #pragma unroll
-    for (int h = 0; h < NH; ++h) {
-        eD[(size_t)h * nesp + j] = scale * D[h];
-        eD32[(size_t)h * nesp + j] = (float)(scale * D[h]);
-    }
+    for (int h = 0; h < NH; ++h) eD[(size_t)h * nesp + j] = scale * D[h];
 }
 
 // ---------------------------------------------------------------------------
@@ -461,13 +453,24 @@ static int esp_prepare_class(pcm_ctx *c, PairClass &pc, const double *dP)
     constexpr int NH = nherm(LA + LB);
     PCM_TRY(pc.eP.alloc(4 * (size_t)n));
     PCM_TRY(pc.eD.alloc((size_t)NH * n));
-    PCM_TRY(pc.eP32.alloc(4 * (size_t)n));
-    PCM_TRY(pc.eD32.alloc((size_t)NH * n));
     esp_coef_kernel<LA, LB><<<(n + 127) / 128, 128, 0, c->stream>>>(
         n, c->idx32.p, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_off.p, c->sh_bf.p,
-        c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, dP, c->nbf, pc.eP.p, pc.eD.p, pc.eP32.p,
-        pc.eD32.p);
+        c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, dP, c->nbf, pc.eP.p, pc.eD.p);
     PCM_LAUNCHED(c);
+    return PCM_OK;
+}
+
+static int esp_class_stats(pcm_ctx *c)
+{
+    for (int k = 0; k < 6; ++k) {
+        c->stats.esp_class_pairs[k] = c->cls[k].nesp;
+        c->stats.ms_esp_class[k] = 0.0;
+        if (c->have_events && c->cls[k].nesp > 0) {
+            float ms = 0.f;
+            PCM_CUDA(cudaEventElapsedTime(&ms, c->ev_a[k], c->ev_b[k]));
+            c->stats.ms_esp_class[k] = ms;
+        }
+    }
     return PCM_OK;
 }
 
@@ -480,6 +483,18 @@ int esp_compute(pcm_ctx *c, const double *dP, double *dc)
     PCM_TRY((esp_prepare_class<2, 1>(c, c->cls[4], dP)));
     PCM_TRY((esp_prepare_class<2, 2>(c, c->cls[5], dP)));
 
+    if (c->opt.precision == PCM_MIXED) {
+        long long pesp = 0;
+        double ints = 0.0;
+        for (int k = 0; k < 6; ++k) {
+            pesp += c->cls[k].nesp;
+            ints += (double)c->cls[k].nesp * ncart(c->cls[k].la) * ncart(c->cls[k].lb) * c->M;
+        }
+        c->stats.pairs_esp = pesp;
+        c->stats.integrals_esp = ints;
+        PCM_TRY(esp_compute_mixed(c, dc));
+        return esp_class_stats(c);
+    }
     std::vector<int> off;
     esp_blocks(c, off);
     const int nblk = (int)off.size() - 1;
@@ -532,16 +547,7 @@ int esp_compute(pcm_ctx *c, const double *dP, double *dc)
     esp_reduce_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
     PCM_LAUNCHED(c);
     PCM_CUDA(cudaStreamSynchronize(c->stream));  // blk is freed on return
-    for (int k = 0; k < 6; ++k) {
-        c->stats.esp_class_pairs[k] = c->cls[k].nesp;
-        c->stats.ms_esp_class[k] = 0.0;
-        if (c->have_events && c->cls[k].nesp > 0) {
-            float ms = 0.f;
-            PCM_CUDA(cudaEventElapsedTime(&ms, c->ev_a[k], c->ev_b[k]));
-            c->stats.ms_esp_class[k] = ms;
-        }
-    }
-    return PCM_OK;
+    return esp_class_stats(c);
 }
 
 template <int LA, int LB>
@@ -561,10 +567,15 @@ static int fock_class(pcm_ctx *c, PairClass &pc, const double *dq, double *ddF)
         PCM_TRY(c->fock_W.alloc((size_t)nsplit * NH * pc.npair));
         dim3 grid(nb, nsplit);
         if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[6 + (int)(&pc - c->cls)], c->stream));
-        fock_kernel_f64<L><<<grid, FOCK_NT, 0, c->stream>>>(pc.npair, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, ks, c->px.p,
-                                                             c->py.p, c->pz.p, dq, c->M, c->ncls, c->cls_off.p,
-                                                             c->cls_zeta.p, c->boys64.p, c->fock_W.p);
-        PCM_LAUNCHED(c);
+        if (c->opt.precision == PCM_MIXED) {
+            PCM_TRY(fock_mixed_class(c, (int)(&pc - c->cls), dq, nsplit, ks, c->fock_W.p));
+        } else {
+            fock_kernel_f64<L><<<grid, FOCK_NT, 0, c->stream>>>(pc.npair, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, ks,
+                                                                 c->px.p, c->py.p, c->pz.p, dq, c->M, c->ncls,
+                                                                 c->cls_off.p, c->cls_zeta.p, c->boys64.p,
+                                                                 c->fock_W.p);
+            PCM_LAUNCHED(c);
+        }
         if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[6 + (int)(&pc - c->cls)], c->stream));
     }
     fock_epilogue_kernel<LA, LB><<<(pc.nsp + 127) / 128, 128, 0, c->stream>>>(

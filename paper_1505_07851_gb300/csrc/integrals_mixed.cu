@@ -1,0 +1,404 @@
+// PCM_MIXED integral kernels: the same McMurchie-Davidson contractions as
+// integrals.cu, evaluated on the FP32 pipes (62x the FP64 rate on GB300) with
+// FP64 accumulation across tiles.
+//
+// Error control.  FP32 rounding that is the same for every surface point
+// (a per-pair constant) would bias c_k for all k alike and add up in the
+// energy (dE = q^T dc); rounding that varies from point to point averages
+// out.  So every per-pair or per-(pair, class) constant is carried as an
+// FP32 hi + lo pair computed in FP64: the Hermite density D_tuv times U, rho
+// (T = rho_hi R^2 + rho_lo R^2, and (-2 rho)^n corrected to first order in
+// rho_lo / rho_hi), and sqrt(pi)/2 in the far-field Boys branch.  Coordinates
+// are split as hi (on a 2^-10 grid, so hi differences are exact) + lo, so
+// every distance is the FP32 rounding of the exact one.  Sums run in FP32
+// within a tile of 32 pairs (ESP, Kahan-compensated) or 128 points (Fock)
+// and in FP64 across tiles.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "boys.cuh"
+#include "common.cuh"
+#include "context.h"
+
+namespace pcm {
+
+__device__ __forceinline__ void split_val(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+__device__ __forceinline__ void split_coord(double v, float &hi, float &lo)
+{
+    const double h = rint(v * 1024.0) * (1.0 / 1024.0);
+    hi = (float)h;
+    lo = (float)(v - h);
+}
+
+// point coordinates -> FP32 hi/lo [3][M] each
+__global__ void point_split_kernel(int M, const double *__restrict__ px, const double *__restrict__ py,
+                                   const double *__restrict__ pz, float *__restrict__ hi, float *__restrict__ lo)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    split_coord(px[k], hi[k], lo[k]);
+    split_coord(py[k], hi[(size_t)M + k], lo[(size_t)M + k]);
+    split_coord(pz[k], hi[2 * (size_t)M + k], lo[2 * (size_t)M + k]);
+}
+
+int points_split(pcm_ctx *c)
+{
+    PCM_TRY(c->p32.alloc(3 * (size_t)c->M));
+    PCM_TRY(c->p32lo.alloc(3 * (size_t)c->M));
+    point_split_kernel<<<(c->M + 127) / 128, 128, 0, c->stream>>>(c->M, c->px.p, c->py.p, c->pz.p, c->p32.p,
+                                                                  c->p32lo.p);
+    PCM_LAUNCHED(c);
+    return PCM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ESP: per-(class e, pair j) constants
+//   eX[0..2][j] = hi(P), eX[3..5][j] = lo(P)
+//   eC[e][0][j] = rho_hi, [1] = rho_lo, [2] = rho_lo / rho_hi,
+//   eC[e][3 + h][j] = hi(U D_h), eC[e][3 + NH + h][j] = lo(U D_h)
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void esp_mixed_prep_kernel(int nesp, int ncls, const double *__restrict__ cls_zeta,
+                                      const double *__restrict__ eP, const double *__restrict__ eD,
+                                      float *__restrict__ eX, float *__restrict__ eC)
+{
+    constexpr int NH = nherm(L);
+    constexpr int F = 3 + 2 * NH;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nesp) return;
+    for (int d = 0; d < 3; ++d) split_coord(eP[(size_t)d * nesp + j], eX[(size_t)d * nesp + j], eX[(size_t)(3 + d) * nesp + j]);
+    const double p = eP[3 * (size_t)nesp + j];
+    for (int e = 0; e < ncls; ++e) {
+        float *C = eC + (size_t)e * F * nesp;
+        const double z2 = cls_zeta[e] * cls_zeta[e];
+        const double inv = 1.0 / (p + z2);
+        const double rho = p * z2 * inv;
+        const double U = sqrt(z2 * inv);
+        float rh, rl;
+        split_val(rho, rh, rl);
+        C[0 * (size_t)nesp + j] = rh;
+        C[1 * (size_t)nesp + j] = rl;
+        C[2 * (size_t)nesp + j] = (float)((rho - (double)rh) / (double)rh);
+        for (int h = 0; h < NH; ++h) {
+            float dh, dl;
+            split_val(U * eD[(size_t)h * nesp + j], dh, dl);
+            C[(size_t)(3 + h) * nesp + j] = dh;
+            C[(size_t)(3 + NH + h) * nesp + j] = dl;
+        }
+    }
+}
+
+constexpr int MESP_NT = 128;
+constexpr int MESP_PPT = 2;
+constexpr int MESP_TP = 32;
+
+template <int L>
+__global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int seglen, const float *__restrict__ eX,
+                                                          const float *__restrict__ eC, const int *__restrict__ blk_off,
+                                                          const int *__restrict__ blk_cls, const float *__restrict__ ph,
+                                                          const float *__restrict__ pl, const float *__restrict__ boys,
+                                                          int M, double *__restrict__ part)
+{
+    constexpr int NH = nherm(L);
+    constexpr int F = 3 + 2 * NH;
+    __shared__ float sX[6][MESP_TP];
+    __shared__ float sC[F][MESP_TP];
+    const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
+    const float *C = eC + (size_t)blk_cls[blockIdx.x] * F * nesp;
+    const int j0 = blockIdx.y * seglen;
+    const int j1 = min(nesp, j0 + seglen);
+
+    float xh[MESP_PPT], yh[MESP_PPT], zh[MESP_PPT], xl[MESP_PPT], yl[MESP_PPT], zl[MESP_PPT];
+    double acc[MESP_PPT];
+    bool on[MESP_PPT];
+#pragma unroll
+    for (int q = 0; q < MESP_PPT; ++q) {
+        const int k = k0 + threadIdx.x + q * MESP_NT;
+        on[q] = k < k1;
+        const int kk = on[q] ? k : k0;
+        xh[q] = ph[kk];
+        yh[q] = ph[(size_t)M + kk];
+        zh[q] = ph[2 * (size_t)M + kk];
+        xl[q] = pl[kk];
+        yl[q] = pl[(size_t)M + kk];
+        zl[q] = pl[2 * (size_t)M + kk];
+        acc[q] = 0.0;
+    }
+    for (int jt = j0; jt < j1; jt += MESP_TP) {
+        const int nt = min(MESP_TP, j1 - jt);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 6 * MESP_TP; t += MESP_NT) {
+            const int f = t / MESP_TP, jj = t % MESP_TP;
+            sX[f][jj] = jj < nt ? eX[(size_t)f * nesp + jt + jj] : 0.f;
+        }
+        for (int t = threadIdx.x; t < F * MESP_TP; t += MESP_NT) {
+            const int f = t / MESP_TP, jj = t % MESP_TP;
+            sC[f][jj] = jj < nt ? C[(size_t)f * nesp + jt + jj] : (f == 0 ? 1.f : 0.f);
+        }
+        __syncthreads();
+        // Kahan-compensated FP32 sums: adding a small term to a larger running
+        // sum in plain FP32 drops its bits below half an ulp, always towards
+        // a smaller magnitude for same-sign terms (a bias, not noise)
+        float a32[MESP_PPT], k32[MESP_PPT];
+#pragma unroll
+        for (int q = 0; q < MESP_PPT; ++q) a32[q] = k32[q] = 0.f;
+        for (int jj = 0; jj < nt; ++jj) {
+            const float rh = sC[0][jj], rl = sC[1][jj];
+#pragma unroll
+            for (int q = 0; q < MESP_PPT; ++q) {
+                const float X = (sX[0][jj] - xh[q]) + (sX[3][jj] - xl[q]);
+                const float Y = (sX[1][jj] - yh[q]) + (sX[4][jj] - yl[q]);
+                const float Z = (sX[2][jj] - zh[q]) + (sX[5][jj] - zl[q]);
+                const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+                const float T = fmaf(rh, R2, rl * R2);
+                float Fb[L + 1];
+                boys_eval<L>(T, boys, Fb);
+                float dot;
+                if constexpr (L == 0) {
+                    dot = fmaf(sC[3][jj], Fb[0], sC[4][jj] * Fb[0]);
+                } else {
+                    const float dr = sC[2][jj];
+                    const float m2r = -2.f * rh;
+                    float Rn[L + 1];
+                    float f = 1.f;
+#pragma unroll
+                    for (int n = 0; n <= L; ++n) {
+                        const float v = f * Fb[n];
+                        Rn[n] = (n == 0) ? v : fmaf(v, (float)n * dr, v);
+                        f *= m2r;
+                    }
+                    float R[NH];
+                    hermite_R<L, float>(X, Y, Z, Rn, R);
+                    dot = 0.f;
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) dot = fmaf(sC[3 + h][jj], R[h], fmaf(sC[3 + NH + h][jj], R[h], dot));
+                }
+                const float y = dot - k32[q];
+                const float t = a32[q] + y;
+                k32[q] = (t - a32[q]) - y;
+                a32[q] = t;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MESP_PPT; ++q) acc[q] += (double)a32[q] - (double)k32[q];
+    }
+#pragma unroll
+    for (int q = 0; q < MESP_PPT; ++q) {
+        const int k = k0 + threadIdx.x + q * MESP_NT;
+        if (on[q]) part[(size_t)blockIdx.y * M + k] = acc[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fock: thread per primitive pair; per class rho and U in FP64 (hi/lo for rho),
+// per point tile FP32 sums of q_k R_tuv, folded into FP64 with U.
+// ---------------------------------------------------------------------------
+constexpr int MF_NT = 128;
+constexpr int MF_TQ = 128;
+
+template <int L>
+__global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double *__restrict__ gp,
+                                                         const float *__restrict__ Phl, int ksplit,
+                                                         const float *__restrict__ ph, const float *__restrict__ pl,
+                                                         const double *__restrict__ q, int M, int ncls,
+                                                         const int *__restrict__ cls_off,
+                                                         const double *__restrict__ cls_zeta,
+                                                         const float *__restrict__ boys, double *__restrict__ W)
+{
+    constexpr int NH = nherm(L);
+    __shared__ float sxh[MF_TQ], syh[MF_TQ], szh[MF_TQ], sxl[MF_TQ], syl[MF_TQ], szl[MF_TQ], sq[MF_TQ];
+    const int r = blockIdx.x * MF_NT + threadIdx.x;
+    const bool active = r < npair;
+    const int rr = active ? r : 0;
+    const float Pxh = Phl[rr], Pyh = Phl[(size_t)npair + rr], Pzh = Phl[2 * (size_t)npair + rr];
+    const float Pxl = Phl[3 * (size_t)npair + rr], Pyl = Phl[4 * (size_t)npair + rr],
+                Pzl = Phl[5 * (size_t)npair + rr];
+    const double p = gp[rr];
+    const int ka = blockIdx.y * ksplit;
+    const int kb = min(M, ka + ksplit);
+    double w64[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) w64[h] = 0.0;
+    for (int ec = 0; ec < ncls; ++ec) {
+        const int a = max(ka, cls_off[ec]), b = min(kb, cls_off[ec + 1]);
+        if (a >= b) continue;
+        const double z2 = cls_zeta[ec] * cls_zeta[ec];
+        const double inv = 1.0 / (p + z2);
+        const double rho = p * z2 * inv;
+        const double U = sqrt(z2 * inv);
+        const float rh = (float)rho;
+        const float rl = (float)(rho - (double)rh);
+        const float dr = (float)((rho - (double)rh) / (double)rh);
+        const float m2r = -2.f * rh;
+        for (int t0 = a; t0 < b; t0 += MF_TQ) {
+            const int nt = min(MF_TQ, b - t0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < nt; t += MF_NT) {
+                sxh[t] = ph[t0 + t];
+                syh[t] = ph[(size_t)M + t0 + t];
+                szh[t] = ph[2 * (size_t)M + t0 + t];
+                sxl[t] = pl[t0 + t];
+                syl[t] = pl[(size_t)M + t0 + t];
+                szl[t] = pl[2 * (size_t)M + t0 + t];
+                sq[t] = (float)q[t0 + t];
+            }
+            __syncthreads();
+            float w32[NH];
+#pragma unroll
+            for (int h = 0; h < NH; ++h) w32[h] = 0.f;
+            for (int kk = 0; kk < nt; ++kk) {
+                const float X = (Pxh - sxh[kk]) + (Pxl - sxl[kk]);
+                const float Y = (Pyh - syh[kk]) + (Pyl - syl[kk]);
+                const float Z = (Pzh - szh[kk]) + (Pzl - szl[kk]);
+                const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+                const float T = fmaf(rh, R2, rl * R2);
+                float Fb[L + 1];
+                boys_eval<L>(T, boys, Fb);
+                if constexpr (L == 0) {
+                    w32[0] = fmaf(sq[kk], Fb[0], w32[0]);
+                } else {
+                    float Rn[L + 1];
+                    float f = sq[kk];
+#pragma unroll
+                    for (int n = 0; n <= L; ++n) {
+                        const float v = f * Fb[n];
+                        Rn[n] = (n == 0) ? v : fmaf(v, (float)n * dr, v);
+                        f *= m2r;
+                    }
+                    float R[NH];
+                    hermite_R<L, float>(X, Y, Z, Rn, R);
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) w32[h] += R[h];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < NH; ++h) w64[h] = fma(U, (double)w32[h], w64[h]);
+        }
+    }
+    if (active) {
+#pragma unroll
+        for (int h = 0; h < NH; ++h) W[((size_t)blockIdx.y * NH + h) * npair + r] = w64[h];
+    }
+}
+
+__global__ void esp_reduce_mixed_kernel(int M, int nseg, const double *__restrict__ part, double *__restrict__ c)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    double s = 0.0;
+    for (int g = 0; g < nseg; ++g) s += part[(size_t)g * M + k];
+    c[k] = s;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static const int CLASS_L[6] = {0, 1, 2, 2, 3, 4};
+
+template <int L>
+static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, const int *bcls, int nblk, int nseg,
+                            int seglen, double *part)
+{
+    constexpr int NH = nherm(L);
+    constexpr int F = 3 + 2 * NH;
+    const int n = pc.nesp;
+    PCM_TRY(pc.eX32.alloc(6 * (size_t)n));
+    PCM_TRY(pc.eC32.alloc((size_t)c->ncls * F * n));
+    esp_mixed_prep_kernel<L><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->ncls, c->cls_zeta.p, pc.eP.p, pc.eD.p,
+                                                                     pc.eX32.p, pc.eC32.p);
+    PCM_LAUNCHED(c);
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[k], c->stream));
+    dim3 grid(nblk, nseg);
+    esp_kernel_f32<L><<<grid, MESP_NT, 0, c->stream>>>(n, seglen, pc.eX32.p, pc.eC32.p, blk, bcls, c->p32.p,
+                                                        c->p32lo.p, c->boys32.p, c->M, part);
+    PCM_LAUNCHED(c);
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[k], c->stream));
+    return PCM_OK;
+}
+
+int esp_compute_mixed(pcm_ctx *c, double *dc)
+{
+    // single-class point blocks of at most MESP_NT * MESP_PPT points
+    std::vector<int> off{0}, bc;
+    for (int e = 0; e < c->ncls; ++e)
+        for (int k = c->h_cls_off[e]; k < c->h_cls_off[e + 1]; k += MESP_NT * MESP_PPT) {
+            off.push_back(std::min(c->h_cls_off[e + 1], k + MESP_NT * MESP_PPT));
+            bc.push_back(e);
+        }
+    const int nblk = (int)bc.size();
+    DBuf<int> blk, bcls;
+    PCM_TRY(blk.alloc(off.size()));
+    PCM_TRY(bcls.alloc(bc.size()));
+    PCM_CUDA(cudaMemcpyAsync(blk.p, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    PCM_CUDA(cudaMemcpyAsync(bcls.p, bc.data(), bc.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    int nseg[6], seglen[6], total = 0;
+    const int target = 152 * 8;
+    for (int k = 0; k < 6; ++k) {
+        PairClass &pc = c->cls[k];
+        nseg[k] = seglen[k] = 0;
+        if (pc.nesp == 0) continue;
+        const int maxseg = (pc.nesp + MESP_TP - 1) / MESP_TP;
+        int ns = std::max(1, std::min(maxseg, (target + nblk - 1) / nblk));
+        int sl = (pc.nesp + ns - 1) / ns;
+        sl = (sl + MESP_TP - 1) / MESP_TP * MESP_TP;
+        nseg[k] = (pc.nesp + sl - 1) / sl;
+        seglen[k] = sl;
+        total += nseg[k];
+    }
+    if (total == 0) {
+        PCM_CUDA(cudaMemsetAsync(dc, 0, c->M * sizeof(double), c->stream));
+        PCM_CUDA(cudaStreamSynchronize(c->stream));
+        return PCM_OK;
+    }
+    PCM_TRY(c->esp_part.alloc((size_t)total * c->M));
+    int base = 0;
+    for (int k = 0; k < 6; ++k) {
+        PairClass &pc = c->cls[k];
+        if (pc.nesp == 0) continue;
+        double *part = c->esp_part.p + (size_t)base * c->M;
+        switch (CLASS_L[k]) {
+        case 0: PCM_TRY(esp_mixed_launch<0>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
+        case 1: PCM_TRY(esp_mixed_launch<1>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
+        case 2: PCM_TRY(esp_mixed_launch<2>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
+        case 3: PCM_TRY(esp_mixed_launch<3>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
+        case 4: PCM_TRY(esp_mixed_launch<4>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
+        }
+        base += nseg[k];
+    }
+    esp_reduce_mixed_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
+    PCM_LAUNCHED(c);
+    PCM_CUDA(cudaStreamSynchronize(c->stream));  // blk, bcls are freed on return
+    return PCM_OK;
+}
+
+int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W)
+{
+    PairClass &pc = c->cls[k];
+    const int nb = (pc.npair + MF_NT - 1) / MF_NT;
+    dim3 grid(nb, nsplit);
+    switch (CLASS_L[k]) {
+#define PCM_FOCK_F32(LL)                                                                                           \
+    case LL:                                                                                                       \
+        fock_kernel_f32<LL><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit, c->p32.p,        \
+                                                            c->p32lo.p, dq, c->M, c->ncls, c->cls_off.p,           \
+                                                            c->cls_zeta.p, c->boys32.p, W);                        \
+        break;
+        PCM_FOCK_F32(0)
+        PCM_FOCK_F32(1)
+        PCM_FOCK_F32(2)
+        PCM_FOCK_F32(3)
+        PCM_FOCK_F32(4)
+#undef PCM_FOCK_F32
+    }
+    PCM_LAUNCHED(c);
+    return PCM_OK;
+}
+
+}  // namespace pcm

@@ -165,10 +165,14 @@ __global__ void pair_gather_kernel(int n, const int *__restrict__ idx, const int
     p[r] = c_p[g];
     pref[r] = c_pref[g];
     Q[r] = c_Q[g];
-    P32[0 * (size_t)n + r] = (float)c_P[3 * g + 0];
-    P32[1 * (size_t)n + r] = (float)c_P[3 * g + 1];
-    P32[2 * (size_t)n + r] = (float)c_P[3 * g + 2];
-    P32[3 * (size_t)n + r] = (float)c_p[g];
+    // FP32 hi/lo split of the centre: hi on a 2^-10 grid, so that differences of
+    // hi parts are exact in FP32
+    for (int d = 0; d < 3; ++d) {
+        const double v = c_P[3 * g + d];
+        const double h = rint(v * 1024.0) * (1.0 / 1024.0);
+        P32[(size_t)d * n + r] = (float)h;
+        P32[(size_t)(3 + d) * n + r] = (float)(v - h);
+    }
 }
 
 __global__ void sp_start_kernel(int nsp, const long long *__restrict__ sp_cand, const int *__restrict__ pos,
@@ -216,7 +220,7 @@ static int screen_class(pcm_ctx *c, PairClass &pc)
     PCM_TRY(pc.p.alloc(kept));
     PCM_TRY(pc.pref.alloc(kept));
     PCM_TRY(pc.Q.alloc(kept));
-    PCM_TRY(pc.Pxyz32.alloc(4 * (size_t)kept));
+    PCM_TRY(pc.Pxyz32.alloc(6 * (size_t)kept));
     if (kept > 0) {
         pair_gather_kernel<<<(kept + 127) / 128, 128, 0, c->stream>>>(
             kept, idx.p, c_sp.p, c_i.p, c_j.p, c_P.p, c_p.p, c_pref.p, c_Q.p, pc.sp.p, pc.ia.p, pc.ib.p, pc.Px.p,

@@ -330,6 +330,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     PCM_TRY(c->dinv.alloc(M));
     dinv_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, c->lda, c->A.p, c->dinv.p);
     PCM_LAUNCHED(c);
+    PCM_TRY(points_split(c));
     PCM_CUDA(cudaStreamSynchronize(c->stream));  // local scratch buffers are freed on return
     c->pc_ready = false;
     c->have_c = false;

@@ -74,7 +74,8 @@ __global__ void boys_table_kernel(const double *__restrict__ gx, const double *_
         s += 0.5 * h * ps;
     }
     tab64[(size_t)row * BOYS_STRIDE64 + m] = s;
-    if (m < BOYS_STRIDE32) tab32[(size_t)row * BOYS_STRIDE32 + m] = (float)s;
+    if (m < BOYS_LO32) tab32[(size_t)row * BOYS_STRIDE32 + m] = (float)s;
+    if (m < BOYS_STRIDE32 - BOYS_LO32) tab32[(size_t)row * BOYS_STRIDE32 + BOYS_LO32 + m] = (float)(s - (double)(float)s);
 }
 
 int boys_build_tables(pcm_ctx *c)

@@ -487,7 +487,7 @@ def test_gauss_law_compact_molecule():
     rng = np.random.default_rng(0)
     basis = workloads.make_basis(mol, {"O": [(0, 3, (2.0, 60.0)), (-1, 3, (1.5, 20.0))],
                                        "H": [(0, 3, (1.5, 30.0))]}, rng)
-    P = workloads.make_density(basis.nbf, 5, rng)
+    P = workloads.make_density(basis, mol.xyz, 5, rng)
     eb = oracle.ExpandedBasis(basis, mol.xyz)
     zs = 1e-5
     S = np.zeros((eb.nbf, eb.nbf))

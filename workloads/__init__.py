@@ -123,11 +123,110 @@ def make_basis(mol: Molecule, recipe: dict, rng, d_on_heavy: bool = False) -> Ba
                  np.array(ex, np.float64), np.array(co, np.float64))
 
 
-def make_density(nbf: int, nocc: int, rng) -> np.ndarray:
-    """P = 2 C C^T with C the Euclidean-orthonormalised columns of a seeded
-    Gaussian nbf x nocc matrix (QR)."""
-    G = rng.standard_normal((nbf, nocc))
-    C, _ = np.linalg.qr(G)
+def _cart(l):
+    return [(lx, ly, l - lx - ly) for lx in range(l, -1, -1) for ly in range(l - lx, -1, -1)]
+
+
+def _dfact(n):
+    r = 1.0
+    while n > 1:
+        r *= n
+        n -= 2
+    return r
+
+
+def overlap_matrix(basis: Basis, xyz: np.ndarray, block: int = 2048, cut: float = 1e-17) -> np.ndarray:
+    """Overlap S_{mu nu} of the basis functions (input preparation for the
+    density; not part of the solvation method).  Each Cartesian primitive
+    component is normalised to unit self-overlap and multiplied by the raw
+    contraction coefficient.  One-dimensional factors by the Obara-Saika
+    overlap recurrence s(i+1, j) = X_PA s(i, j) + (i s(i-1, j) + j s(i, j-1)) / 2p,
+    s(0, 0) = sqrt(pi / p) exp(-a b / p X_AB^2); primitive pairs whose
+    prefactor is below `cut` are skipped."""
+    # expanded primitives (sp -> s and p)
+    pl, pe, pc, pa, pbf = [], [], [], [], []
+    off = cpos = bf = 0
+    for s_ in range(basis.nshell):
+        l, n = int(basis.shell_l[s_]), int(basis.shell_nprim[s_])
+        e = basis.exps[off:off + n]
+        parts = [(0, basis.coefs[cpos:cpos + n]), (1, basis.coefs[cpos + n:cpos + 2 * n])] if l == -1 \
+            else [(l, basis.coefs[cpos:cpos + n])]
+        cpos += 2 * n if l == -1 else n
+        for ll, c in parts:
+            for k in range(n):
+                pl.append(ll); pe.append(e[k]); pa.append(basis.shell_atom[s_]); pbf.append(bf)
+                pc.append(c[k] * (2 * e[k] / np.pi) ** 0.75 * (4 * e[k]) ** (ll / 2) / np.sqrt(_dfact(2 * ll - 1)))
+            bf += len(_cart(ll))
+        off += n
+    pl = np.array(pl); pe = np.array(pe); pc = np.array(pc); pcen = xyz[np.array(pa)]; pbf = np.array(pbf)
+    S = np.zeros(bf * bf)
+
+    def s1d(la, lb, PA, PB, inv2p, s00):
+        t = {(0, 0): s00}
+        for i in range(la + 1):
+            for j in range(lb + 1):
+                if (i, j) in t:
+                    continue
+                if i > 0:
+                    v = PA * t[(i - 1, j)]
+                    if i > 1: v = v + (i - 1) * inv2p * t[(i - 2, j)]
+                    if j > 0: v = v + j * inv2p * t[(i - 1, j - 1)]
+                else:
+                    v = PB * t[(i, j - 1)]
+                    if j > 1: v = v + (j - 1) * inv2p * t[(i, j - 2)]
+                t[(i, j)] = v
+        return t
+
+    for la in range(3):
+        ia_all = np.nonzero(pl == la)[0]
+        for lb in range(3):
+            ib = np.nonzero(pl == lb)[0]
+            if len(ia_all) == 0 or len(ib) == 0:
+                continue
+            ca, cb = _cart(la), _cart(lb)
+            fa = np.array([np.sqrt(_dfact(2 * la - 1) / (_dfact(2 * x - 1) * _dfact(2 * y - 1) * _dfact(2 * z - 1)))
+                           for x, y, z in ca])
+            fb = np.array([np.sqrt(_dfact(2 * lb - 1) / (_dfact(2 * x - 1) * _dfact(2 * y - 1) * _dfact(2 * z - 1)))
+                           for x, y, z in cb])
+            for b0 in range(0, len(ia_all), block):
+                ia = ia_all[b0:b0 + block]
+                a = pe[ia][:, None]; b = pe[ib][None, :]
+                p = a + b
+                A = pcen[ia][:, None, :]; B = pcen[ib][None, :, :]
+                d2 = np.sum((A - B) ** 2, axis=-1)
+                K = np.exp(-a * b / p * d2)
+                w = pc[ia][:, None] * pc[ib][None, :] * K
+                m = np.abs(w) > cut
+                ii, jj = np.nonzero(m)
+                if len(ii) == 0:
+                    continue
+                a1 = a[ii, 0]; b1 = b[0, jj]; p1 = a1 + b1; w1 = w[ii, jj]
+                P = (a1[:, None] * A[ii, 0, :] + b1[:, None] * B[0, jj, :]) / p1[:, None]
+                PA = P - A[ii, 0, :]; PB = P - B[0, jj, :]
+                inv2p = 0.5 / p1
+                s00 = np.sqrt(np.pi / p1)
+                tx = s1d(la, lb, PA[:, 0], PB[:, 0], inv2p, s00)
+                ty = s1d(la, lb, PA[:, 1], PB[:, 1], inv2p, s00)
+                tz = s1d(la, lb, PA[:, 2], PB[:, 2], inv2p, s00)
+                rows = pbf[ia][ii]; cols = pbf[ib][jj]
+                for u, (ax, ay, az) in enumerate(ca):
+                    for v, (bx, by, bz) in enumerate(cb):
+                        val = w1 * fa[u] * fb[v] * tx[(ax, bx)] * ty[(ay, by)] * tz[(az, bz)]
+                        S += np.bincount((rows + u) * bf + cols + v, weights=val, minlength=bf * bf)
+    S = S.reshape(bf, bf)
+    return 0.5 * (S + S.T)
+
+
+def make_density(basis: Basis, xyz: np.ndarray, nocc: int, rng) -> np.ndarray:
+    """P = 2 C C^T for nocc seeded occupied orbitals that are orthonormal in the
+    overlap metric (C^T S C = I, so tr(P S) = 2 nocc): the columns of a seeded
+    Gaussian nbf x nocc matrix G, symmetrically orthonormalised,
+    C = G (G^T S G)^(-1/2)."""
+    S = overlap_matrix(basis, xyz)
+    nocc = min(nocc, basis.nbf)
+    G = rng.standard_normal((basis.nbf, nocc))
+    e, V = np.linalg.eigh(G.T @ S @ G)
+    C = G @ (V / np.sqrt(e)) @ V.T
     P = 2.0 * C @ C.T
     return 0.5 * (P + P.T)
 
@@ -141,7 +240,7 @@ def water(seed: int = 150507851 + 0) -> Workload:
     recipe = {"O": [(0, 3, (0.1, 130.0)), (-1, 3, (0.1, 130.0))],
               "H": [(0, 3, (0.1, 130.0))]}
     basis = make_basis(mol, recipe, rng)
-    P = make_density(basis.nbf, 5, rng)
+    P = make_density(basis, mol.xyz, 5, rng)
     return Workload("water", mol, basis, P, 5, seed)
 
 
@@ -193,7 +292,7 @@ def cluster(natom: int, seed: int, globule_radius_A: float, d_shells: bool = Fal
     basis = make_basis(mol, _SHELLS_631G, rng, d_on_heavy=d_shells)
     nocc = 2 * natom if nocc is None else nocc
     nocc = min(nocc, basis.nbf)
-    P = make_density(basis.nbf, nocc, rng)
+    P = make_density(basis, mol.xyz, nocc, rng)
     return Workload(name, mol, basis, P, nocc, seed)
 
 
