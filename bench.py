@@ -204,17 +204,37 @@ def _timed_steps(pcm, w, precision, args, dev, stream, flush, delta, steps, warm
     Pd = torch.tensor(w.P, dtype=torch.float64, device=dev)
     bufs = {}
 
-    def step():
+    phase = {k: 0.0 for k in ("surface", "basis", "esp", "solve", "fock", "energy")}
+
+    def mark(ev):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        ev.append(e)
+
+    def step(timed=False):
+        ev = []
+        mark(ev)
         M = ctx.build_surface(w.mol.xyz, w.mol.Z, w.mol.radius, 110)
+        mark(ev)
         nbf = ctx.set_basis(b.shell_atom, b.shell_l, b.shell_nprim, b.exps, b.coefs)
+        mark(ev)
         if "c" not in bufs or bufs["c"].numel() != M:
             bufs["c"] = torch.empty(M, dtype=torch.float64, device=dev)
             bufs["q"] = torch.empty(M, dtype=torch.float64, device=dev)
             bufs["dF"] = torch.empty((nbf, nbf), dtype=torch.float64, device=dev)
         ctx.esp(Pd, out=bufs["c"])
+        mark(ev)
         q, st = ctx.solve(delta=delta, q=bufs["q"])
+        mark(ev)
         ctx.fock(q, out=bufs["dF"])
-        return ctx.energy(q), st
+        mark(ev)
+        E = ctx.energy(q)
+        mark(ev)
+        if timed:
+            ev[-1].synchronize()
+            for k, a, b_ in zip(phase, ev[:-1], ev[1:]):
+                phase[k] += a.elapsed_time(b_)
+        return E, st
 
     for _ in range(warmup):
         step()
@@ -227,7 +247,7 @@ def _timed_steps(pcm, w, precision, args, dev, stream, flush, delta, steps, warm
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        E, st = step()
+        E, st = step(timed=True)
         e1.record(stream)
         e1.synchronize()
         out["times"].append(e0.elapsed_time(e1))
@@ -239,6 +259,7 @@ def _timed_steps(pcm, w, precision, args, dev, stream, flush, delta, steps, warm
         out["esp_cls"] += np.array(s["ms_esp_class"])
         out["fock_cls"] += np.array(s["ms_fock_class"])
     s = ctx.stats()
+    out["phase_ms"] = {k: v / max(1, steps) for k, v in phase.items()}
     out["launches"] = s["launches"] - launches0
     out["stats"] = s
     out["ctx"] = ctx
@@ -350,6 +371,7 @@ def run_ours(args):
             "esp_kernel_ms": float(main["esp_cls"].sum() / args.steps),
             "fock_kernel_ms": float(main["fock_cls"].sum() / args.steps),
             "integrals_per_step": main["ints"] / args.steps, "pairs_kept": s["pairs_kept"],
+            "phase_ms": main["phase_ms"],
             "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": main["launches"],
             "cpu_baseline": cpu,
         }
@@ -360,7 +382,7 @@ def run_ours(args):
                             "pcg_solve_ms": statistics.mean(other["solve_ms"]),
                             "esp_kernel_ms": float(other["esp_cls"].sum() / n),
                             "fock_kernel_ms": float(other["fock_cls"].sum() / n),
-                            "energy_err_Eh": abs(other["E"][-1] - E_ref),
+                            "energy_err_Eh": abs(other["E"][-1] - E_ref), "phase_ms": other["phase_ms"],
                             "roofline": _dominant(other, "fp64", n)}
             line["speedup_vs_fp64"] = line["fp64"]["ms_per_step"] / line["ms_per_step"]
         print(json.dumps(line))

@@ -239,7 +239,7 @@ int pcm_get_surface(pcm_ctx *c, double *xyzzs, int *index, int flags)
     const int M = c->M;
     if (xyzzs) {
         double *dst = xyzzs;
-        DBuf<double> tmp;
+        DBuf<double> &tmp = c->sd[2];
         if (!(flags & PCM_PTR_DEVICE)) {
             PCM_TRY(tmp.alloc(5 * (size_t)M));
             dst = tmp.p;
@@ -407,7 +407,7 @@ int pcm_energy(pcm_ctx *c, const double *q, const double *cv, double *E, int fla
     }
     DeviceGuard g(c->device);
     const double *dq, *dcv;
-    DBuf<double> stq, stc;
+    DBuf<double> &stq = c->sd[3], &stc = c->sd[4];
     PCM_TRY(to_device(c, q, c->M, stq, &dq, flags));
     if (cv) PCM_TRY(to_device(c, cv, c->M, stc, &dcv, flags));
     else dcv = c->c_last.p;

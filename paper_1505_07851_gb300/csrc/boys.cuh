@@ -59,9 +59,12 @@ __device__ __forceinline__ void boys_eval(float T, const float *__restrict__ tab
     // both bias the result in the same direction for every interaction
     static_assert(MM + 4 < BOYS_LO32 && MM <= 5, "Boys table too narrow");
     if (T < (float)BOYS_TMAX) {
-        const int i = min(max(__float2int_rn(T * (float)BOYS_INV_DT), 0), BOYS_NROW - 1);
-        const float d = fmaf((float)i, -(float)BOYS_DT, T);
-        const float *row = tab + (size_t)i * BOYS_STRIDE32;
+        // nearest row without float<->int conversions: adding 1.5 * 2^23 leaves
+        // round(T * 32) in the low mantissa bits (0 <= T * 32 < 2^22)
+        const float t = fmaf(T, (float)BOYS_INV_DT, 12582912.0f);
+        const int i = __float_as_int(t) - 0x4B400000;
+        const float d = fmaf(t - 12582912.0f, -(float)BOYS_DT, T);
+        const float *row = tab + i * BOYS_STRIDE32;
         float r[MM + 5], lo[MM + 1];
 #pragma unroll
         for (int k = 0; k < MM + 5; ++k) r[k] = __ldg(row + k);

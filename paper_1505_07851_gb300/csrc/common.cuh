@@ -126,6 +126,61 @@ __device__ inline void hermite_E1D(int la, int lb, double PA, double PB, double 
     }
 }
 
+// Compile-time Cartesian exponents (l <= 3) in the order above, so that fully
+// unrolled component loops index register arrays with constants.
+__host__ __device__ constexpr int cart_e(int l, int c, int axis)
+{
+    // rows: x^l, x^(l-1) y, x^(l-1) z, ..., z^l
+    int n = 0;
+    for (int a = l; a >= 0; --a)
+        for (int b = l - a; b >= 0; --b) {
+            if (n == c) return axis == 0 ? a : (axis == 1 ? b : l - a - b);
+            ++n;
+        }
+    return 0;
+}
+static_assert(cart_e(2, 1, 0) == 1 && cart_e(2, 1, 1) == 1 && cart_e(2, 4, 2) == 1 && cart_e(2, 5, 2) == 2, "cart_e");
+
+// Hermite expansion coefficients of one direction, sized for (LA, LB) and
+// fully unrolled (registers): same recurrences as hermite_E1D.
+template <int LA, int LB>
+struct E1T {
+    double e[LA + 1][LB + 1][LA + LB + 1];
+};
+
+template <int LA, int LB>
+__device__ __forceinline__ void hermite_E1T(double PA, double PB, double inv2p, E1T<LA, LB> &E)
+{
+#pragma unroll
+    for (int i = 0; i <= LA; ++i)
+#pragma unroll
+        for (int j = 0; j <= LB; ++j)
+#pragma unroll
+            for (int t = 0; t <= LA + LB; ++t) E.e[i][j][t] = 0.0;
+    E.e[0][0][0] = 1.0;
+#pragma unroll
+    for (int i = 0; i <= LA; ++i) {
+        if (i > 0) {
+#pragma unroll
+            for (int t = 0; t <= i; ++t) {
+                double v = PA * E.e[i - 1][0][t];
+                if (t > 0) v += inv2p * E.e[i - 1][0][t - 1];
+                if (t + 1 <= i - 1) v += (t + 1) * E.e[i - 1][0][t + 1];
+                E.e[i][0][t] = v;
+            }
+        }
+#pragma unroll
+        for (int j = 1; j <= LB; ++j)
+#pragma unroll
+            for (int t = 0; t <= i + j; ++t) {
+                double v = PB * E.e[i][j - 1][t];
+                if (t > 0) v += inv2p * E.e[i][j - 1][t - 1];
+                if (t + 1 <= i + j - 1) v += (t + 1) * E.e[i][j - 1][t + 1];
+                E.e[i][j][t] = v;
+            }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Reductions
 // ---------------------------------------------------------------------------

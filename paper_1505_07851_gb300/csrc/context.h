@@ -167,6 +167,12 @@ struct pcm_ctx {
     pcm::DBuf<int> idx32, scan32;
     pcm::DBuf<long long> scan64;
 
+    // grow-only scratch reused by successive calls, so that steady-state calls
+    // make no cudaMalloc/cudaFree (cudaFree synchronises the device)
+    pcm::DBuf<double> sd[8];
+    pcm::DBuf<int> si[8];
+    pcm::DBuf<unsigned char> su8[2];
+
     pcm_stats stats;
     cudaEvent_t ev_a[13], ev_b[13];         // timing events: 0-5 ESP classes, 6-11 Fock classes, 12 solve
     bool have_events = false;

@@ -83,34 +83,33 @@ __global__ void esp_coef_kernel(int nesp, const int *__restrict__ list, const in
     const double p = pp[r];
     const double P[3] = {Px[r], Py[r], Pz[r]};
     const double *RA = xyz + 3 * sh_atom[A], *RB = xyz + 3 * sh_atom[B];
-    E1D Ex, Ey, Ez;
+    E1T<LA, LB> Ex, Ey, Ez;
     const double inv2p = 0.5 / p;
-    hermite_E1D(LA, LB, P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
-    hermite_E1D(LA, LB, P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
-    hermite_E1D(LA, LB, P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
+    hermite_E1T<LA, LB>(P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
+    hermite_E1T<LA, LB>(P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
+    hermite_E1T<LA, LB>(P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
     const double cc = cnorm[sh_off[A] + i1] * cnorm[sh_off[B] + i2];
     const int fa = sh_bf[A], fb = sh_bf[B];
     double D[NH];
 #pragma unroll
     for (int h = 0; h < NH; ++h) D[h] = 0.0;
+#pragma unroll
     for (int a = 0; a < ncart(LA); ++a) {
-        int ax, ay, az;
-        cart_xyz(LA, a, ax, ay, az);
+        const int ax = cart_e(LA, a, 0), ay = cart_e(LA, a, 1), az = cart_e(LA, a, 2);
+#pragma unroll
         for (int b = 0; b < ncart(LB); ++b) {
-            int bx, by, bz;
-            cart_xyz(LB, b, bx, by, bz);
+            const int bx = cart_e(LB, b, 0), by = cart_e(LB, b, 1), bz = cart_e(LB, b, 2);
             double w = Pm[(size_t)(fa + a) * nbf + fb + b];
             if (mirror) w += Pm[(size_t)(fb + b) * nbf + fa + a];
             w *= cc * comp_factor_i(LA, a) * comp_factor_i(LB, b);
+            // E_t vanishes for t > i + j: the full loops add exact zeros there
 #pragma unroll
             for (int t = 0; t <= L; ++t)
 #pragma unroll
                 for (int u = 0; u <= L - t; ++u)
 #pragma unroll
-                    for (int v = 0; v <= L - t - u; ++v) {
-                        if (t > ax + bx || u > ay + by || v > az + bz) continue;
+                    for (int v = 0; v <= L - t - u; ++v)
                         D[hidx(t, u, v)] += w * Ex.e[ax][bx][t] * Ey.e[ay][by][u] * Ez.e[az][bz][v];
-                    }
         }
     }
     const double scale = -pref[r];
@@ -354,30 +353,28 @@ __global__ void fock_epilogue_kernel(int nsp, int npair, int nsplit, const int *
         }
         const double p = pp[r];
         const double P[3] = {Px[r], Py[r], Pz[r]};
-        E1D Ex, Ey, Ez;
+        E1T<LA, LB> Ex, Ey, Ez;
         const double inv2p = 0.5 / p;
-        hermite_E1D(LA, LB, P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
-        hermite_E1D(LA, LB, P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
-        hermite_E1D(LA, LB, P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
+        hermite_E1T<LA, LB>(P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
+        hermite_E1T<LA, LB>(P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
+        hermite_E1T<LA, LB>(P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
         const int i1 = ia[r], i2 = ib[r];
         const double cc = -pref[r] * cnorm[sh_off[A] + i1] * cnorm[sh_off[B] + i2];
         const bool mirror = (A == B) && (i1 != i2);
+#pragma unroll
         for (int a = 0; a < NA; ++a) {
-            int ax, ay, az;
-            cart_xyz(LA, a, ax, ay, az);
+            const int ax = cart_e(LA, a, 0), ay = cart_e(LA, a, 1), az = cart_e(LA, a, 2);
+#pragma unroll
             for (int b = 0; b < NB; ++b) {
-                int bx, by, bz;
-                cart_xyz(LB, b, bx, by, bz);
+                const int bx = cart_e(LB, b, 0), by = cart_e(LB, b, 1), bz = cart_e(LB, b, 2);
                 double v = 0.0;
 #pragma unroll
                 for (int t = 0; t <= L; ++t)
 #pragma unroll
                     for (int u = 0; u <= L - t; ++u)
 #pragma unroll
-                        for (int vv = 0; vv <= L - t - u; ++vv) {
-                            if (t > ax + bx || u > ay + by || vv > az + bz) continue;
+                        for (int vv = 0; vv <= L - t - u; ++vv)
                             v += Ex.e[ax][bx][t] * Ey.e[ay][by][u] * Ez.e[az][bz][vv] * w[hidx(t, u, vv)];
-                        }
                 v *= cc * comp_factor_i(LA, a) * comp_factor_i(LB, b);
                 G[a * NB + b] += v;
                 if (mirror) G[b * NB + a] += v;
@@ -385,7 +382,9 @@ __global__ void fock_epilogue_kernel(int nsp, int npair, int nsplit, const int *
         }
     }
     const int fa = sh_bf[A], fb = sh_bf[B];
+#pragma unroll
     for (int a = 0; a < NA; ++a)
+#pragma unroll
         for (int b = 0; b < NB; ++b) {
             dF[(size_t)(fa + a) * nbf + fb + b] = G[a * NB + b];
             dF[(size_t)(fb + b) * nbf + fa + a] = G[a * NB + b];
@@ -498,7 +497,7 @@ int esp_compute(pcm_ctx *c, const double *dP, double *dc)
     std::vector<int> off;
     esp_blocks(c, off);
     const int nblk = (int)off.size() - 1;
-    DBuf<int> blk;
+    DBuf<int> &blk = c->si[5];
     PCM_TRY(blk.alloc(off.size()));
     PCM_CUDA(cudaMemcpyAsync(blk.p, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
 
@@ -546,7 +545,7 @@ int esp_compute(pcm_ctx *c, const double *dP, double *dc)
     base += nseg[5];
     esp_reduce_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
     PCM_LAUNCHED(c);
-    PCM_CUDA(cudaStreamSynchronize(c->stream));  // blk is freed on return
+    PCM_CUDA(cudaStreamSynchronize(c->stream));  // the class timers are read next
     return esp_class_stats(c);
 }
 

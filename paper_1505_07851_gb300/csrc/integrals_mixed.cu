@@ -96,9 +96,12 @@ __global__ void esp_mixed_prep_kernel(int nesp, int ncls, const double *__restri
 }
 
 constexpr int MESP_NT = 128;
-constexpr int MESP_PPT = 2;
 constexpr int MESP_TP = 32;
+// points per thread: more independent work for the light classes
+template <int L> struct EspPPT { static constexpr int value = L <= 1 ? 4 : 2; };
 
+// Per tile of TP pairs, shared memory holds per pair float4 (xh, yh, zh, rho_hi),
+// float4 (xl, yl, zl, rho_lo), rho_lo/rho_hi and NH float2 (hi, lo) of U D_h.
 template <int L>
 __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int seglen, const float *__restrict__ eX,
                                                           const float *__restrict__ eC, const int *__restrict__ blk_off,
@@ -108,64 +111,68 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int seglen, 
 {
     constexpr int NH = nherm(L);
     constexpr int F = 3 + 2 * NH;
-    __shared__ float sX[6][MESP_TP];
-    __shared__ float sC[F][MESP_TP];
+    constexpr int PPT = EspPPT<L>::value;
+    __shared__ float4 sA[MESP_TP], sB[MESP_TP];
+    __shared__ float sR[MESP_TP];
+    __shared__ float2 sD[NH][MESP_TP];
     const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
     const float *C = eC + (size_t)blk_cls[blockIdx.x] * F * nesp;
     const int j0 = blockIdx.y * seglen;
     const int j1 = min(nesp, j0 + seglen);
 
-    float xh[MESP_PPT], yh[MESP_PPT], zh[MESP_PPT], xl[MESP_PPT], yl[MESP_PPT], zl[MESP_PPT];
-    double acc[MESP_PPT];
-    bool on[MESP_PPT];
+    float xh[PPT], yh[PPT], zh[PPT], xl[PPT], yl[PPT], zl[PPT];
+    // Kahan-compensated FP32 sums over the whole segment: adding a small term
+    // to a larger running sum in plain FP32 drops its bits below half an ulp,
+    // always towards a smaller magnitude for same-sign terms (a bias, not noise)
+    float a32[PPT], k32[PPT];
 #pragma unroll
-    for (int q = 0; q < MESP_PPT; ++q) {
-        const int k = k0 + threadIdx.x + q * MESP_NT;
-        on[q] = k < k1;
-        const int kk = on[q] ? k : k0;
-        xh[q] = ph[kk];
-        yh[q] = ph[(size_t)M + kk];
-        zh[q] = ph[2 * (size_t)M + kk];
-        xl[q] = pl[kk];
-        yl[q] = pl[(size_t)M + kk];
-        zl[q] = pl[2 * (size_t)M + kk];
-        acc[q] = 0.0;
+    for (int q = 0; q < PPT; ++q) {
+        const int k = min(k0 + (int)threadIdx.x + q * MESP_NT, k1 - 1);
+        xh[q] = ph[k];
+        yh[q] = ph[(size_t)M + k];
+        zh[q] = ph[2 * (size_t)M + k];
+        xl[q] = pl[k];
+        yl[q] = pl[(size_t)M + k];
+        zl[q] = pl[2 * (size_t)M + k];
+        a32[q] = k32[q] = 0.f;
     }
     for (int jt = j0; jt < j1; jt += MESP_TP) {
         const int nt = min(MESP_TP, j1 - jt);
         __syncthreads();
-        for (int t = threadIdx.x; t < 6 * MESP_TP; t += MESP_NT) {
-            const int f = t / MESP_TP, jj = t % MESP_TP;
-            sX[f][jj] = jj < nt ? eX[(size_t)f * nesp + jt + jj] : 0.f;
+        for (int jj = threadIdx.x; jj < MESP_TP; jj += MESP_NT) {
+            const bool v = jj < nt;
+            const size_t j = jt + jj;
+            sA[jj] = v ? make_float4(eX[j], eX[(size_t)nesp + j], eX[2 * (size_t)nesp + j], C[j])
+                       : make_float4(0.f, 0.f, 0.f, 1.f);
+            sB[jj] = v ? make_float4(eX[3 * (size_t)nesp + j], eX[4 * (size_t)nesp + j], eX[5 * (size_t)nesp + j],
+                                     C[(size_t)nesp + j])
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            sR[jj] = v ? C[2 * (size_t)nesp + j] : 0.f;
         }
-        for (int t = threadIdx.x; t < F * MESP_TP; t += MESP_NT) {
-            const int f = t / MESP_TP, jj = t % MESP_TP;
-            sC[f][jj] = jj < nt ? C[(size_t)f * nesp + jt + jj] : (f == 0 ? 1.f : 0.f);
+        for (int t = threadIdx.x; t < NH * MESP_TP; t += MESP_NT) {
+            const int h = t / MESP_TP, jj = t % MESP_TP;
+            sD[h][jj] = jj < nt ? make_float2(C[(size_t)(3 + h) * nesp + jt + jj], C[(size_t)(3 + NH + h) * nesp + jt + jj])
+                                : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        // Kahan-compensated FP32 sums: adding a small term to a larger running
-        // sum in plain FP32 drops its bits below half an ulp, always towards
-        // a smaller magnitude for same-sign terms (a bias, not noise)
-        float a32[MESP_PPT], k32[MESP_PPT];
-#pragma unroll
-        for (int q = 0; q < MESP_PPT; ++q) a32[q] = k32[q] = 0.f;
         for (int jj = 0; jj < nt; ++jj) {
-            const float rh = sC[0][jj], rl = sC[1][jj];
+            const float4 A = sA[jj], B = sB[jj];
 #pragma unroll
-            for (int q = 0; q < MESP_PPT; ++q) {
-                const float X = (sX[0][jj] - xh[q]) + (sX[3][jj] - xl[q]);
-                const float Y = (sX[1][jj] - yh[q]) + (sX[4][jj] - yl[q]);
-                const float Z = (sX[2][jj] - zh[q]) + (sX[5][jj] - zl[q]);
+            for (int q = 0; q < PPT; ++q) {
+                const float X = (A.x - xh[q]) + (B.x - xl[q]);
+                const float Y = (A.y - yh[q]) + (B.y - yl[q]);
+                const float Z = (A.z - zh[q]) + (B.z - zl[q]);
                 const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
-                const float T = fmaf(rh, R2, rl * R2);
+                const float T = fmaf(A.w, R2, B.w * R2);
                 float Fb[L + 1];
                 boys_eval<L>(T, boys, Fb);
                 float dot;
                 if constexpr (L == 0) {
-                    dot = fmaf(sC[3][jj], Fb[0], sC[4][jj] * Fb[0]);
+                    const float2 D = sD[0][jj];
+                    dot = fmaf(D.x, Fb[0], D.y * Fb[0]);
                 } else {
-                    const float dr = sC[2][jj];
-                    const float m2r = -2.f * rh;
+                    const float dr = sR[jj];
+                    const float m2r = -2.f * A.w;
                     float Rn[L + 1];
                     float f = 1.f;
 #pragma unroll
@@ -178,7 +185,10 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int seglen, 
                     hermite_R<L, float>(X, Y, Z, Rn, R);
                     dot = 0.f;
 #pragma unroll
-                    for (int h = 0; h < NH; ++h) dot = fmaf(sC[3 + h][jj], R[h], fmaf(sC[3 + NH + h][jj], R[h], dot));
+                    for (int h = 0; h < NH; ++h) {
+                        const float2 D = sD[h][jj];
+                        dot = fmaf(D.x, R[h], fmaf(D.y, R[h], dot));
+                    }
                 }
                 const float y = dot - k32[q];
                 const float t = a32[q] + y;
@@ -186,13 +196,11 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int seglen, 
                 a32[q] = t;
             }
         }
-#pragma unroll
-        for (int q = 0; q < MESP_PPT; ++q) acc[q] += (double)a32[q] - (double)k32[q];
     }
 #pragma unroll
-    for (int q = 0; q < MESP_PPT; ++q) {
+    for (int q = 0; q < PPT; ++q) {
         const int k = k0 + threadIdx.x + q * MESP_NT;
-        if (on[q]) part[(size_t)blockIdx.y * M + k] = acc[q];
+        if (k < k1) part[(size_t)blockIdx.y * M + k] = (double)a32[q] - (double)k32[q];
     }
 }
 
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double
                                                          const float *__restrict__ boys, double *__restrict__ W)
 {
     constexpr int NH = nherm(L);
-    __shared__ float sxh[MF_TQ], syh[MF_TQ], szh[MF_TQ], sxl[MF_TQ], syl[MF_TQ], szl[MF_TQ], sq[MF_TQ];
+    __shared__ float4 sH[MF_TQ], sL[MF_TQ];  // (xh, yh, zh, q) and (xl, yl, zl, 0) per point
     const int r = blockIdx.x * MF_NT + threadIdx.x;
     const bool active = r < npair;
     const int rr = active ? r : 0;
@@ -241,31 +249,27 @@ __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double
             const int nt = min(MF_TQ, b - t0);
             __syncthreads();
             for (int t = threadIdx.x; t < nt; t += MF_NT) {
-                sxh[t] = ph[t0 + t];
-                syh[t] = ph[(size_t)M + t0 + t];
-                szh[t] = ph[2 * (size_t)M + t0 + t];
-                sxl[t] = pl[t0 + t];
-                syl[t] = pl[(size_t)M + t0 + t];
-                szl[t] = pl[2 * (size_t)M + t0 + t];
-                sq[t] = (float)q[t0 + t];
+                sH[t] = make_float4(ph[t0 + t], ph[(size_t)M + t0 + t], ph[2 * (size_t)M + t0 + t], (float)q[t0 + t]);
+                sL[t] = make_float4(pl[t0 + t], pl[(size_t)M + t0 + t], pl[2 * (size_t)M + t0 + t], 0.f);
             }
             __syncthreads();
             float w32[NH];
 #pragma unroll
             for (int h = 0; h < NH; ++h) w32[h] = 0.f;
             for (int kk = 0; kk < nt; ++kk) {
-                const float X = (Pxh - sxh[kk]) + (Pxl - sxl[kk]);
-                const float Y = (Pyh - syh[kk]) + (Pyl - syl[kk]);
-                const float Z = (Pzh - szh[kk]) + (Pzl - szl[kk]);
+                const float4 H = sH[kk], Lo = sL[kk];
+                const float X = (Pxh - H.x) + (Pxl - Lo.x);
+                const float Y = (Pyh - H.y) + (Pyl - Lo.y);
+                const float Z = (Pzh - H.z) + (Pzl - Lo.z);
                 const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
                 const float T = fmaf(rh, R2, rl * R2);
                 float Fb[L + 1];
                 boys_eval<L>(T, boys, Fb);
                 if constexpr (L == 0) {
-                    w32[0] = fmaf(sq[kk], Fb[0], w32[0]);
+                    w32[0] = fmaf(H.w, Fb[0], w32[0]);
                 } else {
                     float Rn[L + 1];
-                    float f = sq[kk];
+                    float f = H.w;
 #pragma unroll
                     for (int n = 0; n <= L; ++n) {
                         const float v = f * Fb[n];
@@ -325,24 +329,32 @@ static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, co
 
 int esp_compute_mixed(pcm_ctx *c, double *dc)
 {
-    // single-class point blocks of at most MESP_NT * MESP_PPT points
-    std::vector<int> off{0}, bc;
-    for (int e = 0; e < c->ncls; ++e)
-        for (int k = c->h_cls_off[e]; k < c->h_cls_off[e + 1]; k += MESP_NT * MESP_PPT) {
-            off.push_back(std::min(c->h_cls_off[e + 1], k + MESP_NT * MESP_PPT));
-            bc.push_back(e);
-        }
-    const int nblk = (int)bc.size();
-    DBuf<int> blk, bcls;
-    PCM_TRY(blk.alloc(off.size()));
-    PCM_TRY(bcls.alloc(bc.size()));
-    PCM_CUDA(cudaMemcpyAsync(blk.p, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    PCM_CUDA(cudaMemcpyAsync(bcls.p, bc.data(), bc.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    // single-class point blocks of at most MESP_NT * PPT points (two layouts: PPT 4 and 2)
+    std::vector<int> off[2], bc[2];
+    for (int v = 0; v < 2; ++v) {
+        const int cap = MESP_NT * (v == 0 ? 4 : 2);
+        off[v].push_back(0);
+        for (int e = 0; e < c->ncls; ++e)
+            for (int k = c->h_cls_off[e]; k < c->h_cls_off[e + 1]; k += cap) {
+                off[v].push_back(std::min(c->h_cls_off[e + 1], k + cap));
+                bc[v].push_back(e);
+            }
+    }
+    DBuf<int> *blk = &c->si[4], *bcls = &c->si[6];  // blk[0..1], bcls[0..1]
+    for (int v = 0; v < 2; ++v) {
+        PCM_TRY(blk[v].alloc(off[v].size()));
+        PCM_TRY(bcls[v].alloc(bc[v].size()));
+        PCM_CUDA(cudaMemcpyAsync(blk[v].p, off[v].data(), off[v].size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 c->stream));
+        PCM_CUDA(cudaMemcpyAsync(bcls[v].p, bc[v].data(), bc[v].size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 c->stream));
+    }
     int nseg[6], seglen[6], total = 0;
     const int target = 152 * 8;
     for (int k = 0; k < 6; ++k) {
         PairClass &pc = c->cls[k];
         nseg[k] = seglen[k] = 0;
+        const int nblk = (int)bc[CLASS_L[k] <= 1 ? 0 : 1].size();
         if (pc.nesp == 0) continue;
         const int maxseg = (pc.nesp + MESP_TP - 1) / MESP_TP;
         int ns = std::max(1, std::min(maxseg, (target + nblk - 1) / nblk));
@@ -363,18 +375,20 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
         PairClass &pc = c->cls[k];
         if (pc.nesp == 0) continue;
         double *part = c->esp_part.p + (size_t)base * c->M;
+        const int v = CLASS_L[k] <= 1 ? 0 : 1;
+        const int nblk = (int)bc[v].size();
         switch (CLASS_L[k]) {
-        case 0: PCM_TRY(esp_mixed_launch<0>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
-        case 1: PCM_TRY(esp_mixed_launch<1>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
-        case 2: PCM_TRY(esp_mixed_launch<2>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
-        case 3: PCM_TRY(esp_mixed_launch<3>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
-        case 4: PCM_TRY(esp_mixed_launch<4>(c, pc, k, blk.p, bcls.p, nblk, nseg[k], seglen[k], part)); break;
+        case 0: PCM_TRY(esp_mixed_launch<0>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
+        case 1: PCM_TRY(esp_mixed_launch<1>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
+        case 2: PCM_TRY(esp_mixed_launch<2>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
+        case 3: PCM_TRY(esp_mixed_launch<3>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
+        case 4: PCM_TRY(esp_mixed_launch<4>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
         }
         base += nseg[k];
     }
     esp_reduce_mixed_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
     PCM_LAUNCHED(c);
-    PCM_CUDA(cudaStreamSynchronize(c->stream));  // blk, bcls are freed on return
+    PCM_CUDA(cudaStreamSynchronize(c->stream));  // the class timers are read next
     return PCM_OK;
 }
 

@@ -98,38 +98,49 @@ __global__ void pair_screen_kernel(long long ncand, int nsp, const long long *__
     //             sum_{tuv,t'u'v'} E_tuv E_t'u'v' (-1)^(t'+u'+v') R_{t+t',u+u',v+v'}(p/2, 0),
     // R_{TUV}(alpha, 0) = (-2 alpha)^((T+U+V)/2) (T-1)!!(U-1)!!(V-1)!! / (T+U+V+1)
     // for even T, U, V and 0 otherwise.
-    E1D Ex, Ey, Ez;
+    E1T<LA, LB> Ex, Ey, Ez;
     const double inv2p = 0.5 / p;
-    hermite_E1D(LA, LB, P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
-    hermite_E1D(LA, LB, P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
-    hermite_E1D(LA, LB, P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
-    const double m2a = -p;  // -2 alpha with alpha = p / 2
+    hermite_E1T<LA, LB>(P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
+    hermite_E1T<LA, LB>(P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
+    hermite_E1T<LA, LB>(P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
+    constexpr int LL = LA + LB;
+    // (-2 alpha)^n with alpha = p / 2
+    double pw[LL + 1];
+    pw[0] = 1.0;
+#pragma unroll
+    for (int n = 1; n <= LL; ++n) pw[n] = pw[n - 1] * (-p);
     double qmax = 0.0;
+#pragma unroll
     for (int ca = 0; ca < ncart(LA); ++ca)
+#pragma unroll
         for (int cb = 0; cb < ncart(LB); ++cb) {
-            int ax, ay, az, bx, by, bz;
-            cart_xyz(LA, ca, ax, ay, az);
-            cart_xyz(LB, cb, bx, by, bz);
-            double Gx[7] = {0, 0, 0, 0, 0, 0, 0}, Gy[7] = {0, 0, 0, 0, 0, 0, 0}, Gz[7] = {0, 0, 0, 0, 0, 0, 0};
-            for (int t = 0; t <= ax + bx; ++t)
-                for (int t2 = 0; t2 <= ax + bx; ++t2)
-                    Gx[t + t2] += Ex.e[ax][bx][t] * Ex.e[ax][bx][t2] * ((t2 & 1) ? -1.0 : 1.0);
-            for (int t = 0; t <= ay + by; ++t)
-                for (int t2 = 0; t2 <= ay + by; ++t2)
-                    Gy[t + t2] += Ey.e[ay][by][t] * Ey.e[ay][by][t2] * ((t2 & 1) ? -1.0 : 1.0);
-            for (int t = 0; t <= az + bz; ++t)
-                for (int t2 = 0; t2 <= az + bz; ++t2)
-                    Gz[t + t2] += Ez.e[az][bz][t] * Ez.e[az][bz][t2] * ((t2 & 1) ? -1.0 : 1.0);
+            const int ax = cart_e(LA, ca, 0), ay = cart_e(LA, ca, 1), az = cart_e(LA, ca, 2);
+            const int bx = cart_e(LB, cb, 0), by = cart_e(LB, cb, 1), bz = cart_e(LB, cb, 2);
+            double Gx[2 * LL + 1], Gy[2 * LL + 1], Gz[2 * LL + 1];
+#pragma unroll
+            for (int t = 0; t <= 2 * LL; ++t) Gx[t] = Gy[t] = Gz[t] = 0.0;
+            // E_t vanishes for t > i + j, so the full loops add exact zeros there
+#pragma unroll
+            for (int t = 0; t <= LL; ++t)
+#pragma unroll
+                for (int t2 = 0; t2 <= LL; ++t2) {
+                    const double sg = (t2 & 1) ? -1.0 : 1.0;
+                    Gx[t + t2] += Ex.e[ax][bx][t] * Ex.e[ax][bx][t2] * sg;
+                    Gy[t + t2] += Ey.e[ay][by][t] * Ey.e[ay][by][t2] * sg;
+                    Gz[t + t2] += Ez.e[az][bz][t] * Ez.e[az][bz][t2] * sg;
+                }
             double sum = 0.0;
-            for (int T = 0; T <= 2 * (ax + bx); T += 2)
-                for (int U = 0; U <= 2 * (ay + by); U += 2)
-                    for (int V = 0; V <= 2 * (az + bz); V += 2) {
+#pragma unroll
+            for (int T = 0; T <= 2 * LL; T += 2)
+#pragma unroll
+                for (int U = 0; U <= 2 * LL - T; U += 2)
+#pragma unroll
+                    for (int V = 0; V <= 2 * LL - T - U; V += 2) {
                         const int n = (T + U + V) / 2;
-                        double R = dfact_even(T) * dfact_even(U) * dfact_even(V) / (T + U + V + 1);
-                        for (int k = 0; k < n; ++k) R *= m2a;
+                        const double R = dfact_even(T) * dfact_even(U) * dfact_even(V) / (T + U + V + 1) * pw[n];
                         sum += Gx[T] * Gy[U] * Gz[V] * R;
                     }
-            const double eri = 2.0 * pow(PCM_PI, 2.5) / (p * p * sqrt(2.0 * p)) * K * K * sum;
+            const double eri = 2.0 * 17.493418327624862846 / (p * p * sqrt(2.0 * p)) * K * K * sum;  // 2 pi^(5/2) = 2 * 17.4934...
             const double f = comp_factor(LA, ca) * comp_factor(LB, cb);
             qmax = fmax(qmax, f * f * fabs(eri));
         }
@@ -185,9 +196,9 @@ __global__ void sp_start_kernel(int nsp, const long long *__restrict__ sp_cand, 
 template <int LA, int LB>
 static int screen_class(pcm_ctx *c, PairClass &pc)
 {
-    DBuf<int> c_sp, c_i, c_j, pos;
-    DBuf<double> c_P, c_p, c_pref, c_Q;
-    DBuf<unsigned char> flag;
+    DBuf<int> &c_sp = c->si[0], &c_i = c->si[1], &c_j = c->si[2], &pos = c->si[3];
+    DBuf<double> &c_P = c->sd[0], &c_p = c->sd[1], &c_pref = c->sd[2], &c_Q = c->sd[3];
+    DBuf<unsigned char> &flag = c->su8[0];
     const long long n = pc.ncand;
     PCM_TRY(c_sp.alloc(n));
     PCM_TRY(c_i.alloc(n));
@@ -204,7 +215,7 @@ static int screen_class(pcm_ctx *c, PairClass &pc)
             c->cnorm.p, c->xyz.p, c->opt.schwarz, c_sp.p, c_i.p, c_j.p, c_P.p, c_p.p, c_pref.p, c_Q.p, flag.p);
         PCM_LAUNCHED(c);
     }
-    DBuf<int> idx;
+    DBuf<int> &idx = c->si[4];
     PCM_TRY(idx.alloc(n));
     PCM_TRY(compact_flags(c, flag.p, n, idx.p, pos.p, c->iscal.p));
     int kept = 0;
@@ -230,7 +241,7 @@ static int screen_class(pcm_ctx *c, PairClass &pc)
     PCM_TRY(pc.sp_start.alloc(pc.nsp + 1));
     sp_start_kernel<<<(pc.nsp + 1 + 127) / 128, 128, 0, c->stream>>>(pc.nsp, pc.sp_cand.p, pos.p, pc.sp_start.p);
     PCM_LAUNCHED(c);
-    PCM_CUDA(cudaStreamSynchronize(c->stream));  // candidate scratch is freed on return
+    PCM_CUDA(cudaStreamSynchronize(c->stream));  // the scratch slots are reused by the next class
     return PCM_OK;
 }
 
@@ -292,7 +303,7 @@ int basis_build(pcm_ctx *c, int nshell, const int *shell_atom, const int *shell_
     PCM_TRY(c->sh_bf.alloc(ns));
     PCM_TRY(c->exps.alloc(ex.size()));
     PCM_TRY(c->cnorm.alloc(ex.size()));
-    DBuf<double> dco;
+    DBuf<double> &dco = c->sd[4];
     PCM_TRY(dco.alloc(co.size()));
     PCM_CUDA(cudaMemcpyAsync(c->sh_atom.p, c->h_sh_atom.data(), ns * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     PCM_CUDA(cudaMemcpyAsync(c->sh_l.p, c->h_sh_l.data(), ns * sizeof(int), cudaMemcpyHostToDevice, c->stream));

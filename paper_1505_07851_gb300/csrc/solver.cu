@@ -408,14 +408,28 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
                     if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255], 1u);
                 }
                 __syncthreads();
-                if (threadIdx.x == 0) {
-                    int acc = 0, bin = 255;
-                    for (; bin >= 0; --bin) {
-                        if (acc + (int)hist[bin] >= need) break;
-                        acc += hist[bin];
+                // the bin holding the need-th largest key: warp 0 scans the 256
+                // bins from the top, 8 per lane
+                if (threadIdx.x < 32) {
+                    const int lane = threadIdx.x;
+                    int loc = 0;
+                    for (int b = 0; b < 8; ++b) loc += (int)hist[255 - 8 * lane - b];
+                    int inc = loc;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
                     }
-                    s_prefix = prefix | ((unsigned long long)bin << shift);
-                    s_need_eq = need - acc;
+                    const unsigned ball = __ballot_sync(0xffffffffu, inc >= need);
+                    if (lane == __ffs(ball) - 1) {
+                        int acc = inc - loc, bin = 255 - 8 * lane;
+                        for (int b = 0; b < 7; ++b, --bin) {
+                            if (acc + (int)hist[bin] >= need) break;
+                            acc += (int)hist[bin];
+                        }
+                        s_prefix = prefix | ((unsigned long long)bin << shift);
+                        s_need_eq = need - acc;
+                    }
                 }
                 __syncthreads();
                 prefix = s_prefix;
@@ -586,7 +600,7 @@ int solver_prepare(pcm_ctx *c)
         c->rbj_l = l;
         c->rbj_nblk = (M + l - 1) / l;
         PCM_TRY(c->rbj_perm.alloc(M));
-        DBuf<int> U, U2;
+        DBuf<int> &U = c->si[0], &U2 = c->si[1];
         PCM_TRY(U.alloc(M));
         PCM_TRY(U2.alloc(M));
         PCM_CUDA(cudaMemsetAsync(c->iscal.p, 0, 64 * sizeof(int), c->stream));
@@ -594,7 +608,7 @@ int solver_prepare(pcm_ctx *c)
                                                      c->iscal.p + 16);
         PCM_LAUNCHED(c);
         PCM_TRY(c->rbj_inv.alloc((size_t)c->rbj_nblk * l * l));
-        DBuf<double> work;
+        DBuf<double> &work = c->sd[0];
         PCM_TRY(work.alloc((size_t)c->rbj_nblk * l * l));
         const int nt = std::min(1024, std::max(32, (l + 31) / 32 * 32));
         rbj_invert_kernel<<<c->rbj_nblk, nt, 0, c->stream>>>(M, c->lda, c->A.p, l, c->rbj_perm.p, work.p,
@@ -733,7 +747,7 @@ int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E)
     PCM_TRY(c->vtmp.alloc(M));
     const int gv = gemv_grid(c);
     PCM_TRY(c->red.alloc(2 * MAX_PART));
-    DBuf<double> part2;
+    DBuf<double> &part2 = c->sd[1];
     const int nb = std::min(1024, (M + 255) / 256);
     PCM_TRY(part2.alloc(2 * nb));
     gemv_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, dq, c->vtmp.p, c->red.p);

@@ -196,11 +196,13 @@ __global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, co
                 v = pzeta[k] * 0.79788456080286535588 / pS[k];  // sqrt(2/pi)
             } else {
                 const double dx = px[k] - lx, dy = py[k] - ly, dz = pz[k] - lz;
-                const double d = sqrt(dx * dx + dy * dy + dz * dz);
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                const double inv = rsqrt(d2);
                 const double zk = pzeta[k];
-                const double zp = zk * lzeta / sqrt(zk * zk + lzeta * lzeta);
-                const double a = zp * d;
-                v = (a > 6.0 ? 1.0 : erf(a)) / d;
+                const double zp = zk * lzeta * rsqrt(zk * zk + lzeta * lzeta);
+                const double a = zp * (d2 * inv);
+                // erf(a) rounds to 1 in FP64 for a > 6
+                v = (a > 6.0) ? inv : erf(a) * inv;
             }
             A[(size_t)k * lda + l] = v;
         }
@@ -237,7 +239,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     PCM_CUDA(cudaMemcpyAsync(c->radius.p, radius, natom * sizeof(double), cudaMemcpyHostToDevice, c->stream));
 
     // exponent classes: atoms with equal zeta (Eq. 7) share a class; classes in increasing zeta
-    DBuf<double> azeta;
+    DBuf<double> &azeta = c->sd[0];
     PCM_TRY(azeta.alloc(natom));
     atom_zeta_kernel<<<(natom + 127) / 128, 128, 0, c->stream>>>(natom, c->radius.p, c->opt.zeta, n, azeta.p);
     PCM_LAUNCHED(c);
@@ -252,14 +254,14 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     std::vector<int> h_acls(natom);
     for (int I = 0; I < natom; ++I)
         h_acls[I] = (int)(std::lower_bound(uz.begin(), uz.end(), h_azeta[I]) - uz.begin());
-    DBuf<int> acls;
+    DBuf<int> &acls = c->si[0];
     PCM_TRY(acls.alloc(natom));
     PCM_CUDA(cudaMemcpyAsync(acls.p, h_acls.data(), natom * sizeof(int), cudaMemcpyHostToDevice, c->stream));
 
     // candidates
     const long long ncand = (long long)natom * n;
-    DBuf<double> cx, cy, cz, cS;
-    DBuf<unsigned char> keep;
+    DBuf<double> &cx = c->sd[1], &cy = c->sd[2], &cz = c->sd[3], &cS = c->sd[4];
+    DBuf<unsigned char> &keep = c->su8[0];
     PCM_TRY(cx.alloc(ncand));
     PCM_TRY(cy.alloc(ncand));
     PCM_TRY(cz.alloc(ncand));
@@ -274,7 +276,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     PCM_TRY(c->idx32.alloc(ncand));
     PCM_TRY(c->iscal.alloc(64));
     std::vector<int> counts(c->ncls);
-    DBuf<int> order;
+    DBuf<int> &order = c->si[1];
     PCM_TRY(order.alloc(ncand));
     int M = 0;
     c->h_cls_off.assign(c->ncls + 1, 0);
@@ -331,7 +333,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     dinv_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, c->lda, c->A.p, c->dinv.p);
     PCM_LAUNCHED(c);
     PCM_TRY(points_split(c));
-    PCM_CUDA(cudaStreamSynchronize(c->stream));  // local scratch buffers are freed on return
+    PCM_CUDA(cudaStreamSynchronize(c->stream));
     c->pc_ready = false;
     c->have_c = false;
     return PCM_OK;
