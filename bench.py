@@ -253,6 +253,7 @@ def _timed_steps(pcm, w, precision, args, dev, stream, flush, delta, steps, warm
         out["times"].append(e0.elapsed_time(e1))
         s = ctx.stats()
         out["solve_ms"].append(s["ms_solve"])
+        out.setdefault("precond_ms", []).append(s["ms_precond"])
         out["iters"].append(st["iterations"])
         out["E"].append(E)
         out["ints"] += s["integrals_esp"] + s["integrals_fock"]
@@ -366,6 +367,7 @@ def run_ours(args):
                        "l2": "flushed between timed steps (512 MB write, not timed)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "pcg_solve_ms": statistics.mean(main["solve_ms"]), "pcg_iterations": statistics.mean(main["iters"]),
+            "pcg_precond_setup_ms": statistics.mean(main["precond_ms"]),
             "energy_Eh": main["E"][-1], "energy_ref_fp64_Eh": E_ref,
             "energy_err_Eh": abs(main["E"][-1] - E_ref),
             "esp_kernel_ms": float(main["esp_cls"].sum() / args.steps),

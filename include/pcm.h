@@ -108,6 +108,7 @@ typedef struct pcm_stats {
     double ms_esp_class[6];     /* with timing: main ESP kernel time per class (ms) */
     double ms_fock_class[6];    /* with timing: main Fock kernel time per class (ms) */
     double ms_solve;            /* with timing: device time of the last pcm_solve (ms) */
+    double ms_precond;          /* with timing: preconditioner set-up inside that solve (ms) */
     long long launches;         /* kernels launched by this context since its creation */
 } pcm_stats;
 

@@ -56,7 +56,7 @@ class pcm_stats(ctypes.Structure):
                 ("integrals_esp", ctypes.c_double), ("integrals_fock", ctypes.c_double),
                 ("esp_class_pairs", ctypes.c_longlong * 6), ("fock_class_pairs", ctypes.c_longlong * 6),
                 ("ms_esp_class", ctypes.c_double * 6), ("ms_fock_class", ctypes.c_double * 6),
-                ("ms_solve", ctypes.c_double), ("launches", ctypes.c_longlong)]
+                ("ms_solve", ctypes.c_double), ("ms_precond", ctypes.c_double), ("launches", ctypes.c_longlong)]
 
     def as_dict(self):
         out = {}

@@ -168,7 +168,7 @@ int pcm_create(pcm_ctx **out, const pcm_options *opt)
         c->own_stream = true;
     }
     if (o.timing) {
-        for (int i = 0; i < 13; ++i) {
+        for (int i = 0; i < 14; ++i) {
             cudaEventCreate(&c->ev_a[i]);
             cudaEventCreate(&c->ev_b[i]);
         }
@@ -190,7 +190,7 @@ int pcm_destroy(pcm_ctx *c)
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
     if (c->have_events)
-        for (int i = 0; i < 13; ++i) {
+        for (int i = 0; i < 14; ++i) {
             cudaEventDestroy(c->ev_a[i]);
             cudaEventDestroy(c->ev_b[i]);
         }

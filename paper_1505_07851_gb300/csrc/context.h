@@ -127,7 +127,8 @@ struct pcm_ctx {
     // stored A (FP64), leading dimension lda
     int lda = 0;
     pcm::DBuf<double> A;
-    pcm::DBuf<float> A32;                  // Jacobi-scaled FP32 copy for PCM_MIXED
+    pcm::DBuf<float> A32;                  // FP32 copy of A for the inner solves of PCM_MIXED
+    bool a32_ready = false;
     pcm::DBuf<double> dinv;                // 1 / A_kk
 
     // basis (expanded: sp shells split into an s and a p shell)
@@ -151,7 +152,8 @@ struct pcm_ctx {
     pcm::DBuf<double> rbj_inv;             // nblk x l x l inverses (padded)
 
     // solver work vectors and scalars
-    pcm::DBuf<double> vx, vr, vz, vp, vAp, vrhs, vtmp;
+    pcm::DBuf<double> vx, vr, vz, vp, vAp, vrhs, vtmp, vro, vd;
+    pcm::DBuf<float> vp32;
     pcm::DBuf<double> red;                 // partial sums
     pcm::DBuf<double> scal;                // device scalars
     pcm::DBuf<int> iscal;                  // device ints (done flag, iteration count)
@@ -174,7 +176,7 @@ struct pcm_ctx {
     pcm::DBuf<unsigned char> su8[2];
 
     pcm_stats stats;
-    cudaEvent_t ev_a[13], ev_b[13];         // timing events: 0-5 ESP classes, 6-11 Fock classes, 12 solve
+    cudaEvent_t ev_a[14], ev_b[14];         // timing events: 0-5 ESP classes, 6-11 Fock classes, 12 solve, 13 precond
     bool have_events = false;
 };
 

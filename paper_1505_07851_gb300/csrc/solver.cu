@@ -2,9 +2,9 @@
 // residual test of Eq. 20 (Section 4b), Jacobi or randomized block-Jacobi
 // preconditioning (Section 4b-ii), and the energy of Eq. 13.
 //
-// A is stored in FP64 (row-major, leading dimension lda).  Each PCG
-// iteration is three kernels:
-//   pcg_gemv     Ap = A p, p.Ap                       -> alpha
+// A is stored in FP64 (row-major, leading dimension lda), and for PCM_MIXED
+// also as an FP32 copy.  Each PCG iteration is three kernels:
+//   pcg_gemv_rp  Ap = A p, p.Ap                       -> alpha
 //   pcg_update   x += alpha p, r -= alpha Ap, z = C r, r.r, r.z -> beta, stop test
 //   pcg_dir      p = z + beta p
 // Scalars stay on the device; reductions use per-block partial sums added in
@@ -43,46 +43,6 @@ __device__ __forceinline__ bool last_block(unsigned int *counter)
     return amlast;
 }
 
-// y = A x for rows handled by this block; partial[b] = sum_rows x_row y_row
-__device__ __forceinline__ double gemv_rows(int M, int lda, const double *__restrict__ A,
-                                            const double *__restrict__ x, double *__restrict__ y)
-{
-    const int lane = threadIdx.x & 31;
-    const int wg = (blockIdx.x * GV_NT + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * GV_NT) >> 5;
-    double dotp = 0.0;
-    for (int row = wg; row < M; row += nw) {
-        const double *a = A + (size_t)row * lda;
-        double s0 = 0.0, s1 = 0.0;
-        int col = 2 * lane;
-        // lda is a multiple of 32: double2 loads are aligned
-        for (; col + 193 < M; col += 256) {
-            const double2 a0 = *reinterpret_cast<const double2 *>(a + col);
-            const double2 a1 = *reinterpret_cast<const double2 *>(a + col + 64);
-            const double2 a2 = *reinterpret_cast<const double2 *>(a + col + 128);
-            const double2 a3 = *reinterpret_cast<const double2 *>(a + col + 192);
-            s0 = fma(a0.x, __ldg(x + col), s0);
-            s1 = fma(a0.y, __ldg(x + col + 1), s1);
-            s0 = fma(a1.x, __ldg(x + col + 64), s0);
-            s1 = fma(a1.y, __ldg(x + col + 65), s1);
-            s0 = fma(a2.x, __ldg(x + col + 128), s0);
-            s1 = fma(a2.y, __ldg(x + col + 129), s1);
-            s0 = fma(a3.x, __ldg(x + col + 192), s0);
-            s1 = fma(a3.y, __ldg(x + col + 193), s1);
-        }
-        for (; col < M; col += 64) {
-            s0 = fma(a[col], __ldg(x + col), s0);
-            if (col + 1 < M) s1 = fma(a[col + 1], __ldg(x + col + 1), s1);
-        }
-        const double s = warp_sum(s0 + s1);
-        if (lane == 0) {
-            y[row] = s;
-            dotp = fma(x[row], s, dotp);
-        }
-    }
-    return dotp;  // valid in lane 0 of each warp
-}
-
 __device__ __forceinline__ double block_sum_warps(double v /* lane-0 values */)
 {
     __shared__ double sh[32];
@@ -96,24 +56,108 @@ __device__ __forceinline__ double block_sum_warps(double v /* lane-0 values */)
     return r;
 }
 
-__global__ void __launch_bounds__(GV_NT) pcg_gemv_kernel(int M, int lda, const double *__restrict__ A,
-                                                         const double *__restrict__ p, double *__restrict__ Ap,
-                                                         double *__restrict__ part, double *__restrict__ scal,
-                                                         int *__restrict__ iscal, unsigned int *__restrict__ counter)
+// Row-pair GEMV: a block of 8 warps computes two rows, four warps per row,
+// each warp a quarter of the columns (whole vector loads), so the grid has
+// M/2 blocks and no wave tail.  Returns, in thread 0, the block's x.y partial
+// (x64 the FP64 copy of the input vector).
+template <typename TA>
+__device__ __forceinline__ double gemv_rowpair(int M, int lda, const TA *__restrict__ A, const TA *__restrict__ x,
+                                               const double *__restrict__ x64, double *__restrict__ y)
+{
+    __shared__ double sh[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = blockIdx.x * 2 + (w >> 2), seg = w & 3;
+    constexpr int V = 16 / sizeof(TA);                    // elements per 16-byte load
+    const int seglen = ((M + 3) / 4 + 32 * V - 1) / (32 * V) * (32 * V);
+    const int c0 = seg * seglen, c1 = min(M, c0 + seglen);
+    double part = 0.0;
+    if (row < M && c0 < c1) {
+        const TA *a = A + (size_t)row * lda;
+        TA s0 = TA(0), s1 = TA(0);
+        int col = c0 + V * lane;
+        for (; col + 32 * V + V - 1 < c1; col += 64 * V) {
+            if constexpr (sizeof(TA) == 4) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(a + col);
+                const float4 a1 = *reinterpret_cast<const float4 *>(a + col + 32 * V);
+                const float4 x0 = *reinterpret_cast<const float4 *>(x + col);
+                const float4 x1 = *reinterpret_cast<const float4 *>(x + col + 32 * V);
+                s0 = fmaf(a0.x, x0.x, fmaf(a0.y, x0.y, fmaf(a0.z, x0.z, fmaf(a0.w, x0.w, s0))));
+                s1 = fmaf(a1.x, x1.x, fmaf(a1.y, x1.y, fmaf(a1.z, x1.z, fmaf(a1.w, x1.w, s1))));
+            } else {
+                const double2 a0 = *reinterpret_cast<const double2 *>(a + col);
+                const double2 a1 = *reinterpret_cast<const double2 *>(a + col + 32 * V);
+                const double2 x0 = *reinterpret_cast<const double2 *>(x + col);
+                const double2 x1 = *reinterpret_cast<const double2 *>(x + col + 32 * V);
+                s0 = fma(a0.x, x0.x, fma(a0.y, x0.y, s0));
+                s1 = fma(a1.x, x1.x, fma(a1.y, x1.y, s1));
+            }
+        }
+        for (; col < c1; col += 32 * V)
+#pragma unroll
+            for (int t = 0; t < V; ++t)
+                if (col + t < c1) s0 += a[col + t] * x[col + t];
+        part = (double)warp_sum(s0 + s1);
+    }
+    if (lane == 0) sh[w] = part;
+    __syncthreads();
+    double blk = 0.0;
+    if (threadIdx.x == 0) {
+        for (int r2 = 0; r2 < 2; ++r2) {
+            const int rr = blockIdx.x * 2 + r2;
+            if (rr < M) {
+                const double v = sh[4 * r2] + sh[4 * r2 + 1] + sh[4 * r2 + 2] + sh[4 * r2 + 3];
+                y[rr] = v;
+                blk = fma(x64[rr], v, blk);
+            }
+        }
+    }
+    __syncthreads();
+    return blk;
+}
+
+// fixed-order sum of n partials by the whole (last) block; valid in thread 0
+__device__ __forceinline__ double sum_partials(const double *part, int n)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += ((volatile const double *)part)[i];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    return t;
+}
+
+// Ap = A p (FP64 or FP32 copy of A), p.Ap -> alpha
+template <typename TA>
+__global__ void __launch_bounds__(GV_NT) pcg_gemv_rp_kernel(int M, int lda, const TA *__restrict__ A,
+                                                            const TA *__restrict__ px, const double *__restrict__ p,
+                                                            double *__restrict__ Ap, double *__restrict__ part,
+                                                            double *__restrict__ scal, int *__restrict__ iscal,
+                                                            unsigned int *__restrict__ counter)
 {
     if (iscal[I_DONE]) return;
-    const double d = gemv_rows(M, lda, A, p, Ap);
-    const double bsum = block_sum_warps(d);
+    const double bsum = gemv_rowpair<TA>(M, lda, A, px, p, Ap);
     if (threadIdx.x == 0) part[blockIdx.x] = bsum;
     if (last_block(counter)) {
+        const double t = sum_partials(part, gridDim.x);
         if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (unsigned int b = 0; b < gridDim.x; ++b) s += ((volatile double *)part)[b];
-            scal[S_PAP] = s;
-            scal[S_ALPHA] = scal[S_RZ] / s;
+            scal[S_PAP] = t;
+            scal[S_ALPHA] = scal[S_RZ] / t;
             *counter = 0;
         }
     }
+}
+
+// y = A x (FP64), block partials of x.y
+__global__ void __launch_bounds__(GV_NT) gemv_rp_plain_kernel(int M, int lda, const double *__restrict__ A,
+                                                              const double *__restrict__ x, double *__restrict__ y,
+                                                              double *__restrict__ part)
+{
+    const double bsum = gemv_rowpair<double>(M, lda, A, x, x, y);
+    if (threadIdx.x == 0) part[blockIdx.x] = bsum;
 }
 
 // After the reductions of r.r and r.z: stop test (Eq. 20) and beta.
@@ -184,6 +228,8 @@ __global__ void __launch_bounds__(UP_NT) pcg_update_diag_kernel(int M, const dou
     }
 }
 
+constexpr int RBJ_SPLIT = 4;   // threads per row in the block-Jacobi apply
+
 // Randomized block-Jacobi: one block per RBJ block; the block's indices are
 // perm[b*l .. b*l + nb) and its inverse is inv[b] (l x l, symmetric).
 // With alpha_from_scal = false (initialisation) x and r are left unchanged.
@@ -212,12 +258,21 @@ __global__ void pcg_update_rbj_kernel(int M, int l, const int *__restrict__ perm
     }
     __syncthreads();
     const double *Mi = inv + (size_t)b * l * l;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    // z_i = sum_j Minv_ji r_j (Minv symmetric): RBJ_SPLIT threads share a row,
+    // each summing every RBJ_SPLIT-th column, combined by shuffles
+    const int sub = threadIdx.x % RBJ_SPLIT;
+    for (int i0 = threadIdx.x / RBJ_SPLIT; i0 < ((nb + 31) / 32) * 32; i0 += blockDim.x / RBJ_SPLIT) {
+        const int i = i0;
         double s = 0.0;
-        for (int j = 0; j < nb; ++j) s = fma(Mi[(size_t)j * l + i], srb[j], s);
-        z[perm[base + i]] = s;
-        rr = fma(srb[i], srb[i], rr);
-        rz = fma(srb[i], s, rz);
+        if (i < nb)
+            for (int j = sub; j < nb; j += RBJ_SPLIT) s = fma(Mi[(size_t)j * l + i], srb[j], s);
+#pragma unroll
+        for (int o = RBJ_SPLIT / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (sub == 0 && i < nb) {
+            z[perm[base + i]] = s;
+            rr = fma(srb[i], srb[i], rr);
+            rz = fma(srb[i], s, rz);
+        }
     }
     __shared__ double sh[2][32];
     rr = warp_sum(rr);
@@ -266,6 +321,60 @@ __global__ void pcg_dir_kernel(int M, const double *__restrict__ z, double *__re
     const double beta = scal[S_BETA];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x)
         p[k] = fma(beta, p[k], z[k]);
+}
+
+// p = z + beta p, also as FP32 for the FP32 GEMV
+__global__ void pcg_dir32_kernel(int M, const double *__restrict__ z, double *__restrict__ p, float *__restrict__ p32,
+                                 const double *__restrict__ scal, const int *__restrict__ iscal)
+{
+    if (iscal[I_DONE]) return;
+    const double beta = scal[S_BETA];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        const double v = fma(beta, p[k], z[k]);
+        p[k] = v;
+        p32[k] = (float)v;
+    }
+}
+
+__global__ void copy32_kernel(int M, const double *__restrict__ a, double *__restrict__ b, float *__restrict__ b32)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        b[k] = a[k];
+        b32[k] = (float)a[k];
+    }
+}
+
+// FP32 copy of the stored A for the inner solves of PCM_MIXED
+__global__ void a_to_f32_kernel(long long n, const double *__restrict__ A, float *__restrict__ A32)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        A32[i] = (float)A[i];
+}
+
+// r = b - y and per-block partial sums of r.r
+__global__ void residual_kernel(int M, const double *__restrict__ b, const double *__restrict__ y,
+                                double *__restrict__ r, double *__restrict__ part)
+{
+    double s = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        const double v = b[k] - y[k];
+        r[k] = v;
+        s = fma(v, v, s);
+    }
+    __shared__ double sh[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void axpy_kernel(int M, const double *__restrict__ d, double *__restrict__ x)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) x[k] += d[k];
 }
 
 // initialisation: r = b - (A x0) or r = b; x = x0 or 0
@@ -337,14 +446,6 @@ __global__ void copy_kernel(int M, const double *__restrict__ a, double *__restr
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) b[k] = a[k];
 }
 
-__global__ void gemv_plain_kernel(int M, int lda, const double *__restrict__ A, const double *__restrict__ x,
-                                  double *__restrict__ y, double *__restrict__ part)
-{
-    const double d = gemv_rows(M, lda, A, x, y);
-    const double bsum = block_sum_warps(d);
-    if (threadIdx.x == 0) part[blockIdx.x] = bsum;
-}
-
 // ---------------------------------------------------------------------------
 // RBJ permutation (Section 4b-ii), one block of 1024 threads walking the
 // pivots in sequence.  Pivot j is position floor((r_j >> 32) * nU / 2^32) of
@@ -363,15 +464,56 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t j)
     return z ^ (z >> 31);
 }
 
+// block-wide exclusive scan of one int per thread (RBJ_NT threads); returns
+// the exclusive prefix and writes the block total to *total
+__device__ __forceinline__ int rbj_block_scan(int v, int *sh /* RBJ_NT/32 + 1 */, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int t = sh[lane];
+        int xs = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, xs, o);
+            if (lane >= o) xs += y;
+        }
+        sh[lane] = xs - t;
+        if (lane == 31) sh[32] = xs;
+    }
+    __syncthreads();
+    const int r = sh[wid] + x - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+constexpr int RBJ_NBIN = 2048;   // histogram of the top 11 bits of the FP32 key
+constexpr int RBJ_LMAX = 3072;   // boundary-bin elements resolved exactly in shared memory
+
+// key of |A_kj| for ordering: FP64 bits (|A| >= 0, so bit order = value order)
+__device__ __forceinline__ unsigned long long rbj_key64(double a) { return (unsigned long long)__double_as_longlong(fabs(a)); }
+// coarse bin: top 11 bits of the FP32 value (monotone in |A|)
+__device__ __forceinline__ int rbj_bin(double a) { return (int)(__float_as_uint((float)fabs(a)) >> 20); }
+
 __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const double *__restrict__ A, int l,
                                                           unsigned long long seed, int *__restrict__ U,
                                                           int *__restrict__ U2, int *__restrict__ perm,
                                                           int *__restrict__ status)
 {
-    __shared__ unsigned int hist[256];
+    __shared__ unsigned int hist[RBJ_NBIN];
+    __shared__ unsigned long long lkey[RBJ_LMAX];
+    __shared__ int lidx[RBJ_LMAX];
+    __shared__ unsigned char lsel[RBJ_LMAX];
     __shared__ int sh_int[RBJ_NT / 32 + 1];
-    __shared__ int s_nU, s_k, s_cnt_gt, s_need_eq;
-    __shared__ unsigned long long s_prefix;
+    __shared__ int s_nU, s_k, s_bin, s_need, s_nlist;
     for (int i = threadIdx.x; i < M; i += RBJ_NT) U[i] = i;
     if (threadIdx.x == 0) s_nU = M;
     __syncthreads();
@@ -388,139 +530,108 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
             const uint64_t r = splitmix64_at(seed, draw);
             const int pos = (int)(((r >> 32) * (uint64_t)nU) >> 32);
             s_k = U[pos];
+            s_bin = RBJ_NBIN;          // above every bin: nothing selected
+            s_need = 0;
+            s_nlist = 0;
         }
         ++draw;
+        for (int i = threadIdx.x; i < RBJ_NBIN; i += RBJ_NT) hist[i] = 0;
         __syncthreads();
         const int k = s_k;
         const int nsel = min(l - 1, nU - 1);
         const double *row = A + (size_t)k * lda;
-        // radix select of the nsel-th largest key (bits of |A_kj|, j != k)
-        unsigned long long prefix = 0, mask = 0;
-        int need = nsel;  // how many still to take at or below the current prefix
         if (nsel > 0) {
-            for (int shift = 56; shift >= 0; shift -= 8) {
-                for (int i = threadIdx.x; i < 256; i += RBJ_NT) hist[i] = 0;
-                __syncthreads();
-                for (int i = threadIdx.x; i < nU; i += RBJ_NT) {
-                    const int j = U[i];
-                    if (j == k) continue;
-                    const unsigned long long key = (unsigned long long)__double_as_longlong(fabs(row[j]));
-                    if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255], 1u);
-                }
-                __syncthreads();
-                // the bin holding the need-th largest key: warp 0 scans the 256
-                // bins from the top, 8 per lane
-                if (threadIdx.x < 32) {
-                    const int lane = threadIdx.x;
-                    int loc = 0;
-                    for (int b = 0; b < 8; ++b) loc += (int)hist[255 - 8 * lane - b];
-                    int inc = loc;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += y;
-                    }
-                    const unsigned ball = __ballot_sync(0xffffffffu, inc >= need);
-                    if (lane == __ffs(ball) - 1) {
-                        int acc = inc - loc, bin = 255 - 8 * lane;
-                        for (int b = 0; b < 7; ++b, --bin) {
-                            if (acc + (int)hist[bin] >= need) break;
-                            acc += (int)hist[bin];
-                        }
-                        s_prefix = prefix | ((unsigned long long)bin << shift);
-                        s_need_eq = need - acc;
-                    }
-                }
-                __syncthreads();
-                prefix = s_prefix;
-                need = s_need_eq;
-                mask |= 255ull << shift;
-                __syncthreads();
+            // 1. coarse histogram
+            for (int i = threadIdx.x; i < nU; i += RBJ_NT) {
+                const int j = U[i];
+                if (j != k) atomicAdd(&hist[rbj_bin(row[j])], 1u);
             }
-            // keys > prefix are all taken; `need` of the keys == prefix (lowest index first)
+            __syncthreads();
+            // 2. bin holding the nsel-th largest key: warp 0 scans from the top, 64 bins per lane
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                const int top = RBJ_NBIN - 1 - 64 * lane;
+                int loc = 0;
+                for (int b = 0; b < 64; ++b) loc += (int)hist[top - b];
+                int inc = loc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                const unsigned ball = __ballot_sync(0xffffffffu, inc >= nsel);
+                if (lane == __ffs(ball) - 1) {
+                    int acc = inc - loc, bin = top;
+                    for (int b = 0; b < 63; ++b, --bin) {
+                        if (acc + (int)hist[bin] >= nsel) break;
+                        acc += (int)hist[bin];
+                    }
+                    s_bin = bin;
+                    s_need = nsel - acc;   // taken from the boundary bin
+                }
+            }
+            __syncthreads();
+            // 3. boundary-bin elements with their exact keys
+            const int bstar = s_bin;
+            for (int i = threadIdx.x; i < nU; i += RBJ_NT) {
+                const int j = U[i];
+                if (j != k && rbj_bin(row[j]) == bstar) {
+                    const int p = atomicAdd(&s_nlist, 1);
+                    if (p < RBJ_LMAX) {
+                        lkey[p] = rbj_key64(row[j]);
+                        lidx[p] = j;
+                    }
+                }
+            }
+            __syncthreads();
+            const int nl = s_nlist;
+            if (nl > RBJ_LMAX) {  // more equal-bin keys than shared memory holds
+                if (threadIdx.x == 0) *status = 4;
+                return;
+            }
+            // 4. exact rank in the boundary bin: larger key first, then lower index
+            const int need = s_need;
+            for (int a = threadIdx.x; a < nl; a += RBJ_NT) {
+                const unsigned long long ka = lkey[a];
+                const int ja = lidx[a];
+                int rank = 0;
+                for (int b = 0; b < nl; ++b) {
+                    const unsigned long long kb = lkey[b];
+                    rank += (kb > ka || (kb == ka && lidx[b] < ja)) ? 1 : 0;
+                }
+                lsel[a] = rank < need ? 1 : 0;
+            }
+            __syncthreads();
         }
-        const unsigned long long thr = prefix;
-        const int need_eq = need;
-        // scan in list order: flag = taken (pivot, key > thr, or among the first need_eq keys == thr)
-        if (threadIdx.x == 0) {
-            perm[out] = k;
-            s_cnt_gt = 0;
-        }
-        __syncthreads();
-        int taken_base = out + 1;
-        int eq_seen = 0, kept_base = 0;
+        // 5. one compaction pass in list order: taken -> perm (after the pivot), kept -> U2
+        if (threadIdx.x == 0) perm[out] = k;
+        const int bstar = s_bin, nl = min(s_nlist, RBJ_LMAX);
+        int taken_base = out + 1, kept_base = 0;
         for (int c0 = 0; c0 < nU; c0 += RBJ_NT) {
             const int i = c0 + threadIdx.x;
-            int j = -1, sel = 0, iseq = 0;
+            int j = -1, sel = 0, keep = 0;
             if (i < nU) {
                 j = U[i];
-                if (j != k && nsel > 0) {
-                    const unsigned long long key = (unsigned long long)__double_as_longlong(fabs(row[j]));
-                    if (key > thr) sel = 1;
-                    else if (key == thr) iseq = 1;
-                }
-            }
-            // rank among equal keys in this chunk
-            int eqx;
-            {
-                int tot;
-                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-                int xs = iseq;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int y = __shfl_up_sync(0xffffffffu, xs, o);
-                    if (lane >= o) xs += y;
-                }
-                if (lane == 31) sh_int[wid] = xs;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int run = 0;
-                    for (int w = 0; w < RBJ_NT / 32; ++w) {
-                        int t = sh_int[w];
-                        sh_int[w] = run;
-                        run += t;
+                if (j != k) {
+                    if (nsel > 0) {
+                        const int bn = rbj_bin(row[j]);
+                        if (bn > bstar) {
+                            sel = 1;
+                        } else if (bn == bstar) {
+                            for (int b = 0; b < nl; ++b)
+                                if (lidx[b] == j) {
+                                    sel = lsel[b];
+                                    break;
+                                }
+                        }
                     }
-                    sh_int[RBJ_NT / 32] = run;
+                    keep = !sel;
                 }
-                __syncthreads();
-                eqx = sh_int[wid] + xs - iseq;
-                tot = sh_int[RBJ_NT / 32];
-                __syncthreads();
-                if (iseq && eq_seen + eqx < need_eq) sel = 1;
-                eq_seen += tot;
             }
-            // compact: selected -> perm, unselected (and not pivot) -> U2
-            const int keep = (i < nU && j != k && !sel) ? 1 : 0;
-            int ex_sel, ex_keep, tot_sel, tot_keep;
-            {
-                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-                int packed = (sel << 16) | keep;  // counts < 65536 per chunk
-                int xs = packed;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int y = __shfl_up_sync(0xffffffffu, xs, o);
-                    if (lane >= o) xs += y;
-                }
-                if (lane == 31) sh_int[wid] = xs;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int run = 0;
-                    for (int w = 0; w < RBJ_NT / 32; ++w) {
-                        int t = sh_int[w];
-                        sh_int[w] = run;
-                        run += t;
-                    }
-                    sh_int[RBJ_NT / 32] = run;
-                }
-                __syncthreads();
-                const int ex = sh_int[wid] + xs - packed;
-                const int tt = sh_int[RBJ_NT / 32];
-                __syncthreads();
-                ex_sel = ex >> 16;
-                ex_keep = ex & 0xffff;
-                tot_sel = tt >> 16;
-                tot_keep = tt & 0xffff;
-            }
+            // one scan of both counts: chunk totals stay below 2^16
+            int tot;
+            const int ex = rbj_block_scan((sel << 16) | keep, sh_int, &tot);
+            const int ex_sel = ex >> 16, ex_keep = ex & 0xffff, tot_sel = tot >> 16, tot_keep = tot & 0xffff;
             if (sel) perm[taken_base + ex_sel] = j;
             if (keep) U2[kept_base + ex_keep] = j;
             taken_base += tot_sel;
@@ -585,7 +696,7 @@ __global__ void rbj_invert_kernel(int M, int lda, const double *__restrict__ A, 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-static int gemv_grid(pcm_ctx *c) { return std::min(MAX_PART, std::max(1, (c->M + 7) / 8)); }
+static int gemv_grid(pcm_ctx *c) { return std::max(1, (c->M + 1) / 2); }
 
 int solver_prepare(pcm_ctx *c)
 {
@@ -619,7 +730,8 @@ int solver_prepare(pcm_ctx *c)
         PCM_CUDA(cudaStreamSynchronize(c->stream));
         if (st != 0) {
             set_last_error("RBJ set-up failed (status %d: %s)", st,
-                           st == 3 ? "a diagonal block is not positive definite" : "bad permutation");
+                           st == 3 ? "a diagonal block is not positive definite"
+                                   : (st == 4 ? "too many equal keys for the selection buffer" : "bad permutation"));
             return PCM_ERR_CUDA;
         }
     }
@@ -627,39 +739,37 @@ int solver_prepare(pcm_ctx *c)
     return PCM_OK;
 }
 
-int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st)
+// Preconditioned CG on A x = b from x (warm) or 0 until the recursively
+// updated residual is below delta or max_iter steps; the FP64 stored A, or
+// with use32 the FP32 copy (FP32 GEMV).  Returns iterations, the stop flag
+// and the final residual norm.
+static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double delta, int max_iter, bool use32,
+                    int *iters, int *conv, double *rnorm)
 {
-    PCM_TRY(solver_prepare(c));
     const int M = c->M;
-    PCM_TRY(c->vr.alloc(M));
-    PCM_TRY(c->vz.alloc(M));
-    PCM_TRY(c->vp.alloc(M));
-    PCM_TRY(c->vAp.alloc(M));
-    PCM_TRY(c->red.alloc(2 * (size_t)std::max(MAX_PART, c->rbj_nblk)));
-    PCM_TRY(c->scal.alloc(S_NSCAL));
-    PCM_TRY(c->counter.alloc(4));
     PCM_CUDA(cudaMemsetAsync(c->counter.p, 0, 4 * sizeof(unsigned int), c->stream));
-    PCM_CUDA(cudaMemsetAsync(c->iscal.p, 0, I_NINT * sizeof(int), c->stream));
     {
         double hs[S_NSCAL] = {0, 0, 0, 0, 0, delta, 0};
-        int hi[I_NINT] = {0, 0, c->opt.max_iter, 0};
+        int hi[I_NINT] = {0, 0, max_iter, 0};
         PCM_CUDA(cudaMemcpyAsync(c->scal.p, hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
         PCM_CUDA(cudaMemcpyAsync(c->iscal.p, hi, sizeof(hi), cudaMemcpyHostToDevice, c->stream));
         // hs, hi are read before the synchronisation below
         PCM_CUDA(cudaStreamSynchronize(c->stream));
     }
-    double *x = dq, *r = c->vr.p, *z = c->vz.p, *p = c->vp.p, *Ap = c->vAp.p;
+    double *r = c->vr.p, *z = c->vz.p, *p = c->vp.p, *Ap = c->vAp.p;
+    float *p32 = c->vp32.p;
     const int gv = gemv_grid(c);
     const int ub = std::min(MAX_PART, (M + UP_NT - 1) / UP_NT);
+    const int eb = std::min(1024, (M + 255) / 256);
     if (warm) {
-        gemv_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, x, Ap, c->red.p);
+        gemv_rp_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, x, Ap, c->red.p);
         PCM_LAUNCHED(c);
     }
-    pcg_init_kernel<<<std::min(1024, (M + 255) / 256), 256, 0, c->stream>>>(M, drhs, Ap, warm ? 1 : 0, x, r);
+    pcg_init_kernel<<<eb, 256, 0, c->stream>>>(M, drhs, Ap, warm ? 1 : 0, x, r);
     PCM_LAUNCHED(c);
     const double *dinv = (c->pc_kind == PCM_PRECOND_JACOBI) ? c->dinv.p : nullptr;
     const bool rbj = c->pc_kind == PCM_PRECOND_RBJ;
-    const int rbj_nt = std::min(1024, std::max(32, (c->rbj_l + 31) / 32 * 32));
+    const int rbj_nt = std::min(1024, RBJ_SPLIT * std::max(32, (c->rbj_l + 31) / 32 * 32));
     const size_t rbj_smem = (size_t)c->rbj_l * sizeof(double);
     if (rbj) {
         if (rbj_smem > 48 * 1024)
@@ -672,15 +782,20 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
                                                           c->counter.p);
     }
     PCM_LAUNCHED(c);
-    copy_kernel<<<std::min(1024, (M + 255) / 256), 256, 0, c->stream>>>(M, z, p);
+    if (use32) copy32_kernel<<<eb, 256, 0, c->stream>>>(M, z, p, p32);
+    else copy_kernel<<<eb, 256, 0, c->stream>>>(M, z, p);
     PCM_LAUNCHED(c);
 
     const int batch = 8;
     int h_i[I_NINT] = {0, 0, 0, 0};
     for (int done_it = 0;;) {
         for (int b = 0; b < batch; ++b) {
-            pcg_gemv_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, p, Ap, c->red.p, c->scal.p, c->iscal.p,
-                                                         c->counter.p);
+            if (use32)
+                pcg_gemv_rp_kernel<float><<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A32.p, p32, p, Ap, c->red.p,
+                                                                       c->scal.p, c->iscal.p, c->counter.p);
+            else
+                pcg_gemv_rp_kernel<double><<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, p, p, Ap, c->red.p,
+                                                                        c->scal.p, c->iscal.p, c->counter.p);
             if (rbj)
                 pcg_update_rbj_kernel<<<c->rbj_nblk, rbj_nt, rbj_smem, c->stream>>>(
                     M, c->rbj_l, c->rbj_perm.p, c->rbj_inv.p, x, r, z, p, Ap, c->red.p, c->scal.p, c->iscal.p,
@@ -688,7 +803,8 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
             else
                 pcg_update_diag_kernel<<<ub, UP_NT, 0, c->stream>>>(M, dinv, x, r, z, p, Ap, c->red.p, c->scal.p,
                                                                     c->iscal.p, c->counter.p);
-            pcg_dir_kernel<<<std::min(1024, (M + 255) / 256), 256, 0, c->stream>>>(M, z, p, c->scal.p, c->iscal.p);
+            if (use32) pcg_dir32_kernel<<<eb, 256, 0, c->stream>>>(M, z, p, p32, c->scal.p, c->iscal.p);
+            else pcg_dir_kernel<<<eb, 256, 0, c->stream>>>(M, z, p, c->scal.p, c->iscal.p);
             c->stats.launches += 3;
         }
         PCM_CUDA(cudaGetLastError());
@@ -696,7 +812,7 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
         PCM_CUDA(cudaStreamSynchronize(c->stream));
         done_it += batch;
         if (h_i[I_DONE]) break;
-        if (done_it > c->opt.max_iter + 2 * batch) {  // the device cap ends the loop first
+        if (done_it > max_iter + 2 * batch) {  // the device cap ends the loop first
             set_last_error("solver loop did not stop at its iteration cap");
             return PCM_ERR_TIMEOUT;
         }
@@ -704,13 +820,101 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
     double h_s[S_NSCAL];
     PCM_CUDA(cudaMemcpyAsync(h_s, c->scal.p, sizeof(h_s), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
-    c->stats.iterations = h_i[I_ITER];
-    c->stats.converged = h_i[I_CONV];
-    c->stats.rnorm = h_s[S_RNORM];
+    *iters = h_i[I_ITER];
+    *conv = h_i[I_CONV];
+    *rnorm = h_s[S_RNORM];
+    return PCM_OK;
+}
+
+// ||b - A x||_2 with the FP64 stored A; r receives the residual
+static int true_residual(pcm_ctx *c, const double *b, const double *x, double *r, double *norm)
+{
+    const int M = c->M;
+    const int gv = gemv_grid(c);
+    gemv_rp_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, x, c->vtmp.p, c->red.p);
+    PCM_LAUNCHED(c);
+    const int nb = std::min(256, (M + 255) / 256);
+    residual_kernel<<<nb, 256, 0, c->stream>>>(M, b, c->vtmp.p, r, c->red.p);
+    PCM_LAUNCHED(c);
+    double h[256];
+    PCM_CUDA(cudaMemcpyAsync(h, c->red.p, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PCM_CUDA(cudaStreamSynchronize(c->stream));
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += h[i];
+    *norm = sqrt(s);
+    return PCM_OK;
+}
+
+int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st)
+{
+    const bool fresh = !c->pc_ready;
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[13], c->stream));
+    PCM_TRY(solver_prepare(c));
+    c->stats.ms_precond = 0.0;
+    if (c->have_events && fresh) {
+        PCM_CUDA(cudaEventRecord(c->ev_b[13], c->stream));
+        PCM_CUDA(cudaEventSynchronize(c->ev_b[13]));
+        float ms = 0.f;
+        PCM_CUDA(cudaEventElapsedTime(&ms, c->ev_a[13], c->ev_b[13]));
+        c->stats.ms_precond = ms;
+    }
+    const int M = c->M;
+    PCM_TRY(c->vr.alloc(M));
+    PCM_TRY(c->vz.alloc(M));
+    PCM_TRY(c->vp.alloc(M));
+    PCM_TRY(c->vAp.alloc(M));
+    PCM_TRY(c->vtmp.alloc(M));
+    PCM_TRY(c->vp32.alloc(M));
+    PCM_TRY(c->red.alloc(2 * (size_t)std::max(std::max(MAX_PART, c->rbj_nblk), gemv_grid(c))));
+    PCM_TRY(c->scal.alloc(S_NSCAL));
+    PCM_TRY(c->counter.alloc(4));
+    PCM_CUDA(cudaMemsetAsync(c->iscal.p, 0, I_NINT * sizeof(int), c->stream));
+    int iters = 0, conv = 0, refinements = 0;
+    double rnorm = 0.0;
+    if (c->opt.precision != PCM_MIXED) {
+        PCM_TRY(pcg_core(c, drhs, dq, warm, delta, c->opt.max_iter, false, &iters, &conv, &rnorm));
+    } else {
+        // FP64 iterative refinement around FP32-GEMV inner solves: the true
+        // residual b - A x is formed with the FP64 A, each inner solve reduces
+        // it by ETA (or to delta / 2), and x accumulates the corrections
+        constexpr double ETA = 1e-3;
+        constexpr int MAX_REFINE = 12;
+        if (!c->a32_ready) {
+            PCM_TRY(c->A32.alloc((size_t)M * c->lda));
+            const long long n = (long long)M * c->lda;
+            a_to_f32_kernel<<<4 * 152, 256, 0, c->stream>>>(n, c->A.p, c->A32.p);
+            PCM_LAUNCHED(c);
+            c->a32_ready = true;
+        }
+        PCM_TRY(c->vro.alloc(M));
+        PCM_TRY(c->vd.alloc(M));
+        if (!warm) PCM_CUDA(cudaMemsetAsync(dq, 0, M * sizeof(double), c->stream));
+        for (;;) {
+            PCM_TRY(true_residual(c, drhs, dq, c->vro.p, &rnorm));
+            if (rnorm < delta) {
+                conv = 1;
+                break;
+            }
+            if (iters >= c->opt.max_iter || refinements >= MAX_REFINE || !std::isfinite(rnorm)) break;
+            int it_in = 0, conv_in = 0;
+            double rn_in = 0.0;
+            const double tol = std::max(ETA * rnorm, 0.5 * delta);
+            PCM_TRY(pcg_core(c, c->vro.p, c->vd.p, false, tol, std::max(1, c->opt.max_iter - iters), true, &it_in,
+                             &conv_in, &rn_in));
+            iters += it_in;
+            ++refinements;
+            const int eb = std::min(1024, (M + 255) / 256);
+            axpy_kernel<<<eb, 256, 0, c->stream>>>(M, c->vd.p, dq);
+            PCM_LAUNCHED(c);
+        }
+    }
+    c->stats.iterations = iters;
+    c->stats.converged = conv;
+    c->stats.rnorm = rnorm;
     c->stats.delta = delta;
-    c->stats.refinements = 0;
+    c->stats.refinements = refinements;
     if (st) *st = c->stats;
-    return h_i[I_CONV] ? PCM_OK : PCM_ERR_NOT_CONVERGED;
+    return conv ? PCM_OK : PCM_ERR_NOT_CONVERGED;
 }
 
 // E = (Bz)^T q + c^T q + q^T A q / (2 f)  (Eq. 13)
@@ -746,11 +950,11 @@ int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E)
     const int M = c->M;
     PCM_TRY(c->vtmp.alloc(M));
     const int gv = gemv_grid(c);
-    PCM_TRY(c->red.alloc(2 * MAX_PART));
+    PCM_TRY(c->red.alloc(2 * (size_t)std::max(MAX_PART, gv)));
     DBuf<double> &part2 = c->sd[1];
     const int nb = std::min(1024, (M + 255) / 256);
     PCM_TRY(part2.alloc(2 * nb));
-    gemv_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, dq, c->vtmp.p, c->red.p);
+    gemv_rp_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, dq, c->vtmp.p, c->red.p);
     PCM_LAUNCHED(c);
     dot2_kernel<<<nb, 256, 0, c->stream>>>(M, c->Bz.p, dcv, dq, part2.p);
     PCM_LAUNCHED(c);

@@ -161,8 +161,18 @@ __global__ void bz_kernel(int M, int natom, const double *__restrict__ px, const
 constexpr int AT = 32;
 __global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, const double *__restrict__ py,
                                const double *__restrict__ pz, const double *__restrict__ pzeta,
-                               const double *__restrict__ pS, double *__restrict__ A)
+                               const double *__restrict__ pS, const int *__restrict__ pcls, int ncls,
+                               const double *__restrict__ cls_zeta, double *__restrict__ A)
 {
+    // zeta'_kl of Eq. 8 depends only on the two exponent classes
+    __shared__ double zp_tab[16 * 16];
+    const bool tab = ncls <= 16;
+    if (tab)
+        for (int t = threadIdx.x; t < ncls * ncls; t += blockDim.x) {
+            const double a = cls_zeta[t / ncls], b = cls_zeta[t % ncls];
+            zp_tab[t] = a * b / sqrt(a * a + b * b);
+        }
+    __syncthreads();
     // map the linear block id onto the upper triangle of tiles
     const int nt = (M + AT - 1) / AT;
     long long t = blockIdx.x;
@@ -182,11 +192,13 @@ __global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, co
     const int ty = threadIdx.x / AT;  // 0 .. 7
     const int l = bj * AT + tx;
     double lx = 0, ly = 0, lz = 0, lzeta = 1;
+    int lcls = 0;
     if (l < M) {
         lx = px[l];
         ly = py[l];
         lz = pz[l];
         lzeta = pzeta[l];
+        lcls = pcls[l];
     }
     for (int r = ty; r < AT; r += 8) {
         const int k = bi * AT + r;
@@ -199,7 +211,7 @@ __global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, co
                 const double d2 = dx * dx + dy * dy + dz * dz;
                 const double inv = rsqrt(d2);
                 const double zk = pzeta[k];
-                const double zp = zk * lzeta * rsqrt(zk * zk + lzeta * lzeta);
+                const double zp = tab ? zp_tab[pcls[k] * ncls + lcls] : zk * lzeta / sqrt(zk * zk + lzeta * lzeta);
                 const double a = zp * (d2 * inv);
                 // erf(a) rounds to 1 in FP64 for a > 6
                 v = (a > 6.0) ? inv : erf(a) * inv;
@@ -326,7 +338,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
         const long long nt = (M + AT - 1) / AT;
         const long long ntiles = nt * (nt + 1) / 2;
         a_build_kernel<<<(unsigned)ntiles, 256, 0, c->stream>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
-                                                               c->pS.p, c->A.p);
+                                                               c->pS.p, c->pcls.p, c->ncls, c->cls_zeta.p, c->A.p);
         PCM_LAUNCHED(c);
     }
     PCM_TRY(c->dinv.alloc(M));
@@ -335,6 +347,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     PCM_TRY(points_split(c));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
     c->pc_ready = false;
+    c->a32_ready = false;
     c->have_c = false;
     return PCM_OK;
 }
