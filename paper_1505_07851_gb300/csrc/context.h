@@ -87,6 +87,7 @@ struct PairClass {
     DBuf<double> Px, Py, Pz, p, pref, Q;   // centre, exponent sum, (2 pi / p) K_AB, Schwarz bound
     // per-call ESP pairs (after the density test of Eq. 18), SoA; D has nherm(L) rows
     int nesp = 0;
+    int nesp_same = 0;                     // the first nesp_same ESP pairs join primitives on one atom
     DBuf<double> eP, eD;                   // eP: 4 x nesp (Px, Py, Pz, p); eD: nherm x nesp
     DBuf<float> eX32, eC32;                // PCM_MIXED ESP: 6 x nesp split centres; ncls x (3 + 2 nherm) x nesp constants
     DBuf<float> Pxyz32;                    // 6 x npair: hi (3) and lo (3) FP32 parts of the centre (Fock, PCM_MIXED)

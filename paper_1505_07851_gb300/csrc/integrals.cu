@@ -38,11 +38,15 @@ __device__ inline double comp_factor_i(int l, int c)
 // with W_ab = P_ab + P_ba for off-diagonal primitive pairs (a pair stands for
 // itself and its mirror image) and W_ab = P_ab for i = j in a diagonal shell pair.
 // ---------------------------------------------------------------------------
+// flag[r] (first npair bytes): pair kept and both primitives on one atom;
+// flag[npair + r]: kept and on two atoms.  Same-atom pairs (centre P = the
+// atom) come first in the ESP list; PCM_MIXED evaluates them more precisely.
 template <int LA, int LB>
 __global__ void esp_flag_kernel(int npair, const int *__restrict__ sp, const int *__restrict__ ia,
                                 const int *__restrict__ ib, const int *__restrict__ spA, const int *__restrict__ spB,
-                                const int *__restrict__ sh_bf, const double *__restrict__ Q,
-                                const double *__restrict__ Pm, int nbf, double thresh, unsigned char *__restrict__ flag)
+                                const int *__restrict__ sh_bf, const int *__restrict__ sh_atom,
+                                const double *__restrict__ Q, const double *__restrict__ Pm, int nbf, double thresh,
+                                unsigned char *__restrict__ flag)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= npair) return;
@@ -57,7 +61,10 @@ __global__ void esp_flag_kernel(int npair, const int *__restrict__ sp, const int
             if (mirror) w += Pm[(size_t)(fb + b) * nbf + fa + a];
             wmax = fmax(wmax, fabs(w));
         }
-    flag[r] = (thresh <= 0.0 || wmax * Q[r] >= thresh) ? 1 : 0;
+    const bool kept = thresh <= 0.0 || wmax * Q[r] >= thresh;
+    const bool same = sh_atom[A] == sh_atom[B];
+    flag[r] = (kept && same) ? 1 : 0;
+    flag[(size_t)npair + r] = (kept && !same) ? 1 : 0;
 }
 
 template <int LA, int LB>
@@ -437,17 +444,23 @@ static int esp_prepare_class(pcm_ctx *c, PairClass &pc, const double *dP)
 {
     pc.nesp = 0;
     if (pc.npair == 0) return PCM_OK;
-    PCM_TRY(c->flags8.alloc(pc.npair));
+    PCM_TRY(c->flags8.alloc(2 * (size_t)pc.npair));
     PCM_TRY(c->idx32.alloc(pc.npair));
     esp_flag_kernel<LA, LB><<<(pc.npair + 127) / 128, 128, 0, c->stream>>>(
-        pc.npair, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_bf.p, pc.Q.p, dP, c->nbf, c->opt.schwarz,
-        c->flags8.p);
+        pc.npair, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_bf.p, c->sh_atom.p, pc.Q.p, dP, c->nbf,
+        c->opt.schwarz, c->flags8.p);
     PCM_LAUNCHED(c);
+    // same-atom pairs first, then the others, each in pair order
     PCM_TRY(compact_flags(c, c->flags8.p, pc.npair, c->idx32.p, nullptr, c->iscal.p));
-    int n = 0;
-    PCM_CUDA(cudaMemcpyAsync(&n, c->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    int cnt[2] = {0, 0};
+    PCM_CUDA(cudaMemcpyAsync(&cnt[0], c->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
+    PCM_TRY(compact_flags(c, c->flags8.p + pc.npair, pc.npair, c->idx32.p + cnt[0], nullptr, c->iscal.p + 1));
+    PCM_CUDA(cudaMemcpyAsync(&cnt[1], c->iscal.p + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PCM_CUDA(cudaStreamSynchronize(c->stream));
+    const int n = cnt[0] + cnt[1];
     pc.nesp = n;
+    pc.nesp_same = cnt[0];
     if (n == 0) return PCM_OK;
     constexpr int NH = nherm(LA + LB);
     PCM_TRY(pc.eP.alloc(4 * (size_t)n));

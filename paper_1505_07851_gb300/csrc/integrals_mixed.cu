@@ -95,6 +95,71 @@ __global__ void esp_mixed_prep_kernel(int nesp, int ncls, const double *__restri
     }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float helpers (a value carried as hi + lo FP32 parts) for the pairs
+// whose two primitives sit on one atom: their contributions are the largest
+// terms of every c_k, and their FP32 rounding sets the error of the energy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+// F_0 (hi, lo) and F_1..F_MM (FP32) at T = Th + Tl
+template <int MM>
+__device__ __forceinline__ void boys_df(float Th, float Tl, const float *__restrict__ tab, float &F0h, float &F0l,
+                                        float (&F)[MM + 1])
+{
+    if (Th < (float)BOYS_TMAX) {
+        const float t = fmaf(Th, (float)BOYS_INV_DT, 12582912.0f);
+        const int i = __float_as_int(t) - 0x4B400000;
+        const float d = fmaf(t - 12582912.0f, -(float)BOYS_DT, Th) + Tl;
+        const float *row = tab + i * BOYS_STRIDE32;
+        float r[MM + 5], lo[MM + 1];
+#pragma unroll
+        for (int k = 0; k < MM + 5; ++k) r[k] = __ldg(row + k);
+#pragma unroll
+        for (int k = 0; k <= MM; ++k) lo[k] = __ldg(row + BOYS_LO32 + k);
+        const float e1 = -d, e2 = -d * 0.5f, e3 = -d * (1.0f / 3.0f), e4 = -d * 0.25f;
+#pragma unroll
+        for (int m = 0; m <= MM; ++m) {
+            float s = fmaf(r[m + 4], e4, r[m + 3]);
+            s = fmaf(s, e3, r[m + 2]);
+            s = fmaf(s, e2, r[m + 1]);
+            const float corr = fmaf(s, e1, lo[m]);
+            if (m == 0) {
+                F0h = r[0];
+                F0l = corr;
+            }
+            F[m] = corr + r[m];
+        }
+    } else {
+        constexpr float C_HI = 0.88622692545275801365f;
+        constexpr float C_LO = (float)(0.88622692545275801365 - (double)C_HI);
+        const float r0 = rsqrtf(Th);
+        // 1/sqrt(T) = r0 (1 + e/2) with e = 1 - T r0^2 formed to ~2^-48
+        const float hh = Th * r0;
+        const float hl = fmaf(Th, r0, -hh);
+        const float e = (fmaf(-hh, r0, 1.0f) - hl * r0) - Tl * r0 * r0;
+        const float rsl = 0.5f * r0 * e;
+        F0h = C_HI * r0;
+        F0l = (fmaf(C_HI, r0, -F0h) + C_HI * rsl) + C_LO * r0;
+        const float rs = r0 + rsl;
+        const float half_inv_T = 0.5f * rs * rs;
+        F[0] = F0h + F0l;
+#pragma unroll
+        for (int m = 1; m <= MM; ++m) F[m] = F[m - 1] * (float)(2 * m - 1) * half_inv_T;
+    }
+}
+
 constexpr int MESP_NT = 128;
 constexpr int MESP_TP = 32;
 // points per thread: more independent work for the light classes
@@ -102,9 +167,10 @@ template <int L> struct EspPPT { static constexpr int value = L <= 1 ? 4 : 2; };
 
 // Per tile of TP pairs, shared memory holds per pair float4 (xh, yh, zh, rho_hi),
 // float4 (xl, yl, zl, rho_lo), rho_lo/rho_hi and NH float2 (hi, lo) of U D_h.
-template <int L>
-__global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int seglen, const float *__restrict__ eX,
-                                                          const float *__restrict__ eC, const int *__restrict__ blk_off,
+template <int L, bool SC>
+__global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int jbeg, int jend, int seglen,
+                                                          const float *__restrict__ eX, const float *__restrict__ eC,
+                                                          const int *__restrict__ blk_off,
                                                           const int *__restrict__ blk_cls, const float *__restrict__ ph,
                                                           const float *__restrict__ pl, const float *__restrict__ boys,
                                                           int M, double *__restrict__ part)
@@ -117,8 +183,8 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int seglen, 
     __shared__ float2 sD[NH][MESP_TP];
     const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
     const float *C = eC + (size_t)blk_cls[blockIdx.x] * F * nesp;
-    const int j0 = blockIdx.y * seglen;
-    const int j1 = min(nesp, j0 + seglen);
+    const int j0 = jbeg + blockIdx.y * seglen;
+    const int j1 = min(jend, j0 + seglen);
 
     float xh[PPT], yh[PPT], zh[PPT], xl[PPT], yl[PPT], zl[PPT];
     // Kahan-compensated FP32 sums over the whole segment: adding a small term
@@ -159,6 +225,54 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int seglen, 
             const float4 A = sA[jj], B = sB[jj];
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
+                if constexpr (SC) {
+                    // double-float distance, T, F_0 and D_000 F_0; the Hermite
+                    // terms beyond the charge stay FP32 (they are smaller)
+                    float X, Xl, Y, Yl, Z, Zl;
+                    two_sum(A.x - xh[q], B.x - xl[q], X, Xl);
+                    two_sum(A.y - yh[q], B.y - yl[q], Y, Yl);
+                    two_sum(A.z - zh[q], B.z - zl[q], Z, Zl);
+                    const float p1 = X * X, p2 = Y * Y, p3 = Z * Z;
+                    const float e1 = fmaf(X, X, -p1), e2 = fmaf(Y, Y, -p2), e3 = fmaf(Z, Z, -p3);
+                    float s1, t1, s2, t2;
+                    two_sum(p1, p2, s1, t1);
+                    two_sum(s1, p3, s2, t2);
+                    const float lo = ((e1 + e2) + e3) + (t1 + t2) + 2.f * (X * Xl + Y * Yl + Z * Zl);
+                    float R2h, R2l;
+                    fast_two_sum(s2, lo, R2h, R2l);
+                    const float Th = A.w * R2h;
+                    const float Tl = fmaf(A.w, R2h, -Th) + (A.w * R2l + B.w * R2h);
+                    float F0h, F0l, Fb[L + 1];
+                    boys_df<L>(Th, Tl, boys, F0h, F0l, Fb);
+                    const float2 D0 = sD[0][jj];
+                    const float ph0 = D0.x * F0h;
+                    const float pl0 = (fmaf(D0.x, F0h, -ph0) + D0.x * F0l) + D0.y * F0h;
+                    float rest = 0.f;
+                    if constexpr (L > 0) {
+                        const float dr = sR[jj];
+                        const float m2r = -2.f * A.w;
+                        float Rn[L + 1];
+                        float f = 1.f;
+#pragma unroll
+                        for (int n = 0; n <= L; ++n) {
+                            const float v = f * Fb[n];
+                            Rn[n] = (n == 0) ? v : fmaf(v, (float)n * dr, v);
+                            f *= m2r;
+                        }
+                        float R[NH];
+                        hermite_R<L, float>(X, Y, Z, Rn, R);
+#pragma unroll
+                        for (int h = 1; h < NH; ++h) {
+                            const float2 D = sD[h][jj];
+                            rest = fmaf(D.x, R[h], fmaf(D.y, R[h], rest));
+                        }
+                    }
+                    const float y = (ph0 - k32[q]) + (pl0 + rest);
+                    const float t = a32[q] + y;
+                    k32[q] = (t - a32[q]) - y;
+                    a32[q] = t;
+                    continue;
+                }
                 const float X = (A.x - xh[q]) + (B.x - xl[q]);
                 const float Y = (A.y - yh[q]) + (B.y - yl[q]);
                 const float Z = (A.z - zh[q]) + (B.z - zl[q]);
@@ -306,9 +420,25 @@ __global__ void esp_reduce_mixed_kernel(int M, int nseg, const double *__restric
 // ---------------------------------------------------------------------------
 static const int CLASS_L[6] = {0, 1, 2, 2, 3, 4};
 
+// segments of [0, n) pairs for nblk point blocks: enough CTAs to fill the GPU
+static void esp_plan(int n, int nblk, int *seglen, int *rows)
+{
+    if (n <= 0) {
+        *seglen = 0;
+        *rows = 0;
+        return;
+    }
+    const int target = 152 * 8;
+    const int maxseg = (n + MESP_TP - 1) / MESP_TP;
+    const int ns = std::max(1, std::min(maxseg, (target + nblk - 1) / nblk));
+    int sl = (n + ns - 1) / ns;
+    sl = (sl + MESP_TP - 1) / MESP_TP * MESP_TP;
+    *seglen = sl;
+    *rows = (n + sl - 1) / sl;
+}
+
 template <int L>
-static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, const int *bcls, int nblk, int nseg,
-                            int seglen, double *part)
+static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, const int *bcls, int nblk, double *part)
 {
     constexpr int NH = nherm(L);
     constexpr int F = 3 + 2 * NH;
@@ -319,10 +449,24 @@ static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, co
                                                                      pc.eX32.p, pc.eC32.p);
     PCM_LAUNCHED(c);
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[k], c->stream));
-    dim3 grid(nblk, nseg);
-    esp_kernel_f32<L><<<grid, MESP_NT, 0, c->stream>>>(n, seglen, pc.eX32.p, pc.eC32.p, blk, bcls, c->p32.p,
-                                                        c->p32lo.p, c->boys32.p, c->M, part);
-    PCM_LAUNCHED(c);
+    // same-atom pairs [0, nesp_same) in double-float, the rest in FP32
+    const int ns = pc.nesp_same, nx = n - ns;
+    int sl, rows;
+    esp_plan(ns, nblk, &sl, &rows);
+    if (rows > 0) {
+        dim3 grid(nblk, rows);
+        esp_kernel_f32<L, true><<<grid, MESP_NT, 0, c->stream>>>(n, 0, ns, sl, pc.eX32.p, pc.eC32.p, blk, bcls,
+                                                                  c->p32.p, c->p32lo.p, c->boys32.p, c->M, part);
+        PCM_LAUNCHED(c);
+        part += (size_t)rows * c->M;
+    }
+    esp_plan(nx, nblk, &sl, &rows);
+    if (rows > 0) {
+        dim3 grid(nblk, rows);
+        esp_kernel_f32<L, false><<<grid, MESP_NT, 0, c->stream>>>(n, ns, n, sl, pc.eX32.p, pc.eC32.p, blk, bcls,
+                                                                   c->p32.p, c->p32lo.p, c->boys32.p, c->M, part);
+        PCM_LAUNCHED(c);
+    }
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[k], c->stream));
     return PCM_OK;
 }
@@ -349,20 +493,15 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
         PCM_CUDA(cudaMemcpyAsync(bcls[v].p, bc[v].data(), bc[v].size() * sizeof(int), cudaMemcpyHostToDevice,
                                  c->stream));
     }
-    int nseg[6], seglen[6], total = 0;
-    const int target = 152 * 8;
+    int rows[6], total = 0;
     for (int k = 0; k < 6; ++k) {
         PairClass &pc = c->cls[k];
-        nseg[k] = seglen[k] = 0;
         const int nblk = (int)bc[CLASS_L[k] <= 1 ? 0 : 1].size();
-        if (pc.nesp == 0) continue;
-        const int maxseg = (pc.nesp + MESP_TP - 1) / MESP_TP;
-        int ns = std::max(1, std::min(maxseg, (target + nblk - 1) / nblk));
-        int sl = (pc.nesp + ns - 1) / ns;
-        sl = (sl + MESP_TP - 1) / MESP_TP * MESP_TP;
-        nseg[k] = (pc.nesp + sl - 1) / sl;
-        seglen[k] = sl;
-        total += nseg[k];
+        int sl, r1, r2;
+        esp_plan(pc.nesp_same, nblk, &sl, &r1);
+        esp_plan(pc.nesp - pc.nesp_same, nblk, &sl, &r2);
+        rows[k] = r1 + r2;
+        total += rows[k];
     }
     if (total == 0) {
         PCM_CUDA(cudaMemsetAsync(dc, 0, c->M * sizeof(double), c->stream));
@@ -378,13 +517,13 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
         const int v = CLASS_L[k] <= 1 ? 0 : 1;
         const int nblk = (int)bc[v].size();
         switch (CLASS_L[k]) {
-        case 0: PCM_TRY(esp_mixed_launch<0>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
-        case 1: PCM_TRY(esp_mixed_launch<1>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
-        case 2: PCM_TRY(esp_mixed_launch<2>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
-        case 3: PCM_TRY(esp_mixed_launch<3>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
-        case 4: PCM_TRY(esp_mixed_launch<4>(c, pc, k, blk[v].p, bcls[v].p, nblk, nseg[k], seglen[k], part)); break;
+        case 0: PCM_TRY(esp_mixed_launch<0>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
+        case 1: PCM_TRY(esp_mixed_launch<1>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
+        case 2: PCM_TRY(esp_mixed_launch<2>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
+        case 3: PCM_TRY(esp_mixed_launch<3>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
+        case 4: PCM_TRY(esp_mixed_launch<4>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
         }
-        base += nseg[k];
+        base += rows[k];
     }
     esp_reduce_mixed_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
     PCM_LAUNCHED(c);
