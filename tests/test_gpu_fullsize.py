@@ -1,0 +1,121 @@
+"""Full-size checks on the 300-atom cluster (M = 11973, nbf = 1662), in the
+configuration bench.py times (Schwarz screening 1e-12, RBJ-100, the Eq. 21
+threshold for a 1e-6 Eh energy error), against the oracle on sampled
+outputs it computes one by one, and against properties that hold at any
+size.  Tolerances: unscreened FP64 1e-10 relative (normwise); screened FP64
+1e-8 (screening drops pairs with Schwarz bound below 1e-12); mixed 1e-6;
+energies 1e-6 Eh against the FP64 solve at delta = 1e-10."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+DELTA = (1e-6 / 0.01) ** (1.0 / 1.07)
+
+
+@pytest.fixture(scope="module")
+def full():
+    import paper_1505_07851_gb300 as pcm
+    w = workloads.config(1)
+    out = {"w": w}
+    for name, prec, schwarz, delta in (("fp64", "fp64", 1e-12, DELTA), ("mixed", "mixed", 1e-12, DELTA),
+                                       ("tight", "fp64", 1e-12, 1e-10), ("noscreen", "fp64", 0.0, 1e-10)):
+        with pcm.Context(precision=prec, schwarz=schwarz) as ctx:
+            M, nbf = ctx.setup(w.mol, w.basis)
+            Bz = np.zeros(M)
+            c = ctx.esp(w.P, bz_out=Bz)
+            q, st = ctx.solve(delta=delta)
+            dF = ctx.fock(q)
+            E = ctx.energy(q)
+            xyzzs, idx = ctx.get_surface()
+        out[name] = dict(c=c, q=q, st=st, dF=dF, E=E, Bz=Bz, xyzzs=xyzzs, idx=idx)
+    s = oracle.surface(w.mol.xyz, w.mol.radius)
+    out["surf"] = s
+    out["eb"] = oracle.ExpandedBasis(w.basis, w.mol.xyz)
+    pos = {int(k): i for i, k in enumerate(s["index"])}
+    out["perm"] = np.array([pos[int(k)] for k in out["fp64"]["idx"]])
+    return out
+
+
+def test_surface_size_and_order(full):
+    assert len(full["fp64"]["c"]) == len(full["surf"]["zeta"]) == 11973
+    for name in ("mixed", "tight", "noscreen"):
+        assert np.array_equal(full[name]["idx"], full["fp64"]["idx"])
+
+
+def test_esp_sampled_against_oracle(full):
+    rng = np.random.default_rng(11)
+    s, p = full["surf"], full["perm"]
+    sample = rng.choice(len(p), 24, replace=False)
+    ref = oracle.esp(full["eb"], full["w"].P, s["r"][p[sample]], s["zeta"][p[sample]])
+    scale = np.max(np.abs(ref))
+    for name, tol in (("noscreen", 1e-10), ("fp64", 1e-8), ("mixed", 1e-6)):
+        err = np.max(np.abs(full[name]["c"][sample] - ref)) / scale
+        assert err <= tol, (name, err)
+
+
+def test_fock_sampled_against_oracle(full):
+    rng = np.random.default_rng(12)
+    eb, s, p = full["eb"], full["surf"], full["perm"]
+    pairs = [tuple(sorted(rng.choice(eb.nshell, 2, replace=False))) for _ in range(10)]
+    pairs += [(a, a) for a in rng.choice(eb.nshell, 4, replace=False)]
+    for name, tol in (("noscreen", 1e-10), ("fp64", 1e-8), ("mixed", 1e-6)):
+        g = full[name]
+        q_o = np.empty_like(g["q"])
+        q_o[p] = g["q"]
+        blocks = oracle.fock_blocks(eb, q_o, s["r"], s["zeta"], pairs)
+        scale = np.max(np.abs(g["dF"]))
+        for (a, b), blk in zip(pairs, blocks):
+            ia, ib = eb.sh_bf[a], eb.sh_bf[b]
+            got = g["dF"][ia:ia + blk.shape[0], ib:ib + blk.shape[1]]
+            assert np.max(np.abs(got - blk)) <= tol * scale, (name, a, b)
+
+
+def test_energy_at_the_eq21_threshold(full):
+    E_ref = full["tight"]["E"]
+    assert abs(full["fp64"]["E"] - E_ref) <= 1e-6
+    assert abs(full["mixed"]["E"] - E_ref) <= 1e-6
+    assert abs(full["noscreen"]["E"] - E_ref) <= 1e-7
+    assert full["fp64"]["st"]["converged"] and full["mixed"]["st"]["converged"]
+    assert full["mixed"]["st"]["refinements"] >= 1
+
+
+def test_solution_residual_with_oracle_matrix(full):
+    g = full["fp64"]
+    xyzzs = g["xyzzs"]
+    A = oracle.a_matrix({"r": xyzzs[:, :3], "zeta": xyzzs[:, 3], "S": xyzzs[:, 4]})
+    f = oracle.f_factor()
+    for name in ("fp64", "mixed", "tight"):
+        h = full[name]
+        rhs = -f * (h["Bz"] + h["c"])
+        res = np.linalg.norm(A @ h["q"] - rhs)
+        delta = 1e-10 if name == "tight" else DELTA
+        # the recursively updated residual (FP64) or the true one (mixed) met delta
+        assert res <= 1.05 * delta + 1e-9 * np.linalg.norm(rhs), (name, res)
+
+
+def test_rbj_steps_match_oracle_pcg(full):
+    g = full["fp64"]
+    s, p = full["surf"], full["perm"]
+    A = oracle.a_matrix(s)
+    f = oracle.f_factor()
+    rhs = np.empty_like(g["c"])
+    rhs[p] = -f * (g["Bz"] + g["c"])
+    pc = oracle.Preconditioner(A, "rbj", 100, 0)
+    x, it, ok, rn = oracle.pcg(A, rhs, DELTA, pc)
+    assert ok and abs(it - g["st"]["iterations"]) <= 1, (it, g["st"]["iterations"])
+    # both solutions have residuals below delta, so they differ by at most 2 delta in the A norm
+    q_o = np.empty_like(g["q"])
+    q_o[p] = g["q"]
+    assert np.linalg.norm(A @ (q_o - x)) <= 2.1 * DELTA
+
+
+def test_duality_at_full_size(full):
+    w = full["w"]
+    g = full["noscreen"]
+    lhs = g["q"] @ g["c"]
+    rhs = np.sum(w.P * g["dF"])
+    assert abs(lhs - rhs) <= 1e-11 * (np.abs(g["q"]) @ np.abs(g["c"]))
