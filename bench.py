@@ -91,6 +91,10 @@ def flops_per_interaction_f32(L, kind):
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
 
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernels (profiles/); a kernel missing here reports traffic null.
+NCU_TRAFFIC_BYTES = {"esp_kernel_f32<L=1> (ps)": 35.884032e6 + 15.36e3}
+
 CLASS_L = [0, 1, 2, 2, 3, 4]
 CLASS_NAME = ["ss", "ps", "pp", "ds", "dp", "dd"]
 
@@ -325,7 +329,7 @@ def run_ours(args):
     ints_all = main["ints"] * world                 # every rank ran a molecule of the same size class
     value = ints_all / (total_ms_max * 1e-3)
     roofline = _dominant(main, args.precision, args.steps)
-    roofline["traffic"] = args.traffic
+    roofline["traffic"] = args.traffic if args.traffic is not None else NCU_TRAFFIC_BYTES.get(roofline["kernel"])
     s = main["stats"]
     ctx = main["ctx"]
 
