@@ -23,6 +23,15 @@
  * and the recurrences keep their point-charge form.  zeta = +inf gives the
  * ordinary point-charge nuclear attraction integrals (U = 1).
  *
+ * Gradient (Eq. 14, Eq. 22): the derivative of sum_k q_k c_k with respect
+ * to the nuclear positions at fixed P.  Each integral depends on the centre
+ * of chi_a (the atom of its shell), the centre of chi_b and the point r_k,
+ * which moves with the atom of its sphere.  The centre derivatives follow
+ * from differentiating the primitive itself,
+ *   d/dA_x [x_A^ax ... exp(-alpha r_A^2)] = 2 alpha G_{a+1_x} - ax G_{a-1_x},
+ * and the point derivative from translational invariance,
+ *   d/dC = -(d/dA + d/dB).
+ *
  * Boys function: the series e^-T sum_i (2T)^i / ((2m+1)(2m+3)...(2m+2i+1))
  * for T < 30, else F_0 = (1/2) sqrt(pi/T) erf(sqrt T) and upward recursion.
  * No screening of any kind is applied.
@@ -263,5 +272,92 @@ void oracle_fock_pairs(const int *sh_atom, const int *sh_l, const int *sh_nprim,
                         zeta[k], blk);
             for (int t = 0; t < na * nb; t++) o[t] -= q[k] * blk[t];
         }
+    }
+}
+
+/* Position of the Cartesian component with exponents e in shell l (the order
+ * of cart_exponents). */
+static int cart_index(int l, const int e[3])
+{
+    int m = l - e[0];
+    return m * (m + 1) / 2 + (m - e[1]);
+}
+
+/* Gradient of sum_k q_k c_k = -sum_k q_k sum_{mu nu} P_{mu nu} (mu|J_k|nu)
+ * with respect to the nuclear positions at fixed P (the second term of
+ * Eq. 14, split as in Eq. 22 into the bra-centre, ket-centre and point parts).
+ * point_atom[k]: the atom whose sphere holds point k.  grad: natom*3,
+ * accumulated into (the caller zeroes it).  Points with q_k = 0 are skipped. */
+void oracle_grad_c(int nshell, const int *sh_atom, const int *sh_l, const int *sh_nprim, const int *sh_off,
+                   const int *sh_bf, const double *exps, const double *coefs, const double *axyz, int nbf,
+                   const double *P, int npts, const double *pts, const double *zeta, const double *q,
+                   const int *point_atom, int natom, double *grad)
+{
+#pragma omp parallel
+    {
+        double *g = (double *)calloc((size_t)natom * 3, sizeof(double));
+        /* raw blocks of (la+1, lb), (la-1, lb), (la, lb+1), (la, lb-1): at most
+         * ncart(3) x ncart(2) = 60 entries each */
+        double up_a[60], dn_a[60], up_b[60], dn_b[60];
+#pragma omp for schedule(dynamic, 1)
+        for (int k = 0; k < npts; k++) {
+            if (q[k] == 0.0) continue;
+            const double *C = pts + 3 * k;
+            for (int sa = 0; sa < nshell; sa++)
+                for (int sb = sa; sb < nshell; sb++) {
+                    const int la = sh_l[sa], lb = sh_l[sb];
+                    const int na = oracle_ncart(la), nb = oracle_ncart(lb);
+                    const int IA = sh_atom[sa], IB = sh_atom[sb], IC = point_atom[k];
+                    const double *A = axyz + 3 * IA, *B = axyz + 3 * IB;
+                    const double w = (sa == sb) ? 1.0 : 2.0;
+                    for (int i = 0; i < sh_nprim[sa]; i++)
+                        for (int j = 0; j < sh_nprim[sb]; j++) {
+                            const double al = exps[sh_off[sa] + i], be = exps[sh_off[sb] + j];
+                            const double cc = coefs[sh_off[sa] + i] * coefs[sh_off[sb] + j];
+                            oracle_prim(la + 1, al, A, lb, be, B, C, zeta[k], up_a);
+                            if (la > 0) oracle_prim(la - 1, al, A, lb, be, B, C, zeta[k], dn_a);
+                            oracle_prim(la, al, A, lb + 1, be, B, C, zeta[k], up_b);
+                            if (lb > 0) oracle_prim(la, al, A, lb - 1, be, B, C, zeta[k], dn_b);
+                            const int nbu = oracle_ncart(lb + 1), nbd = lb > 0 ? oracle_ncart(lb - 1) : 0;
+                            for (int ia = 0; ia < na; ia++) {
+                                int ea[3] = {0, 0, 0};
+                                cart_exponents(la, ia, ea);
+                                const double Na = oracle_norm(al, ea[0], ea[1], ea[2]);
+                                for (int ib = 0; ib < nb; ib++) {
+                                    int eb[3] = {0, 0, 0};
+                                    cart_exponents(lb, ib, eb);
+                                    const double Nb = oracle_norm(be, eb[0], eb[1], eb[2]);
+                                    const double Pw = P[(size_t)(sh_bf[sa] + ia) * nbf + sh_bf[sb] + ib];
+                                    /* this integral's weight in sum_k q_k c_k */
+                                    const double s = -q[k] * w * Pw * cc * Na * Nb;
+                                    for (int d = 0; d < 3; d++) {
+                                        int e1[3] = {ea[0], ea[1], ea[2]};
+                                        e1[d] += 1;
+                                        double dA = 2.0 * al * up_a[cart_index(la + 1, e1) * nb + ib];
+                                        if (ea[d] > 0) {
+                                            int e2[3] = {ea[0], ea[1], ea[2]};
+                                            e2[d] -= 1;
+                                            dA -= ea[d] * dn_a[cart_index(la - 1, e2) * nb + ib];
+                                        }
+                                        int f1[3] = {eb[0], eb[1], eb[2]};
+                                        f1[d] += 1;
+                                        double dB = 2.0 * be * up_b[ia * nbu + cart_index(lb + 1, f1)];
+                                        if (eb[d] > 0) {
+                                            int f2[3] = {eb[0], eb[1], eb[2]};
+                                            f2[d] -= 1;
+                                            dB -= eb[d] * dn_b[ia * nbd + cart_index(lb - 1, f2)];
+                                        }
+                                        g[3 * IA + d] += s * dA;
+                                        g[3 * IB + d] += s * dB;
+                                        g[3 * IC + d] -= s * (dA + dB);
+                                    }
+                                }
+                            }
+                        }
+                }
+        }
+#pragma omp critical
+        for (int t = 0; t < natom * 3; t++) grad[t] += g[t];
+        free(g);
     }
 }

@@ -17,6 +17,10 @@ Contents, each following the passage cited:
     test of Eq. 20 (Section 4b), the RBJ permutation of Section 4b-ii.
   * dynamic_delta(): Eq. 21 and the rule that follows it.
   * energy(): Eq. 13.
+  * gradient_bz(), gradient_a(), gradient_c(), gradient(): the nuclear
+    gradient of Eq. 13 at fixed P and q (Eq. 14, Eq. 22), with the points
+    moving with their atoms and the switching function of Eq. 9
+    differentiated.
 
 Readings of the paper where it is silent or garbled (shared with the CUDA
 path as specification, not as code):
@@ -64,6 +68,8 @@ def lib():
                                  ctypes.c_int, dp, dp, dp]
         L.oracle_fock_pairs.argtypes = [ip, ip, ip, ip, dp, dp, dp, ctypes.c_int, dp, dp, dp,
                                         ctypes.c_int, ip, ip, ctypes.POINTER(ctypes.c_long), dp]
+        L.oracle_grad_c.argtypes = [ctypes.c_int, ip, ip, ip, ip, ip, dp, dp, dp, ctypes.c_int, dp,
+                                    ctypes.c_int, dp, dp, dp, ip, ctypes.c_int, dp]
         _lib = L
     return _lib
 
@@ -437,3 +443,100 @@ def run(w, eps=78.39, k=0.0, zeta=4.9, n=110, drop=1e-8, delta=None, prev_diis=N
     out["E"] = energy(Bz_, c, q, A, f)
     out["E_lu"] = energy(Bz_, c, q_lu, A, f)
     return out
+
+
+# --------------------------------------------------------------------------
+# Nuclear gradient at fixed P and q (Eq. 14, Eq. 22)
+# --------------------------------------------------------------------------
+# Every surface point r_k = R_I + R_I u_i moves with its atom I = atom[k];
+# zeta_k does not depend on the geometry.  Derivatives of erf(z d)/d:
+#   d/dd [erf(z d) / d] = (2 z / sqrt(pi)) exp(-z^2 d^2) / d - erf(z d) / d^2.
+
+def _derf_over_r(z, d):
+    return 2.0 * z / math.sqrt(math.pi) * np.exp(-(z * d) ** 2) / d - erf(z * d) / d ** 2
+
+
+def gradient_bz(surf, xyz, Z, q):
+    """d/dR of (B z)^T q (Eq. 4, first term of Eq. 14): natom x 3."""
+    xyz = np.asarray(xyz, np.float64)
+    r, z, atom = surf["r"], surf["zeta"], surf["atom"]
+    natom = len(xyz)
+    g = np.zeros((natom, 3))
+    for J in range(natom):
+        v = r - xyz[J]
+        d = np.linalg.norm(v, axis=1)
+        # d/dr_k of q_k Z_J erf(zeta_k d)/d; r_k moves with atom[k], R_J with J
+        t = (q * Z[J] * _derf_over_r(z, d) / d)[:, None] * v
+        for x in range(3):
+            g[:, x] += np.bincount(atom, weights=t[:, x], minlength=natom)
+        g[J] -= t.sum(axis=0)
+    return g
+
+
+def gradient_a(surf, xyz, radius, q, f):
+    """d/dR of q^T A q / (2 f) (Eq. 2, Eq. 3, Eq. 8, Eq. 9; third term of
+    Eq. 14): off-diagonal erf(zeta' r)/r terms and the diagonal through the
+    switching values S_k.  natom x 3."""
+    xyz = np.asarray(xyz, np.float64)
+    radius = np.asarray(radius, np.float64)
+    r, z, atom, S = surf["r"], surf["zeta"], surf["atom"], surf["S"]
+    natom = len(xyz)
+    M = len(z)
+    g = np.zeros((natom, 3))
+    nz = np.nonzero(q)[0]
+    # off-diagonal: sum over ordered pairs k != l of q_k q_l A_kl / (2 f);
+    # d/dr_k A_kl = h'(r_kl) (r_k - r_l) / r_kl = -d/dr_l A_kl
+    for b0 in range(0, len(nz), 512):
+        kk = nz[b0:b0 + 512]
+        v = r[kk, None, :] - r[None, nz, :]
+        d = np.linalg.norm(v, axis=2)
+        zp = z[kk, None] * z[None, nz] / np.sqrt(z[kk, None] ** 2 + z[None, nz] ** 2)   # Eq. 8
+        same = kk[:, None] == nz[None, :]
+        d_safe = np.where(same, 1.0, d)
+        coef = np.where(same, 0.0, q[kk, None] * q[None, nz] * _derf_over_r(zp, d_safe) / d_safe) / (2.0 * f)
+        t = coef[:, :, None] * v                       # d/dr_k of the (k, l) term
+        tk = t.sum(axis=1)
+        tl = t.sum(axis=0)
+        for x in range(3):
+            g[:, x] += np.bincount(atom[kk], weights=tk[:, x], minlength=natom)
+            g[:, x] -= np.bincount(atom[nz], weights=tl[:, x], minlength=natom)
+    # diagonal: A_kk = zeta_k sqrt(2/pi) / S_k with S_k = prod_{J != atom[k]} s_J (Eq. 9);
+    # d/dd s_J = (zeta/sqrt(pi)) [exp(-zeta^2 (R_J - d)^2) - exp(-zeta^2 (R_J + d)^2)],
+    # d A_kk = -A_kk d ln S_k
+    Akk = z * math.sqrt(2.0 / math.pi) / S
+    for J in range(natom):
+        v = r - xyz[J]
+        d = np.linalg.norm(v, axis=1)
+        sJ = switching_factor(z, d, radius[J])
+        ds = z / math.sqrt(math.pi) * (np.exp(-(z * (radius[J] - d)) ** 2) - np.exp(-(z * (radius[J] + d)) ** 2))
+        other = atom != J
+        coef = np.where(other, -(q * q) / (2.0 * f) * Akk * ds / np.where(other, sJ, 1.0) / d, 0.0)
+        t = coef[:, None] * v                          # d/dr_k; R_J gets the opposite
+        for x in range(3):
+            g[:, x] += np.bincount(atom, weights=t[:, x], minlength=natom)
+        g[J] -= t.sum(axis=0)
+    return g
+
+
+def gradient_c(eb: ExpandedBasis, P, q, surf):
+    """d/dR of c^T q at fixed P (second term of Eq. 14, Eq. 22): natom x 3."""
+    natom = len(eb.xyz)
+    g = np.zeros(natom * 3)
+    pts = np.ascontiguousarray(surf["r"], np.float64)
+    lib().oracle_grad_c(eb.nshell, _i(eb.sh_atom), _i(eb.sh_l), _i(eb.sh_nprim), _i(eb.sh_off),
+                        _i(eb.sh_bf), _d(eb.exps), _d(eb.coefs), _d(eb.xyz), eb.nbf,
+                        _d(np.ascontiguousarray(P, np.float64)), len(pts), _d(pts),
+                        _d(np.asarray(surf["zeta"], np.float64)), _d(np.asarray(q, np.float64)),
+                        _i(surf["atom"]), natom, _d_out(g))
+    return g.reshape(natom, 3)
+
+
+def gradient(eb: ExpandedBasis, P, q, surf, xyz, Z, radius, f):
+    """Eq. 14: z^T (dB^T) q + (d*c^T) q + q^T (dA) q / (2 f) at fixed P and
+    q.  At the solution of Eq. 1 this is the derivative of Delta G_els
+    (Eq. 13) at fixed P, because Delta G_els is stationary in q there.
+    Returns dict with the three terms and their sum (natom x 3 each)."""
+    gb = gradient_bz(surf, xyz, Z, q)
+    ga = gradient_a(surf, xyz, radius, q, f)
+    gc = gradient_c(eb, P, q, surf)
+    return {"B": gb, "A": ga, "C": gc, "total": gb + ga + gc}
