@@ -13,6 +13,7 @@
  *   L^k_{mu nu} = -(mu | erf(zeta_k |r - r_k|)/|r - r_k| | nu)   (Eq. 6, Eq. 12)
  *   dF_{mu nu} = sum_k q_k L^k_{mu nu}                    (Eq. 10)
  *   dG = (Bz)^T q + c^T q + q^T A q / (2 f)               (Eq. 13)
+ *   d*dG/dR = z^T (dB^T/dR) q + (d*c^T/dR) q + q^T (dA/dR) q / (2 f)   (Eq. 14, Eq. 22)
  *
  * Units: atomic units (bohr, hartree).
  *
@@ -62,6 +63,9 @@ typedef enum pcm_status {
 #define PCM_PTR_DEVICE 1        /* array arguments are device pointers */
 #define PCM_ASYNC 2             /* do not synchronise the stream before returning */
 #define PCM_WARM 4              /* pcm_solve: q holds the initial guess */
+#define PCM_GRAD_B 8            /* pcm_gradient: include z^T (dB^T/dR) q */
+#define PCM_GRAD_C 16           /* pcm_gradient: include (d*c^T/dR) q (the integrals) */
+#define PCM_GRAD_A 32           /* pcm_gradient: include q^T (dA/dR) q / (2 f) (with switching) */
 
 /* precision modes */
 #define PCM_FP64 0              /* every step in FP64 */
@@ -110,6 +114,8 @@ typedef struct pcm_stats {
     double ms_solve;            /* with timing: device time of the last pcm_solve (ms) */
     double ms_precond;          /* with timing: preconditioner set-up inside that solve (ms) */
     long long launches;         /* kernels launched by this context since its creation */
+    double integrals_grad;      /* equivalent Cartesian primitive integrals of the last pcm_gradient (two passes) */
+    double ms_grad;             /* with timing: device time of the last pcm_gradient (ms) */
 } pcm_stats;
 
 typedef struct pcm_ctx pcm_ctx;
@@ -182,6 +188,21 @@ int pcm_fock(pcm_ctx *ctx, const double *q, double *dF, int flags);
  * E = (Bz)^T q + c^T q + q^T A q / (2 f).  q, c: M inputs (c may be NULL
  * for the last pcm_esp result).  E: one host double. */
 int pcm_energy(pcm_ctx *ctx, const double *q, const double *c, double *E, int flags);
+
+/* Nuclear gradient of the solvation energy at fixed density and charges
+ * (Eq. 14; its integral term split as in Eq. 22), in hartree/bohr:
+ *   g_I = z^T (dB^T/dR_I) q + (d*c^T/dR_I) q + q^T (dA/dR_I) q / (2 f)
+ * where every surface point moves with its atom, the diagonal of A varies
+ * through the switching factors S_k (Eq. 9), and d* leaves P fixed.  At the
+ * solution q of Eq. 1 this is the derivative of Eq. 13 at fixed P (Eq. 13 is
+ * stationary in q there); the density's own response is the caller's.
+ * P: nbf*nbf symmetric (may be NULL when PCM_GRAD_C is not requested);
+ * q: M charges in library order; grad: natom*3 outputs.  Needs
+ * pcm_build_surface (and pcm_set_basis for the integral term).  flags:
+ * PCM_PTR_DEVICE, PCM_ASYNC, and any of PCM_GRAD_B / PCM_GRAD_C / PCM_GRAD_A
+ * to select terms (none of them: all three).  Primitive pairs are screened
+ * as in pcm_esp (Eq. 18).  Computed in FP64 in both precision modes. */
+int pcm_gradient(pcm_ctx *ctx, const double *P, const double *q, double *grad, int flags);
 
 /* Statistics of the context's last calls. */
 int pcm_get_stats(pcm_ctx *ctx, pcm_stats *st);

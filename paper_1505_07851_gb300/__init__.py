@@ -14,6 +14,12 @@ this package fails if the compiled library is missing.
     q, st = ctx.solve(prev_diis_error=-1)            # pcm_solve
     dF = ctx.fock(q)                                 # pcm_fock
     E = ctx.energy(q)                                # pcm_energy
+    g = ctx.gradient(q, P)                           # pcm_gradient
+
+``SolvationEnergy`` wraps the whole path as a torch.autograd.Function of the
+nuclear positions and the density: its backward is pcm_gradient (Eq. 14) for
+the positions and pcm_fock (Eq. 10, the derivative of Eq. 13 with respect to
+P) for the density.
 """
 from __future__ import annotations
 
@@ -35,6 +41,9 @@ PCM_ERR_TIMEOUT = 6
 PCM_PTR_DEVICE = 1
 PCM_ASYNC = 2
 PCM_WARM = 4
+PCM_GRAD_B = 8
+PCM_GRAD_C = 16
+PCM_GRAD_A = 32
 PCM_FP64 = 0
 PCM_MIXED = 1
 PRECOND = {"auto": 0, "none": 1, "jacobi": 2, "rbj": 3}
@@ -56,7 +65,8 @@ class pcm_stats(ctypes.Structure):
                 ("integrals_esp", ctypes.c_double), ("integrals_fock", ctypes.c_double),
                 ("esp_class_pairs", ctypes.c_longlong * 6), ("fock_class_pairs", ctypes.c_longlong * 6),
                 ("ms_esp_class", ctypes.c_double * 6), ("ms_fock_class", ctypes.c_double * 6),
-                ("ms_solve", ctypes.c_double), ("ms_precond", ctypes.c_double), ("launches", ctypes.c_longlong)]
+                ("ms_solve", ctypes.c_double), ("ms_precond", ctypes.c_double), ("launches", ctypes.c_longlong),
+                ("integrals_grad", ctypes.c_double), ("ms_grad", ctypes.c_double)]
 
     def as_dict(self):
         out = {}
@@ -94,6 +104,7 @@ def _load():
         "pcm_solve": (i, [vp, vp, d, d, vp, ctypes.POINTER(pcm_stats), i]),
         "pcm_fock": (i, [vp, vp, vp, i]),
         "pcm_energy": (i, [vp, vp, vp, ctypes.POINTER(d), i]),
+        "pcm_gradient": (i, [vp, vp, vp, vp, i]),
         "pcm_get_stats": (i, [vp, ctypes.POINTER(pcm_stats)]),
         "pcm_energy_noalloc": (i, [i, vp, i, vp, vp, vp, d, vp, vp]),
     }
@@ -163,6 +174,8 @@ class Context:
         self.options = o
         self.M = 0
         self.nbf = 0
+        self.natom = 0
+        self.generation = 0          # incremented by every build_surface
 
     def _check(self, st, where, ok=(PCM_OK,)):
         if st not in ok:
@@ -196,6 +209,8 @@ class Context:
                                            int(pts_per_sphere), ctypes.byref(M)), "pcm_build_surface")
         self.M = M.value
         self.nbf = 0
+        self.natom = len(Z)
+        self.generation += 1
         return self.M
 
     def get_surface(self):
@@ -265,6 +280,23 @@ class Context:
         self._check(_lib.pcm_energy(self._h, pq, pc, ctypes.byref(E), fl), "pcm_energy")
         return E.value
 
+    def gradient(self, q, P=None, out=None, terms="BCA", async_=False):
+        """Nuclear gradient (natom, 3) of Eq. 13 at fixed P and q (Eq. 14):
+        terms is any combination of "B" (z^T dB q), "C" (the integrals, needs
+        P) and "A" (q^T dA q / 2f, with the switching factors)."""
+        pq, fl, keep = _ptr(q, np.float64)
+        pP, flP, keepP = _ptr(P, np.float64)
+        g = out if out is not None else self._out(q, (self.natom, 3))
+        pg, flg, keepg = _ptr(g, np.float64)
+        if flg != fl or (P is not None and flP != fl):
+            raise TypeError("q, P and the output must live on the same side (host or device)")
+        bits = {"B": PCM_GRAD_B, "C": PCM_GRAD_C, "A": PCM_GRAD_A}
+        flags = fl | (PCM_ASYNC if async_ else 0)
+        for t in terms:
+            flags |= bits[t]
+        self._check(_lib.pcm_gradient(self._h, pP, pq, pg, flags), "pcm_gradient")
+        return g
+
     def stats(self):
         st = pcm_stats()
         self._check(_lib.pcm_get_stats(self._h, ctypes.byref(st)), "pcm_get_stats")
@@ -276,3 +308,63 @@ class Context:
         M = self.build_surface(mol.xyz, mol.Z, mol.radius, pts_per_sphere)
         nbf = self.set_basis(basis.shell_atom, basis.shell_l, basis.shell_nprim, basis.exps, basis.coefs)
         return M, nbf
+
+
+# --------------------------------------------------------------------------
+# autograd
+# --------------------------------------------------------------------------
+def _autograd_function():
+    import torch
+
+    class SolvationEnergy(torch.autograd.Function):
+        """Delta G_els (Eq. 13) as a function of the nuclear positions xyz
+        (natom, 3) and the density P (nbf, nbf, CUDA float64), with q solved
+        from Eq. 1 to `delta` in the forward pass.  Backward: dG/dxyz by
+        pcm_gradient (Eq. 14; exact at the solution of Eq. 1 because Eq. 13 is
+        stationary in q) and dG/dP = dF by pcm_fock (Eq. 10)."""
+
+        @staticmethod
+        def forward(fctx, xyz, P, pcm, mol, basis, delta):
+            x = xyz.detach().to("cpu", torch.float64).numpy()
+            pcm.build_surface(x, mol.Z, mol.radius)
+            pcm.set_basis(basis.shell_atom, basis.shell_l, basis.shell_nprim, basis.exps, basis.coefs)
+            Pd = P.detach().contiguous()
+            pcm.esp(Pd)
+            q, _ = pcm.solve(delta=delta, like=Pd)
+            E = pcm.energy(q)
+            fctx.save_for_backward(Pd, q)
+            fctx.pcm, fctx.mol, fctx.basis = pcm, mol, basis
+            fctx.generation = pcm.generation
+            fctx.x = x
+            fctx.xyz_device = xyz.device
+            return torch.tensor(E, dtype=torch.float64, device=P.device)
+
+        @staticmethod
+        def backward(fctx, gE):
+            Pd, q = fctx.saved_tensors
+            pcm = fctx.pcm
+            if pcm.generation != fctx.generation:        # the context moved on: rebuild this geometry
+                b = fctx.basis
+                pcm.build_surface(fctx.x, fctx.mol.Z, fctx.mol.radius)
+                pcm.set_basis(b.shell_atom, b.shell_l, b.shell_nprim, b.exps, b.coefs)
+                fctx.generation = pcm.generation
+            gx = gP = None
+            if fctx.needs_input_grad[0]:
+                gx = (gE * pcm.gradient(q, Pd)).to(fctx.xyz_device)
+            if fctx.needs_input_grad[1]:
+                gP = gE * pcm.fock(q)
+            return gx, gP, None, None, None, None
+
+    return SolvationEnergy
+
+
+def solvation_energy(xyz, P, pcm, mol, basis, delta=1e-10):
+    """Differentiable Delta G_els(xyz, P) on the context `pcm` (see
+    SolvationEnergy); mol supplies Z and the cavity radii, basis the shells."""
+    global SolvationEnergy
+    if SolvationEnergy is None:
+        SolvationEnergy = _autograd_function()
+    return SolvationEnergy.apply(xyz, P, pcm, mol, basis, float(delta))
+
+
+SolvationEnergy = None

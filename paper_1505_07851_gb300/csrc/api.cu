@@ -415,6 +415,42 @@ int pcm_energy(pcm_ctx *c, const double *q, const double *cv, double *E, int fla
     return PCM_OK;
 }
 
+int pcm_gradient(pcm_ctx *c, const double *P, const double *q, double *grad, int flags)
+{
+    if (!c || !q || !grad || c->M == 0) {
+        set_last_error("pcm_gradient: bad arguments");
+        return PCM_ERR_ARG;
+    }
+    int terms = flags & (PCM_GRAD_B | PCM_GRAD_C | PCM_GRAD_A);
+    if (terms == 0) terms = PCM_GRAD_B | PCM_GRAD_C | PCM_GRAD_A;
+    if ((terms & PCM_GRAD_C) && (!P || c->nbf == 0)) {
+        set_last_error("pcm_gradient: the integral term needs P and pcm_set_basis");
+        return PCM_ERR_ARG;
+    }
+    DeviceGuard g(c->device);
+    const double *dq, *dP = nullptr;
+    DBuf<double> &stq = c->sd[3];
+    PCM_TRY(to_device(c, q, c->M, stq, &dq, flags));
+    if (terms & PCM_GRAD_C) PCM_TRY(to_device(c, P, (size_t)c->nbf * c->nbf, c->dP, &dP, flags));
+    double *dg = grad;
+    if (!(flags & PCM_PTR_DEVICE)) {
+        PCM_TRY(c->g_out.alloc(3 * (size_t)c->natom));
+        dg = c->g_out.p;
+    }
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[12], c->stream));
+    PCM_TRY(gradient_compute(c, dP, dq, terms, dg));
+    if (c->have_events) {
+        PCM_CUDA(cudaEventRecord(c->ev_b[12], c->stream));
+        PCM_CUDA(cudaEventSynchronize(c->ev_b[12]));
+        float ms = 0.f;
+        PCM_CUDA(cudaEventElapsedTime(&ms, c->ev_a[12], c->ev_b[12]));
+        c->stats.ms_grad = ms;
+    }
+    if (!(flags & PCM_PTR_DEVICE))
+        PCM_CUDA(cudaMemcpyAsync(grad, dg, 3 * (size_t)c->natom * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return finish(c, flags);
+}
+
 int pcm_get_stats(pcm_ctx *c, pcm_stats *st)
 {
     if (!c || !st) return PCM_ERR_ARG;

@@ -91,6 +91,10 @@ struct PairClass {
     DBuf<double> eP, eD;                   // eP: 4 x nesp (Px, Py, Pz, p); eD: nherm x nesp
     DBuf<float> eX32, eC32;                // PCM_MIXED ESP: 6 x nesp split centres; ncls x (3 + 2 nherm) x nesp constants
     DBuf<float> Pxyz32;                    // 6 x npair: hi (3) and lo (3) FP32 parts of the centre (Fock, PCM_MIXED)
+    DBuf<int> elist;                       // nesp: ESP pair -> kept pair index (valid after each ESP preparation)
+    // shell pairs by atom for the gradient: entry 2 s + side (side 0: atom of A, 1: atom of B)
+    bool csr_ready = false;
+    DBuf<int> csr_off, csr_ent;            // natom + 1 offsets, 2 nsp entries
 };
 
 struct pcm_ctx_impl;
@@ -162,9 +166,12 @@ struct pcm_ctx {
     double *h_pinned = nullptr;            // pinned host scratch for scalars
 
     // integral scratch
-    pcm::DBuf<double> esp_part;            // nseg x M partial potentials
+    pcm::DBuf<double> esp_part;            // nseg x M partial potentials (x 3 for the gradient)
     pcm::DBuf<double> fock_W;              // nsplit x nherm x npair accumulators
     pcm::DBuf<double> dP, dF;              // device copies of P and dF for host-pointer calls
+    // gradient scratch
+    pcm::DBuf<int> patom, arange;          // atom of each point; per-atom point range (2 x natom)
+    pcm::DBuf<double> g_pt, g_atom, g_pair, g_full, g_out;  // 3 x M, natom x 3, natom x 3, 6 x npair, natom x 3
     pcm::DBuf<double> vin, vout;           // device copies of M-vectors for host-pointer calls
     pcm::DBuf<unsigned char> flags8;
     pcm::DBuf<int> idx32, scan32;
@@ -196,6 +203,10 @@ int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit
 int solver_prepare(pcm_ctx *c);
 int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st);
 int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E);
+// gradient (gradient.cu, integrals.cu)
+int esp_prepare_all(pcm_ctx *c, const double *dP);
+int grad_integrals(pcm_ctx *c, const double *dP, const double *dq, double *gk, double *gpair);
+int gradient_compute(pcm_ctx *c, const double *dP, const double *dq, int terms, double *dgrad);
 
 // stable compaction of n byte flags: out[j] = i of the j-th nonzero flag (if
 // out != nullptr), pos[i] = number of nonzero flags before i (n + 1 entries,

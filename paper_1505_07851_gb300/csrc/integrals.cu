@@ -398,6 +398,268 @@ __global__ void fock_epilogue_kernel(int nsp, int npair, int nsplit, const int *
         }
 }
 
+
+// ---------------------------------------------------------------------------
+// Integral part of the nuclear gradient (Eq. 14, second term; Eq. 22).
+// Each integral [a|J_k|b] depends on the centre of a, the centre of b and the
+// point r_k, which moves with its atom.
+//
+// Point part (gc of Eq. 22): d/dC R_tuv(P - C) = -R_{t+1,u,v} (and y, z), so
+//   d c_k / dC_k = -sum_pairs U sum_tuv eD_tuv R_{tuv + 1_d}
+// with the ESP pairs' density coefficients eD (t+u+v <= L) and R up to L+1.
+// One thread per point as in the ESP kernel; three sums per point.
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(ESP_NT) esp_grad_kernel(int nesp, int seglen, const double *__restrict__ eP,
+                                                          const double *__restrict__ eD,
+                                                          const int *__restrict__ blk_off,
+                                                          const double *__restrict__ px, const double *__restrict__ py,
+                                                          const double *__restrict__ pz, const int *__restrict__ pcls,
+                                                          const double *__restrict__ cls_zeta,
+                                                          const double *__restrict__ boys, int M,
+                                                          double *__restrict__ part)
+{
+    constexpr int NH = nherm(L);
+    constexpr int L1 = L + 1;
+    constexpr int NH1 = nherm(L1);
+    __shared__ double sP[4][ESP_TP];
+    __shared__ double sD[NH][ESP_TP];
+    __shared__ double sRho[ESP_MAXCB][ESP_TP];
+    __shared__ double sU[ESP_MAXCB][ESP_TP];
+
+    const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
+    const int cmin = pcls[k0];
+    const int ncb = pcls[k1 - 1] - cmin + 1;
+    const int j0 = blockIdx.y * seglen;
+    const int j1 = min(nesp, j0 + seglen);
+
+    double x[ESP_PPT], y[ESP_PPT], z[ESP_PPT], gx[ESP_PPT], gy[ESP_PPT], gz[ESP_PPT];
+    int e[ESP_PPT];
+    bool on[ESP_PPT];
+#pragma unroll
+    for (int q = 0; q < ESP_PPT; ++q) {
+        const int k = k0 + threadIdx.x + q * ESP_NT;
+        on[q] = k < k1;
+        const int kk = on[q] ? k : k0;
+        x[q] = px[kk];
+        y[q] = py[kk];
+        z[q] = pz[kk];
+        e[q] = pcls[kk] - cmin;
+        gx[q] = gy[q] = gz[q] = 0.0;
+    }
+
+    for (int jt = j0; jt < j1; jt += ESP_TP) {
+        const int nt = min(ESP_TP, j1 - jt);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 4 * ESP_TP; t += ESP_NT) {
+            const int f = t / ESP_TP, jj = t % ESP_TP;
+            sP[f][jj] = jj < nt ? eP[(size_t)f * nesp + jt + jj] : 1.0;
+        }
+        for (int t = threadIdx.x; t < NH * ESP_TP; t += ESP_NT) {
+            const int h = t / ESP_TP, jj = t % ESP_TP;
+            sD[h][jj] = jj < nt ? eD[(size_t)h * nesp + jt + jj] : 0.0;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ncb * ESP_TP; t += ESP_NT) {
+            const int ec = t / ESP_TP, jj = t % ESP_TP;
+            const double zz = cls_zeta[cmin + ec];
+            const double z2 = zz * zz;
+            const double p = sP[3][jj];
+            const double inv = 1.0 / (p + z2);
+            sRho[ec][jj] = p * z2 * inv;
+            sU[ec][jj] = sqrt(z2 * inv);
+        }
+        __syncthreads();
+        for (int jj = 0; jj < nt; ++jj) {
+            const double Px = sP[0][jj], Py = sP[1][jj], Pz = sP[2][jj];
+#pragma unroll
+            for (int q = 0; q < ESP_PPT; ++q) {
+                const double rho = sRho[e[q]][jj];
+                const double X = Px - x[q], Y = Py - y[q], Z = Pz - z[q];
+                const double T = rho * (X * X + Y * Y + Z * Z);
+                double F[L1 + 1];
+                boys_eval<L1>(T, boys, F);
+                double Rn[L1 + 1];
+                double m2r = -2.0 * rho, f = 1.0;
+#pragma unroll
+                for (int n = 0; n <= L1; ++n) {
+                    Rn[n] = f * F[n];
+                    f *= m2r;
+                }
+                double R[NH1];
+                hermite_R<L1, double>(X, Y, Z, Rn, R);
+                double sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+                for (int t = 0; t <= L; ++t)
+#pragma unroll
+                    for (int u = 0; u <= L - t; ++u)
+#pragma unroll
+                        for (int v = 0; v <= L - t - u; ++v) {
+                            const double d = sD[hidx(t, u, v)][jj];
+                            sx = fma(d, R[hidx(t + 1, u, v)], sx);
+                            sy = fma(d, R[hidx(t, u + 1, v)], sy);
+                            sz = fma(d, R[hidx(t, u, v + 1)], sz);
+                        }
+                const double U = sU[e[q]][jj];
+                gx[q] = fma(U, sx, gx[q]);
+                gy[q] = fma(U, sy, gy[q]);
+                gz[q] = fma(U, sz, gz[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < ESP_PPT; ++q) {
+        const int k = k0 + threadIdx.x + q * ESP_NT;
+        if (on[q]) {
+            part[((size_t)blockIdx.y * 3 + 0) * M + k] = gx[q];
+            part[((size_t)blockIdx.y * 3 + 1) * M + k] = gy[q];
+            part[((size_t)blockIdx.y * 3 + 2) * M + k] = gz[q];
+        }
+    }
+}
+
+// g[d][k] += -q_k sum over segments of the point-part sums, in segment order
+__global__ void grad_point_reduce_kernel(int M, int nseg, const double *__restrict__ part,
+                                         const double *__restrict__ q, double *__restrict__ g)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double s = 0.0;
+        for (int seg = 0; seg < nseg; ++seg) s += part[((size_t)seg * 3 + d) * M + k];
+        g[(size_t)d * M + k] -= q[k] * s;
+    }
+}
+
+// Bra- and ket-centre parts (ga, gb of Eq. 22) for one ESP pair.  With
+// W_tuv = sum_k q_k U_k R_tuv (t+u+v <= L+1, accumulated by the Fock kernel
+// over the ESP pairs) and the derivative of a Cartesian Gaussian with respect
+// to its centre, d/dA_x G_a = 2 alpha G_{a+1_x} - a_x G_{a-1_x},
+//   d/dA_x sum_k q_k c_k (this pair) = -(2 pi/p) K sum_ab w_ab
+//       sum_tuv (2 alpha E^{a+1_x,b}_t - a_x E^{a-1_x,b}_t) E^{ab}_u E^{ab}_v W_tuv
+// (w_ab the density weights of the ESP prologue), and likewise for y, z and
+// for the centre of b.  Written to gfull[d][r] (A) and gfull[3 + d][r] (B) at
+// the kept-pair index r.
+template <int LA, int LB>
+__global__ void grad_pair_kernel(int nesp, int npair, int nsplit, const int *__restrict__ elist,
+                                 const int *__restrict__ sp, const int *__restrict__ ia, const int *__restrict__ ib,
+                                 const int *__restrict__ spA, const int *__restrict__ spB,
+                                 const int *__restrict__ sh_atom, const int *__restrict__ sh_off,
+                                 const int *__restrict__ sh_bf, const double *__restrict__ exps,
+                                 const double *__restrict__ cnorm, const double *__restrict__ xyz,
+                                 const double *__restrict__ Px, const double *__restrict__ Py,
+                                 const double *__restrict__ Pz, const double *__restrict__ pp,
+                                 const double *__restrict__ pref, const double *__restrict__ Pm, int nbf,
+                                 const double *__restrict__ W, double *__restrict__ gfull)
+{
+    constexpr int L1 = LA + LB + 1;
+    constexpr int NH1 = nherm(L1);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nesp) return;
+    const int r = elist[j];
+    const int s = sp[r];
+    const int A = spA[s], B = spB[s];
+    const int i1 = ia[r], i2 = ib[r];
+    const bool mirror = (A != B) || (i1 != i2);
+    double w[NH1];
+#pragma unroll
+    for (int h = 0; h < NH1; ++h) {
+        double acc = 0.0;
+        for (int g = 0; g < nsplit; ++g) acc += W[((size_t)g * NH1 + h) * nesp + j];
+        w[h] = acc;
+    }
+    const double p = pp[r];
+    const double P[3] = {Px[r], Py[r], Pz[r]};
+    const double *RA = xyz + 3 * sh_atom[A], *RB = xyz + 3 * sh_atom[B];
+    E1T<LA + 1, LB + 1> Ex, Ey, Ez;
+    const double inv2p = 0.5 / p;
+    hermite_E1T<LA + 1, LB + 1>(P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
+    hermite_E1T<LA + 1, LB + 1>(P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
+    hermite_E1T<LA + 1, LB + 1>(P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
+    const double al2 = 2.0 * exps[sh_off[A] + i1], be2 = 2.0 * exps[sh_off[B] + i2];
+    const double cc = cnorm[sh_off[A] + i1] * cnorm[sh_off[B] + i2];
+    const int fa = sh_bf[A], fb = sh_bf[B];
+    double gA[3] = {0.0, 0.0, 0.0}, gB[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < ncart(LA); ++a) {
+        const int ax = cart_e(LA, a, 0), ay = cart_e(LA, a, 1), az = cart_e(LA, a, 2);
+#pragma unroll
+        for (int b = 0; b < ncart(LB); ++b) {
+            const int bx = cart_e(LB, b, 0), by = cart_e(LB, b, 1), bz = cart_e(LB, b, 2);
+            double wab = Pm[(size_t)(fa + a) * nbf + fb + b];
+            if (mirror) wab += Pm[(size_t)(fb + b) * nbf + fa + a];
+            wab *= cc * comp_factor_i(LA, a) * comp_factor_i(LB, b);
+            // one-dimensional factors: plain, centre-A derivative, centre-B derivative
+            double X0[L1 + 1], XA[L1 + 1], XB[L1 + 1], Y0[L1 + 1], YA[L1 + 1], YB[L1 + 1];
+            double Z0[L1 + 1], ZA[L1 + 1], ZB[L1 + 1];
+#pragma unroll
+            for (int t = 0; t <= L1; ++t) {
+                X0[t] = Ex.e[ax][bx][t];
+                Y0[t] = Ey.e[ay][by][t];
+                Z0[t] = Ez.e[az][bz][t];
+                XA[t] = al2 * Ex.e[ax + 1][bx][t] - (ax > 0 ? ax * Ex.e[ax > 0 ? ax - 1 : 0][bx][t] : 0.0);
+                YA[t] = al2 * Ey.e[ay + 1][by][t] - (ay > 0 ? ay * Ey.e[ay > 0 ? ay - 1 : 0][by][t] : 0.0);
+                ZA[t] = al2 * Ez.e[az + 1][bz][t] - (az > 0 ? az * Ez.e[az > 0 ? az - 1 : 0][bz][t] : 0.0);
+                XB[t] = be2 * Ex.e[ax][bx + 1][t] - (bx > 0 ? bx * Ex.e[ax][bx > 0 ? bx - 1 : 0][t] : 0.0);
+                YB[t] = be2 * Ey.e[ay][by + 1][t] - (by > 0 ? by * Ey.e[ay][by > 0 ? by - 1 : 0][t] : 0.0);
+                ZB[t] = be2 * Ez.e[az][bz + 1][t] - (bz > 0 ? bz * Ez.e[az][bz > 0 ? bz - 1 : 0][t] : 0.0);
+            }
+            double sA[3] = {0.0, 0.0, 0.0}, sB[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int t = 0; t <= L1; ++t)
+#pragma unroll
+                for (int u = 0; u <= L1 - t; ++u)
+#pragma unroll
+                    for (int v = 0; v <= L1 - t - u; ++v) {
+                        const double wh = w[hidx(t, u, v)];
+                        sA[0] += XA[t] * Y0[u] * Z0[v] * wh;
+                        sA[1] += X0[t] * YA[u] * Z0[v] * wh;
+                        sA[2] += X0[t] * Y0[u] * ZA[v] * wh;
+                        sB[0] += XB[t] * Y0[u] * Z0[v] * wh;
+                        sB[1] += X0[t] * YB[u] * Z0[v] * wh;
+                        sB[2] += X0[t] * Y0[u] * ZB[v] * wh;
+                    }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                gA[d] = fma(wab, sA[d], gA[d]);
+                gB[d] = fma(wab, sB[d], gB[d]);
+            }
+        }
+    }
+    const double scale = -pref[r];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        gfull[(size_t)d * npair + r] = scale * gA[d];
+        gfull[(size_t)(3 + d) * npair + r] = scale * gB[d];
+    }
+}
+
+// Per-atom sums of the pair parts: one block per atom walks its shell pairs
+// (entry 2 s + side) and their kept primitive pairs; fixed-order reduction.
+constexpr int GPA_NT = 128;
+__global__ void __launch_bounds__(GPA_NT) pair_atom_reduce_kernel(int natom, const int *__restrict__ off,
+                                                                  const int *__restrict__ ent,
+                                                                  const int *__restrict__ sp_start, int npair,
+                                                                  const double *__restrict__ gfull,
+                                                                  double *__restrict__ g)
+{
+    __shared__ double red[GPA_NT / 32];
+    const int I = blockIdx.x;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int e = off[I] + threadIdx.x; e < off[I + 1]; e += GPA_NT) {
+        const int s = ent[e] >> 1, side = ent[e] & 1;
+        for (int r = sp_start[s]; r < sp_start[s + 1]; ++r)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) acc[d] += gfull[(size_t)(3 * side + d) * npair + r];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double v = block_sum<double, GPA_NT>(acc[d], red);
+        if (threadIdx.x == 0) g[3 * I + d] += v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -445,17 +707,17 @@ static int esp_prepare_class(pcm_ctx *c, PairClass &pc, const double *dP)
     pc.nesp = 0;
     if (pc.npair == 0) return PCM_OK;
     PCM_TRY(c->flags8.alloc(2 * (size_t)pc.npair));
-    PCM_TRY(c->idx32.alloc(pc.npair));
+    PCM_TRY(pc.elist.alloc(pc.npair));
     esp_flag_kernel<LA, LB><<<(pc.npair + 127) / 128, 128, 0, c->stream>>>(
         pc.npair, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_bf.p, c->sh_atom.p, pc.Q.p, dP, c->nbf,
         c->opt.schwarz, c->flags8.p);
     PCM_LAUNCHED(c);
     // same-atom pairs first, then the others, each in pair order
-    PCM_TRY(compact_flags(c, c->flags8.p, pc.npair, c->idx32.p, nullptr, c->iscal.p));
+    PCM_TRY(compact_flags(c, c->flags8.p, pc.npair, pc.elist.p, nullptr, c->iscal.p));
     int cnt[2] = {0, 0};
     PCM_CUDA(cudaMemcpyAsync(&cnt[0], c->iscal.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
-    PCM_TRY(compact_flags(c, c->flags8.p + pc.npair, pc.npair, c->idx32.p + cnt[0], nullptr, c->iscal.p + 1));
+    PCM_TRY(compact_flags(c, c->flags8.p + pc.npair, pc.npair, pc.elist.p + cnt[0], nullptr, c->iscal.p + 1));
     PCM_CUDA(cudaMemcpyAsync(&cnt[1], c->iscal.p + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
     const int n = cnt[0] + cnt[1];
@@ -466,7 +728,7 @@ static int esp_prepare_class(pcm_ctx *c, PairClass &pc, const double *dP)
     PCM_TRY(pc.eP.alloc(4 * (size_t)n));
     PCM_TRY(pc.eD.alloc((size_t)NH * n));
     esp_coef_kernel<LA, LB><<<(n + 127) / 128, 128, 0, c->stream>>>(
-        n, c->idx32.p, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_off.p, c->sh_bf.p,
+        n, pc.elist.p, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_off.p, c->sh_bf.p,
         c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, dP, c->nbf, pc.eP.p, pc.eD.p);
     PCM_LAUNCHED(c);
     return PCM_OK;
@@ -486,7 +748,8 @@ static int esp_class_stats(pcm_ctx *c)
     return PCM_OK;
 }
 
-int esp_compute(pcm_ctx *c, const double *dP, double *dc)
+// density test and Hermite density coefficients of every class
+int esp_prepare_all(pcm_ctx *c, const double *dP)
 {
     PCM_TRY((esp_prepare_class<0, 0>(c, c->cls[0], dP)));
     PCM_TRY((esp_prepare_class<1, 0>(c, c->cls[1], dP)));
@@ -494,6 +757,12 @@ int esp_compute(pcm_ctx *c, const double *dP, double *dc)
     PCM_TRY((esp_prepare_class<2, 0>(c, c->cls[3], dP)));
     PCM_TRY((esp_prepare_class<2, 1>(c, c->cls[4], dP)));
     PCM_TRY((esp_prepare_class<2, 2>(c, c->cls[5], dP)));
+    return PCM_OK;
+}
+
+int esp_compute(pcm_ctx *c, const double *dP, double *dc)
+{
+    PCM_TRY(esp_prepare_all(c, dP));
 
     if (c->opt.precision == PCM_MIXED) {
         long long pesp = 0;
@@ -617,6 +886,137 @@ int fock_compute(pcm_ctx *c, const double *dq, double *ddF)
             c->stats.ms_fock_class[k] = ms;
         }
     }
+    return PCM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// integral part of the gradient (host side)
+// ---------------------------------------------------------------------------
+// shell pairs of a class listed by atom: for atom I, entries 2 s (atom of A is
+// I) and 2 s + 1 (atom of B is I), in increasing s
+static int pair_csr(pcm_ctx *c, PairClass &pc)
+{
+    if (pc.csr_ready) return PCM_OK;
+    const int natom = c->natom;
+    std::vector<int> off(natom + 1, 0), ent(2 * (size_t)pc.nsp);
+    for (int s = 0; s < pc.nsp; ++s) {
+        ++off[c->h_sh_atom[pc.h_spA[s]] + 1];
+        ++off[c->h_sh_atom[pc.h_spB[s]] + 1];
+    }
+    for (int I = 0; I < natom; ++I) off[I + 1] += off[I];
+    std::vector<int> pos(off.begin(), off.end() - 1);
+    for (int s = 0; s < pc.nsp; ++s) {
+        ent[pos[c->h_sh_atom[pc.h_spA[s]]]++] = 2 * s;
+        ent[pos[c->h_sh_atom[pc.h_spB[s]]]++] = 2 * s + 1;
+    }
+    PCM_TRY(pc.csr_off.alloc(natom + 1));
+    PCM_TRY(pc.csr_ent.alloc(ent.size()));
+    PCM_CUDA(cudaMemcpyAsync(pc.csr_off.p, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    if (!ent.empty())
+        PCM_CUDA(cudaMemcpyAsync(pc.csr_ent.p, ent.data(), ent.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 c->stream));
+    PCM_CUDA(cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+    pc.csr_ready = true;
+    return PCM_OK;
+}
+
+template <int L>
+static void launch_esp_grad(pcm_ctx *c, PairClass &pc, const int *blk, int nblk, int seg_base, int nseg_cls,
+                            int seglen)
+{
+    dim3 grid(nblk, nseg_cls);
+    esp_grad_kernel<L><<<grid, ESP_NT, 0, c->stream>>>(pc.nesp, seglen, pc.eP.p, pc.eD.p, blk, c->px.p, c->py.p,
+                                                        c->pz.p, c->pcls.p, c->cls_zeta.p, c->boys64.p, c->M,
+                                                        c->esp_part.p + (size_t)seg_base * 3 * c->M);
+}
+
+template <int LA, int LB>
+static int grad_pair_class(pcm_ctx *c, PairClass &pc, const double *dP, const double *dq, double *gpair)
+{
+    constexpr int L1 = LA + LB + 1;
+    constexpr int NH1 = nherm(L1);
+    if (pc.nesp == 0) return PCM_OK;
+    const int n = pc.nesp;
+    const int nb = (n + FOCK_NT - 1) / FOCK_NT;
+    const int maxsplit = std::max(1, (c->M + FOCK_TQ - 1) / FOCK_TQ);
+    int nsplit = std::max(1, std::min(maxsplit, (target_ctas(c) + nb - 1) / nb));
+    int ks = (c->M + nsplit - 1) / nsplit;
+    ks = (ks + FOCK_TQ - 1) / FOCK_TQ * FOCK_TQ;
+    nsplit = (c->M + ks - 1) / ks;
+    PCM_TRY(c->fock_W.alloc((size_t)nsplit * NH1 * n));
+    dim3 grid(nb, nsplit);
+    fock_kernel_f64<L1><<<grid, FOCK_NT, 0, c->stream>>>(n, pc.eP.p, pc.eP.p + n, pc.eP.p + 2 * (size_t)n,
+                                                          pc.eP.p + 3 * (size_t)n, ks, c->px.p, c->py.p, c->pz.p, dq,
+                                                          c->M, c->ncls, c->cls_off.p, c->cls_zeta.p, c->boys64.p,
+                                                          c->fock_W.p);
+    PCM_LAUNCHED(c);
+    PCM_TRY(c->g_full.alloc(6 * (size_t)pc.npair));
+    PCM_CUDA(cudaMemsetAsync(c->g_full.p, 0, 6 * (size_t)pc.npair * sizeof(double), c->stream));
+    grad_pair_kernel<LA, LB><<<(n + 127) / 128, 128, 0, c->stream>>>(
+        n, pc.npair, nsplit, pc.elist.p, pc.sp.p, pc.ia.p, pc.ib.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_off.p,
+        c->sh_bf.p, c->exps.p, c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, dP, c->nbf,
+        c->fock_W.p, c->g_full.p);
+    PCM_LAUNCHED(c);
+    PCM_TRY(pair_csr(c, pc));
+    pair_atom_reduce_kernel<<<c->natom, GPA_NT, 0, c->stream>>>(c->natom, pc.csr_off.p, pc.csr_ent.p, pc.sp_start.p,
+                                                                pc.npair, c->g_full.p, gpair);
+    PCM_LAUNCHED(c);
+    return PCM_OK;
+}
+
+// gk (3 x M): += the point part, -q_k d c_k / dC_k; gpair (natom x 3): += the
+// bra/ket-centre parts.  FP64 in both precision modes.
+int grad_integrals(pcm_ctx *c, const double *dP, const double *dq, double *gk, double *gpair)
+{
+    PCM_TRY(esp_prepare_all(c, dP));
+    std::vector<int> off;
+    esp_blocks(c, off);
+    const int nblk = (int)off.size() - 1;
+    DBuf<int> &blk = c->si[5];
+    PCM_TRY(blk.alloc(off.size()));
+    PCM_CUDA(cudaMemcpyAsync(blk.p, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    int nseg[6], seglen[6], total = 0;
+    double ints = 0.0;
+    for (int k = 0; k < 6; ++k) {
+        PairClass &pc = c->cls[k];
+        nseg[k] = seglen[k] = 0;
+        if (pc.nesp == 0) continue;
+        ints += (double)pc.nesp * ncart(pc.la) * ncart(pc.lb) * c->M;
+        const int maxseg = (pc.nesp + ESP_TP - 1) / ESP_TP;
+        int ns = std::max(1, std::min(maxseg, (target_ctas(c) + nblk - 1) / nblk));
+        int sl = (pc.nesp + ns - 1) / ns;
+        sl = (sl + ESP_TP - 1) / ESP_TP * ESP_TP;
+        nseg[k] = (pc.nesp + sl - 1) / sl;
+        seglen[k] = sl;
+        total += nseg[k];
+    }
+    c->stats.integrals_grad = 2.0 * ints;
+    if (total > 0) {
+        PCM_TRY(c->esp_part.alloc((size_t)total * 3 * c->M));
+        int base = 0;
+        static const int LSUM[6] = {0, 1, 2, 2, 3, 4};
+        for (int k = 0; k < 6; ++k) {
+            PairClass &pc = c->cls[k];
+            if (nseg[k] == 0) continue;
+            switch (LSUM[k]) {
+            case 0: launch_esp_grad<0>(c, pc, blk.p, nblk, base, nseg[k], seglen[k]); break;
+            case 1: launch_esp_grad<1>(c, pc, blk.p, nblk, base, nseg[k], seglen[k]); break;
+            case 2: launch_esp_grad<2>(c, pc, blk.p, nblk, base, nseg[k], seglen[k]); break;
+            case 3: launch_esp_grad<3>(c, pc, blk.p, nblk, base, nseg[k], seglen[k]); break;
+            case 4: launch_esp_grad<4>(c, pc, blk.p, nblk, base, nseg[k], seglen[k]); break;
+            }
+            PCM_LAUNCHED(c);
+            base += nseg[k];
+        }
+        grad_point_reduce_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dq, gk);
+        PCM_LAUNCHED(c);
+    }
+    PCM_TRY((grad_pair_class<0, 0>(c, c->cls[0], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<1, 0>(c, c->cls[1], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<1, 1>(c, c->cls[2], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<2, 0>(c, c->cls[3], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<2, 1>(c, c->cls[4], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<2, 2>(c, c->cls[5], dP, dq, gpair)));
     return PCM_OK;
 }
 

@@ -337,6 +337,7 @@ int basis_build(pcm_ctx *c, int nshell, const int *shell_atom, const int *shell_
         PairClass &pc = c->cls[k];
         pc.la = LA[k];
         pc.lb = LB[k];
+        pc.csr_ready = false;
         pc.nsp = (int)pc.h_spA.size();
         std::vector<long long> cand(pc.nsp + 1, 0);
         for (int s = 0; s < pc.nsp; ++s) {
