@@ -201,7 +201,10 @@ int pcm_energy(pcm_ctx *ctx, const double *q, const double *c, double *E, int fl
  * pcm_build_surface (and pcm_set_basis for the integral term).  flags:
  * PCM_PTR_DEVICE, PCM_ASYNC, and any of PCM_GRAD_B / PCM_GRAD_C / PCM_GRAD_A
  * to select terms (none of them: all three).  Primitive pairs are screened
- * as in pcm_esp (Eq. 18).  Computed in FP64 in both precision modes. */
+ * as in pcm_esp (Eq. 18).  PCM_FP64: every step in FP64.  PCM_MIXED: the
+ * integral kernels and the off-diagonal A term (once a solve has made the
+ * FP32 copy of A) run on the FP32 pipes with FP64 accumulation across tiles;
+ * the nuclear B term, the switching term and every reduction stay FP64. */
 int pcm_gradient(pcm_ctx *ctx, const double *P, const double *q, double *grad, int flags);
 
 /* Statistics of the context's last calls. */

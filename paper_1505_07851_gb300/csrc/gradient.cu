@@ -13,7 +13,9 @@
 //       the other atoms (Eq. 2, Eq. 3, Eq. 8, Eq. 9)
 //   C:  the integrals' bra, ket and point centres (integrals.cu)
 // Per-point contributions are summed per atom over its point range, per-atom
-// ones by one block per atom; every sum has a fixed order.
+// ones by one block per atom; every sum has a fixed order.  PCM_MIXED runs
+// the integral kernels and the off-diagonal A term on the FP32 pipes (FP64
+// accumulation across tiles); the B and switching terms stay FP64.
 #include <math.h>
 
 #include <algorithm>
@@ -206,6 +208,66 @@ __global__ void __launch_bounds__(GAO_NT) grad_aoff_kernel(int M, int lda, const
     }
 }
 
+// The same on the FP32 pipes (PCM_MIXED) from the FP32 copy of A and the
+// hi/lo split coordinates (hi on a 2^-10 grid, so hi differences are exact);
+// per-thread FP32 sums, the block reduction in FP64.
+__global__ void __launch_bounds__(GAO_NT) grad_aoff_kernel_f32(int M, int lda, const float *__restrict__ A,
+                                                               const float *__restrict__ ph,
+                                                               const float *__restrict__ pl,
+                                                               const int *__restrict__ pcls, int ncls,
+                                                               const double *__restrict__ cls_zeta,
+                                                               const double *__restrict__ q, double inv_f,
+                                                               double *__restrict__ g)
+{
+    __shared__ float zp_tab[16], zp2_tab[16];
+    __shared__ double red[GAO_NT / 32];
+    const int k = blockIdx.x;
+    const int ck = pcls[k];
+    for (int t = threadIdx.x; t < ncls && t < 16; t += GAO_NT) {
+        const double a = cls_zeta[ck], b = cls_zeta[t];
+        const double zp = a * b / sqrt(a * a + b * b);  // Eq. 8
+        zp_tab[t] = (float)zp;
+        zp2_tab[t] = (float)(zp * zp);
+    }
+    __syncthreads();
+    const float xh = ph[k], yh = ph[(size_t)M + k], zh = ph[2 * (size_t)M + k];
+    const float xl = pl[k], yl = pl[(size_t)M + k], zl = pl[2 * (size_t)M + k];
+    const float *row = A + (size_t)k * lda;
+    float a[3] = {0.f, 0.f, 0.f};
+    for (int l = threadIdx.x; l < M; l += GAO_NT) {
+        if (l == k) continue;
+        const float dx = (xh - ph[l]) + (xl - pl[l]);
+        const float dy = (yh - ph[(size_t)M + l]) + (yl - pl[(size_t)M + l]);
+        const float dz = (zh - ph[2 * (size_t)M + l]) + (zl - pl[2 * (size_t)M + l]);
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float Akl = row[l];
+        const int cl = pcls[l];
+        float zp, zp2;
+        if (ncls <= 16) {
+            zp = zp_tab[cl];
+            zp2 = zp2_tab[cl];
+        } else {
+            const double za = cls_zeta[ck], zb = cls_zeta[cl];
+            const double z = za * zb / sqrt(za * za + zb * zb);
+            zp = (float)z;
+            zp2 = (float)(z * z);
+        }
+        const float x2 = zp2 * d2;
+        const float t = (x2 > 36.f) ? -Akl * Akl * Akl
+                                    : (1.1283791670955126f * zp * __expf(-x2) - Akl) / d2;
+        const float w = (float)q[l] * t;
+        a[0] = fmaf(w, dx, a[0]);
+        a[1] = fmaf(w, dy, a[1]);
+        a[2] = fmaf(w, dz, a[2]);
+    }
+    const double s = q[k] * inv_f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double v = block_sum<double, GAO_NT>((double)a[d], red);
+        if (threadIdx.x == 0) g[(size_t)d * M + k] += s * v;
+    }
+}
+
 // grad[I] = sum over the points of I of g_pt + gJ[I] + gpair[I], one block per atom
 __global__ void __launch_bounds__(GPT_NT) grad_combine_kernel(int M, int natom, const int *__restrict__ range,
                                                               const double *__restrict__ gpt,
@@ -254,8 +316,13 @@ int gradient_compute(pcm_ctx *c, const double *dP, const double *dq, int terms, 
     PCM_LAUNCHED(c);
     // off-diagonal A
     if (terms & PCM_GRAD_A) {
-        grad_aoff_kernel<<<M, GAO_NT, 0, c->stream>>>(M, c->lda, c->A.p, c->px.p, c->py.p, c->pz.p, c->pcls.p,
-                                                      c->ncls, c->cls_zeta.p, dq, 1.0 / f, c->g_pt.p);
+        if (c->opt.precision == PCM_MIXED && c->a32_ready) {
+            grad_aoff_kernel_f32<<<M, GAO_NT, 0, c->stream>>>(M, c->lda, c->A32.p, c->p32.p, c->p32lo.p, c->pcls.p,
+                                                              c->ncls, c->cls_zeta.p, dq, 1.0 / f, c->g_pt.p);
+        } else {
+            grad_aoff_kernel<<<M, GAO_NT, 0, c->stream>>>(M, c->lda, c->A.p, c->px.p, c->py.p, c->pz.p, c->pcls.p,
+                                                          c->ncls, c->cls_zeta.p, dq, 1.0 / f, c->g_pt.p);
+        }
         PCM_LAUNCHED(c);
     }
     // integrals

@@ -944,12 +944,16 @@ static int grad_pair_class(pcm_ctx *c, PairClass &pc, const double *dP, const do
     ks = (ks + FOCK_TQ - 1) / FOCK_TQ * FOCK_TQ;
     nsplit = (c->M + ks - 1) / ks;
     PCM_TRY(c->fock_W.alloc((size_t)nsplit * NH1 * n));
-    dim3 grid(nb, nsplit);
-    fock_kernel_f64<L1><<<grid, FOCK_NT, 0, c->stream>>>(n, pc.eP.p, pc.eP.p + n, pc.eP.p + 2 * (size_t)n,
-                                                          pc.eP.p + 3 * (size_t)n, ks, c->px.p, c->py.p, c->pz.p, dq,
-                                                          c->M, c->ncls, c->cls_off.p, c->cls_zeta.p, c->boys64.p,
-                                                          c->fock_W.p);
-    PCM_LAUNCHED(c);
+    if (c->opt.precision == PCM_MIXED) {
+        PCM_TRY(grad_w_mixed(c, (int)(&pc - c->cls), dq, nsplit, ks, c->fock_W.p));
+    } else {
+        dim3 grid(nb, nsplit);
+        fock_kernel_f64<L1><<<grid, FOCK_NT, 0, c->stream>>>(n, pc.eP.p, pc.eP.p + n, pc.eP.p + 2 * (size_t)n,
+                                                              pc.eP.p + 3 * (size_t)n, ks, c->px.p, c->py.p, c->pz.p,
+                                                              dq, c->M, c->ncls, c->cls_off.p, c->cls_zeta.p,
+                                                              c->boys64.p, c->fock_W.p);
+        PCM_LAUNCHED(c);
+    }
     PCM_TRY(c->g_full.alloc(6 * (size_t)pc.npair));
     PCM_CUDA(cudaMemsetAsync(c->g_full.p, 0, 6 * (size_t)pc.npair * sizeof(double), c->stream));
     grad_pair_kernel<LA, LB><<<(n + 127) / 128, 128, 0, c->stream>>>(
@@ -964,11 +968,38 @@ static int grad_pair_class(pcm_ctx *c, PairClass &pc, const double *dP, const do
     return PCM_OK;
 }
 
+static int grad_pair_all(pcm_ctx *c, const double *dP, const double *dq, double *gpair)
+{
+    PCM_TRY((grad_pair_class<0, 0>(c, c->cls[0], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<1, 0>(c, c->cls[1], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<1, 1>(c, c->cls[2], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<2, 0>(c, c->cls[3], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<2, 1>(c, c->cls[4], dP, dq, gpair)));
+    PCM_TRY((grad_pair_class<2, 2>(c, c->cls[5], dP, dq, gpair)));
+    return PCM_OK;
+}
+
 // gk (3 x M): += the point part, -q_k d c_k / dC_k; gpair (natom x 3): += the
-// bra/ket-centre parts.  FP64 in both precision modes.
+// bra/ket-centre parts.  PCM_FP64: FP64 throughout; PCM_MIXED: the point part
+// and the W accumulation on the FP32 pipes (FP64 across tiles and segments),
+// the per-pair contraction and every reduction in FP64.
 int grad_integrals(pcm_ctx *c, const double *dP, const double *dq, double *gk, double *gpair)
 {
     PCM_TRY(esp_prepare_all(c, dP));
+    if (c->opt.precision == PCM_MIXED) {
+        double ints = 0.0;
+        for (int k = 0; k < 6; ++k)
+            ints += (double)c->cls[k].nesp * ncart(c->cls[k].la) * ncart(c->cls[k].lb) * c->M;
+        c->stats.integrals_grad = 2.0 * ints;
+        int total = 0;
+        PCM_TRY(grad_point_mixed(c, &total));
+        if (total > 0) {
+            grad_point_reduce_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dq,
+                                                                                  gk);
+            PCM_LAUNCHED(c);
+        }
+        return grad_pair_all(c, dP, dq, gpair);
+    }
     std::vector<int> off;
     esp_blocks(c, off);
     const int nblk = (int)off.size() - 1;
@@ -1011,13 +1042,7 @@ int grad_integrals(pcm_ctx *c, const double *dP, const double *dq, double *gk, d
         grad_point_reduce_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dq, gk);
         PCM_LAUNCHED(c);
     }
-    PCM_TRY((grad_pair_class<0, 0>(c, c->cls[0], dP, dq, gpair)));
-    PCM_TRY((grad_pair_class<1, 0>(c, c->cls[1], dP, dq, gpair)));
-    PCM_TRY((grad_pair_class<1, 1>(c, c->cls[2], dP, dq, gpair)));
-    PCM_TRY((grad_pair_class<2, 0>(c, c->cls[3], dP, dq, gpair)));
-    PCM_TRY((grad_pair_class<2, 1>(c, c->cls[4], dP, dq, gpair)));
-    PCM_TRY((grad_pair_class<2, 2>(c, c->cls[5], dP, dq, gpair)));
-    return PCM_OK;
+    return grad_pair_all(c, dP, dq, gpair);
 }
 
 }  // namespace pcm

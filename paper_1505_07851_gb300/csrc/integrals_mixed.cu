@@ -406,6 +406,126 @@ __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Point part of the integral gradient on the FP32 pipes (the FP64 statement
+// is esp_grad_kernel in integrals.cu): per point the three sums
+//   sum_pairs U sum_tuv eD_tuv R_{tuv + 1_d},  R up to L+1,
+// from the ESP pairs' split constants (eX, eC as prepared for the ESP), with
+// Kahan-compensated FP32 sums per segment.
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(MESP_NT) esp_grad_kernel_f32(int nesp, int seglen, const float *__restrict__ eX,
+                                                               const float *__restrict__ eC,
+                                                               const int *__restrict__ blk_off,
+                                                               const int *__restrict__ blk_cls,
+                                                               const float *__restrict__ ph,
+                                                               const float *__restrict__ pl,
+                                                               const float *__restrict__ boys, int M,
+                                                               double *__restrict__ part)
+{
+    constexpr int NH = nherm(L);
+    constexpr int L1 = L + 1;
+    constexpr int NH1 = nherm(L1);
+    constexpr int F = 3 + 2 * NH;
+    constexpr int PPT = EspPPT<L>::value;
+    __shared__ float4 sA[MESP_TP], sB[MESP_TP];
+    __shared__ float sR[MESP_TP];
+    __shared__ float2 sD[NH][MESP_TP];
+    const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
+    const float *C = eC + (size_t)blk_cls[blockIdx.x] * F * nesp;
+    const int j0 = blockIdx.y * seglen;
+    const int j1 = min(nesp, j0 + seglen);
+
+    float xh[PPT], yh[PPT], zh[PPT], xl[PPT], yl[PPT], zl[PPT];
+    float a32[3][PPT], k32[3][PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int k = min(k0 + (int)threadIdx.x + q * MESP_NT, k1 - 1);
+        xh[q] = ph[k];
+        yh[q] = ph[(size_t)M + k];
+        zh[q] = ph[2 * (size_t)M + k];
+        xl[q] = pl[k];
+        yl[q] = pl[(size_t)M + k];
+        zl[q] = pl[2 * (size_t)M + k];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) a32[d][q] = k32[d][q] = 0.f;
+    }
+    for (int jt = j0; jt < j1; jt += MESP_TP) {
+        const int nt = min(MESP_TP, j1 - jt);
+        __syncthreads();
+        for (int jj = threadIdx.x; jj < MESP_TP; jj += MESP_NT) {
+            const bool v = jj < nt;
+            const size_t j = jt + jj;
+            sA[jj] = v ? make_float4(eX[j], eX[(size_t)nesp + j], eX[2 * (size_t)nesp + j], C[j])
+                       : make_float4(0.f, 0.f, 0.f, 1.f);
+            sB[jj] = v ? make_float4(eX[3 * (size_t)nesp + j], eX[4 * (size_t)nesp + j], eX[5 * (size_t)nesp + j],
+                                     C[(size_t)nesp + j])
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            sR[jj] = v ? C[2 * (size_t)nesp + j] : 0.f;
+        }
+        for (int t = threadIdx.x; t < NH * MESP_TP; t += MESP_NT) {
+            const int h = t / MESP_TP, jj = t % MESP_TP;
+            sD[h][jj] = jj < nt ? make_float2(C[(size_t)(3 + h) * nesp + jt + jj], C[(size_t)(3 + NH + h) * nesp + jt + jj])
+                                : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int jj = 0; jj < nt; ++jj) {
+            const float4 A = sA[jj], B = sB[jj];
+            const float dr = sR[jj];
+            const float m2r = -2.f * A.w;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                const float X = (A.x - xh[q]) + (B.x - xl[q]);
+                const float Y = (A.y - yh[q]) + (B.y - yl[q]);
+                const float Z = (A.z - zh[q]) + (B.z - zl[q]);
+                const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+                const float T = fmaf(A.w, R2, B.w * R2);
+                float Fb[L1 + 1];
+                boys_eval<L1>(T, boys, Fb);
+                float Rn[L1 + 1];
+                float f = 1.f;
+#pragma unroll
+                for (int n = 0; n <= L1; ++n) {
+                    const float v = f * Fb[n];
+                    Rn[n] = (n == 0) ? v : fmaf(v, (float)n * dr, v);
+                    f *= m2r;
+                }
+                float R[NH1];
+                hermite_R<L1, float>(X, Y, Z, Rn, R);
+                float s[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int t = 0; t <= L; ++t)
+#pragma unroll
+                    for (int u = 0; u <= L - t; ++u)
+#pragma unroll
+                        for (int v = 0; v <= L - t - u; ++v) {
+                            const float2 D = sD[hidx(t, u, v)][jj];
+                            const float Dt = D.x + D.y;
+                            s[0] = fmaf(Dt, R[hidx(t + 1, u, v)], s[0]);
+                            s[1] = fmaf(Dt, R[hidx(t, u + 1, v)], s[1]);
+                            s[2] = fmaf(Dt, R[hidx(t, u, v + 1)], s[2]);
+                        }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float y = s[d] - k32[d][q];
+                    const float t = a32[d][q] + y;
+                    k32[d][q] = (t - a32[d][q]) - y;
+                    a32[d][q] = t;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int k = k0 + threadIdx.x + q * MESP_NT;
+        if (k < k1)
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                part[((size_t)blockIdx.y * 3 + d) * M + k] = (double)a32[d][q] - (double)k32[d][q];
+    }
+}
+
 __global__ void esp_reduce_mixed_kernel(int M, int nseg, const double *__restrict__ part, double *__restrict__ c)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -471,9 +591,11 @@ static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, co
     return PCM_OK;
 }
 
-int esp_compute_mixed(pcm_ctx *c, double *dc)
+// single-class point blocks of at most MESP_NT * PPT points (two layouts:
+// PPT 4 and 2) in c->si[4..5] (offsets) and c->si[6..7] (classes); returns
+// the number of blocks of each layout
+static int mixed_point_blocks(pcm_ctx *c, int nblk[2])
 {
-    // single-class point blocks of at most MESP_NT * PPT points (two layouts: PPT 4 and 2)
     std::vector<int> off[2], bc[2];
     for (int v = 0; v < 2; ++v) {
         const int cap = MESP_NT * (v == 0 ? 4 : 2);
@@ -484,7 +606,7 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
                 bc[v].push_back(e);
             }
     }
-    DBuf<int> *blk = &c->si[4], *bcls = &c->si[6];  // blk[0..1], bcls[0..1]
+    DBuf<int> *blk = &c->si[4], *bcls = &c->si[6];
     for (int v = 0; v < 2; ++v) {
         PCM_TRY(blk[v].alloc(off[v].size()));
         PCM_TRY(bcls[v].alloc(bc[v].size()));
@@ -492,11 +614,22 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
                                  c->stream));
         PCM_CUDA(cudaMemcpyAsync(bcls[v].p, bc[v].data(), bc[v].size() * sizeof(int), cudaMemcpyHostToDevice,
                                  c->stream));
+        nblk[v] = (int)bc[v].size();
     }
+    // the host vectors are read by the copies above before they go out of scope
+    PCM_CUDA(cudaStreamSynchronize(c->stream));
+    return PCM_OK;
+}
+
+int esp_compute_mixed(pcm_ctx *c, double *dc)
+{
+    int nb[2];
+    PCM_TRY(mixed_point_blocks(c, nb));
+    DBuf<int> *blk = &c->si[4], *bcls = &c->si[6];  // blk[0..1], bcls[0..1]
     int rows[6], total = 0;
     for (int k = 0; k < 6; ++k) {
         PairClass &pc = c->cls[k];
-        const int nblk = (int)bc[CLASS_L[k] <= 1 ? 0 : 1].size();
+        const int nblk = nb[CLASS_L[k] <= 1 ? 0 : 1];
         int sl, r1, r2;
         esp_plan(pc.nesp_same, nblk, &sl, &r1);
         esp_plan(pc.nesp - pc.nesp_same, nblk, &sl, &r2);
@@ -515,7 +648,7 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
         if (pc.nesp == 0) continue;
         double *part = c->esp_part.p + (size_t)base * c->M;
         const int v = CLASS_L[k] <= 1 ? 0 : 1;
-        const int nblk = (int)bc[v].size();
+        const int nblk = nb[v];
         switch (CLASS_L[k]) {
         case 0: PCM_TRY(esp_mixed_launch<0>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
         case 1: PCM_TRY(esp_mixed_launch<1>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
@@ -549,6 +682,92 @@ int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit
         PCM_FOCK_F32(3)
         PCM_FOCK_F32(4)
 #undef PCM_FOCK_F32
+    }
+    PCM_LAUNCHED(c);
+    return PCM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gradient (PCM_MIXED): point part and the W accumulation on the FP32 pipes
+// ---------------------------------------------------------------------------
+template <int L>
+static int grad_point_mixed_class(pcm_ctx *c, PairClass &pc, const int *blk, const int *bcls, int nblk,
+                                  double *part, int rows, int sl)
+{
+    constexpr int NH = nherm(L);
+    constexpr int F = 3 + 2 * NH;
+    const int n = pc.nesp;
+    PCM_TRY(pc.eX32.alloc(6 * (size_t)n));
+    PCM_TRY(pc.eC32.alloc((size_t)c->ncls * F * n));
+    esp_mixed_prep_kernel<L><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->ncls, c->cls_zeta.p, pc.eP.p, pc.eD.p,
+                                                                     pc.eX32.p, pc.eC32.p);
+    PCM_LAUNCHED(c);
+    dim3 grid(nblk, rows);
+    esp_grad_kernel_f32<L><<<grid, MESP_NT, 0, c->stream>>>(n, sl, pc.eX32.p, pc.eC32.p, blk, bcls, c->p32.p,
+                                                             c->p32lo.p, c->boys32.p, c->M, part);
+    PCM_LAUNCHED(c);
+    return PCM_OK;
+}
+
+// Point-part partial sums of every class into c->esp_part (rows x 3 x M);
+// *total_rows receives the number of rows.  Needs the ESP preparation.
+int grad_point_mixed(pcm_ctx *c, int *total_rows)
+{
+    int nb[2];
+    PCM_TRY(mixed_point_blocks(c, nb));
+    DBuf<int> *blk = &c->si[4], *bcls = &c->si[6];
+    int rows[6], sls[6], total = 0;
+    for (int k = 0; k < 6; ++k) {
+        esp_plan(c->cls[k].nesp, nb[CLASS_L[k] <= 1 ? 0 : 1], &sls[k], &rows[k]);
+        total += rows[k];
+    }
+    *total_rows = total;
+    if (total == 0) return PCM_OK;
+    PCM_TRY(c->esp_part.alloc((size_t)total * 3 * c->M));
+    int base = 0;
+    for (int k = 0; k < 6; ++k) {
+        PairClass &pc = c->cls[k];
+        if (rows[k] == 0) continue;
+        double *part = c->esp_part.p + (size_t)base * 3 * c->M;
+        const int v = CLASS_L[k] <= 1 ? 0 : 1;
+        switch (CLASS_L[k]) {
+#define PCM_GPM(LL)                                                                                      \
+    case LL:                                                                                             \
+        PCM_TRY(grad_point_mixed_class<LL>(c, pc, blk[v].p, bcls[v].p, nb[v], part, rows[k], sls[k])); \
+        break;
+            PCM_GPM(0)
+            PCM_GPM(1)
+            PCM_GPM(2)
+            PCM_GPM(3)
+            PCM_GPM(4)
+#undef PCM_GPM
+        }
+        base += rows[k];
+    }
+    return PCM_OK;
+}
+
+// W_tuv (t+u+v <= L+1) over the ESP pairs of class k on the FP32 pipes; the
+// pairs' split centres come from the point-part preparation (eX32)
+int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W)
+{
+    PairClass &pc = c->cls[k];
+    const int n = pc.nesp;
+    const int nb = (n + MF_NT - 1) / MF_NT;
+    dim3 grid(nb, nsplit);
+    switch (CLASS_L[k] + 1) {
+#define PCM_GW(LL)                                                                                             \
+    case LL:                                                                                                   \
+        fock_kernel_f32<LL><<<grid, MF_NT, 0, c->stream>>>(n, pc.eP.p + 3 * (size_t)n, pc.eX32.p, ksplit,        \
+                                                            c->p32.p, c->p32lo.p, dq, c->M, c->ncls,           \
+                                                            c->cls_off.p, c->cls_zeta.p, c->boys32.p, W);      \
+        break;
+        PCM_GW(1)
+        PCM_GW(2)
+        PCM_GW(3)
+        PCM_GW(4)
+        PCM_GW(5)
+#undef PCM_GW
     }
     PCM_LAUNCHED(c);
     return PCM_OK;

@@ -144,3 +144,31 @@ def test_gradient_errors():
         assert np.all(g == 0.0)
         with pytest.raises(pcm.PCMError):
             ctx.gradient(q, w.P, terms="C")
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def mixed_case(request):
+    pcm = _pcm()
+    w = CASES[request.param]()
+    o = oracle.run(w, delta=1e-10)
+    s = o["surf"]
+    og = oracle.gradient(o["eb"], w.P, o["q_lu"], s, w.mol.xyz, w.mol.Z, w.mol.radius, o["f"])
+    with pcm.Context(schwarz=0.0, precision="mixed") as ctx:
+        ctx.setup(w.mol, w.basis)
+        _, idx = ctx.get_surface()
+        ctx.esp(w.P)
+        ctx.solve(delta=1e-8)                  # makes the FP32 copy of A
+        q = o["q_lu"][_perm(idx, s["index"])]
+        g = {t: ctx.gradient(q, w.P, terms=t) for t in ("B", "C", "A")}
+        g["total"] = ctx.gradient(q, w.P)
+    return request.param, og, g
+
+
+@pytest.mark.parametrize("term", ["B", "C", "A", "total"])
+def test_mixed_gradient_matches_oracle(mixed_case, term):
+    """PCM_MIXED: FP32 integral and off-diagonal A kernels; the bar is
+    1e-5 Eh/bohr absolute, and 1e-6 relative to the largest component."""
+    name, og, g = mixed_case
+    err = np.max(np.abs(g[term] - og[term]))
+    assert err <= 1e-5, (name, term, err)
+    assert err <= 1e-6 * max(1.0, np.max(np.abs(og[term]))), (name, term, err)
