@@ -290,6 +290,26 @@ def _timed_steps(pcm, w, precision, args, dev, stream, flush, delta, steps, warm
     return out
 
 
+def _time_gradient(res, q, flush, stream, steps):
+    """Nuclear gradient (Eq. 14) on the step's final state: CUDA-event time
+    per call, L2 flushed before each call.  Returns (ms, gradient, stats)."""
+    import torch
+    ctx, Pd = res["ctx"], res["Pd"]
+    g = torch.empty((ctx.natom, 3), dtype=torch.float64, device=Pd.device)
+    ctx.gradient(q, Pd, out=g)                      # warm-up
+    ts = []
+    for _ in range(max(1, steps)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.gradient(q, Pd, out=g)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts), g.cpu().numpy(), ctx.stats()
+
+
 def _dominant(res, precision, steps):
     s = res["stats"]
     M = s["M"]
@@ -395,6 +415,30 @@ def run_ours(args):
             "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": main["launches"],
             "cpu_baseline": cpu,
         }
+        if not args.no_grad:
+            q = main["bufs"]["q"]
+            g_ms, g_main, gst = _time_gradient(main, q, flush, stream, args.steps)
+            grad = {"ms": g_ms, "integrals_per_s": gst["integrals_grad"] / (g_ms * 1e-3),
+                    "precision": args.precision}
+            if other is not None:
+                # the FP64 gradient with the same charges
+                g64_ms, g64, _ = _time_gradient(other, q, flush, stream, 1)
+                grad.update(fp64_ms=g64_ms, speedup_vs_fp64=g64_ms / g_ms,
+                            max_abs_diff_vs_fp64_Eh_per_bohr=float(np.max(np.abs(g_main - g64))))
+            line["gradient"] = grad
+        if not args.no_scf:
+            # Section 4b-i: CG steps and solve time along a synthetic SCF history
+            from paper_1505_07851_gb300.scf import run_sequence
+            seq = workloads.scf_sequence(w, 14)
+            sc = {}
+            for scheme in ("fixed", "2delta", "dynamic"):
+                rec = run_sequence(main["ctx"], seq, scheme, delta_tight=1e-6)
+                sc[scheme] = {"cg_steps": [r["cg_steps"] for r in rec],
+                              "total_cg_steps": sum(r["cg_steps"] for r in rec),
+                              "total_solve_ms": sum(r["solve_ms"] for r in rec),
+                              "final_energy_Eh": rec[-1]["energy"]}
+            sc["workload"] = "%s, 14 iterations, DIIS error 0.1 x 0.4^n, warm start, delta_2 = 1e-6" % w.name
+            line["scf_sequence"] = sc
         if other is not None:
             n = len(other["times"])
             line["fp64"] = {"value": other["ints"] * world / (sum(other["times"]) * 1e-3), "unit": UNIT,
@@ -490,6 +534,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch of the dominant kernel (ncu)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-grad", action="store_true", help="skip the nuclear-gradient timing")
+    ap.add_argument("--no-scf", action="store_true", help="skip the SCF-sequence threshold comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -1,0 +1,80 @@
+"""SCF-sequence driver (Section 4b-i) on the GPU against the same sequence
+run with the oracle's PCG: per iteration the threshold, the CG steps (+-1:
+rounding changes the last step) and the energy; and the shape of the
+paper's comparison (the dynamic and 2-delta schemes need fewer CG steps in
+total than the fixed threshold, and the dynamic one spreads them evenly)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+DELTA_TIGHT = 1e-6
+
+
+def _oracle_sequence(w, seq, scheme, precond):
+    s = oracle.surface(w.mol.xyz, w.mol.radius)
+    eb = oracle.ExpandedBasis(w.basis, w.mol.xyz)
+    f = oracle.f_factor()
+    A = oracle.a_matrix(s)
+    Bz = oracle.bz(s, w.mol.xyz, w.mol.Z)
+    pc = oracle.Preconditioner(A, precond, 100, 0)
+    prev, x, out = None, None, []
+    for P, e in seq:
+        c = oracle.esp(eb, P, s["r"], s["zeta"])
+        if scheme == "fixed":
+            delta = DELTA_TIGHT
+        elif scheme == "2delta":
+            # the loose threshold 1e4 x delta_2 until the DIIS error reaches 1e-3
+            delta = 1e4 * DELTA_TIGHT if (prev is None or prev > 1e-3) else DELTA_TIGHT
+        else:
+            delta = oracle.dynamic_delta(prev)
+        x, it, ok, rn = oracle.pcg(A, -f * (Bz + c), delta, pc, x0=x)
+        out.append({"delta": delta, "cg_steps": it, "energy": oracle.energy(Bz, c, x, A, f)})
+        prev = e
+    return s, out
+
+
+@pytest.fixture(scope="module")
+def runs():
+    import paper_1505_07851_gb300 as pcm
+    from paper_1505_07851_gb300.scf import run_sequence
+    w = workloads.small_cluster(24, seed=31)
+    seq = workloads.scf_sequence(w, 12)
+    res = {}
+    with pcm.Context(schwarz=0.0, precond="rbj", timing=True) as ctx:
+        M, _ = ctx.setup(w.mol, w.basis)
+        _, idx = ctx.get_surface()
+        for scheme in ("fixed", "2delta", "dynamic"):
+            res[scheme] = run_sequence(ctx, seq, scheme, delta_tight=DELTA_TIGHT)
+    orc = {}
+    for scheme in ("fixed", "2delta", "dynamic"):
+        s, orc[scheme] = _oracle_sequence(w, seq, scheme, "rbj")
+    return M, res, orc
+
+
+@pytest.mark.parametrize("scheme", ["fixed", "2delta", "dynamic"])
+def test_sequence_matches_oracle(runs, scheme):
+    M, res, orc = runs
+    assert M >= 1000                                   # the RBJ regime
+    for g, o in zip(res[scheme], orc[scheme]):
+        assert g["delta"] == pytest.approx(o["delta"], rel=1e-12)
+        assert g["converged"]
+        assert abs(g["cg_steps"] - o["cg_steps"]) <= 1, (scheme, g, o)
+        # both solutions meet the threshold: the energies differ by O(delta)
+        assert abs(g["energy"] - o["energy"]) <= 1e-9 + 0.1 * g["delta"]
+
+
+def test_scheme_totals(runs):
+    M, res, orc = runs
+    tot = {k: sum(r["cg_steps"] for r in v) for k, v in res.items()}
+    assert tot["dynamic"] < tot["fixed"]
+    assert tot["2delta"] < tot["fixed"]
+    # the last iterations of every scheme agree on the energy (delta_tight or tighter)
+    E = [res[k][-1]["energy"] for k in res]
+    assert max(E) - min(E) <= 1e-7
+    # dynamic: no iteration needs more than twice the mean (Fig. 5: uniform steps)
+    dyn = [r["cg_steps"] for r in res["dynamic"]]
+    assert max(dyn) <= 2 * np.mean(dyn) + 1

@@ -81,6 +81,7 @@ class Workload:
     P: np.ndarray            # (nbf, nbf) symmetric density
     nocc: int
     seed: int
+    C: np.ndarray | None = None   # (nbf, nocc) occupied orbitals, P = 2 C C^T
 
 
 def _mol(symbols, xyz_bohr):
@@ -217,18 +218,48 @@ def overlap_matrix(basis: Basis, xyz: np.ndarray, block: int = 2048, cut: float 
     return 0.5 * (S + S.T)
 
 
-def make_density(basis: Basis, xyz: np.ndarray, nocc: int, rng) -> np.ndarray:
-    """P = 2 C C^T for nocc seeded occupied orbitals that are orthonormal in the
-    overlap metric (C^T S C = I, so tr(P S) = 2 nocc): the columns of a seeded
-    Gaussian nbf x nocc matrix G, symmetrically orthonormalised,
-    C = G (G^T S G)^(-1/2)."""
-    S = overlap_matrix(basis, xyz)
-    nocc = min(nocc, basis.nbf)
-    G = rng.standard_normal((basis.nbf, nocc))
+def _orthonormalise(G: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """Symmetric orthonormalisation in the overlap metric: G (G^T S G)^(-1/2)."""
     e, V = np.linalg.eigh(G.T @ S @ G)
-    C = G @ (V / np.sqrt(e)) @ V.T
+    return G @ (V / np.sqrt(e)) @ V.T
+
+
+def _density(C: np.ndarray) -> np.ndarray:
     P = 2.0 * C @ C.T
     return 0.5 * (P + P.T)
+
+
+def make_orbitals(basis: Basis, xyz: np.ndarray, nocc: int, rng) -> np.ndarray:
+    """nocc seeded occupied orbitals, orthonormal in the overlap metric
+    (C^T S C = I): the columns of a seeded Gaussian nbf x nocc matrix G,
+    symmetrically orthonormalised, C = G (G^T S G)^(-1/2)."""
+    S = overlap_matrix(basis, xyz)
+    nocc = min(nocc, basis.nbf)
+    return _orthonormalise(rng.standard_normal((basis.nbf, nocc)), S)
+
+
+def make_density(basis: Basis, xyz: np.ndarray, nocc: int, rng) -> np.ndarray:
+    """P = 2 C C^T for the orbitals of make_orbitals (tr(P S) = 2 nocc)."""
+    return _density(make_orbitals(basis, xyz, nocc, rng))
+
+
+def scf_sequence(w: "Workload", n_iter: int = 14, e0: float = 0.1, ratio: float = 0.4,
+                 seed: int | None = None):
+    """A synthetic SCF history ending at w.P, for the CG threshold schemes of
+    Section 4b-i: iteration n has the DIIS error e_n = e0 ratio^n and the
+    density of the occupied orbitals perturbed by e_n times a seeded Gaussian
+    matrix (re-orthonormalised in the overlap metric), so that the densities
+    approach w.P as the DIIS errors fall.  Returns [(P_n, e_n), ...]."""
+    if w.C is None:
+        raise ValueError("the workload carries no orbitals")
+    rng = np.random.default_rng(w.seed + 77 if seed is None else seed)
+    S = overlap_matrix(w.basis, w.mol.xyz)
+    out = []
+    for n in range(n_iter):
+        e = e0 * ratio ** n
+        G = w.C + e * rng.standard_normal(w.C.shape)
+        out.append((_density(_orthonormalise(G, S)), e))
+    return out
 
 
 def water(seed: int = 150507851 + 0) -> Workload:
@@ -240,8 +271,8 @@ def water(seed: int = 150507851 + 0) -> Workload:
     recipe = {"O": [(0, 3, (0.1, 130.0)), (-1, 3, (0.1, 130.0))],
               "H": [(0, 3, (0.1, 130.0))]}
     basis = make_basis(mol, recipe, rng)
-    P = make_density(basis, mol.xyz, 5, rng)
-    return Workload("water", mol, basis, P, 5, seed)
+    C = make_orbitals(basis, mol.xyz, 5, rng)
+    return Workload("water", mol, basis, _density(C), 5, seed, C)
 
 
 def _composition(natom: int, ratios=(("H", 50), ("C", 31), ("N", 9), ("O", 9), ("S", 1))):
@@ -292,8 +323,8 @@ def cluster(natom: int, seed: int, globule_radius_A: float, d_shells: bool = Fal
     basis = make_basis(mol, _SHELLS_631G, rng, d_on_heavy=d_shells)
     nocc = 2 * natom if nocc is None else nocc
     nocc = min(nocc, basis.nbf)
-    P = make_density(basis, mol.xyz, nocc, rng)
-    return Workload(name, mol, basis, P, nocc, seed)
+    C = make_orbitals(basis, mol.xyz, nocc, rng)
+    return Workload(name, mol, basis, _density(C), nocc, seed, C)
 
 
 # Globule radii (angstrom) chosen so that the 110-point ISWIG surface of the
