@@ -19,6 +19,13 @@ constexpr int BOYS_STRIDE64 = 16;          // doubles per row: m = 0 .. 15
 constexpr int BOYS_STRIDE32 = 16;          // floats per row: F_0..F_9 (hi) then the lo parts of F_0..F_5
 constexpr int BOYS_LO32 = 10;              // offset of the lo parts
 constexpr int BOYS_MCOL = 16;              // columns generated
+// The FP32 table holds a second block of BOYS_NROW rows after the first, for
+// m <= 1: the Taylor coefficients pre-scaled for Horner evaluation in d,
+//   h_{m,k} = (-1)^k F_{m+k}(T_i) / k!,  k = 0..4,
+// laid out per row as h00 h01 h02 h03 | h04 lo0 h10 h11 | h12 h13 h14 lo1 | pad,
+// with lo_m the FP32 residual of F_m(T_i) - h_{m,0}.
+constexpr int BOYS_H32 = BOYS_NROW * BOYS_STRIDE32;
+constexpr int BOYS_ALLOC32 = 2 * BOYS_NROW * BOYS_STRIDE32;
 
 template <int MM>
 __device__ __forceinline__ void boys_eval(double T, const double *__restrict__ tab, double (&F)[MM + 1])
@@ -64,19 +71,35 @@ __device__ __forceinline__ void boys_eval(float T, const float *__restrict__ tab
         const float t = fmaf(T, (float)BOYS_INV_DT, 12582912.0f);
         const int i = __float_as_int(t) - 0x4B400000;
         const float d = fmaf(t - 12582912.0f, -(float)BOYS_DT, T);
-        const float *row = tab + i * BOYS_STRIDE32;
-        float r[MM + 5], lo[MM + 1];
+        if constexpr (MM <= 1) {
+            // pre-scaled coefficients: Horner in d, the small terms first and
+            // one rounding of the sum with the leading term
+            const float4 *row = reinterpret_cast<const float4 *>(tab + BOYS_H32 + i * BOYS_STRIDE32);
+            const float4 a = __ldg(row), b = __ldg(row + 1);
+            F[0] = fmaf(fmaf(fmaf(fmaf(b.x, d, a.w), d, a.z), d, a.y), d, b.y) + a.x;
+            if constexpr (MM == 1) {
+                const float4 c = __ldg(row + 2);
+                F[1] = fmaf(fmaf(fmaf(fmaf(c.z, d, c.y), d, c.x), d, b.w), d, c.w) + b.z;
+            }
+        } else {
+            const float4 *row = reinterpret_cast<const float4 *>(tab + i * BOYS_STRIDE32);
+            float r[BOYS_STRIDE32];
 #pragma unroll
-        for (int k = 0; k < MM + 5; ++k) r[k] = __ldg(row + k);
+            for (int v = 0; v < BOYS_STRIDE32 / 4; ++v) {
+                const float4 x = __ldg(row + v);
+                r[4 * v] = x.x;
+                r[4 * v + 1] = x.y;
+                r[4 * v + 2] = x.z;
+                r[4 * v + 3] = x.w;
+            }
+            const float e1 = -d, e2 = -d * 0.5f, e3 = -d * (1.0f / 3.0f), e4 = -d * 0.25f;
 #pragma unroll
-        for (int k = 0; k <= MM; ++k) lo[k] = __ldg(row + BOYS_LO32 + k);
-        const float e1 = -d, e2 = -d * 0.5f, e3 = -d * (1.0f / 3.0f), e4 = -d * 0.25f;
-#pragma unroll
-        for (int m = 0; m <= MM; ++m) {
-            float s = fmaf(r[m + 4], e4, r[m + 3]);
-            s = fmaf(s, e3, r[m + 2]);
-            s = fmaf(s, e2, r[m + 1]);
-            F[m] = fmaf(s, e1, lo[m]) + r[m];  // the small terms first, one rounding of the sum
+            for (int m = 0; m <= MM; ++m) {
+                float s = fmaf(r[m + 4], e4, r[m + 3]);
+                s = fmaf(s, e3, r[m + 2]);
+                s = fmaf(s, e2, r[m + 1]);
+                F[m] = fmaf(s, e1, r[BOYS_LO32 + m]) + r[m];  // the small terms first, one rounding of the sum
+            }
         }
     } else {
         // sqrt(pi)/2 carried as hi + lo so that its FP32 rounding does not bias

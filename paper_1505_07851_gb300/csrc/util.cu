@@ -56,8 +56,7 @@ __global__ void boys_table_kernel(const double *__restrict__ gx, const double *_
                                   float *tab32)
 {
     const int row = blockIdx.x;
-    const int m = threadIdx.x;  // 0 .. BOYS_MCOL-1
-    if (row >= BOYS_NROW || m >= BOYS_MCOL) return;
+    const int m = threadIdx.x;  // 0 .. BOYS_MCOL-1 (launched with exactly BOYS_MCOL threads)
     const double T = row * BOYS_DT;
     double s = 0.0;
     const double h = 1.0 / BOYS_PANELS;
@@ -76,6 +75,21 @@ __global__ void boys_table_kernel(const double *__restrict__ gx, const double *_
     tab64[(size_t)row * BOYS_STRIDE64 + m] = s;
     if (m < BOYS_LO32) tab32[(size_t)row * BOYS_STRIDE32 + m] = (float)s;
     if (m < BOYS_STRIDE32 - BOYS_LO32) tab32[(size_t)row * BOYS_STRIDE32 + BOYS_LO32 + m] = (float)(s - (double)(float)s);
+    // Horner block for m <= 1 (layout in boys.cuh)
+    __shared__ double F[BOYS_MCOL];
+    F[m] = s;
+    __syncthreads();
+    if (m < BOYS_STRIDE32) {
+        constexpr double inv_fact[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
+        // slot -> (m, k) or the lo part of m
+        static constexpr int SM[16] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, -1, -1, -1, -1};
+        static constexpr int SK[16] = {0, 1, 2, 3, 4, -1, 0, 1, 2, 3, 4, -1, 0, 0, 0, 0};
+        const int mm = SM[m], k = SK[m];
+        float v = 0.f;
+        if (mm >= 0 && k >= 0) v = (float)(((k & 1) ? -1.0 : 1.0) * F[mm + k] * inv_fact[k]);
+        else if (mm >= 0) v = (float)(F[mm] - (double)(float)F[mm]);
+        tab32[BOYS_H32 + (size_t)row * BOYS_STRIDE32 + m] = v;
+    }
 }
 
 int boys_build_tables(pcm_ctx *c)
@@ -88,7 +102,7 @@ int boys_build_tables(pcm_ctx *c)
     PCM_CUDA(cudaMemcpyAsync(gx.p, x.data(), BOYS_GL * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     PCM_CUDA(cudaMemcpyAsync(gw.p, w.data(), BOYS_GL * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     PCM_TRY(c->boys64.alloc((size_t)BOYS_NROW * BOYS_STRIDE64));
-    PCM_TRY(c->boys32.alloc((size_t)BOYS_NROW * BOYS_STRIDE32));
+    PCM_TRY(c->boys32.alloc((size_t)BOYS_ALLOC32));
     PCM_CUDA(cudaMemsetAsync(c->boys64.p, 0, (size_t)BOYS_NROW * BOYS_STRIDE64 * sizeof(double), c->stream));
     boys_table_kernel<<<BOYS_NROW, BOYS_MCOL, 0, c->stream>>>(gx.p, gw.p, c->boys64.p, c->boys32.p);
     PCM_LAUNCHED(c);
