@@ -200,6 +200,7 @@ int fock_compute(pcm_ctx *c, const double *dq, double *ddF);
 int points_split(pcm_ctx *c);
 int esp_compute_mixed(pcm_ctx *c, double *dc);
 int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W);
+int fock_mixed_pairs_per_thread(int L);
 int grad_point_mixed(pcm_ctx *c, int *total_rows);
 int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W);
 int solver_prepare(pcm_ctx *c);

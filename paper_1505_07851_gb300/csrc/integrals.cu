@@ -839,7 +839,8 @@ static int fock_class(pcm_ctx *c, PairClass &pc, const double *dq, double *ddF)
     if (pc.nsp == 0) return PCM_OK;
     int nsplit = 1;
     if (pc.npair > 0) {
-        const int nb = (pc.npair + FOCK_NT - 1) / FOCK_NT;
+        const int per = FOCK_NT * (c->opt.precision == PCM_MIXED ? fock_mixed_pairs_per_thread(L) : 1);
+        const int nb = (pc.npair + per - 1) / per;
         const int maxsplit = std::max(1, (c->M + FOCK_TQ - 1) / FOCK_TQ);
         nsplit = std::max(1, std::min(maxsplit, (target_ctas(c) + nb - 1) / nb));
         int ks = (c->M + nsplit - 1) / nsplit;
@@ -937,7 +938,8 @@ static int grad_pair_class(pcm_ctx *c, PairClass &pc, const double *dP, const do
     constexpr int NH1 = nherm(L1);
     if (pc.nesp == 0) return PCM_OK;
     const int n = pc.nesp;
-    const int nb = (n + FOCK_NT - 1) / FOCK_NT;
+    const int per = FOCK_NT * (c->opt.precision == PCM_MIXED ? fock_mixed_pairs_per_thread(L1) : 1);
+    const int nb = (n + per - 1) / per;
     const int maxsplit = std::max(1, (c->M + FOCK_TQ - 1) / FOCK_TQ);
     int nsplit = std::max(1, std::min(maxsplit, (target_ctas(c) + nb - 1) / nb));
     int ks = (c->M + nsplit - 1) / nsplit;

@@ -326,11 +326,16 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int jbeg, in
 }
 
 // ---------------------------------------------------------------------------
-// Fock: thread per primitive pair; per class rho and U in FP64 (hi/lo for rho),
-// per point tile FP32 sums of q_k R_tuv, folded into FP64 with U.
+// Fock: NPT primitive pairs per thread (the point data staged in shared memory
+// serve them all); per class rho and U in FP64 (hi/lo for rho), per point tile
+// FP32 sums of q_k R_tuv, folded into FP64 with U.  The next tile's points are
+// read into registers while the current one is computed.
 // ---------------------------------------------------------------------------
 constexpr int MF_NT = 128;
 constexpr int MF_TQ = 128;
+template <int L> struct FockNPT { static constexpr int value = L <= 1 ? 2 : 1; };
+
+int fock_mixed_pairs_per_thread(int L) { return L <= 1 ? 2 : 1; }
 
 template <int L>
 __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double *__restrict__ gp,
@@ -342,77 +347,112 @@ __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double
                                                          const float *__restrict__ boys, double *__restrict__ W)
 {
     constexpr int NH = nherm(L);
+    constexpr int NPT = FockNPT<L>::value;
     __shared__ float4 sH[MF_TQ], sL[MF_TQ];  // (xh, yh, zh, q) and (xl, yl, zl, 0) per point
-    const int r = blockIdx.x * MF_NT + threadIdx.x;
-    const bool active = r < npair;
-    const int rr = active ? r : 0;
-    const float Pxh = Phl[rr], Pyh = Phl[(size_t)npair + rr], Pzh = Phl[2 * (size_t)npair + rr];
-    const float Pxl = Phl[3 * (size_t)npair + rr], Pyl = Phl[4 * (size_t)npair + rr],
-                Pzl = Phl[5 * (size_t)npair + rr];
-    const double p = gp[rr];
+    int r[NPT];
+    bool active[NPT];
+    float Pxh[NPT], Pyh[NPT], Pzh[NPT], Pxl[NPT], Pyl[NPT], Pzl[NPT];
+    double p[NPT];
+    double w64[NPT][NH];
+#pragma unroll
+    for (int i = 0; i < NPT; ++i) {
+        r[i] = (blockIdx.x * NPT + i) * MF_NT + threadIdx.x;
+        active[i] = r[i] < npair;
+        const int rr = active[i] ? r[i] : 0;
+        Pxh[i] = Phl[rr];
+        Pyh[i] = Phl[(size_t)npair + rr];
+        Pzh[i] = Phl[2 * (size_t)npair + rr];
+        Pxl[i] = Phl[3 * (size_t)npair + rr];
+        Pyl[i] = Phl[4 * (size_t)npair + rr];
+        Pzl[i] = Phl[5 * (size_t)npair + rr];
+        p[i] = gp[rr];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) w64[i][h] = 0.0;
+    }
     const int ka = blockIdx.y * ksplit;
     const int kb = min(M, ka + ksplit);
-    double w64[NH];
-#pragma unroll
-    for (int h = 0; h < NH; ++h) w64[h] = 0.0;
     for (int ec = 0; ec < ncls; ++ec) {
         const int a = max(ka, cls_off[ec]), b = min(kb, cls_off[ec + 1]);
         if (a >= b) continue;
         const double z2 = cls_zeta[ec] * cls_zeta[ec];
-        const double inv = 1.0 / (p + z2);
-        const double rho = p * z2 * inv;
-        const double U = sqrt(z2 * inv);
-        const float rh = (float)rho;
-        const float rl = (float)(rho - (double)rh);
-        const float dr = (float)((rho - (double)rh) / (double)rh);
-        const float m2r = -2.f * rh;
+        double U[NPT];
+        float rh[NPT], rl[NPT], dr[NPT], m2r[NPT];
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+            const double inv = 1.0 / (p[i] + z2);
+            const double rho = p[i] * z2 * inv;
+            U[i] = sqrt(z2 * inv);
+            rh[i] = (float)rho;
+            rl[i] = (float)(rho - (double)rh[i]);
+            dr[i] = (float)((rho - (double)rh[i]) / (double)rh[i]);
+            m2r[i] = -2.f * rh[i];
+        }
+        // this thread's point of the first tile
+        float4 nH = make_float4(0.f, 0.f, 0.f, 0.f), nL = nH;
+        if (a + (int)threadIdx.x < b) {
+            const int k = a + threadIdx.x;
+            nH = make_float4(ph[k], ph[(size_t)M + k], ph[2 * (size_t)M + k], (float)q[k]);
+            nL = make_float4(pl[k], pl[(size_t)M + k], pl[2 * (size_t)M + k], 0.f);
+        }
         for (int t0 = a; t0 < b; t0 += MF_TQ) {
             const int nt = min(MF_TQ, b - t0);
             __syncthreads();
-            for (int t = threadIdx.x; t < nt; t += MF_NT) {
-                sH[t] = make_float4(ph[t0 + t], ph[(size_t)M + t0 + t], ph[2 * (size_t)M + t0 + t], (float)q[t0 + t]);
-                sL[t] = make_float4(pl[t0 + t], pl[(size_t)M + t0 + t], pl[2 * (size_t)M + t0 + t], 0.f);
-            }
+            sH[threadIdx.x] = nH;
+            sL[threadIdx.x] = nL;
             __syncthreads();
-            float w32[NH];
+            // prefetch the next tile while this one is computed
+            if (t0 + MF_TQ + (int)threadIdx.x < b) {
+                const int k = t0 + MF_TQ + threadIdx.x;
+                nH = make_float4(ph[k], ph[(size_t)M + k], ph[2 * (size_t)M + k], (float)q[k]);
+                nL = make_float4(pl[k], pl[(size_t)M + k], pl[2 * (size_t)M + k], 0.f);
+            }
+            float w32[NPT][NH];
 #pragma unroll
-            for (int h = 0; h < NH; ++h) w32[h] = 0.f;
+            for (int i = 0; i < NPT; ++i)
+#pragma unroll
+                for (int h = 0; h < NH; ++h) w32[i][h] = 0.f;
             for (int kk = 0; kk < nt; ++kk) {
                 const float4 H = sH[kk], Lo = sL[kk];
-                const float X = (Pxh - H.x) + (Pxl - Lo.x);
-                const float Y = (Pyh - H.y) + (Pyl - Lo.y);
-                const float Z = (Pzh - H.z) + (Pzl - Lo.z);
-                const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
-                const float T = fmaf(rh, R2, rl * R2);
-                float Fb[L + 1];
-                boys_eval<L>(T, boys, Fb);
-                if constexpr (L == 0) {
-                    w32[0] = fmaf(H.w, Fb[0], w32[0]);
-                } else {
-                    float Rn[L + 1];
-                    float f = H.w;
 #pragma unroll
-                    for (int n = 0; n <= L; ++n) {
-                        const float v = f * Fb[n];
-                        Rn[n] = (n == 0) ? v : fmaf(v, (float)n * dr, v);
-                        f *= m2r;
+                for (int i = 0; i < NPT; ++i) {
+                    const float X = (Pxh[i] - H.x) + (Pxl[i] - Lo.x);
+                    const float Y = (Pyh[i] - H.y) + (Pyl[i] - Lo.y);
+                    const float Z = (Pzh[i] - H.z) + (Pzl[i] - Lo.z);
+                    const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+                    const float T = fmaf(rh[i], R2, rl[i] * R2);
+                    float Fb[L + 1];
+                    boys_eval<L>(T, boys, Fb);
+                    if constexpr (L == 0) {
+                        w32[i][0] = fmaf(H.w, Fb[0], w32[i][0]);
+                    } else {
+                        float Rn[L + 1];
+                        float f = H.w;
+#pragma unroll
+                        for (int n = 0; n <= L; ++n) {
+                            const float v = f * Fb[n];
+                            Rn[n] = (n == 0) ? v : fmaf(v, (float)n * dr[i], v);
+                            f *= m2r[i];
+                        }
+                        float R[NH];
+                        hermite_R<L, float>(X, Y, Z, Rn, R);
+#pragma unroll
+                        for (int h = 0; h < NH; ++h) w32[i][h] += R[h];
                     }
-                    float R[NH];
-                    hermite_R<L, float>(X, Y, Z, Rn, R);
-#pragma unroll
-                    for (int h = 0; h < NH; ++h) w32[h] += R[h];
                 }
             }
 #pragma unroll
-            for (int h = 0; h < NH; ++h) w64[h] = fma(U, (double)w32[h], w64[h]);
+            for (int i = 0; i < NPT; ++i)
+#pragma unroll
+                for (int h = 0; h < NH; ++h) w64[i][h] = fma(U[i], (double)w32[i][h], w64[i][h]);
         }
     }
-    if (active) {
 #pragma unroll
-        for (int h = 0; h < NH; ++h) W[((size_t)blockIdx.y * NH + h) * npair + r] = w64[h];
-    }
+    for (int i = 0; i < NPT; ++i)
+        if (active[i]) {
+#pragma unroll
+            for (int h = 0; h < NH; ++h) W[((size_t)blockIdx.y * NH + h) * npair + r[i]] = w64[i][h];
+        }
 }
-
 
 // ---------------------------------------------------------------------------
 // Point part of the integral gradient on the FP32 pipes (the FP64 statement
@@ -674,7 +714,8 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
 int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W)
 {
     PairClass &pc = c->cls[k];
-    const int nb = (pc.npair + MF_NT - 1) / MF_NT;
+    const int per = MF_NT * fock_mixed_pairs_per_thread(CLASS_L[k]);
+    const int nb = (pc.npair + per - 1) / per;
     dim3 grid(nb, nsplit);
     switch (CLASS_L[k]) {
 #define PCM_FOCK_F32(LL)                                                                                           \
@@ -760,7 +801,8 @@ int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, do
 {
     PairClass &pc = c->cls[k];
     const int n = pc.nesp;
-    const int nb = (n + MF_NT - 1) / MF_NT;
+    const int per = MF_NT * fock_mixed_pairs_per_thread(CLASS_L[k] + 1);
+    const int nb = (n + per - 1) / per;
     dim3 grid(nb, nsplit);
     switch (CLASS_L[k] + 1) {
 #define PCM_GW(LL)                                                                                             \
