@@ -207,6 +207,48 @@ int pcm_energy(pcm_ctx *ctx, const double *q, const double *c, double *E, int fl
  * the nuclear B term, the switching term and every reduction stay FP64. */
 int pcm_gradient(pcm_ctx *ctx, const double *P, const double *q, double *grad, int flags);
 
+/* ------------------------------------------------------------------------
+ * Batches: many molecules of uneven size in one call.
+ *
+ * A batch holds one context per molecule (options as for pcm_create; every
+ * molecule's A, its FP32 copy under PCM_MIXED, and its preconditioner stay
+ * resident).  pcm_batch_run computes, for every molecule, the ESP (Eq. 5),
+ * the solve of Eq. 1 to ||A q - rhs||_2 < delta (Eq. 20; fixed delta), the
+ * Fock correction (Eq. 10) and the energy (Eq. 13).  The solves of all
+ * molecules run in lockstep on the device: one launch per PCG step serves
+ * every molecule, the iteration loop is a CUDA graph whose loop condition the
+ * device sets (per-molecule convergence), and PCM_MIXED wraps it in FP64
+ * iterative refinement as in pcm_solve.
+ * ---------------------------------------------------------------------- */
+typedef struct pcm_batch pcm_batch;
+
+/* A batch of nmol molecules (opt NULL: defaults).  Destroy with pcm_batch_destroy. */
+int pcm_batch_create(pcm_batch **batch, const pcm_options *opt, int nmol);
+int pcm_batch_destroy(pcm_batch *batch);
+
+/* Molecule i (0 <= i < nmol): surface as pcm_build_surface, basis as
+ * pcm_set_basis (host pointers), then its preconditioner (and FP32 A). */
+int pcm_batch_set_molecule(pcm_batch *batch, int i, int natom, const double *xyz, const double *Z,
+                           const double *radius, int pts_per_sphere, int nshell, const int *shell_atom,
+                           const int *shell_l, const int *shell_nprim, const double *exps,
+                           const double *coefs);
+
+/* Surface points and basis functions of molecule i. */
+int pcm_batch_sizes(pcm_batch *batch, int i, int *M, int *nbf);
+
+/* Run every molecule: P[i] its density (nbf_i^2, symmetric, row-major);
+ * delta > 0 the residual threshold; E: nmol energies (host array, hartree);
+ * q, dF: optional arrays of nmol pointers (M_i charges in library order,
+ * nbf_i^2 Fock corrections), NULL or a NULL entry to skip.  flags:
+ * PCM_PTR_DEVICE (P, q and dF entries are device pointers). */
+int pcm_batch_run(pcm_batch *batch, const double *const *P, double delta, double *E, double *const *q,
+                  double *const *dF, int flags);
+
+/* Per-molecule statistics of the last run (iterations, convergence, final
+ * residual, refinements, integrals); i = -1: batch totals (launches,
+ * integrals, the largest iteration count, total points and functions). */
+int pcm_batch_get_stats(pcm_batch *batch, int i, pcm_stats *st);
+
 /* Statistics of the context's last calls. */
 int pcm_get_stats(pcm_ctx *ctx, pcm_stats *st);
 

@@ -105,6 +105,12 @@ def _load():
         "pcm_fock": (i, [vp, vp, vp, i]),
         "pcm_energy": (i, [vp, vp, vp, ctypes.POINTER(d), i]),
         "pcm_gradient": (i, [vp, vp, vp, vp, i]),
+        "pcm_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(pcm_options), i]),
+        "pcm_batch_destroy": (i, [vp]),
+        "pcm_batch_set_molecule": (i, [vp, i, i, vp, vp, vp, i, i, vp, vp, vp, vp, vp]),
+        "pcm_batch_sizes": (i, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "pcm_batch_run": (i, [vp, vp, d, vp, vp, vp, i]),
+        "pcm_batch_get_stats": (i, [vp, i, ctypes.POINTER(pcm_stats)]),
         "pcm_get_stats": (i, [vp, ctypes.POINTER(pcm_stats)]),
         "pcm_energy_noalloc": (i, [i, vp, i, vp, vp, vp, d, vp, vp]),
     }
@@ -308,6 +314,106 @@ class Context:
         M = self.build_surface(mol.xyz, mol.Z, mol.radius, pts_per_sphere)
         nbf = self.set_basis(basis.shell_atom, basis.shell_l, basis.shell_nprim, basis.exps, basis.coefs)
         return M, nbf
+
+
+
+class Batch:
+    """One pcm_batch: many molecules run together (pcm_batch_run)."""
+
+    def __init__(self, nmol, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
+                 precond="auto", jacobi_below=1000, precision="mixed", max_iter=5000, device=0, seed=0,
+                 stream=None):
+        o = pcm_options()
+        _lib.pcm_default_options(ctypes.byref(o))
+        o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
+        o.rbj_block, o.precond, o.jacobi_below = rbj_block, PRECOND[precond], jacobi_below
+        o.precision = {"fp64": PCM_FP64, "mixed": PCM_MIXED}[precision]
+        o.max_iter, o.device, o.seed, o.stream = max_iter, device, seed, stream
+        h = ctypes.c_void_p()
+        st = _lib.pcm_batch_create(ctypes.byref(h), ctypes.byref(o), int(nmol))
+        if st != PCM_OK:
+            raise PCMError(st, "pcm_batch_create", _lib.pcm_last_error().decode())
+        self._h = h
+        self.nmol = int(nmol)
+        self.device = device
+        self.sizes = [None] * self.nmol
+
+    def _check(self, st, where):
+        if st != PCM_OK:
+            raise PCMError(st, where, _lib.pcm_last_error().decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pcm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_molecule(self, i, mol, basis, pts_per_sphere=110):
+        xyz = np.ascontiguousarray(mol.xyz, np.float64)
+        Z = np.ascontiguousarray(mol.Z, np.float64)
+        rad = np.ascontiguousarray(mol.radius, np.float64)
+        a = np.ascontiguousarray(basis.shell_atom, np.int32)
+        l = np.ascontiguousarray(basis.shell_l, np.int32)
+        n = np.ascontiguousarray(basis.shell_nprim, np.int32)
+        e = np.ascontiguousarray(basis.exps, np.float64)
+        c = np.ascontiguousarray(basis.coefs, np.float64)
+        self._check(_lib.pcm_batch_set_molecule(self._h, int(i), len(Z), xyz.ctypes.data, Z.ctypes.data,
+                                                rad.ctypes.data, int(pts_per_sphere), len(l), a.ctypes.data,
+                                                l.ctypes.data, n.ctypes.data, e.ctypes.data, c.ctypes.data),
+                    "pcm_batch_set_molecule")
+        M, nbf = ctypes.c_int(), ctypes.c_int()
+        self._check(_lib.pcm_batch_sizes(self._h, int(i), ctypes.byref(M), ctypes.byref(nbf)), "pcm_batch_sizes")
+        self.sizes[i] = (M.value, nbf.value)
+        return self.sizes[i]
+
+    def run(self, Ps, delta, want_q=False, want_dF=False):
+        """Ps: nmol densities (all NumPy arrays or all CUDA tensors).  Returns
+        (E, q list or None, dF list or None); outputs live where Ps live."""
+        if len(Ps) != self.nmol:
+            raise ValueError("one density per molecule")
+        dev = _is_torch(Ps[0])
+        keep = []
+        P_ptrs = (ctypes.c_void_p * self.nmol)()
+        for i, P in enumerate(Ps):
+            p, fl, k = _ptr(P, np.float64)
+            if bool(fl) != dev:
+                raise TypeError("all densities must live on the same side (host or device)")
+            P_ptrs[i] = p
+            keep.append(k)
+        E = np.zeros(self.nmol)
+        q = dF = None
+        q_ptrs = dF_ptrs = None
+        if want_q:
+            q = [self._alloc(Ps[i], (self.sizes[i][0],)) for i in range(self.nmol)]
+            q_ptrs = (ctypes.c_void_p * self.nmol)(*[_ptr(a, np.float64)[0] for a in q])
+        if want_dF:
+            dF = [self._alloc(Ps[i], (self.sizes[i][1], self.sizes[i][1])) for i in range(self.nmol)]
+            dF_ptrs = (ctypes.c_void_p * self.nmol)(*[_ptr(a, np.float64)[0] for a in dF])
+        self._check(_lib.pcm_batch_run(self._h, P_ptrs, float(delta), E.ctypes.data, q_ptrs, dF_ptrs,
+                                       PCM_PTR_DEVICE if dev else 0), "pcm_batch_run")
+        return E, q, dF
+
+    def _alloc(self, like, shape):
+        if _is_torch(like):
+            import torch
+            return torch.empty(shape, dtype=torch.float64, device=like.device)
+        return np.zeros(shape)
+
+    def stats(self, i=-1):
+        st = pcm_stats()
+        self._check(_lib.pcm_batch_get_stats(self._h, int(i), ctypes.byref(st)), "pcm_batch_get_stats")
+        return st.as_dict()
 
 
 # --------------------------------------------------------------------------

@@ -204,6 +204,7 @@ int fock_mixed_pairs_per_thread(int L);
 int grad_point_mixed(pcm_ctx *c, int *total_rows);
 int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W);
 int solver_prepare(pcm_ctx *c);
+int solver_prepare_full(pcm_ctx *c);
 int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st);
 int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E);
 // gradient (gradient.cu, integrals.cu)

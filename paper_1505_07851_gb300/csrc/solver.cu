@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "context.h"
+#include "gemv.cuh"
 
 namespace pcm {
 
@@ -56,65 +57,6 @@ __device__ __forceinline__ double block_sum_warps(double v /* lane-0 values */)
     return r;
 }
 
-// Row-pair GEMV: a block of 8 warps computes two rows, four warps per row,
-// each warp a quarter of the columns (whole vector loads), so the grid has
-// M/2 blocks and no wave tail.  Returns, in thread 0, the block's x.y partial
-// (x64 the FP64 copy of the input vector).
-template <typename TA>
-__device__ __forceinline__ double gemv_rowpair(int M, int lda, const TA *__restrict__ A, const TA *__restrict__ x,
-                                               const double *__restrict__ x64, double *__restrict__ y)
-{
-    __shared__ double sh[8];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int row = blockIdx.x * 2 + (w >> 2), seg = w & 3;
-    constexpr int V = 16 / sizeof(TA);                    // elements per 16-byte load
-    const int seglen = ((M + 3) / 4 + 32 * V - 1) / (32 * V) * (32 * V);
-    const int c0 = seg * seglen, c1 = min(M, c0 + seglen);
-    double part = 0.0;
-    if (row < M && c0 < c1) {
-        const TA *a = A + (size_t)row * lda;
-        TA s0 = TA(0), s1 = TA(0);
-        int col = c0 + V * lane;
-        for (; col + 32 * V + V - 1 < c1; col += 64 * V) {
-            if constexpr (sizeof(TA) == 4) {
-                const float4 a0 = *reinterpret_cast<const float4 *>(a + col);
-                const float4 a1 = *reinterpret_cast<const float4 *>(a + col + 32 * V);
-                const float4 x0 = *reinterpret_cast<const float4 *>(x + col);
-                const float4 x1 = *reinterpret_cast<const float4 *>(x + col + 32 * V);
-                s0 = fmaf(a0.x, x0.x, fmaf(a0.y, x0.y, fmaf(a0.z, x0.z, fmaf(a0.w, x0.w, s0))));
-                s1 = fmaf(a1.x, x1.x, fmaf(a1.y, x1.y, fmaf(a1.z, x1.z, fmaf(a1.w, x1.w, s1))));
-            } else {
-                const double2 a0 = *reinterpret_cast<const double2 *>(a + col);
-                const double2 a1 = *reinterpret_cast<const double2 *>(a + col + 32 * V);
-                const double2 x0 = *reinterpret_cast<const double2 *>(x + col);
-                const double2 x1 = *reinterpret_cast<const double2 *>(x + col + 32 * V);
-                s0 = fma(a0.x, x0.x, fma(a0.y, x0.y, s0));
-                s1 = fma(a1.x, x1.x, fma(a1.y, x1.y, s1));
-            }
-        }
-        for (; col < c1; col += 32 * V)
-#pragma unroll
-            for (int t = 0; t < V; ++t)
-                if (col + t < c1) s0 += a[col + t] * x[col + t];
-        part = (double)warp_sum(s0 + s1);
-    }
-    if (lane == 0) sh[w] = part;
-    __syncthreads();
-    double blk = 0.0;
-    if (threadIdx.x == 0) {
-        for (int r2 = 0; r2 < 2; ++r2) {
-            const int rr = blockIdx.x * 2 + r2;
-            if (rr < M) {
-                const double v = sh[4 * r2] + sh[4 * r2 + 1] + sh[4 * r2 + 2] + sh[4 * r2 + 3];
-                y[rr] = v;
-                blk = fma(x64[rr], v, blk);
-            }
-        }
-    }
-    __syncthreads();
-    return blk;
-}
-
 // fixed-order sum of n partials by the whole (last) block; valid in thread 0
 __device__ __forceinline__ double sum_partials(const double *part, int n)
 {
@@ -139,7 +81,7 @@ __global__ void __launch_bounds__(GV_NT) pcg_gemv_rp_kernel(int M, int lda, cons
                                                             unsigned int *__restrict__ counter)
 {
     if (iscal[I_DONE]) return;
-    const double bsum = gemv_rowpair<TA>(M, lda, A, px, p, Ap);
+    const double bsum = gemv_rowpair<TA>(blockIdx.x, M, lda, A, px, p, Ap);
     if (threadIdx.x == 0) part[blockIdx.x] = bsum;
     if (last_block(counter)) {
         const double t = sum_partials(part, gridDim.x);
@@ -156,7 +98,7 @@ __global__ void __launch_bounds__(GV_NT) gemv_rp_plain_kernel(int M, int lda, co
                                                               const double *__restrict__ x, double *__restrict__ y,
                                                               double *__restrict__ part)
 {
-    const double bsum = gemv_rowpair<double>(M, lda, A, x, x, y);
+    const double bsum = gemv_rowpair<double>(blockIdx.x, M, lda, A, x, x, y);
     if (threadIdx.x == 0) part[blockIdx.x] = bsum;
 }
 
@@ -230,21 +172,18 @@ __global__ void __launch_bounds__(UP_NT) pcg_update_diag_kernel(int M, const dou
 
 constexpr int RBJ_SPLIT = 4;   // threads per row in the block-Jacobi apply
 
-// Randomized block-Jacobi: one block per RBJ block; the block's indices are
-// perm[b*l .. b*l + nb) and its inverse is inv[b] (l x l, symmetric).
-// With alpha_from_scal = false (initialisation) x and r are left unchanged.
-__global__ void pcg_update_rbj_kernel(int M, int l, const int *__restrict__ perm, const double *__restrict__ inv,
-                                      double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
-                                      const double *__restrict__ p, const double *__restrict__ Ap,
-                                      double *__restrict__ part, double *__restrict__ scal, int *__restrict__ iscal,
-                                      unsigned int *__restrict__ counter, int init)
+// Randomized block-Jacobi apply for RBJ block b: its indices are
+// perm[b*l .. b*l + nb) and its inverse is inv[b] (l x l, symmetric).  Unless
+// init, first x += alpha p and r -= alpha Ap on the block's indices; then
+// z = Minv r there.  Returns the block's r.r and r.z in thread 0.
+__device__ __forceinline__ void rbj_apply_block(int M, int l, int b, const int *__restrict__ perm,
+                                                const double *__restrict__ inv, double *__restrict__ x,
+                                                double *__restrict__ r, double *__restrict__ z,
+                                                const double *__restrict__ p, const double *__restrict__ Ap,
+                                                double alpha, int init, double *srb, double *rr_out, double *rz_out)
 {
-    extern __shared__ double srb[];  // l entries
-    if (iscal[I_DONE]) return;
-    const int b = blockIdx.x;
     const int base = b * l;
     const int nb = min(l, M - base);
-    const double alpha = init ? 0.0 : scal[S_ALPHA];
     double rr = 0.0, rz = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         const int k = perm[base + i];
@@ -288,6 +227,27 @@ __global__ void pcg_update_rbj_kernel(int M, int l, const int *__restrict__ perm
             a += sh[0][i];
             c += sh[1][i];
         }
+        *rr_out = a;
+        *rz_out = c;
+    }
+}
+
+// Randomized block-Jacobi update, one block per RBJ block; the last block
+// to finish sums the partials.  With init (initialisation) x and r are left
+// unchanged.
+__global__ void pcg_update_rbj_kernel(int M, int l, const int *__restrict__ perm, const double *__restrict__ inv,
+                                      double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
+                                      const double *__restrict__ p, const double *__restrict__ Ap,
+                                      double *__restrict__ part, double *__restrict__ scal, int *__restrict__ iscal,
+                                      unsigned int *__restrict__ counter, int init)
+{
+    extern __shared__ double srb[];  // l entries
+    if (iscal[I_DONE]) return;
+    const int b = blockIdx.x;
+    const double alpha = init ? 0.0 : scal[S_ALPHA];
+    double a = 0.0, c = 0.0;
+    rbj_apply_block(M, l, b, perm, inv, x, r, z, p, Ap, alpha, init, srb, &a, &c);
+    if (threadIdx.x == 0) {
         part[2 * b] = a;
         part[2 * b + 1] = c;
     }
@@ -736,6 +696,21 @@ int solver_prepare(pcm_ctx *c)
         }
     }
     c->pc_ready = true;
+    return PCM_OK;
+}
+
+// Everything a solve needs before its first iteration: the preconditioner
+// and, for PCM_MIXED, the FP32 copy of A.
+int solver_prepare_full(pcm_ctx *c)
+{
+    PCM_TRY(solver_prepare(c));
+    if (c->opt.precision == PCM_MIXED && !c->a32_ready) {
+        PCM_TRY(c->A32.alloc((size_t)c->M * c->lda));
+        const long long n = (long long)c->M * c->lda;
+        a_to_f32_kernel<<<4 * 152, 256, 0, c->stream>>>(n, c->A.p, c->A32.p);
+        PCM_LAUNCHED(c);
+        c->a32_ready = true;
+    }
     return PCM_OK;
 }
 
