@@ -518,6 +518,102 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batch(args):
+    """The batch workload: conformations of 150-600 atoms (s/sp shells, M
+    about 6k-24k each), ESP + lockstep PCG + Fock + energy for all of them per
+    step (pcm_batch_run, PCM_MIXED), inputs resident on the device."""
+    import torch
+    rank, world, local = dist_init("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1505_07851_gb300 as pcm
+    t0 = time.time()
+    confs = workloads.conformations(args.nmol, seed=150507851 + 4 + 1000 * rank, workers=os.cpu_count() or 1)
+    gen_s = time.time() - t0
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    delta = args.delta if args.delta else DELTA_1E6
+    b = pcm.Batch(len(confs), precision=args.precision, device=local, stream=stream.cuda_stream)
+    t0 = time.time()
+    for i, w in enumerate(confs):
+        b.set_molecule(i, w.mol, w.basis)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    Pd = [torch.tensor(w.P, dtype=torch.float64, device=dev) for w in confs]
+    for _ in range(args.warmup):
+        b.run(Pd, delta)
+    torch.cuda.synchronize()
+    launches0 = b.stats()["launches"]
+    times, ints = [], 0.0
+    barrier(world)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            E, _, _ = b.run(Pd, delta)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            tot = b.stats()
+            ints += tot["integrals_esp"] + tot["integrals_fock"]
+    torch.cuda.synchronize()
+    barrier(world)
+    tot = b.stats()
+    launches = tot["launches"] - launches0
+    per = [b.stats(i) for i in range(len(confs))]
+    value, ms_max = replica_throughput(ints, sum(times), world, dev)
+    solves = dist_sum(len(confs) * args.steps, world, dev) / (ms_max * 1e-3)
+    # end to end: host densities in, energies out
+    e2e = None
+    if not args.no_e2e:
+        Ph = [np.ascontiguousarray(w.P) for w in confs]
+        et = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            b.run(Ph, delta)
+            et.append(time.perf_counter() - t1)
+        e_val, e_ms = replica_throughput(ints * len(et) / args.steps, sum(et) * 1e3, world, dev)
+        e2e = {"value": e_val, "unit": UNIT, "h2d_bytes_per_step": int(sum(P.nbytes for P in Ph)),
+               "d2h_bytes_per_step": 8 * len(confs), "ms_per_step": e_ms / len(et)}
+    # per-conformation error against the FP64 single-molecule path (a sample)
+    errs = []
+    for i in range(min(args.ref_mols, len(confs))):
+        w = confs[i]
+        with pcm.Context(precision="fp64", device=local, stream=stream.cuda_stream) as ctx:
+            ctx.setup(w.mol, w.basis)
+            ctx.esp(w.P)
+            q, _ = ctx.solve(delta=1e-10)
+            errs.append(abs(E[i] - ctx.energy(q)))
+    b.close()
+    if rank == 0:
+        Ms = [p["M"] for p in per]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64",
+            "data": "synthetic (seeded peptide-like clusters of 150-600 atoms)",
+            "config": {"workload": "batch%d_conformations_150to600_sp" % len(confs), "nmol": len(confs),
+                       "M_min": min(Ms), "M_max": max(Ms), "M_total": sum(Ms), "precision": args.precision,
+                       "delta": delta, "l2": "flushed between timed steps (512 MB write, not timed)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "solves_per_s": solves,
+            "pcg_iterations_max": max(p["iterations"] for p in per),
+            "pcg_iterations_mean": statistics.mean(p["iterations"] for p in per),
+            "all_converged": all(p["converged"] for p in per),
+            "energy_err_vs_fp64_Eh": {"max": max(errs) if errs else None, "n": len(errs)},
+            "setup_s": setup_s, "workload_generation_s": gen_s, "autotune": pcm.autotune_table(),
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -535,12 +631,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the nuclear-gradient timing")
+    ap.add_argument("--nmol", type=int, default=64, help="conformations in the batch workload (--config 4)")
+    ap.add_argument("--ref-mols", type=int, default=4, help="batch members checked against the FP64 path")
     ap.add_argument("--no-scf", action="store_true", help="skip the SCF-sequence threshold comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 4:
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -92,6 +92,7 @@ typedef struct pcm_options {
     unsigned long long seed;    /* RBJ pivot stream seed (splitmix64), default 0 */
     void *stream;               /* cudaStream_t to use; NULL: the context creates its own */
     int timing;                 /* 1: time the integral kernels and the solve with CUDA events (stats) */
+    int autotune;               /* 1: pick the FP32 integral kernels' tile shapes by timed trials (default 0) */
 } pcm_options;
 
 typedef struct pcm_stats {
@@ -248,6 +249,12 @@ int pcm_batch_run(pcm_batch *batch, const double *const *P, double delta, double
  * residual, refinements, integrals); i = -1: batch totals (launches,
  * integrals, the largest iteration count, total points and functions). */
 int pcm_batch_get_stats(pcm_batch *batch, int i, pcm_stats *st);
+
+/* The autotuner's choices so far in this process: up to max_entries records
+ * of five ints (device, kernel family 0 = ESP points per thread (choice 0:
+ * 4, 1: 2), 1 = Fock pairs per thread (choice 1 or 2); angular momentum L;
+ * size bucket floor(log2(pairs)); choice).  Returns the number of records. */
+int pcm_autotune_table(int *entries, int max_entries);
 
 /* Statistics of the context's last calls. */
 int pcm_get_stats(pcm_ctx *ctx, pcm_stats *st);

@@ -54,7 +54,8 @@ class pcm_options(ctypes.Structure):
                 ("switch_drop", ctypes.c_double), ("schwarz", ctypes.c_double),
                 ("rbj_block", ctypes.c_int), ("precond", ctypes.c_int), ("jacobi_below", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("device", ctypes.c_int),
-                ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class pcm_stats(ctypes.Structure):
@@ -112,6 +113,7 @@ def _load():
         "pcm_batch_run": (i, [vp, vp, d, vp, vp, vp, i]),
         "pcm_batch_get_stats": (i, [vp, i, ctypes.POINTER(pcm_stats)]),
         "pcm_get_stats": (i, [vp, ctypes.POINTER(pcm_stats)]),
+        "pcm_autotune_table": (i, [vp, i]),
         "pcm_energy_noalloc": (i, [i, vp, i, vp, vp, vp, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -143,6 +145,24 @@ def _ptr(a, dtype):
     return arr.ctypes.data, 0, arr
 
 
+def autotune_table():
+    """The autotuner's choices so far: list of dicts (device, kernel, L,
+    bucket, choice) with kernel "esp_points_per_thread" (choice 4 or 2) or
+    "fock_pairs_per_thread" (1 or 2)."""
+    n = _lib.pcm_autotune_table(None, 0)
+    buf = (ctypes.c_int * (5 * max(1, n)))()
+    n = _lib.pcm_autotune_table(buf, n)
+    out = []
+    for i in range(n):
+        dev, kind, L, bucket, ch = buf[5 * i:5 * i + 5]
+        if kind == 0:
+            out.append({"device": dev, "kernel": "esp_points_per_thread", "L": L, "bucket": bucket,
+                        "choice": 4 if ch == 0 else 2})
+        else:
+            out.append({"device": dev, "kernel": "fock_pairs_per_thread", "L": L, "bucket": bucket, "choice": ch})
+    return out
+
+
 def energy_noalloc(A, Bz, c, q, f, E, stream=None):
     """pcm_energy_noalloc on CUDA torch tensors: A (M, lda >= M) row-major,
     Bz, c, q (M,), E (1,) output; nothing is allocated by the library.  The
@@ -165,7 +185,7 @@ class Context:
 
     def __init__(self, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
                  precond="auto", jacobi_below=1000, precision="fp64", max_iter=5000, device=0, seed=0,
-                 stream=None, timing=False):
+                 stream=None, timing=False, autotune=False):
         o = pcm_options()
         _lib.pcm_default_options(ctypes.byref(o))
         o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
@@ -174,6 +194,7 @@ class Context:
         o.max_iter, o.device, o.seed = max_iter, device, seed
         o.stream = stream
         o.timing = 1 if timing else 0
+        o.autotune = 1 if autotune else 0
         h = ctypes.c_void_p()
         self._check(_lib.pcm_create(ctypes.byref(h), ctypes.byref(o)), "pcm_create")
         self._h = h
@@ -322,13 +343,14 @@ class Batch:
 
     def __init__(self, nmol, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
                  precond="auto", jacobi_below=1000, precision="mixed", max_iter=5000, device=0, seed=0,
-                 stream=None):
+                 stream=None, autotune=True):
         o = pcm_options()
         _lib.pcm_default_options(ctypes.byref(o))
         o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
         o.rbj_block, o.precond, o.jacobi_below = rbj_block, PRECOND[precond], jacobi_below
         o.precision = {"fp64": PCM_FP64, "mixed": PCM_MIXED}[precision]
         o.max_iter, o.device, o.seed, o.stream = max_iter, device, seed, stream
+        o.autotune = 1 if autotune else 0
         h = ctypes.c_void_p()
         st = _lib.pcm_batch_create(ctypes.byref(h), ctypes.byref(o), int(nmol))
         if st != PCM_OK:

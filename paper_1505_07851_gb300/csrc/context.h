@@ -199,10 +199,10 @@ int fock_compute(pcm_ctx *c, const double *dq, double *ddF);
 // PCM_MIXED (integrals_mixed.cu)
 int points_split(pcm_ctx *c);
 int esp_compute_mixed(pcm_ctx *c, double *dc);
-int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W);
-int fock_mixed_pairs_per_thread(int L);
+int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt);
+int fock_mixed_pairs_per_thread(pcm_ctx *c, int L, long long npair);
 int grad_point_mixed(pcm_ctx *c, int *total_rows);
-int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W);
+int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt);
 int solver_prepare(pcm_ctx *c);
 int solver_prepare_full(pcm_ctx *c);
 int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st);

@@ -23,6 +23,7 @@
 #include "boys.cuh"
 #include "common.cuh"
 #include "context.h"
+#include "tune.h"
 
 namespace pcm {
 
@@ -831,6 +832,48 @@ int esp_compute(pcm_ctx *c, const double *dP, double *dc)
     return esp_class_stats(c);
 }
 
+// points of each split and the number of splits for a Fock launch of nb
+// pair blocks: enough CTAs to fill the GPU, splits on whole point tiles
+static void fock_split(pcm_ctx *c, int nb, int *nsplit, int *ks)
+{
+    const int maxsplit = std::max(1, (c->M + FOCK_TQ - 1) / FOCK_TQ);
+    int ns = std::max(1, std::min(maxsplit, (target_ctas(c) + nb - 1) / nb));
+    int k = (c->M + ns - 1) / ns;
+    k = (k + FOCK_TQ - 1) / FOCK_TQ * FOCK_TQ;
+    *ks = k;
+    *nsplit = (c->M + k - 1) / k;
+}
+
+// The autotuner's trial for the FP32 Fock kernel of class k: one and two
+// pairs per thread, each timed once; the faster is remembered.
+static int fock_tune(pcm_ctx *c, int k, int L, const double *dq)
+{
+    PairClass &pc = c->cls[k];
+    const int bucket = tune_bucket(pc.npair);
+    if (tune_get(c->device, TUNE_FOCK_NPT, L, bucket) >= 0) return PCM_OK;
+    float ms[2] = {0.f, 0.f};
+    cudaEvent_t e0, e1;
+    PCM_CUDA(cudaEventCreate(&e0));
+    PCM_CUDA(cudaEventCreate(&e1));
+    int st = PCM_OK;
+    for (int npt = 1; npt <= 2 && st == PCM_OK; ++npt) {
+        const int nb = (pc.npair + FOCK_NT * npt - 1) / (FOCK_NT * npt);
+        int nsplit, ks;
+        fock_split(c, nb, &nsplit, &ks);
+        st = c->fock_W.alloc((size_t)nsplit * nherm(L) * pc.npair);
+        if (st != PCM_OK) break;
+        cudaEventRecord(e0, c->stream);
+        st = fock_mixed_class(c, k, dq, nsplit, ks, c->fock_W.p, npt);
+        cudaEventRecord(e1, c->stream);
+        if (st == PCM_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms[npt - 1], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PCM_OK) return st;
+    tune_set(c->device, TUNE_FOCK_NPT, L, bucket, ms[1] < ms[0] ? 2 : 1, ms[0], ms[1]);
+    return PCM_OK;
+}
+
 template <int LA, int LB>
 static int fock_class(pcm_ctx *c, PairClass &pc, const double *dq, double *ddF)
 {
@@ -839,18 +882,18 @@ static int fock_class(pcm_ctx *c, PairClass &pc, const double *dq, double *ddF)
     if (pc.nsp == 0) return PCM_OK;
     int nsplit = 1;
     if (pc.npair > 0) {
-        const int per = FOCK_NT * (c->opt.precision == PCM_MIXED ? fock_mixed_pairs_per_thread(L) : 1);
-        const int nb = (pc.npair + per - 1) / per;
-        const int maxsplit = std::max(1, (c->M + FOCK_TQ - 1) / FOCK_TQ);
-        nsplit = std::max(1, std::min(maxsplit, (target_ctas(c) + nb - 1) / nb));
-        int ks = (c->M + nsplit - 1) / nsplit;
-        ks = (ks + FOCK_TQ - 1) / FOCK_TQ * FOCK_TQ;
-        nsplit = (c->M + ks - 1) / ks;
+        const bool mixed = c->opt.precision == PCM_MIXED;
+        const int k = (int)(&pc - c->cls);
+        if (mixed && c->opt.autotune) PCM_TRY(fock_tune(c, k, L, dq));
+        const int npt = mixed ? fock_mixed_pairs_per_thread(c, L, pc.npair) : 1;
+        const int nb = (pc.npair + FOCK_NT * npt - 1) / (FOCK_NT * npt);
+        int ks;
+        fock_split(c, nb, &nsplit, &ks);
         PCM_TRY(c->fock_W.alloc((size_t)nsplit * NH * pc.npair));
         dim3 grid(nb, nsplit);
-        if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[6 + (int)(&pc - c->cls)], c->stream));
-        if (c->opt.precision == PCM_MIXED) {
-            PCM_TRY(fock_mixed_class(c, (int)(&pc - c->cls), dq, nsplit, ks, c->fock_W.p));
+        if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[6 + k], c->stream));
+        if (mixed) {
+            PCM_TRY(fock_mixed_class(c, k, dq, nsplit, ks, c->fock_W.p, npt));
         } else {
             fock_kernel_f64<L><<<grid, FOCK_NT, 0, c->stream>>>(pc.npair, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, ks,
                                                                  c->px.p, c->py.p, c->pz.p, dq, c->M, c->ncls,
@@ -858,7 +901,7 @@ static int fock_class(pcm_ctx *c, PairClass &pc, const double *dq, double *ddF)
                                                                  c->fock_W.p);
             PCM_LAUNCHED(c);
         }
-        if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[6 + (int)(&pc - c->cls)], c->stream));
+        if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[6 + k], c->stream));
     }
     fock_epilogue_kernel<LA, LB><<<(pc.nsp + 127) / 128, 128, 0, c->stream>>>(
         pc.nsp, pc.npair, nsplit, pc.spA.p, pc.spB.p, pc.sp_start.p, pc.ia.p, pc.ib.p, c->sh_atom.p, c->sh_off.p,
@@ -938,16 +981,13 @@ static int grad_pair_class(pcm_ctx *c, PairClass &pc, const double *dP, const do
     constexpr int NH1 = nherm(L1);
     if (pc.nesp == 0) return PCM_OK;
     const int n = pc.nesp;
-    const int per = FOCK_NT * (c->opt.precision == PCM_MIXED ? fock_mixed_pairs_per_thread(L1) : 1);
-    const int nb = (n + per - 1) / per;
-    const int maxsplit = std::max(1, (c->M + FOCK_TQ - 1) / FOCK_TQ);
-    int nsplit = std::max(1, std::min(maxsplit, (target_ctas(c) + nb - 1) / nb));
-    int ks = (c->M + nsplit - 1) / nsplit;
-    ks = (ks + FOCK_TQ - 1) / FOCK_TQ * FOCK_TQ;
-    nsplit = (c->M + ks - 1) / ks;
+    const int npt = c->opt.precision == PCM_MIXED ? fock_mixed_pairs_per_thread(c, L1, n) : 1;
+    const int nb = (n + FOCK_NT * npt - 1) / (FOCK_NT * npt);
+    int nsplit, ks;
+    fock_split(c, nb, &nsplit, &ks);
     PCM_TRY(c->fock_W.alloc((size_t)nsplit * NH1 * n));
     if (c->opt.precision == PCM_MIXED) {
-        PCM_TRY(grad_w_mixed(c, (int)(&pc - c->cls), dq, nsplit, ks, c->fock_W.p));
+        PCM_TRY(grad_w_mixed(c, (int)(&pc - c->cls), dq, nsplit, ks, c->fock_W.p, npt));
     } else {
         dim3 grid(nb, nsplit);
         fock_kernel_f64<L1><<<grid, FOCK_NT, 0, c->stream>>>(n, pc.eP.p, pc.eP.p + n, pc.eP.p + 2 * (size_t)n,

@@ -21,6 +21,7 @@
 #include "boys.cuh"
 #include "common.cuh"
 #include "context.h"
+#include "tune.h"
 
 namespace pcm {
 
@@ -163,11 +164,13 @@ __device__ __forceinline__ void boys_df(float Th, float Tl, const float *__restr
 constexpr int MESP_NT = 128;
 constexpr int MESP_TP = 32;
 // points per thread: more independent work for the light classes
-template <int L> struct EspPPT { static constexpr int value = L <= 1 ? 4 : 2; };
+// points per thread: the autotuner picks 4 or 2 per class (default: 4 for
+// the light classes, which have more independent work per pair)
+constexpr int esp_default_ppt(int L) { return L <= 1 ? 4 : 2; }
 
 // Per tile of TP pairs, shared memory holds per pair float4 (xh, yh, zh, rho_hi),
 // float4 (xl, yl, zl, rho_lo), rho_lo/rho_hi and NH float2 (hi, lo) of U D_h.
-template <int L, bool SC>
+template <int L, bool SC, int PPT>
 __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int jbeg, int jend, int seglen,
                                                           const float *__restrict__ eX, const float *__restrict__ eC,
                                                           const int *__restrict__ blk_off,
@@ -177,7 +180,6 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int jbeg, in
 {
     constexpr int NH = nherm(L);
     constexpr int F = 3 + 2 * NH;
-    constexpr int PPT = EspPPT<L>::value;
     __shared__ float4 sA[MESP_TP], sB[MESP_TP];
     __shared__ float sR[MESP_TP];
     __shared__ float2 sD[NH][MESP_TP];
@@ -333,11 +335,17 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int jbeg, in
 // ---------------------------------------------------------------------------
 constexpr int MF_NT = 128;
 constexpr int MF_TQ = 128;
-template <int L> struct FockNPT { static constexpr int value = L <= 1 ? 2 : 1; };
+constexpr int fock_default_npt(int L) { return L <= 1 ? 2 : 1; }
 
-int fock_mixed_pairs_per_thread(int L) { return L <= 1 ? 2 : 1; }
+// pairs per thread of the FP32 Fock kernel for class L: the autotuner's
+// choice when it has one for this context's GPU, else the default
+int fock_mixed_pairs_per_thread(pcm_ctx *c, int L, long long npair)
+{
+    const int t = c->opt.autotune ? tune_get(c->device, TUNE_FOCK_NPT, L, tune_bucket(npair)) : -1;
+    return t > 0 ? t : fock_default_npt(L);
+}
 
-template <int L>
+template <int L, int NPT>
 __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double *__restrict__ gp,
                                                          const float *__restrict__ Phl, int ksplit,
                                                          const float *__restrict__ ph, const float *__restrict__ pl,
@@ -347,7 +355,6 @@ __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double
                                                          const float *__restrict__ boys, double *__restrict__ W)
 {
     constexpr int NH = nherm(L);
-    constexpr int NPT = FockNPT<L>::value;
     __shared__ float4 sH[MF_TQ], sL[MF_TQ];  // (xh, yh, zh, q) and (xl, yl, zl, 0) per point
     int r[NPT];
     bool active[NPT];
@@ -475,7 +482,7 @@ __global__ void __launch_bounds__(MESP_NT) esp_grad_kernel_f32(int nesp, int seg
     constexpr int L1 = L + 1;
     constexpr int NH1 = nherm(L1);
     constexpr int F = 3 + 2 * NH;
-    constexpr int PPT = EspPPT<L>::value;
+    constexpr int PPT = esp_default_ppt(L);
     __shared__ float4 sA[MESP_TP], sB[MESP_TP];
     __shared__ float sR[MESP_TP];
     __shared__ float2 sD[NH][MESP_TP];
@@ -604,7 +611,7 @@ static void esp_plan(int n, int nblk, int *seglen, int *rows)
     *rows = (n + sl - 1) / sl;
 }
 
-template <int L>
+template <int L, int PPT>
 static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, const int *bcls, int nblk, double *part)
 {
     constexpr int NH = nherm(L);
@@ -622,7 +629,7 @@ static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, co
     esp_plan(ns, nblk, &sl, &rows);
     if (rows > 0) {
         dim3 grid(nblk, rows);
-        esp_kernel_f32<L, true><<<grid, MESP_NT, 0, c->stream>>>(n, 0, ns, sl, pc.eX32.p, pc.eC32.p, blk, bcls,
+        esp_kernel_f32<L, true, PPT><<<grid, MESP_NT, 0, c->stream>>>(n, 0, ns, sl, pc.eX32.p, pc.eC32.p, blk, bcls,
                                                                   c->p32.p, c->p32lo.p, c->boys32.p, c->M, part);
         PCM_LAUNCHED(c);
         part += (size_t)rows * c->M;
@@ -630,7 +637,8 @@ static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, co
     esp_plan(nx, nblk, &sl, &rows);
     if (rows > 0) {
         dim3 grid(nblk, rows);
-        esp_kernel_f32<L, false><<<grid, MESP_NT, 0, c->stream>>>(n, ns, n, sl, pc.eX32.p, pc.eC32.p, blk, bcls,
+        esp_kernel_f32<L, false, PPT><<<grid, MESP_NT, 0, c->stream>>>(n, ns, n, sl, pc.eX32.p, pc.eC32.p, blk,
+                                                                        bcls,
                                                                    c->p32.p, c->p32lo.p, c->boys32.p, c->M, part);
         PCM_LAUNCHED(c);
     }
@@ -668,19 +676,80 @@ static int mixed_point_blocks(pcm_ctx *c, int nblk[2])
     return PCM_OK;
 }
 
+// layout v of the point blocks: PPT 4 (v = 0) or 2 (v = 1)
+static int esp_launch_variant(pcm_ctx *c, int k, int v, DBuf<int> *blk, DBuf<int> *bcls, const int nb[2], double *part)
+{
+    PairClass &pc = c->cls[k];
+#define PCM_ESPV(LL)                                                                                         \
+    case LL:                                                                                                 \
+        return v == 0 ? esp_mixed_launch<LL, 4>(c, pc, k, blk[0].p, bcls[0].p, nb[0], part)                  \
+                      : esp_mixed_launch<LL, 2>(c, pc, k, blk[1].p, bcls[1].p, nb[1], part);
+    switch (CLASS_L[k]) {
+        PCM_ESPV(0)
+        PCM_ESPV(1)
+        PCM_ESPV(2)
+        PCM_ESPV(3)
+        PCM_ESPV(4)
+    }
+#undef PCM_ESPV
+    return PCM_ERR_ARG;
+}
+
+static int esp_rows(pcm_ctx *c, int k, int nblk)
+{
+    int sl, r1, r2;
+    esp_plan(c->cls[k].nesp_same, nblk, &sl, &r1);
+    esp_plan(c->cls[k].nesp - c->cls[k].nesp_same, nblk, &sl, &r2);
+    return r1 + r2;
+}
+
+// The autotuner's trial for class k: both layouts timed once with CUDA
+// events on the context's stream; the faster one is remembered for this GPU,
+// kernel family, angular momentum and size bucket.
+static int esp_tune(pcm_ctx *c, int k, DBuf<int> *blk, DBuf<int> *bcls, const int nb[2], int *choice)
+{
+    const int L = CLASS_L[k];
+    const int bucket = tune_bucket((long long)c->cls[k].nesp);
+    const int t = tune_get(c->device, TUNE_ESP_PPT, L, bucket);
+    if (t >= 0) {
+        *choice = t;
+        return PCM_OK;
+    }
+    const int rmax = std::max(esp_rows(c, k, nb[0]), esp_rows(c, k, nb[1]));
+    PCM_TRY(c->esp_part.alloc((size_t)std::max(1, rmax) * c->M));
+    cudaEvent_t e[3];
+    for (int i = 0; i < 3; ++i) PCM_CUDA(cudaEventCreate(&e[i]));
+    float ms[2] = {0.f, 0.f};
+    int st = PCM_OK;
+    PCM_CUDA(cudaEventRecord(e[0], c->stream));
+    st = esp_launch_variant(c, k, 0, blk, bcls, nb, c->esp_part.p);
+    if (st == PCM_OK) {
+        PCM_CUDA(cudaEventRecord(e[1], c->stream));
+        st = esp_launch_variant(c, k, 1, blk, bcls, nb, c->esp_part.p);
+    }
+    if (st == PCM_OK) {
+        PCM_CUDA(cudaEventRecord(e[2], c->stream));
+        PCM_CUDA(cudaEventSynchronize(e[2]));
+        PCM_CUDA(cudaEventElapsedTime(&ms[0], e[0], e[1]));
+        PCM_CUDA(cudaEventElapsedTime(&ms[1], e[1], e[2]));
+    }
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+    if (st != PCM_OK) return st;
+    *choice = ms[1] < ms[0] ? 1 : 0;
+    tune_set(c->device, TUNE_ESP_PPT, L, bucket, *choice, ms[0], ms[1]);
+    return PCM_OK;
+}
+
 int esp_compute_mixed(pcm_ctx *c, double *dc)
 {
     int nb[2];
     PCM_TRY(mixed_point_blocks(c, nb));
     DBuf<int> *blk = &c->si[4], *bcls = &c->si[6];  // blk[0..1], bcls[0..1]
-    int rows[6], total = 0;
+    int var[6], rows[6], total = 0;
     for (int k = 0; k < 6; ++k) {
-        PairClass &pc = c->cls[k];
-        const int nblk = nb[CLASS_L[k] <= 1 ? 0 : 1];
-        int sl, r1, r2;
-        esp_plan(pc.nesp_same, nblk, &sl, &r1);
-        esp_plan(pc.nesp - pc.nesp_same, nblk, &sl, &r2);
-        rows[k] = r1 + r2;
+        var[k] = esp_default_ppt(CLASS_L[k]) == 4 ? 0 : 1;
+        if (c->opt.autotune && c->cls[k].nesp > 0) PCM_TRY(esp_tune(c, k, blk, bcls, nb, &var[k]));
+        rows[k] = c->cls[k].nesp > 0 ? esp_rows(c, k, nb[var[k]]) : 0;
         total += rows[k];
     }
     if (total == 0) {
@@ -691,18 +760,8 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
     PCM_TRY(c->esp_part.alloc((size_t)total * c->M));
     int base = 0;
     for (int k = 0; k < 6; ++k) {
-        PairClass &pc = c->cls[k];
-        if (pc.nesp == 0) continue;
-        double *part = c->esp_part.p + (size_t)base * c->M;
-        const int v = CLASS_L[k] <= 1 ? 0 : 1;
-        const int nblk = nb[v];
-        switch (CLASS_L[k]) {
-        case 0: PCM_TRY(esp_mixed_launch<0>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
-        case 1: PCM_TRY(esp_mixed_launch<1>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
-        case 2: PCM_TRY(esp_mixed_launch<2>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
-        case 3: PCM_TRY(esp_mixed_launch<3>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
-        case 4: PCM_TRY(esp_mixed_launch<4>(c, pc, k, blk[v].p, bcls[v].p, nblk, part)); break;
-        }
+        if (c->cls[k].nesp == 0) continue;
+        PCM_TRY(esp_launch_variant(c, k, var[k], blk, bcls, nb, c->esp_part.p + (size_t)base * c->M));
         base += rows[k];
     }
     esp_reduce_mixed_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
@@ -711,18 +770,23 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
     return PCM_OK;
 }
 
-int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W)
+int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt)
 {
     PairClass &pc = c->cls[k];
-    const int per = MF_NT * fock_mixed_pairs_per_thread(CLASS_L[k]);
+    const int per = MF_NT * npt;
     const int nb = (pc.npair + per - 1) / per;
     dim3 grid(nb, nsplit);
     switch (CLASS_L[k]) {
 #define PCM_FOCK_F32(LL)                                                                                           \
     case LL:                                                                                                       \
-        fock_kernel_f32<LL><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit, c->p32.p,        \
-                                                            c->p32lo.p, dq, c->M, c->ncls, c->cls_off.p,           \
-                                                            c->cls_zeta.p, c->boys32.p, W);                        \
+        if (npt == 2)                                                                                              \
+            fock_kernel_f32<LL, 2><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit, c->p32.p, \
+                                                                   c->p32lo.p, dq, c->M, c->ncls, c->cls_off.p,    \
+                                                                   c->cls_zeta.p, c->boys32.p, W);                 \
+        else                                                                                                       \
+            fock_kernel_f32<LL, 1><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit, c->p32.p, \
+                                                                   c->p32lo.p, dq, c->M, c->ncls, c->cls_off.p,    \
+                                                                   c->cls_zeta.p, c->boys32.p, W);                 \
         break;
         PCM_FOCK_F32(0)
         PCM_FOCK_F32(1)
@@ -797,19 +861,26 @@ int grad_point_mixed(pcm_ctx *c, int *total_rows)
 
 // W_tuv (t+u+v <= L+1) over the ESP pairs of class k on the FP32 pipes; the
 // pairs' split centres come from the point-part preparation (eX32)
-int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W)
+int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt)
 {
     PairClass &pc = c->cls[k];
     const int n = pc.nesp;
-    const int per = MF_NT * fock_mixed_pairs_per_thread(CLASS_L[k] + 1);
+    const int per = MF_NT * npt;
     const int nb = (n + per - 1) / per;
     dim3 grid(nb, nsplit);
     switch (CLASS_L[k] + 1) {
 #define PCM_GW(LL)                                                                                             \
     case LL:                                                                                                   \
-        fock_kernel_f32<LL><<<grid, MF_NT, 0, c->stream>>>(n, pc.eP.p + 3 * (size_t)n, pc.eX32.p, ksplit,        \
-                                                            c->p32.p, c->p32lo.p, dq, c->M, c->ncls,           \
-                                                            c->cls_off.p, c->cls_zeta.p, c->boys32.p, W);      \
+        if (npt == 2)                                                                                          \
+            fock_kernel_f32<LL, 2><<<grid, MF_NT, 0, c->stream>>>(n, pc.eP.p + 3 * (size_t)n, pc.eX32.p,         \
+                                                                   ksplit, c->p32.p, c->p32lo.p, dq, c->M,     \
+                                                                   c->ncls, c->cls_off.p, c->cls_zeta.p,       \
+                                                                   c->boys32.p, W);                            \
+        else                                                                                                   \
+            fock_kernel_f32<LL, 1><<<grid, MF_NT, 0, c->stream>>>(n, pc.eP.p + 3 * (size_t)n, pc.eX32.p,         \
+                                                                   ksplit, c->p32.p, c->p32lo.p, dq, c->M,     \
+                                                                   c->ncls, c->cls_off.p, c->cls_zeta.p,       \
+                                                                   c->boys32.p, W);                            \
         break;
         PCM_GW(1)
         PCM_GW(2)

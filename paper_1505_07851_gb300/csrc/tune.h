@@ -1,0 +1,22 @@
+// Autotuner cache: for each (GPU, kernel family, angular momentum, size
+// bucket) the launch variant that ran fastest in a timed trial.  Process-wide
+// and thread-safe; a trial runs once per key, on the first call that needs it.
+#pragma once
+
+namespace pcm {
+
+enum TuneKind {
+    TUNE_ESP_PPT = 0,    // FP32 ESP kernel: surface points per thread (variant 0: 4, 1: 2)
+    TUNE_FOCK_NPT = 1,   // FP32 Fock kernel: primitive pairs per thread (1 or 2)
+};
+
+// size bucket of a kernel's work: floor(log2(n)) (pairs of the class)
+int tune_bucket(long long n);
+// the remembered choice, or -1
+int tune_get(int device, int kind, int L, int bucket);
+// remember a choice with the trial times of the two variants (ms)
+void tune_set(int device, int kind, int L, int bucket, int choice, float ms0, float ms1);
+// copy up to max entries of (device, kind, L, bucket, choice) into out; returns the count
+int tune_table(int *out, int max);
+
+}  // namespace pcm

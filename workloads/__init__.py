@@ -364,12 +364,34 @@ def small_cluster(natom: int, seed: int, d_shells: bool = False, radius_A: float
                    name="cluster%d%s" % (natom, "_spd" if d_shells else "_sp"))
 
 
-def conformations(n: int = 64, seed: int = 150507851 + 4, lo: int = 150, hi: int = 600):
-    """Seeded batch of peptide-like clusters with uniform-random sizes."""
+def _conformation(args):
+    na, seed, j = args
+    r = 8.0 * (na / 300.0) ** (1.0 / 3.0)
+    return cluster(int(na), seed * 1000 + j, r, name="conf%d" % j)
+
+
+def conformations(n: int = 64, seed: int = 150507851 + 4, lo: int = 150, hi: int = 600, workers: int = 0):
+    """Seeded batch of peptide-like clusters with uniform-random sizes in
+    [lo, hi] atoms (s/sp shells, 2 natom occupied orbitals).  workers > 1
+    builds them in that many processes (spawned, so that a CUDA context of the
+    caller is never forked); the result does not depend on it."""
     rng = np.random.default_rng(seed)
     sizes = rng.integers(lo, hi + 1, size=n)
-    out = []
-    for j, na in enumerate(sizes):
-        r = 8.0 * (na / 300.0) ** (1.0 / 3.0)
-        out.append(cluster(int(na), seed * 1000 + j, r, name="conf%d" % j))
-    return out
+    jobs = [(int(na), seed, j) for j, na in enumerate(sizes)]
+    if workers > 1:
+        import multiprocessing as mp
+        import os
+        # one BLAS thread per worker process (the workers already fill the cores)
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        os.environ.update({k: "1" for k in keys})
+        try:
+            with mp.get_context("spawn").Pool(workers) as pool:
+                return pool.map(_conformation, jobs, chunksize=1)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+    return [_conformation(a) for a in jobs]
