@@ -540,8 +540,10 @@ def run_batch(args):
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     Pd = [torch.tensor(w.P, dtype=torch.float64, device=dev) for w in confs]
+    # outputs every step: the energies, and the Fock corrections on the device
+    Fd = [torch.empty((w.basis.nbf, w.basis.nbf), dtype=torch.float64, device=dev) for w in confs]
     for _ in range(args.warmup):
-        b.run(Pd, delta)
+        b.run(Pd, delta, dF_out=Fd)
     torch.cuda.synchronize()
     launches0 = b.stats()["launches"]
     times, ints = [], 0.0
@@ -552,7 +554,7 @@ def run_batch(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            E, _, _ = b.run(Pd, delta)
+            E, _, _ = b.run(Pd, delta, dF_out=Fd)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -569,16 +571,17 @@ def run_batch(args):
     e2e = None
     if not args.no_e2e:
         Ph = [np.ascontiguousarray(w.P) for w in confs]
+        Fh = [np.empty_like(P) for P in Ph]
         et = []
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            b.run(Ph, delta)
+            b.run(Ph, delta, dF_out=Fh)
             et.append(time.perf_counter() - t1)
         e_val, e_ms = replica_throughput(ints * len(et) / args.steps, sum(et) * 1e3, world, dev)
         e2e = {"value": e_val, "unit": UNIT, "h2d_bytes_per_step": int(sum(P.nbytes for P in Ph)),
-               "d2h_bytes_per_step": 8 * len(confs), "ms_per_step": e_ms / len(et)}
+               "d2h_bytes_per_step": int(sum(F.nbytes for F in Fh)) + 8 * len(confs), "ms_per_step": e_ms / len(et)}
     # per-conformation error against the FP64 single-molecule path (a sample)
     errs = []
     for i in range(min(args.ref_mols, len(confs))):

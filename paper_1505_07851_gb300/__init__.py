@@ -399,9 +399,10 @@ class Batch:
         self.sizes[i] = (M.value, nbf.value)
         return self.sizes[i]
 
-    def run(self, Ps, delta, want_q=False, want_dF=False):
+    def run(self, Ps, delta, want_q=False, want_dF=False, dF_out=None):
         """Ps: nmol densities (all NumPy arrays or all CUDA tensors).  Returns
-        (E, q list or None, dF list or None); outputs live where Ps live."""
+        (E, q list or None, dF list or None); outputs live where Ps live.
+        dF_out: caller-owned Fock-correction outputs (one per molecule)."""
         if len(Ps) != self.nmol:
             raise ValueError("one density per molecule")
         dev = _is_torch(Ps[0])
@@ -419,8 +420,12 @@ class Batch:
         if want_q:
             q = [self._alloc(Ps[i], (self.sizes[i][0],)) for i in range(self.nmol)]
             q_ptrs = (ctypes.c_void_p * self.nmol)(*[_ptr(a, np.float64)[0] for a in q])
-        if want_dF:
-            dF = [self._alloc(Ps[i], (self.sizes[i][1], self.sizes[i][1])) for i in range(self.nmol)]
+        if want_dF or dF_out is not None:
+            dF = list(dF_out) if dF_out is not None else \
+                [self._alloc(Ps[i], (self.sizes[i][1], self.sizes[i][1])) for i in range(self.nmol)]
+            for i, a in enumerate(dF):
+                if tuple(a.shape) != (self.sizes[i][1], self.sizes[i][1]) or _is_torch(a) != dev:
+                    raise TypeError("dF_out[%d] must be an nbf x nbf array on the densities' side" % i)
             dF_ptrs = (ctypes.c_void_p * self.nmol)(*[_ptr(a, np.float64)[0] for a in dF])
         self._check(_lib.pcm_batch_run(self._h, P_ptrs, float(delta), E.ctypes.data, q_ptrs, dF_ptrs,
                                        PCM_PTR_DEVICE if dev else 0), "pcm_batch_run")
