@@ -76,6 +76,7 @@ typedef enum pcm_status {
 #define PCM_PRECOND_NONE 1
 #define PCM_PRECOND_JACOBI 2
 #define PCM_PRECOND_RBJ 3
+#define PCM_PRECOND_OCTREE 4    /* block Jacobi on octree leaves of at most octree_leaf points (comparison) */
 
 typedef struct pcm_options {
     double eps;                 /* dielectric constant, default 78.39 (Section 3) */
@@ -93,6 +94,7 @@ typedef struct pcm_options {
     void *stream;               /* cudaStream_t to use; NULL: the context creates its own */
     int timing;                 /* 1: time the integral kernels and the solve with CUDA events (stats) */
     int autotune;               /* 1: pick the FP32 integral kernels' tile shapes by timed trials (default 0) */
+    int octree_leaf;            /* PCM_PRECOND_OCTREE: most points per octree leaf (block), default 800 */
 } pcm_options;
 
 typedef struct pcm_stats {

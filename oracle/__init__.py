@@ -9,5 +9,5 @@ other.
 from .pcm import *  # noqa: F401,F403
 from .pcm import (ExpandedBasis, Preconditioner, a_matrix, boys, bz, dynamic_delta, energy, esp,
                   f_factor, fibonacci_directions, fock, fock_blocks, gradient, gradient_a,
-                  gradient_bz, gradient_c, pcg, prim_integrals, prim_norm,
+                  gradient_bz, gradient_c, octree_blocks, pcg, prim_integrals, prim_norm,
                   rbj_blocks, run, solve_lu, splitmix64, surface, switching_factor)

@@ -14,7 +14,8 @@ Contents, each following the passage cited:
   * esp(), fock(): Eq. 5, Eq. 6, Eq. 10, Eq. 12 via the C part (integrals.c).
   * solve_lu(): dense LU solve of Eq. 1 (LAPACK via numpy).
   * pcg(): CG / Jacobi-PCG / randomized block-Jacobi PCG with the residual
-    test of Eq. 20 (Section 4b), the RBJ permutation of Section 4b-ii.
+    test of Eq. 20 (Section 4b), the RBJ permutation of Section 4b-ii, and
+    the octree block-Jacobi the paper compares RBJ with.
   * dynamic_delta(): Eq. 21 and the rule that follows it.
   * energy(): Eq. 13.
   * gradient_bz(), gradient_a(), gradient_c(), gradient(): the nuclear
@@ -344,19 +345,50 @@ def rbj_blocks(A, l, seed):
     return blocks
 
 
-class Preconditioner:
-    """z = C r for C = I (none), diag(A)^-1 (Jacobi) or P M^-1 P (RBJ)."""
+def octree_blocks(r, leaf):
+    """Octree partition of the points r (M x 3) used by the block-Jacobi
+    comparison of Section 4b-ii (reading: the bounding cube, centred on the
+    bounding box with side equal to its largest extent, is split at its
+    centre into octants 4[x >= cx] + 2[y >= cy] + [z >= cz] until a box holds
+    at most `leaf` points; non-empty leaves in depth-first octant order, points
+    in ascending index).  Returns a list of index arrays."""
+    r = np.asarray(r, np.float64)
+    lo, hi = r.min(axis=0), r.max(axis=0)
+    out = []
 
-    def __init__(self, A, kind="rbj", l=100, seed=0):
+    def split(idx, c, h, depth):
+        if len(idx) <= leaf or depth >= 40:
+            if len(idx):
+                out.append(np.sort(idx))
+            return
+        o = 4 * (r[idx, 0] >= c[0]) + 2 * (r[idx, 1] >= c[1]) + (r[idx, 2] >= c[2])
+        q = 0.5 * h
+        for k in range(8):
+            sub = idx[o == k]
+            cc = c + q * np.array([1 if k & 4 else -1, 1 if k & 2 else -1, 1 if k & 1 else -1])
+            split(sub, cc, q, depth + 1)
+
+    split(np.arange(len(r)), 0.5 * (lo + hi), 0.5 * float(np.max(hi - lo)), 0)
+    return out
+
+
+class Preconditioner:
+    """z = C r for C = I (none), diag(A)^-1 (Jacobi), P M^-1 P (RBJ), or
+    block Jacobi on octree leaves (pass the points as `points`)."""
+
+    def __init__(self, A, kind="rbj", l=100, seed=0, points=None):
         self.kind = kind
         if kind == "none":
             return
         if kind == "jacobi":
             self.dinv = 1.0 / np.diag(A)
             return
-        if kind != "rbj":
+        if kind == "rbj":
+            self.blocks = rbj_blocks(A, l, seed)
+        elif kind == "octree":
+            self.blocks = octree_blocks(points, l)
+        else:
             raise ValueError(kind)
-        self.blocks = rbj_blocks(A, l, seed)
         self.inv = [np.linalg.inv(A[np.ix_(b, b)]) for b in self.blocks]
 
     def apply(self, r):

@@ -46,7 +46,7 @@ PCM_GRAD_C = 16
 PCM_GRAD_A = 32
 PCM_FP64 = 0
 PCM_MIXED = 1
-PRECOND = {"auto": 0, "none": 1, "jacobi": 2, "rbj": 3}
+PRECOND = {"auto": 0, "none": 1, "jacobi": 2, "rbj": 3, "octree": 4}
 
 
 class pcm_options(ctypes.Structure):
@@ -55,7 +55,7 @@ class pcm_options(ctypes.Structure):
                 ("rbj_block", ctypes.c_int), ("precond", ctypes.c_int), ("jacobi_below", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("device", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("octree_leaf", ctypes.c_int)]
 
 
 class pcm_stats(ctypes.Structure):
@@ -185,7 +185,7 @@ class Context:
 
     def __init__(self, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
                  precond="auto", jacobi_below=1000, precision="fp64", max_iter=5000, device=0, seed=0,
-                 stream=None, timing=False, autotune=False):
+                 stream=None, timing=False, autotune=False, octree_leaf=800):
         o = pcm_options()
         _lib.pcm_default_options(ctypes.byref(o))
         o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
@@ -195,6 +195,7 @@ class Context:
         o.stream = stream
         o.timing = 1 if timing else 0
         o.autotune = 1 if autotune else 0
+        o.octree_leaf = int(octree_leaf)
         h = ctypes.c_void_p()
         self._check(_lib.pcm_create(ctypes.byref(h), ctypes.byref(o)), "pcm_create")
         self._h = h

@@ -680,6 +680,10 @@ int pcm_batch_set_molecule(pcm_batch *bt, int i, int natom, const double *xyz, c
         set_last_error("pcm_batch_set_molecule: bad molecule index");
         return PCM_ERR_ARG;
     }
+    if (bt->opt.precond == PCM_PRECOND_OCTREE) {
+        set_last_error("pcm_batch_set_molecule: batches use RBJ or Jacobi preconditioners");
+        return PCM_ERR_UNSUPPORTED;
+    }
     pcm_ctx *c = bt->mol[i];
     bt->ready[i] = 0;
     bt->layout_ok = false;

@@ -155,6 +155,7 @@ struct pcm_ctx {
     int rbj_l = 0, rbj_nblk = 0;
     pcm::DBuf<int> rbj_perm;               // M: block-ordered point indices
     pcm::DBuf<double> rbj_inv;             // nblk x l x l inverses (padded)
+    pcm::DBuf<int> rbj_bstart;             // octree: nblk + 1 block starts in rbj_perm (blocks of varying size)
 
     // solver work vectors and scalars
     pcm::DBuf<double> vx, vr, vz, vp, vAp, vrhs, vtmp, vro, vd;
@@ -205,6 +206,8 @@ int grad_point_mixed(pcm_ctx *c, int *total_rows);
 int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt);
 int solver_prepare(pcm_ctx *c);
 int solver_prepare_full(pcm_ctx *c);
+void octree_partition(const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
+                      int leaf, std::vector<int> &perm, std::vector<int> &start);
 int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st);
 int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E);
 // gradient (gradient.cu, integrals.cu)

@@ -177,13 +177,14 @@ constexpr int RBJ_SPLIT = 4;   // threads per row in the block-Jacobi apply
 // init, first x += alpha p and r -= alpha Ap on the block's indices; then
 // z = Minv r there.  Returns the block's r.r and r.z in thread 0.
 __device__ __forceinline__ void rbj_apply_block(int M, int l, int b, const int *__restrict__ perm,
-                                                const double *__restrict__ inv, double *__restrict__ x,
-                                                double *__restrict__ r, double *__restrict__ z,
-                                                const double *__restrict__ p, const double *__restrict__ Ap,
-                                                double alpha, int init, double *srb, double *rr_out, double *rz_out)
+                                                const int *__restrict__ bstart, const double *__restrict__ inv,
+                                                double *__restrict__ x, double *__restrict__ r,
+                                                double *__restrict__ z, const double *__restrict__ p,
+                                                const double *__restrict__ Ap, double alpha, int init, double *srb,
+                                                double *rr_out, double *rz_out)
 {
-    const int base = b * l;
-    const int nb = min(l, M - base);
+    const int base = bstart ? bstart[b] : b * l;
+    const int nb = bstart ? bstart[b + 1] - base : min(l, M - base);
     double rr = 0.0, rz = 0.0;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         const int k = perm[base + i];
@@ -235,10 +236,11 @@ __device__ __forceinline__ void rbj_apply_block(int M, int l, int b, const int *
 // Randomized block-Jacobi update, one block per RBJ block; the last block
 // to finish sums the partials.  With init (initialisation) x and r are left
 // unchanged.
-__global__ void pcg_update_rbj_kernel(int M, int l, const int *__restrict__ perm, const double *__restrict__ inv,
-                                      double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
-                                      const double *__restrict__ p, const double *__restrict__ Ap,
-                                      double *__restrict__ part, double *__restrict__ scal, int *__restrict__ iscal,
+__global__ void pcg_update_rbj_kernel(int M, int l, const int *__restrict__ perm, const int *__restrict__ bstart,
+                                      const double *__restrict__ inv, double *__restrict__ x, double *__restrict__ r,
+                                      double *__restrict__ z, const double *__restrict__ p,
+                                      const double *__restrict__ Ap, double *__restrict__ part,
+                                      double *__restrict__ scal, int *__restrict__ iscal,
                                       unsigned int *__restrict__ counter, int init)
 {
     extern __shared__ double srb[];  // l entries
@@ -246,7 +248,7 @@ __global__ void pcg_update_rbj_kernel(int M, int l, const int *__restrict__ perm
     const int b = blockIdx.x;
     const double alpha = init ? 0.0 : scal[S_ALPHA];
     double a = 0.0, c = 0.0;
-    rbj_apply_block(M, l, b, perm, inv, x, r, z, p, Ap, alpha, init, srb, &a, &c);
+    rbj_apply_block(M, l, b, perm, bstart, inv, x, r, z, p, Ap, alpha, init, srb, &a, &c);
     if (threadIdx.x == 0) {
         part[2 * b] = a;
         part[2 * b + 1] = c;
@@ -609,11 +611,13 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
 // In-place Cholesky of one l x l block (lower), then the inverse by solving
 // L L^T X = I column by column.  One thread block per RBJ block.
 __global__ void rbj_invert_kernel(int M, int lda, const double *__restrict__ A, int l, const int *__restrict__ perm,
-                                  double *__restrict__ work, double *__restrict__ inv, int *__restrict__ status)
+                                  const int *__restrict__ bstart, double *__restrict__ work, double *__restrict__ inv,
+                                  int *__restrict__ status)
 {
     const int b = blockIdx.x;
-    const int base = b * l;
-    const int nb = min(l, M - base);
+    // fixed-size blocks (RBJ) or the blocks listed in bstart (octree), stored with stride l
+    const int base = bstart ? bstart[b] : b * l;
+    const int nb = bstart ? bstart[b + 1] - base : min(l, M - base);
     double *W = work + (size_t)b * l * l;
     double *X = inv + (size_t)b * l * l;
     for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
@@ -658,6 +662,53 @@ __global__ void rbj_invert_kernel(int M, int lda, const double *__restrict__ A, 
 // ---------------------------------------------------------------------------
 static int gemv_grid(pcm_ctx *c) { return std::max(1, (c->M + 1) / 2); }
 
+// Octree partition of the points for the block-Jacobi comparison of Section
+// 4b-ii: the bounding cube (centred on the bounding box, side = its largest
+// extent) is split at its centre into octants (index 4 [x >= cx] + 2 [y >= cy]
+// + [z >= cz]) until a box holds at most `leaf` points; non-empty leaves in
+// depth-first octant order, points of a leaf in ascending index.  perm lists
+// the points leaf after leaf; start[b] is where leaf b begins (size nleaf + 1).
+static void octree_split(const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
+                         const std::vector<int> &idx, double cx, double cy, double cz, double h, int leaf,
+                         int depth, std::vector<int> &perm, std::vector<int> &start)
+{
+    if ((int)idx.size() <= leaf || depth >= 40) {
+        if (idx.empty()) return;
+        start.push_back((int)perm.size());
+        perm.insert(perm.end(), idx.begin(), idx.end());
+        return;
+    }
+    std::vector<int> part[8];
+    for (int k : idx) part[4 * (x[k] >= cx) + 2 * (y[k] >= cy) + (z[k] >= cz)].push_back(k);
+    const double q = 0.5 * h;
+    for (int o = 0; o < 8; ++o)
+        octree_split(x, y, z, part[o], cx + ((o & 4) ? q : -q), cy + ((o & 2) ? q : -q), cz + ((o & 1) ? q : -q), q,
+                     leaf, depth + 1, perm, start);
+}
+
+void octree_partition(const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
+                      int leaf, std::vector<int> &perm, std::vector<int> &start)
+{
+    const int M = (int)x.size();
+    perm.clear();
+    start.clear();
+    double lo[3] = {x[0], y[0], z[0]}, hi[3] = {x[0], y[0], z[0]};
+    for (int k = 0; k < M; ++k) {
+        lo[0] = std::min(lo[0], x[k]);
+        hi[0] = std::max(hi[0], x[k]);
+        lo[1] = std::min(lo[1], y[k]);
+        hi[1] = std::max(hi[1], y[k]);
+        lo[2] = std::min(lo[2], z[k]);
+        hi[2] = std::max(hi[2], z[k]);
+    }
+    const double h = 0.5 * std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    std::vector<int> all(M);
+    for (int k = 0; k < M; ++k) all[k] = k;
+    octree_split(x, y, z, all, 0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2]), h, leaf, 0,
+                 perm, start);
+    start.push_back(M);
+}
+
 int solver_prepare(pcm_ctx *c)
 {
     if (c->pc_ready) return PCM_OK;
@@ -666,6 +717,41 @@ int solver_prepare(pcm_ctx *c)
     if (kind == PCM_PRECOND_AUTO) kind = (M < c->opt.jacobi_below) ? PCM_PRECOND_JACOBI : PCM_PRECOND_RBJ;
     c->pc_kind = kind;
     PCM_TRY(c->iscal.alloc(64));
+    if (kind == PCM_PRECOND_OCTREE) {
+        // blocks: the leaves of an octree over the points (sizes up to the leaf
+        // capacity), inverted like RBJ blocks; stride = the largest leaf
+        std::vector<double> hx(M), hy(M), hz(M);
+        PCM_CUDA(cudaMemcpyAsync(hx.data(), c->px.p, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        PCM_CUDA(cudaMemcpyAsync(hy.data(), c->py.p, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        PCM_CUDA(cudaMemcpyAsync(hz.data(), c->pz.p, M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        PCM_CUDA(cudaStreamSynchronize(c->stream));
+        std::vector<int> perm, start;
+        octree_partition(hx, hy, hz, std::max(1, c->opt.octree_leaf), perm, start);
+        int lmax = 1;
+        for (size_t b = 0; b + 1 < start.size(); ++b) lmax = std::max(lmax, start[b + 1] - start[b]);
+        c->rbj_l = lmax;
+        c->rbj_nblk = (int)start.size() - 1;
+        PCM_TRY(c->rbj_perm.alloc(M));
+        PCM_TRY(c->rbj_bstart.alloc(start.size()));
+        PCM_CUDA(cudaMemcpyAsync(c->rbj_perm.p, perm.data(), M * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        PCM_CUDA(cudaMemcpyAsync(c->rbj_bstart.p, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 c->stream));
+        PCM_TRY(c->rbj_inv.alloc((size_t)c->rbj_nblk * lmax * lmax));
+        DBuf<double> &work = c->sd[0];
+        PCM_TRY(work.alloc((size_t)c->rbj_nblk * lmax * lmax));
+        PCM_CUDA(cudaMemsetAsync(c->iscal.p + 16, 0, sizeof(int), c->stream));
+        const int nt = std::min(1024, std::max(32, (lmax + 31) / 32 * 32));
+        rbj_invert_kernel<<<c->rbj_nblk, nt, 0, c->stream>>>(M, c->lda, c->A.p, lmax, c->rbj_perm.p,
+                                                             c->rbj_bstart.p, work.p, c->rbj_inv.p, c->iscal.p + 16);
+        PCM_LAUNCHED(c);
+        int st = 0;
+        PCM_CUDA(cudaMemcpyAsync(&st, c->iscal.p + 16, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PCM_CUDA(cudaStreamSynchronize(c->stream));  // perm, start are read by the copies above
+        if (st != 0) {
+            set_last_error("octree block-Jacobi set-up failed: a diagonal block is not positive definite");
+            return PCM_ERR_CUDA;
+        }
+    }
     if (kind == PCM_PRECOND_RBJ) {
         const int l = std::max(1, std::min(c->opt.rbj_block, M));
         c->rbj_l = l;
@@ -682,7 +768,7 @@ int solver_prepare(pcm_ctx *c)
         DBuf<double> &work = c->sd[0];
         PCM_TRY(work.alloc((size_t)c->rbj_nblk * l * l));
         const int nt = std::min(1024, std::max(32, (l + 31) / 32 * 32));
-        rbj_invert_kernel<<<c->rbj_nblk, nt, 0, c->stream>>>(M, c->lda, c->A.p, l, c->rbj_perm.p, work.p,
+        rbj_invert_kernel<<<c->rbj_nblk, nt, 0, c->stream>>>(M, c->lda, c->A.p, l, c->rbj_perm.p, nullptr, work.p,
                                                              c->rbj_inv.p, c->iscal.p + 16);
         PCM_LAUNCHED(c);
         int st = 0;
@@ -743,7 +829,8 @@ static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double
     pcg_init_kernel<<<eb, 256, 0, c->stream>>>(M, drhs, Ap, warm ? 1 : 0, x, r);
     PCM_LAUNCHED(c);
     const double *dinv = (c->pc_kind == PCM_PRECOND_JACOBI) ? c->dinv.p : nullptr;
-    const bool rbj = c->pc_kind == PCM_PRECOND_RBJ;
+    const bool rbj = c->pc_kind == PCM_PRECOND_RBJ || c->pc_kind == PCM_PRECOND_OCTREE;
+    const int *bstart = c->pc_kind == PCM_PRECOND_OCTREE ? c->rbj_bstart.p : nullptr;
     const int rbj_nt = std::min(1024, RBJ_SPLIT * std::max(32, (c->rbj_l + 31) / 32 * 32));
     const size_t rbj_smem = (size_t)c->rbj_l * sizeof(double);
     if (rbj) {
@@ -751,7 +838,8 @@ static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double
             PCM_CUDA(cudaFuncSetAttribute(pcg_update_rbj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)rbj_smem));
         pcg_update_rbj_kernel<<<c->rbj_nblk, rbj_nt, rbj_smem, c->stream>>>(
-            M, c->rbj_l, c->rbj_perm.p, c->rbj_inv.p, x, r, z, p, Ap, c->red.p, c->scal.p, c->iscal.p, c->counter.p, 1);
+            M, c->rbj_l, c->rbj_perm.p, bstart, c->rbj_inv.p, x, r, z, p, Ap, c->red.p, c->scal.p, c->iscal.p,
+            c->counter.p, 1);
     } else {
         pcg_init_diag_kernel<<<ub, UP_NT, 0, c->stream>>>(M, dinv, r, z, c->red.p, c->scal.p, c->iscal.p,
                                                           c->counter.p);
@@ -773,7 +861,7 @@ static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double
                                                                         c->scal.p, c->iscal.p, c->counter.p);
             if (rbj)
                 pcg_update_rbj_kernel<<<c->rbj_nblk, rbj_nt, rbj_smem, c->stream>>>(
-                    M, c->rbj_l, c->rbj_perm.p, c->rbj_inv.p, x, r, z, p, Ap, c->red.p, c->scal.p, c->iscal.p,
+                    M, c->rbj_l, c->rbj_perm.p, bstart, c->rbj_inv.p, x, r, z, p, Ap, c->red.p, c->scal.p, c->iscal.p,
                     c->counter.p, 0);
             else
                 pcg_update_diag_kernel<<<ub, UP_NT, 0, c->stream>>>(M, dinv, x, r, z, p, Ap, c->red.p, c->scal.p,

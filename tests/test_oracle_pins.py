@@ -503,3 +503,28 @@ def test_gauss_law_compact_molecule():
     q = oracle.solve_lu(A, -f * V)
     Q = mol.Z.sum() - Nel
     assert abs(q.sum() - (-f * Q)) < 0.02 * max(1.0, abs(Q)), (q.sum(), -f * Q)
+
+
+def test_octree_partition_rules():
+    """The octree leaves partition the points, respect the capacity, hold
+    only points of their own box, and reduce to one block when it fits."""
+    rng = np.random.default_rng(9)
+    r = rng.normal(size=(3000, 3)) * np.array([3.0, 1.0, 0.5])
+    blocks = oracle.octree_blocks(r, 200)
+    allidx = np.sort(np.concatenate(blocks))
+    assert np.array_equal(allidx, np.arange(len(r)))
+    assert max(len(b) for b in blocks) <= 200
+    # every leaf lies in an axis-aligned box that no other leaf's points enter
+    for b in blocks[:20]:
+        lo, hi = r[b].min(axis=0), r[b].max(axis=0)
+        inside = np.all((r >= lo) & (r <= hi), axis=1)
+        assert set(np.nonzero(inside)[0]) <= set(b.tolist())
+    assert len(oracle.octree_blocks(r, 3000)) == 1
+    # block Jacobi on a block-diagonal SPD matrix with the octree blocks is exact
+    A = np.zeros((len(r), len(r)))
+    for b in blocks:
+        B = rng.normal(size=(len(b), len(b)))
+        A[np.ix_(b, b)] = B @ B.T + len(b) * np.eye(len(b))
+    pc = oracle.Preconditioner(A, "octree", 200, points=r)
+    x, it, ok, rn = oracle.pcg(A, rng.normal(size=len(r)), 1e-10, pc)
+    assert ok and it == 1
