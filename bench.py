@@ -426,6 +426,20 @@ def run_ours(args):
                 grad.update(fp64_ms=g64_ms, speedup_vs_fp64=g64_ms / g_ms,
                             max_abs_diff_vs_fp64_Eh_per_bohr=float(np.max(np.abs(g_main - g64))))
             line["gradient"] = grad
+        if not args.no_precond:
+            # Section 4b-ii: CG steps and solve time per preconditioner (FP64, fixed delta = 1e-6)
+            pc = {}
+            for name, kw in (("jacobi", {"precond": "jacobi"}), ("rbj-100", {"precond": "rbj", "rbj_block": 100}),
+                             ("rbj-800", {"precond": "rbj", "rbj_block": 800}),
+                             ("octree-800", {"precond": "octree", "octree_leaf": 800})):
+                with pcm.Context(precision="fp64", timing=True, device=dev.index, stream=stream.cuda_stream,
+                                 **kw) as pctx:
+                    pctx.setup(w.mol, w.basis)
+                    pctx.esp(main["Pd"])
+                    _, pst = pctx.solve(delta=1e-6, like=main["Pd"])
+                    pc[name] = {"cg_steps": pst["iterations"], "converged": bool(pst["converged"]),
+                                "solve_ms_incl_setup": pst["ms_solve"], "setup_ms": pst["ms_precond"]}
+            line["preconditioners"] = pc
         if not args.no_scf:
             # Section 4b-i: CG steps and solve time along a synthetic SCF history
             from paper_1505_07851_gb300.scf import run_sequence
@@ -637,6 +651,7 @@ def main():
     ap.add_argument("--nmol", type=int, default=64, help="conformations in the batch workload (--config 4)")
     ap.add_argument("--ref-mols", type=int, default=4, help="batch members checked against the FP64 path")
     ap.add_argument("--no-scf", action="store_true", help="skip the SCF-sequence threshold comparison")
+    ap.add_argument("--no-precond", action="store_true", help="skip the preconditioner comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
