@@ -95,6 +95,8 @@ typedef struct pcm_options {
     int timing;                 /* 1: time the integral kernels and the solve with CUDA events (stats) */
     int autotune;               /* 1: pick the FP32 integral kernels' tile shapes by timed trials (default 0) */
     int octree_leaf;            /* PCM_PRECOND_OCTREE: most points per octree leaf (block), default 800 */
+    int esp_variant;            /* PCM_MIXED ESP kernel: -1 default (or the autotuner's pick), 0 pair-driven with
+                                   4 points per thread, 1 with 2, 2 MS-driven (s and p classes; others default) */
 } pcm_options;
 
 typedef struct pcm_stats {
@@ -253,9 +255,13 @@ int pcm_batch_run(pcm_batch *batch, const double *const *P, double delta, double
 int pcm_batch_get_stats(pcm_batch *batch, int i, pcm_stats *st);
 
 /* The autotuner's choices so far in this process: up to max_entries records
- * of five ints (device, kernel family 0 = ESP points per thread (choice 0:
- * 4, 1: 2), 1 = Fock pairs per thread (choice 1 or 2); angular momentum L;
- * size bucket floor(log2(pairs)); choice).  Returns the number of records. */
+ * of eight ints: device; kernel family (0: ESP variant, choice 0 pair-driven
+ * with 4 points per thread, 1 with 2, 2 MS-driven (one pair per thread with
+ * block reductions per point); 1: Fock pairs per thread, choice 1 or 2);
+ * angular momentum L; size bucket floor(log2(pairs)); the choice; the trial
+ * times of variants 0, 1, 2 in microseconds (0: not tried; for the Fock
+ * family variants 0 and 1 are 1 and 2 pairs per thread).  Returns the number
+ * of records. */
 int pcm_autotune_table(int *entries, int max_entries);
 
 /* Statistics of the context's last calls. */

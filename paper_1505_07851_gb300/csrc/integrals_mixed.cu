@@ -576,6 +576,101 @@ __global__ void __launch_bounds__(MESP_NT) esp_grad_kernel_f32(int nesp, int seg
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The "MS-driven" ESP of Section 4a (an autotuner candidate): one primitive
+// pair per thread, looping over the surface points of its split in tiles
+// staged in shared memory; for each point the block's pairs are summed (warp
+// shuffles, then the four warps in fixed order, in FP64) into the block's
+// partial c_k, part[blockIdx.x][k].  Same split constants as the pair-driven
+// kernel; each interaction is a single FP32 term, so no running FP32 sum.
+// ---------------------------------------------------------------------------
+constexpr int MS_NT = 128;
+constexpr int MS_TQ = 128;
+
+template <int L>
+__global__ void __launch_bounds__(MS_NT) esp_ms_kernel_f32(int nesp, int j0, int j1, int ksplit,
+                                                           const float *__restrict__ eX, const float *__restrict__ eC,
+                                                           int ncls, const int *__restrict__ cls_off,
+                                                           const float *__restrict__ ph, const float *__restrict__ pl,
+                                                           const float *__restrict__ boys, int M,
+                                                           double *__restrict__ part)
+{
+    constexpr int NH = nherm(L);
+    constexpr int F = 3 + 2 * NH;
+    __shared__ float4 sH[MS_TQ], sL[MS_TQ];
+    __shared__ float sw[MS_NT / 32][MS_TQ];
+    const int j = j0 + blockIdx.x * MS_NT + threadIdx.x;
+    const bool active = j < j1;
+    const int jj = active ? j : j0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float xh = eX[jj], yh = eX[(size_t)nesp + jj], zh = eX[2 * (size_t)nesp + jj];
+    const float xl = eX[3 * (size_t)nesp + jj], yl = eX[4 * (size_t)nesp + jj], zl = eX[5 * (size_t)nesp + jj];
+    const int ka = blockIdx.y * ksplit;
+    const int kb = min(M, ka + ksplit);
+    double *out = part + (size_t)blockIdx.x * M;
+    for (int e = 0; e < ncls; ++e) {
+        const int a = max(ka, cls_off[e]), b = min(kb, cls_off[e + 1]);
+        if (a >= b) continue;
+        const float *C = eC + (size_t)e * F * nesp;
+        const float rh = C[jj], rl = C[(size_t)nesp + jj], dr = C[2 * (size_t)nesp + jj];
+        float2 D[NH];
+#pragma unroll
+        for (int h = 0; h < NH; ++h)
+            D[h] = active ? make_float2(C[(size_t)(3 + h) * nesp + jj], C[(size_t)(3 + NH + h) * nesp + jj])
+                          : make_float2(0.f, 0.f);
+        const float m2r = -2.f * rh;
+        for (int t0 = a; t0 < b; t0 += MS_TQ) {
+            const int nt = min(MS_TQ, b - t0);
+            __syncthreads();
+            if (threadIdx.x < nt) {
+                const int k = t0 + threadIdx.x;
+                sH[threadIdx.x] = make_float4(ph[k], ph[(size_t)M + k], ph[2 * (size_t)M + k], 0.f);
+                sL[threadIdx.x] = make_float4(pl[k], pl[(size_t)M + k], pl[2 * (size_t)M + k], 0.f);
+            }
+            __syncthreads();
+            for (int kk = 0; kk < nt; ++kk) {
+                const float4 H = sH[kk], Lo = sL[kk];
+                const float X = (xh - H.x) + (xl - Lo.x);
+                const float Y = (yh - H.y) + (yl - Lo.y);
+                const float Z = (zh - H.z) + (zl - Lo.z);
+                const float R2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
+                const float T = fmaf(rh, R2, rl * R2);
+                float Fb[L + 1];
+                boys_eval<L>(T, boys, Fb);
+                float v;
+                if constexpr (L == 0) {
+                    v = fmaf(D[0].x, Fb[0], D[0].y * Fb[0]);
+                } else {
+                    float Rn[L + 1];
+                    float f = 1.f;
+#pragma unroll
+                    for (int n = 0; n <= L; ++n) {
+                        const float u = f * Fb[n];
+                        Rn[n] = (n == 0) ? u : fmaf(u, (float)n * dr, u);
+                        f *= m2r;
+                    }
+                    float R[NH];
+                    hermite_R<L, float>(X, Y, Z, Rn, R);
+                    v = 0.f;
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) v = fmaf(D[h].x, R[h], fmaf(D[h].y, R[h], v));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) sw[wid][kk] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < nt) {
+                double s = 0.0;
+#pragma unroll
+                for (int w = 0; w < MS_NT / 32; ++w) s += (double)sw[w][threadIdx.x];
+                out[t0 + threadIdx.x] = s;
+            }
+        }
+    }
+}
+
 __global__ void esp_reduce_mixed_kernel(int M, int nseg, const double *__restrict__ part, double *__restrict__ c)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -672,10 +767,71 @@ static int mixed_point_blocks(pcm_ctx *c, int nblk[2])
     return PCM_OK;
 }
 
-// layout v of the point blocks: PPT 4 (v = 0) or 2 (v = 1)
+// points of each split for the MS-driven kernel over n pairs: enough CTAs to
+// fill the GPU, splits on whole point tiles
+static void esp_ms_plan(pcm_ctx *c, int n, int *rows, int *nsplit, int *ksplit)
+{
+    *rows = (n + MS_NT - 1) / MS_NT;
+    const int maxsplit = std::max(1, (c->M + MS_TQ - 1) / MS_TQ);
+    int ns = *rows > 0 ? std::max(1, std::min(maxsplit, (152 * 8 + *rows - 1) / *rows)) : 1;
+    int ks = (c->M + ns - 1) / ns;
+    ks = (ks + MS_TQ - 1) / MS_TQ * MS_TQ;
+    *ksplit = ks;
+    *nsplit = (c->M + ks - 1) / ks;
+}
+
+// variant 2: the same-atom pairs as in the default layout, the others by the
+// MS-driven kernel (L <= 2)
+template <int L>
+static int esp_ms_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, const int *bcls, int nblk, double *part)
+{
+    constexpr int NH = nherm(L);
+    constexpr int F = 3 + 2 * NH;
+    constexpr int PPT = esp_default_ppt(L);
+    const int n = pc.nesp;
+    PCM_TRY(pc.eX32.alloc(6 * (size_t)n));
+    PCM_TRY(pc.eC32.alloc((size_t)c->ncls * F * n));
+    esp_mixed_prep_kernel<L><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->ncls, c->cls_zeta.p, pc.eP.p, pc.eD.p,
+                                                                     pc.eX32.p, pc.eC32.p);
+    PCM_LAUNCHED(c);
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[k], c->stream));
+    const int ns = pc.nesp_same;
+    int sl, rows;
+    esp_plan(ns, nblk, &sl, &rows);
+    if (rows > 0) {
+        dim3 grid(nblk, rows);
+        esp_kernel_f32<L, true, PPT><<<grid, MESP_NT, 0, c->stream>>>(n, 0, ns, sl, pc.eX32.p, pc.eC32.p, blk,
+                                                                       bcls, c->p32.p, c->p32lo.p, c->boys32.p, c->M,
+                                                                       part);
+        PCM_LAUNCHED(c);
+        part += (size_t)rows * c->M;
+    }
+    int mrows, nsplit, ks;
+    esp_ms_plan(c, n - ns, &mrows, &nsplit, &ks);
+    if (mrows > 0) {
+        dim3 grid(mrows, nsplit);
+        esp_ms_kernel_f32<L><<<grid, MS_NT, 0, c->stream>>>(n, ns, n, ks, pc.eX32.p, pc.eC32.p, c->ncls,
+                                                             c->cls_off.p, c->p32.p, c->p32lo.p, c->boys32.p, c->M,
+                                                             part);
+        PCM_LAUNCHED(c);
+    }
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[k], c->stream));
+    return PCM_OK;
+}
+
+// layout v of the point blocks: PPT 4 (v = 0) or 2 (v = 1); v = 2: MS-driven
 static int esp_launch_variant(pcm_ctx *c, int k, int v, DBuf<int> *blk, DBuf<int> *bcls, const int nb[2], double *part)
 {
     PairClass &pc = c->cls[k];
+    if (v == 2) {
+        const int d = esp_default_ppt(CLASS_L[k]) == 4 ? 0 : 1;
+        switch (CLASS_L[k]) {
+        case 0: return esp_ms_launch<0>(c, pc, k, blk[d].p, bcls[d].p, nb[d], part);
+        case 1: return esp_ms_launch<1>(c, pc, k, blk[d].p, bcls[d].p, nb[d], part);
+        case 2: return esp_ms_launch<2>(c, pc, k, blk[d].p, bcls[d].p, nb[d], part);
+        default: return PCM_ERR_ARG;
+        }
+    }
 #define PCM_ESPV(LL)                                                                                         \
     case LL:                                                                                                 \
         return v == 0 ? esp_mixed_launch<LL, 4>(c, pc, k, blk[0].p, bcls[0].p, nb[0], part)                  \
@@ -699,6 +855,17 @@ static int esp_rows(pcm_ctx *c, int k, int nblk)
     return r1 + r2;
 }
 
+// partial-sum rows of variant v of class k
+static int esp_rows_v(pcm_ctx *c, int k, int v, const int nb[2])
+{
+    if (v < 2) return esp_rows(c, k, nb[v]);
+    const int d = esp_default_ppt(CLASS_L[k]) == 4 ? 0 : 1;
+    int sl, r1, mrows, ns, ks;
+    esp_plan(c->cls[k].nesp_same, nb[d], &sl, &r1);
+    esp_ms_plan(c, c->cls[k].nesp - c->cls[k].nesp_same, &mrows, &ns, &ks);
+    return r1 + mrows;
+}
+
 // The autotuner's trial for class k: both layouts timed once with CUDA
 // events on the context's stream; the faster one is remembered for this GPU,
 // kernel family, angular momentum and size bucket.
@@ -711,28 +878,31 @@ static int esp_tune(pcm_ctx *c, int k, DBuf<int> *blk, DBuf<int> *bcls, const in
         *choice = t;
         return PCM_OK;
     }
-    const int rmax = std::max(esp_rows(c, k, nb[0]), esp_rows(c, k, nb[1]));
-    PCM_TRY(c->esp_part.alloc((size_t)std::max(1, rmax) * c->M));
-    cudaEvent_t e[3];
-    for (int i = 0; i < 3; ++i) PCM_CUDA(cudaEventCreate(&e[i]));
-    float ms[2] = {0.f, 0.f};
+    // candidates: pair-driven with 4 or 2 points per thread; MS-driven for L <= 2
+    const int nv = L <= 2 ? 3 : 2;
+    int rmax = 1;
+    for (int v = 0; v < nv; ++v) rmax = std::max(rmax, esp_rows_v(c, k, v, nb));
+    PCM_TRY(c->esp_part.alloc((size_t)rmax * c->M));
+    cudaEvent_t e[4];
+    for (int i = 0; i <= nv; ++i) PCM_CUDA(cudaEventCreate(&e[i]));
+    float ms[3] = {0.f, 0.f, 0.f};
     int st = PCM_OK;
     PCM_CUDA(cudaEventRecord(e[0], c->stream));
-    st = esp_launch_variant(c, k, 0, blk, bcls, nb, c->esp_part.p);
-    if (st == PCM_OK) {
-        PCM_CUDA(cudaEventRecord(e[1], c->stream));
-        st = esp_launch_variant(c, k, 1, blk, bcls, nb, c->esp_part.p);
+    for (int v = 0; v < nv && st == PCM_OK; ++v) {
+        st = esp_launch_variant(c, k, v, blk, bcls, nb, c->esp_part.p);
+        if (st == PCM_OK) PCM_CUDA(cudaEventRecord(e[v + 1], c->stream));
     }
     if (st == PCM_OK) {
-        PCM_CUDA(cudaEventRecord(e[2], c->stream));
-        PCM_CUDA(cudaEventSynchronize(e[2]));
-        PCM_CUDA(cudaEventElapsedTime(&ms[0], e[0], e[1]));
-        PCM_CUDA(cudaEventElapsedTime(&ms[1], e[1], e[2]));
+        PCM_CUDA(cudaEventSynchronize(e[nv]));
+        for (int v = 0; v < nv; ++v) PCM_CUDA(cudaEventElapsedTime(&ms[v], e[v], e[v + 1]));
     }
-    for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+    for (int i = 0; i <= nv; ++i) cudaEventDestroy(e[i]);
     if (st != PCM_OK) return st;
-    *choice = ms[1] < ms[0] ? 1 : 0;
-    tune_set(c->device, TUNE_ESP_PPT, L, bucket, *choice, ms[0], ms[1]);
+    int best = 0;
+    for (int v = 1; v < nv; ++v)
+        if (ms[v] < ms[best]) best = v;
+    *choice = best;
+    tune_set(c->device, TUNE_ESP_PPT, L, bucket, best, ms[0], ms[1], ms[2]);
     return PCM_OK;
 }
 
@@ -744,8 +914,12 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
     int var[6], rows[6], total = 0;
     for (int k = 0; k < 6; ++k) {
         var[k] = esp_default_ppt(CLASS_L[k]) == 4 ? 0 : 1;
-        if (c->opt.autotune && c->cls[k].nesp > 0) PCM_TRY(esp_tune(c, k, blk, bcls, nb, &var[k]));
-        rows[k] = c->cls[k].nesp > 0 ? esp_rows(c, k, nb[var[k]]) : 0;
+        if (c->opt.esp_variant >= 0) {
+            if (c->opt.esp_variant < 2 || CLASS_L[k] <= 2) var[k] = c->opt.esp_variant;
+        } else if (c->opt.autotune && c->cls[k].nesp > 0) {
+            PCM_TRY(esp_tune(c, k, blk, bcls, nb, &var[k]));
+        }
+        rows[k] = c->cls[k].nesp > 0 ? esp_rows_v(c, k, var[k], nb) : 0;
         total += rows[k];
     }
     if (total == 0) {

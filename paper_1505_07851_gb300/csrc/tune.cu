@@ -11,7 +11,7 @@ namespace pcm {
 namespace {
 struct Entry {
     int choice;
-    float ms0, ms1;
+    float ms[3];
 };
 std::mutex g_mu;
 std::map<std::tuple<int, int, int, int>, Entry> g_table;
@@ -34,10 +34,10 @@ int tune_get(int device, int kind, int L, int bucket)
     return it == g_table.end() ? -1 : it->second.choice;
 }
 
-void tune_set(int device, int kind, int L, int bucket, int choice, float ms0, float ms1)
+void tune_set(int device, int kind, int L, int bucket, int choice, float ms0, float ms1, float ms2)
 {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_table[std::make_tuple(device, kind, L, bucket)] = Entry{choice, ms0, ms1};
+    g_table[std::make_tuple(device, kind, L, bucket)] = Entry{choice, {ms0, ms1, ms2}};
 }
 
 int tune_table(int *out, int max)
@@ -46,11 +46,13 @@ int tune_table(int *out, int max)
     int n = 0;
     for (const auto &kv : g_table) {
         if (n < max && out) {
-            out[5 * n + 0] = std::get<0>(kv.first);
-            out[5 * n + 1] = std::get<1>(kv.first);
-            out[5 * n + 2] = std::get<2>(kv.first);
-            out[5 * n + 3] = std::get<3>(kv.first);
-            out[5 * n + 4] = kv.second.choice;
+            int *o = out + 8 * n;
+            o[0] = std::get<0>(kv.first);
+            o[1] = std::get<1>(kv.first);
+            o[2] = std::get<2>(kv.first);
+            o[3] = std::get<3>(kv.first);
+            o[4] = kv.second.choice;
+            for (int v = 0; v < 3; ++v) o[5 + v] = (int)(1000.f * kv.second.ms[v] + 0.5f);
         }
         ++n;
     }

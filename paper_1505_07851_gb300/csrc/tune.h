@@ -6,7 +6,7 @@
 namespace pcm {
 
 enum TuneKind {
-    TUNE_ESP_PPT = 0,    // FP32 ESP kernel: surface points per thread (variant 0: 4, 1: 2)
+    TUNE_ESP_PPT = 0,    // FP32 ESP kernel: pair-driven with 4 (0) or 2 (1) points per thread, or MS-driven (2)
     TUNE_FOCK_NPT = 1,   // FP32 Fock kernel: primitive pairs per thread (1 or 2)
 };
 
@@ -14,9 +14,10 @@ enum TuneKind {
 int tune_bucket(long long n);
 // the remembered choice, or -1
 int tune_get(int device, int kind, int L, int bucket);
-// remember a choice with the trial times of the two variants (ms)
-void tune_set(int device, int kind, int L, int bucket, int choice, float ms0, float ms1);
-// copy up to max entries of (device, kind, L, bucket, choice) into out; returns the count
+// remember a choice with the trial times of up to three variants (ms; 0: not tried)
+void tune_set(int device, int kind, int L, int bucket, int choice, float ms0, float ms1, float ms2 = 0.f);
+// copy up to max records of (device, kind, L, bucket, choice, trial microseconds of variants 0, 1, 2)
+// into out (8 ints each); returns the count
 int tune_table(int *out, int max);
 
 }  // namespace pcm

@@ -29,10 +29,26 @@ def test_autotuned_results_and_table():
     assert abs(E1 - E0) <= 1e-7
     tab = pcm.autotune_table()
     kinds = {t["kernel"] for t in tab}
-    assert {"esp_points_per_thread", "fock_pairs_per_thread"} <= kinds
+    assert {"esp_variant", "fock_pairs_per_thread"} <= kinds
     for t in tab:
-        allowed = (4, 2) if t["kernel"] == "esp_points_per_thread" else (1, 2)
+        allowed = (("pair-driven, 4 points/thread", "pair-driven, 2 points/thread", "MS-driven")
+                   if t["kernel"] == "esp_variant" else (1, 2))
         assert t["choice"] in allowed and 0 <= t["L"] <= 4
     # a second tuned context reuses the choices: identical results
     c2, F2, E2 = _run(w, True)
     assert np.array_equal(c1, c2) and np.array_equal(F1, F2) and E1 == E2
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_each_esp_variant_against_fp64(variant):
+    """Every candidate the autotuner may pick (pair-driven with 4 or 2 points
+    per thread, MS-driven) meets the mixed bar on its own."""
+    import paper_1505_07851_gb300 as pcm
+    w = workloads.small_cluster(8, seed=21)
+    with pcm.Context(precision="fp64") as ref:
+        ref.setup(w.mol, w.basis)
+        c64 = ref.esp(w.P)
+    with pcm.Context(precision="mixed", esp_variant=variant) as ctx:
+        ctx.setup(w.mol, w.basis)
+        c32 = ctx.esp(w.P)
+    assert np.max(np.abs(c32 - c64)) <= 1e-6 * np.max(np.abs(c64))
