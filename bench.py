@@ -220,7 +220,7 @@ def _timed_steps(pcm, w, precision, args, dev, stream, flush, delta, steps, warm
     library's stream; L2 is flushed between steps outside the events."""
     import torch
     ctx = pcm.Context(precision=precision, device=dev.index, stream=stream.cuda_stream, timing=True,
-                      seed=args.seed)
+                      seed=args.seed, autotune=(precision == "mixed" and args.autotune))
     b = w.basis
     Pd = torch.tensor(w.P, dtype=torch.float64, device=dev)
     bufs = {}
@@ -413,6 +413,7 @@ def run_ours(args):
             "integrals_per_step": main["ints"] / args.steps, "pairs_kept": s["pairs_kept"],
             "phase_ms": main["phase_ms"],
             "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": main["launches"],
+            "autotune": pcm.autotune_table(),
             "cpu_baseline": cpu,
         }
         if not args.no_grad:
@@ -652,6 +653,7 @@ def main():
     ap.add_argument("--ref-mols", type=int, default=4, help="batch members checked against the FP64 path")
     ap.add_argument("--no-scf", action="store_true", help="skip the SCF-sequence threshold comparison")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioner comparison")
+    ap.add_argument("--autotune", action="store_true", help="pick tile shapes by timed trials in the warm-up")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -143,6 +143,9 @@ struct pcm_ctx {
     pcm::DBuf<int> sh_atom, sh_l, sh_nprim, sh_off, sh_bf;
     pcm::DBuf<double> exps, cnorm;         // exponent and coefficient x base normalisation per primitive
     pcm::PairClass cls[6];                 // (0,0) (1,0) (1,1) (2,0) (2,1) (2,2)
+    // the shells the class lists were built for (reused while they stay the same)
+    bool pair_layout_ok = false;
+    std::vector<int> pl_atom, pl_l, pl_nprim;
     long long pairs_candidate = 0, pairs_kept = 0;
 
     // last results

@@ -316,19 +316,27 @@ int basis_build(pcm_ctx *c, int nshell, const int *shell_atom, const int *shell_
                                                          c->cnorm.p);
     PCM_LAUNCHED(c);
 
-    // shell pairs by class (la >= lb); the higher-l shell (ties: lower index) comes first
-    for (int k = 0; k < 6; ++k) {
-        c->cls[k].h_spA.clear();
-        c->cls[k].h_spB.clear();
-    }
-    for (int sa = 0; sa < ns; ++sa)
-        for (int sb = sa; sb < ns; ++sb) {
-            int A = sa, B = sb;
-            if (c->h_sh_l[sb] > c->h_sh_l[sa]) std::swap(A, B);
-            const int k = class_index(c->h_sh_l[A], c->h_sh_l[B]);
-            c->cls[k].h_spA.push_back(A);
-            c->cls[k].h_spB.push_back(B);
+    // shell pairs by class (la >= lb); the higher-l shell (ties: lower index) comes
+    // first.  They depend only on the shells' atoms, angular momenta and
+    // primitive counts: a new geometry with the same shells (the next step of an
+    // optimisation or a trajectory) reuses the lists already on the device.
+    const bool same_layout = c->pair_layout_ok && c->pl_atom == c->h_sh_atom && c->pl_l == c->h_sh_l &&
+                             c->pl_nprim == c->h_sh_nprim;
+    if (!same_layout) {
+        c->pair_layout_ok = false;
+        for (int k = 0; k < 6; ++k) {
+            c->cls[k].h_spA.clear();
+            c->cls[k].h_spB.clear();
         }
+        for (int sa = 0; sa < ns; ++sa)
+            for (int sb = sa; sb < ns; ++sb) {
+                int A = sa, B = sb;
+                if (c->h_sh_l[sb] > c->h_sh_l[sa]) std::swap(A, B);
+                const int k = class_index(c->h_sh_l[A], c->h_sh_l[B]);
+                c->cls[k].h_spA.push_back(A);
+                c->cls[k].h_spB.push_back(B);
+            }
+    }
     c->pairs_candidate = 0;
     c->pairs_kept = 0;
     PCM_TRY(c->iscal.alloc(64));
@@ -337,24 +345,30 @@ int basis_build(pcm_ctx *c, int nshell, const int *shell_atom, const int *shell_
         PairClass &pc = c->cls[k];
         pc.la = LA[k];
         pc.lb = LB[k];
-        pc.csr_ready = false;
         pc.nsp = (int)pc.h_spA.size();
-        std::vector<long long> cand(pc.nsp + 1, 0);
-        for (int s = 0; s < pc.nsp; ++s) {
-            const int A = pc.h_spA[s], B = pc.h_spB[s];
-            const long long na = c->h_sh_nprim[A], nb = c->h_sh_nprim[B];
-            cand[s + 1] = cand[s] + (A == B ? na * (na + 1) / 2 : na * nb);
+        if (!same_layout) {
+            pc.csr_ready = false;
+            std::vector<long long> cand(pc.nsp + 1, 0);
+            for (int s = 0; s < pc.nsp; ++s) {
+                const int A = pc.h_spA[s], B = pc.h_spB[s];
+                const long long na = c->h_sh_nprim[A], nb = c->h_sh_nprim[B];
+                cand[s + 1] = cand[s] + (A == B ? na * (na + 1) / 2 : na * nb);
+            }
+            pc.ncand = cand[pc.nsp];
+            PCM_TRY(pc.spA.alloc(pc.nsp));
+            PCM_TRY(pc.spB.alloc(pc.nsp));
+            PCM_TRY(pc.sp_cand.alloc(pc.nsp + 1));
+            if (pc.nsp > 0) {
+                PCM_CUDA(cudaMemcpyAsync(pc.spA.p, pc.h_spA.data(), pc.nsp * sizeof(int), cudaMemcpyHostToDevice,
+                                         c->stream));
+                PCM_CUDA(cudaMemcpyAsync(pc.spB.p, pc.h_spB.data(), pc.nsp * sizeof(int), cudaMemcpyHostToDevice,
+                                         c->stream));
+            }
+            PCM_CUDA(cudaMemcpyAsync(pc.sp_cand.p, cand.data(), (pc.nsp + 1) * sizeof(long long),
+                                     cudaMemcpyHostToDevice, c->stream));
+            // cand is read by the copy before it goes out of scope
+            PCM_CUDA(cudaStreamSynchronize(c->stream));
         }
-        pc.ncand = cand[pc.nsp];
-        PCM_TRY(pc.spA.alloc(pc.nsp));
-        PCM_TRY(pc.spB.alloc(pc.nsp));
-        PCM_TRY(pc.sp_cand.alloc(pc.nsp + 1));
-        if (pc.nsp > 0) {
-            PCM_CUDA(cudaMemcpyAsync(pc.spA.p, pc.h_spA.data(), pc.nsp * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-            PCM_CUDA(cudaMemcpyAsync(pc.spB.p, pc.h_spB.data(), pc.nsp * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-        }
-        PCM_CUDA(cudaMemcpyAsync(pc.sp_cand.p, cand.data(), (pc.nsp + 1) * sizeof(long long), cudaMemcpyHostToDevice,
-                                 c->stream));
         switch (k) {
         case 0: PCM_TRY((screen_class<0, 0>(c, pc))); break;
         case 1: PCM_TRY((screen_class<1, 0>(c, pc))); break;
@@ -365,6 +379,12 @@ int basis_build(pcm_ctx *c, int nshell, const int *shell_atom, const int *shell_
         }
         c->pairs_candidate += pc.ncand;
         c->pairs_kept += pc.npair;
+    }
+    if (!same_layout) {
+        c->pl_atom = c->h_sh_atom;
+        c->pl_l = c->h_sh_l;
+        c->pl_nprim = c->h_sh_nprim;
+        c->pair_layout_ok = true;
     }
     return PCM_OK;
 }

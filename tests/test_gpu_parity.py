@@ -223,3 +223,27 @@ def test_error_codes():
         q, st = ctx.solve(delta=1e-12)
         assert st["converged"] == 0 and st["iterations"] == 2
         assert np.all(np.isfinite(q))
+
+
+def test_context_reuse_matches_fresh_contexts():
+    """One context through several set-ups (same shells at a new geometry, then
+    other shells) gives the results of a fresh context each time, bit for bit:
+    the reused shell-pair lists change nothing."""
+    pcm = _pcm()
+    a = workloads.small_cluster(8, seed=21)
+    b = workloads.small_cluster(5, seed=22, d_shells=True)
+    moved = workloads.Workload(a.name, workloads.Molecule(a.mol.symbols, a.mol.xyz + 0.05 * np.sin(a.mol.xyz),
+                                                          a.mol.Z, a.mol.radius), a.basis, a.P, a.nocc, a.seed)
+
+    def run(ctx, w):
+        ctx.setup(w.mol, w.basis)
+        c = ctx.esp(w.P)
+        q, _ = ctx.solve(delta=1e-9)
+        return c, ctx.fock(q), ctx.energy(q)
+
+    with pcm.Context() as ctx:
+        seq = [run(ctx, w) for w in (a, moved, b, a)]
+    for w, got in zip((a, moved, b, a), seq):
+        with pcm.Context() as fresh:
+            ref = run(fresh, w)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]) and got[2] == ref[2]
