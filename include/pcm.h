@@ -117,7 +117,9 @@ typedef struct pcm_stats {
     double ms_esp_class[6];     /* with timing: main ESP kernel time per class (ms) */
     double ms_fock_class[6];    /* with timing: main Fock kernel time per class (ms) */
     double ms_solve;            /* with timing: device time of the last pcm_solve (ms) */
-    double ms_precond;          /* with timing: preconditioner set-up inside that solve (ms) */
+    double ms_precond;          /* with timing: build of A, its preconditioner and FP32 copy on the context's
+                                   second stream after the last pcm_build_surface (ms; it overlaps the basis
+                                   set-up and the integrals) */
     long long launches;         /* kernels launched by this context since its creation */
     double integrals_grad;      /* equivalent Cartesian primitive integrals of the last pcm_gradient (two passes) */
     double ms_grad;             /* with timing: device time of the last pcm_gradient (ms) */

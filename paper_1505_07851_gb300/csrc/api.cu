@@ -177,10 +177,16 @@ int pcm_create(pcm_ctx **out, const pcm_options *opt)
         }
         c->have_events = true;
     }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming) != cudaSuccess) {
+        set_last_error("cudaStreamCreate / cudaEventCreate failed");
+        pcm_destroy(c);
+        return PCM_ERR_CUDA;
+    }
     int st = boys_build_tables(c);
     if (st != PCM_OK) {
-        if (c->own_stream) cudaStreamDestroy(c->stream);
-        delete c;
+        pcm_destroy(c);
         return st;
     }
     *out = c;
@@ -191,12 +197,16 @@ int pcm_destroy(pcm_ctx *c)
 {
     if (!c) return PCM_OK;
     DeviceGuard g(c->device);
+    if (c->side) cudaStreamSynchronize(c->side);
     cudaStreamSynchronize(c->stream);
     if (c->have_events)
         for (int i = 0; i < 14; ++i) {
             cudaEventDestroy(c->ev_a[i]);
             cudaEventDestroy(c->ev_b[i]);
         }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_side) cudaEventDestroy(c->ev_side);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;  // device buffers free themselves
     return PCM_OK;

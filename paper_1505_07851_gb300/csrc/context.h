@@ -190,6 +190,15 @@ struct pcm_ctx {
     pcm_stats stats;
     cudaEvent_t ev_a[14], ev_b[14];         // timing events: 0-5 ESP classes, 6-11 Fock classes, 12 solve, 13 precond
     bool have_events = false;
+
+    // A, its diagonal and the preconditioner are built on a second stream that
+    // runs beside the basis set-up and the integrals; every use joins it first
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_side = nullptr;
+    bool side_pending = false;
+    bool side_rbj = false;                 // the side work includes an RBJ set-up (status to check)
+    pcm::DBuf<int> rbj_U, rbj_U2, rbj_status;
+    pcm::DBuf<double> rbj_work;
 };
 
 namespace pcm {
@@ -208,6 +217,9 @@ int fock_mixed_pairs_per_thread(pcm_ctx *c, int L, long long npair);
 int grad_point_mixed(pcm_ctx *c, int *total_rows);
 int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt);
 int solver_prepare(pcm_ctx *c);
+int operator_build_async(pcm_ctx *c);   // A, 1/A_kk, preconditioner, FP32 A on the side stream
+int a_build(pcm_ctx *c, cudaStream_t s);
+int join_side(pcm_ctx *c);              // wait for that work; report its errors
 int solver_prepare_full(pcm_ctx *c);
 void octree_partition(const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
                       int leaf, std::vector<int> &perm, std::vector<int> &start);

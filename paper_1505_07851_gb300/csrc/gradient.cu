@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(GPT_NT) grad_combine_kernel(int M, int natom, 
 
 int gradient_compute(pcm_ctx *c, const double *dP, const double *dq, int terms, double *dgrad)
 {
+    PCM_TRY(join_side(c));
     const int M = c->M, natom = c->natom;
     const double f = (c->opt.eps - 1.0) / (c->opt.eps + c->opt.k);
     PCM_TRY(c->patom.alloc(M));

@@ -709,12 +709,103 @@ void octree_partition(const std::vector<double> &x, const std::vector<double> &y
     start.push_back(M);
 }
 
+static int precond_kind(pcm_ctx *c)
+{
+    int kind = c->opt.precond;
+    if (kind == PCM_PRECOND_AUTO) kind = (c->M < c->opt.jacobi_below) ? PCM_PRECOND_JACOBI : PCM_PRECOND_RBJ;
+    return kind;
+}
+
+static int rbj_status_error(int st)
+{
+    set_last_error("RBJ set-up failed (status %d: %s)", st,
+                   st == 3 ? "a diagonal block is not positive definite"
+                           : (st == 4 ? "too many equal keys for the selection buffer" : "bad permutation"));
+    return PCM_ERR_CUDA;
+}
+
+// RBJ permutation and block inverses (Section 4b-ii) on stream s, with the
+// context's own RBJ scratch; the status lands in rbj_status[0]
+static int rbj_build(pcm_ctx *c, cudaStream_t s)
+{
+    const int M = c->M;
+    const int l = std::max(1, std::min(c->opt.rbj_block, M));
+    c->rbj_l = l;
+    c->rbj_nblk = (M + l - 1) / l;
+    PCM_TRY(c->rbj_perm.alloc(M));
+    PCM_TRY(c->rbj_U.alloc(M));
+    PCM_TRY(c->rbj_U2.alloc(M));
+    PCM_TRY(c->rbj_status.alloc(16));
+    PCM_CUDA(cudaMemsetAsync(c->rbj_status.p, 0, 16 * sizeof(int), s));
+    rbj_perm_kernel<<<1, RBJ_NT, 0, s>>>(M, c->lda, c->A.p, l, c->opt.seed, c->rbj_U.p, c->rbj_U2.p, c->rbj_perm.p,
+                                         c->rbj_status.p);
+    PCM_LAUNCHED(c);
+    PCM_TRY(c->rbj_inv.alloc((size_t)c->rbj_nblk * l * l));
+    PCM_TRY(c->rbj_work.alloc((size_t)c->rbj_nblk * l * l));
+    const int nt = std::min(1024, std::max(32, (l + 31) / 32 * 32));
+    rbj_invert_kernel<<<c->rbj_nblk, nt, 0, s>>>(M, c->lda, c->A.p, l, c->rbj_perm.p, nullptr, c->rbj_work.p,
+                                                 c->rbj_inv.p, c->rbj_status.p);
+    PCM_LAUNCHED(c);
+    return PCM_OK;
+}
+
+int operator_build_async(pcm_ctx *c)
+{
+    PCM_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+    PCM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[13], c->side));
+    PCM_TRY(a_build(c, c->side));
+    const int kind = precond_kind(c);
+    c->side_rbj = false;
+    if (kind != PCM_PRECOND_OCTREE) {   // the octree partition needs the points on the host: built at the solve
+        c->pc_kind = kind;
+        if (kind == PCM_PRECOND_RBJ) {
+            PCM_TRY(rbj_build(c, c->side));
+            c->side_rbj = true;
+        }
+        c->pc_ready = true;
+        if (c->opt.precision == PCM_MIXED) {
+            PCM_TRY(c->A32.alloc((size_t)c->M * c->lda));
+            const long long n = (long long)c->M * c->lda;
+            a_to_f32_kernel<<<4 * 152, 256, 0, c->side>>>(n, c->A.p, c->A32.p);
+            PCM_LAUNCHED(c);
+            c->a32_ready = true;
+        }
+    }
+    if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[13], c->side));
+    PCM_CUDA(cudaEventRecord(c->ev_side, c->side));
+    c->side_pending = true;
+    return PCM_OK;
+}
+
+int join_side(pcm_ctx *c)
+{
+    if (!c->side_pending) return PCM_OK;
+    c->side_pending = false;
+    PCM_CUDA(cudaEventSynchronize(c->ev_side));
+    PCM_CUDA(cudaStreamWaitEvent(c->stream, c->ev_side, 0));
+    if (c->have_events) {
+        float ms = 0.f;
+        PCM_CUDA(cudaEventElapsedTime(&ms, c->ev_a[13], c->ev_b[13]));
+        c->stats.ms_precond = ms;
+    }
+    if (c->side_rbj) {
+        int st = 0;
+        PCM_CUDA(cudaMemcpy(&st, c->rbj_status.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st != 0) {
+            c->pc_ready = false;
+            return rbj_status_error(st);
+        }
+    }
+    return PCM_OK;
+}
+
 int solver_prepare(pcm_ctx *c)
 {
+    PCM_TRY(join_side(c));
     if (c->pc_ready) return PCM_OK;
     const int M = c->M;
-    int kind = c->opt.precond;
-    if (kind == PCM_PRECOND_AUTO) kind = (M < c->opt.jacobi_below) ? PCM_PRECOND_JACOBI : PCM_PRECOND_RBJ;
+    const int kind = precond_kind(c);
     c->pc_kind = kind;
     PCM_TRY(c->iscal.alloc(64));
     if (kind == PCM_PRECOND_OCTREE) {
@@ -737,15 +828,16 @@ int solver_prepare(pcm_ctx *c)
         PCM_CUDA(cudaMemcpyAsync(c->rbj_bstart.p, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice,
                                  c->stream));
         PCM_TRY(c->rbj_inv.alloc((size_t)c->rbj_nblk * lmax * lmax));
-        DBuf<double> &work = c->sd[0];
-        PCM_TRY(work.alloc((size_t)c->rbj_nblk * lmax * lmax));
-        PCM_CUDA(cudaMemsetAsync(c->iscal.p + 16, 0, sizeof(int), c->stream));
+        PCM_TRY(c->rbj_work.alloc((size_t)c->rbj_nblk * lmax * lmax));
+        PCM_TRY(c->rbj_status.alloc(16));
+        PCM_CUDA(cudaMemsetAsync(c->rbj_status.p, 0, sizeof(int), c->stream));
         const int nt = std::min(1024, std::max(32, (lmax + 31) / 32 * 32));
         rbj_invert_kernel<<<c->rbj_nblk, nt, 0, c->stream>>>(M, c->lda, c->A.p, lmax, c->rbj_perm.p,
-                                                             c->rbj_bstart.p, work.p, c->rbj_inv.p, c->iscal.p + 16);
+                                                             c->rbj_bstart.p, c->rbj_work.p, c->rbj_inv.p,
+                                                             c->rbj_status.p);
         PCM_LAUNCHED(c);
         int st = 0;
-        PCM_CUDA(cudaMemcpyAsync(&st, c->iscal.p + 16, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PCM_CUDA(cudaMemcpyAsync(&st, c->rbj_status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         PCM_CUDA(cudaStreamSynchronize(c->stream));  // perm, start are read by the copies above
         if (st != 0) {
             set_last_error("octree block-Jacobi set-up failed: a diagonal block is not positive definite");
@@ -753,33 +845,11 @@ int solver_prepare(pcm_ctx *c)
         }
     }
     if (kind == PCM_PRECOND_RBJ) {
-        const int l = std::max(1, std::min(c->opt.rbj_block, M));
-        c->rbj_l = l;
-        c->rbj_nblk = (M + l - 1) / l;
-        PCM_TRY(c->rbj_perm.alloc(M));
-        DBuf<int> &U = c->si[0], &U2 = c->si[1];
-        PCM_TRY(U.alloc(M));
-        PCM_TRY(U2.alloc(M));
-        PCM_CUDA(cudaMemsetAsync(c->iscal.p, 0, 64 * sizeof(int), c->stream));
-        rbj_perm_kernel<<<1, RBJ_NT, 0, c->stream>>>(M, c->lda, c->A.p, l, c->opt.seed, U.p, U2.p, c->rbj_perm.p,
-                                                     c->iscal.p + 16);
-        PCM_LAUNCHED(c);
-        PCM_TRY(c->rbj_inv.alloc((size_t)c->rbj_nblk * l * l));
-        DBuf<double> &work = c->sd[0];
-        PCM_TRY(work.alloc((size_t)c->rbj_nblk * l * l));
-        const int nt = std::min(1024, std::max(32, (l + 31) / 32 * 32));
-        rbj_invert_kernel<<<c->rbj_nblk, nt, 0, c->stream>>>(M, c->lda, c->A.p, l, c->rbj_perm.p, nullptr, work.p,
-                                                             c->rbj_inv.p, c->iscal.p + 16);
-        PCM_LAUNCHED(c);
+        PCM_TRY(rbj_build(c, c->stream));
         int st = 0;
-        PCM_CUDA(cudaMemcpyAsync(&st, c->iscal.p + 16, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PCM_CUDA(cudaMemcpyAsync(&st, c->rbj_status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         PCM_CUDA(cudaStreamSynchronize(c->stream));
-        if (st != 0) {
-            set_last_error("RBJ set-up failed (status %d: %s)", st,
-                           st == 3 ? "a diagonal block is not positive definite"
-                                   : (st == 4 ? "too many equal keys for the selection buffer" : "bad permutation"));
-            return PCM_ERR_CUDA;
-        }
+        if (st != 0) return rbj_status_error(st);
     }
     c->pc_ready = true;
     return PCM_OK;
@@ -910,10 +980,11 @@ static int true_residual(pcm_ctx *c, const double *b, const double *x, double *r
 
 int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st)
 {
+    PCM_TRY(join_side(c));
     const bool fresh = !c->pc_ready;
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[13], c->stream));
     PCM_TRY(solver_prepare(c));
-    c->stats.ms_precond = 0.0;
+    if (fresh) c->stats.ms_precond = 0.0;
     if (c->have_events && fresh) {
         PCM_CUDA(cudaEventRecord(c->ev_b[13], c->stream));
         PCM_CUDA(cudaEventSynchronize(c->ev_b[13]));
@@ -1010,6 +1081,7 @@ __global__ void dot2_kernel(int M, const double *__restrict__ a, const double *_
 
 int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E)
 {
+    PCM_TRY(join_side(c));
     const int M = c->M;
     PCM_TRY(c->vtmp.alloc(M));
     const int gv = gemv_grid(c);

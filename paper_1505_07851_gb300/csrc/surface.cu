@@ -238,6 +238,8 @@ __global__ void dinv_kernel(int M, int lda, const double *__restrict__ A, double
 
 int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, const double *radius, int n)
 {
+    // the previous surface's A may still be in use on the side stream
+    PCM_TRY(join_side(c));
     c->natom = natom;
     c->npts_sphere = n;
     c->h_xyz.assign(xyz, xyz + 3 * natom);
@@ -331,24 +333,31 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
                                                      c->Z.p, c->Bz.p);
     PCM_LAUNCHED(c);
 
-    // stored A
-    c->lda = (M + 31) / 32 * 32;
-    PCM_TRY(c->A.alloc((size_t)M * c->lda));
-    {
-        const long long nt = (M + AT - 1) / AT;
-        const long long ntiles = nt * (nt + 1) / 2;
-        a_build_kernel<<<(unsigned)ntiles, 256, 0, c->stream>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
-                                                               c->pS.p, c->pcls.p, c->ncls, c->cls_zeta.p, c->A.p);
-        PCM_LAUNCHED(c);
-    }
-    PCM_TRY(c->dinv.alloc(M));
-    dinv_kernel<<<(M + 127) / 128, 128, 0, c->stream>>>(M, c->lda, c->A.p, c->dinv.p);
-    PCM_LAUNCHED(c);
     PCM_TRY(points_split(c));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
     c->pc_ready = false;
     c->a32_ready = false;
     c->have_c = false;
+    // the stored A and what depends on it, beside the next stages
+    return operator_build_async(c);
+}
+
+// Stored A in FP64 (Eq. 2, Eq. 3, Eq. 8) and 1/A_kk on stream s.
+int a_build(pcm_ctx *c, cudaStream_t s)
+{
+    const int M = c->M;
+    c->lda = (M + 31) / 32 * 32;
+    PCM_TRY(c->A.alloc((size_t)M * c->lda));
+    {
+        const long long nt = (M + AT - 1) / AT;
+        const long long ntiles = nt * (nt + 1) / 2;
+        a_build_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p, c->pS.p,
+                                                       c->pcls.p, c->ncls, c->cls_zeta.p, c->A.p);
+        PCM_LAUNCHED(c);
+    }
+    PCM_TRY(c->dinv.alloc(M));
+    dinv_kernel<<<(M + 127) / 128, 128, 0, s>>>(M, c->lda, c->A.p, c->dinv.p);
+    PCM_LAUNCHED(c);
     return PCM_OK;
 }
 
