@@ -196,6 +196,7 @@ struct pcm_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_side = nullptr;
     bool side_pending = false;
+    bool op_stale = false;                 // the surface changed: A and its preconditioner are not built yet
     bool side_rbj = false;                 // the side work includes an RBJ set-up (status to check)
     pcm::DBuf<int> rbj_U, rbj_U2, rbj_status;
     pcm::DBuf<double> rbj_work;
@@ -219,7 +220,8 @@ int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, do
 int solver_prepare(pcm_ctx *c);
 int operator_build_async(pcm_ctx *c);   // A, 1/A_kk, preconditioner, FP32 A on the side stream
 int a_build(pcm_ctx *c, cudaStream_t s);
-int join_side(pcm_ctx *c);              // wait for that work; report its errors
+int join_side(pcm_ctx *c);              // wait for that work (starting it if needed); report its errors
+int ensure_operator(pcm_ctx *c);        // start that work if the surface changed since
 int solver_prepare_full(pcm_ctx *c);
 void octree_partition(const std::vector<double> &x, const std::vector<double> &y, const std::vector<double> &z,
                       int leaf, std::vector<int> &perm, std::vector<int> &start);

@@ -763,6 +763,8 @@ int esp_prepare_all(pcm_ctx *c, const double *dP)
 
 int esp_compute(pcm_ctx *c, const double *dP, double *dc)
 {
+    // A and the preconditioner on the second stream, beside these integrals
+    PCM_TRY(ensure_operator(c));
     PCM_TRY(esp_prepare_all(c, dP));
 
     if (c->opt.precision == PCM_MIXED) {

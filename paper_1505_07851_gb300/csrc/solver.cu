@@ -749,6 +749,13 @@ static int rbj_build(pcm_ctx *c, cudaStream_t s)
     return PCM_OK;
 }
 
+int ensure_operator(pcm_ctx *c)
+{
+    if (!c->op_stale) return PCM_OK;
+    c->op_stale = false;
+    return operator_build_async(c);
+}
+
 int operator_build_async(pcm_ctx *c)
 {
     PCM_CUDA(cudaEventRecord(c->ev_fork, c->stream));
@@ -780,6 +787,7 @@ int operator_build_async(pcm_ctx *c)
 
 int join_side(pcm_ctx *c)
 {
+    PCM_TRY(ensure_operator(c));
     if (!c->side_pending) return PCM_OK;
     c->side_pending = false;
     PCM_CUDA(cudaEventSynchronize(c->ev_side));

@@ -238,7 +238,9 @@ __global__ void dinv_kernel(int M, int lda, const double *__restrict__ A, double
 
 int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, const double *radius, int n)
 {
-    // the previous surface's A may still be in use on the side stream
+    // the previous surface's A may still be in use on the side stream (and
+    // need not be built at all if nothing used it)
+    c->op_stale = false;
     PCM_TRY(join_side(c));
     c->natom = natom;
     c->npts_sphere = n;
@@ -338,8 +340,10 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     c->pc_ready = false;
     c->a32_ready = false;
     c->have_c = false;
-    // the stored A and what depends on it, beside the next stages
-    return operator_build_async(c);
+    // the stored A and what depends on it are built on the second stream when
+    // first needed (pcm_esp starts it, so that it runs beside the integrals)
+    c->op_stale = true;
+    return PCM_OK;
 }
 
 // Stored A in FP64 (Eq. 2, Eq. 3, Eq. 8) and 1/A_kk on stream s.
