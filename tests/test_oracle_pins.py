@@ -127,14 +127,6 @@ def test_all_classes_against_brute_force_quadrature(la, lb):
     assert np.max(np.abs(got - q2)) <= 1e-10 * scale, np.max(np.abs(got - q2)) / scale
 
 
-def test_survey_probe_values():
-    # s-s and p_x-s values for a=0.8, b=0.5, zeta=1.3, A=0, B=(0.9,0.3,-0.2),
-    # C=(1.7,-0.6,0.8), from an independent 3D-grid quadrature (h = 0.045).
-    A = np.zeros(3); B = np.array([0.9, 0.3, -0.2]); C = np.array([1.7, -0.6, 0.8])
-    assert abs(oracle.prim_integrals(0, 0.8, A, 0, 0.5, B, C, 1.3)[0, 0] - 1.5425727670) < 2e-10
-    assert abs(oracle.prim_integrals(1, 0.8, A, 0, 0.5, B, C, 1.3)[0, 0] - 0.7457582096) < 2e-10
-
-
 def _fd(fun, x, i, h=1e-4):
     xp = x.copy(); xm = x.copy()
     xp[i] += h; xm[i] -= h
