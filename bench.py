@@ -220,7 +220,8 @@ def _timed_steps(pcm, w, precision, args, dev, stream, flush, delta, steps, warm
     library's stream; L2 is flushed between steps outside the events."""
     import torch
     ctx = pcm.Context(precision=precision, device=dev.index, stream=stream.cuda_stream, timing=True,
-                      seed=args.seed, autotune=(precision == "mixed" and args.autotune))
+                      seed=args.seed, autotune=(precision == "mixed" and args.autotune),
+                      fp32x2=not args.scalar_fp32)
     b = w.basis
     Pd = torch.tensor(w.P, dtype=torch.float64, device=dev)
     bufs = {}
@@ -401,6 +402,7 @@ def run_ours(args):
             "data": "synthetic (seeded protein-shaped cluster; no PDB/basis data in this container)",
             "config": {"workload": w.name, "natom": w.mol.natom, "nbf": s["nbf"], "M": s["M"],
                        "pts_per_sphere": 110, "precision": args.precision, "delta": delta,
+                       "fp32_instructions": "scalar" if args.scalar_fp32 else "packed x2",
                        "precond": "rbj-100" if s["M"] >= 1000 else "jacobi",
                        "l2": "flushed between timed steps (512 MB write, not timed)",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -548,7 +550,8 @@ def run_batch(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     delta = args.delta if args.delta else DELTA_1E6
-    b = pcm.Batch(len(confs), precision=args.precision, device=local, stream=stream.cuda_stream)
+    b = pcm.Batch(len(confs), precision=args.precision, device=local, stream=stream.cuda_stream,
+                  fp32x2=not args.scalar_fp32)
     t0 = time.time()
     for i, w in enumerate(confs):
         b.set_molecule(i, w.mol, w.basis)
@@ -654,6 +657,8 @@ def main():
     ap.add_argument("--no-scf", action="store_true", help="skip the SCF-sequence threshold comparison")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioner comparison")
     ap.add_argument("--autotune", action="store_true", help="pick tile shapes by timed trials in the warm-up")
+    ap.add_argument("--scalar-fp32", action="store_true",
+                    help="scalar FP32 instructions in the mixed kernels instead of packed two-lane ones")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -97,6 +97,9 @@ typedef struct pcm_options {
     int octree_leaf;            /* PCM_PRECOND_OCTREE: most points per octree leaf (block), default 800 */
     int esp_variant;            /* PCM_MIXED ESP kernel: -1 default (or the autotuner's pick), 0 pair-driven with
                                    4 points per thread, 1 with 2, 2 MS-driven (s and p classes; others default) */
+    int fp32x2;                 /* PCM_MIXED: 1 (default) evaluates two primitive pairs (ESP) or two points (Fock)
+                                   per packed FP32x2 instruction (FADD2/FMUL2/FFMA2; each lane rounded as the
+                                   scalar instruction); 0 scalar FP32 instructions (same arithmetic per lane) */
 } pcm_options;
 
 typedef struct pcm_stats {

@@ -55,7 +55,8 @@ class pcm_options(ctypes.Structure):
                 ("rbj_block", ctypes.c_int), ("precond", ctypes.c_int), ("jacobi_below", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("device", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("octree_leaf", ctypes.c_int), ("esp_variant", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("octree_leaf", ctypes.c_int), ("esp_variant", ctypes.c_int),
+                ("fp32x2", ctypes.c_int)]
 
 
 class pcm_stats(ctypes.Structure):
@@ -147,8 +148,8 @@ def _ptr(a, dtype):
 
 def autotune_table():
     """The autotuner's choices so far: list of dicts (device, kernel, L,
-    bucket, choice, trial_us) with kernel "esp_variant" (pair-driven with 4 or
-    2 points per thread, or MS-driven) or "fock_pairs_per_thread" (1 or 2);
+    bucket, choice, fp32x2, trial_us) with kernel "esp_variant" (pair-driven
+    with 4 or 2 points per thread, or MS-driven) or "fock_pairs_per_thread" (1 or 2);
     trial_us the timed trial of each candidate in microseconds."""
     n = _lib.pcm_autotune_table(None, 0)
     buf = (ctypes.c_int * (8 * max(1, n)))()
@@ -157,13 +158,14 @@ def autotune_table():
     out = []
     for i in range(n):
         dev, kind, L, bucket, ch, t0, t1, t2 = buf[8 * i:8 * i + 8]
-        if kind == 0:
+        packed = kind in (0, 1)
+        if kind in (0, 2):
             trials = {names[v]: t for v, t in enumerate((t0, t1, t2)) if t > 0}
             out.append({"device": dev, "kernel": "esp_variant", "L": L, "bucket": bucket, "choice": names[ch],
-                        "trial_us": trials})
+                        "fp32x2": packed, "trial_us": trials})
         else:
             out.append({"device": dev, "kernel": "fock_pairs_per_thread", "L": L, "bucket": bucket, "choice": ch,
-                        "trial_us": {1: t0, 2: t1}})
+                        "fp32x2": packed, "trial_us": {1: t0, 2: t1}})
     return out
 
 
@@ -189,7 +191,7 @@ class Context:
 
     def __init__(self, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
                  precond="auto", jacobi_below=1000, precision="fp64", max_iter=5000, device=0, seed=0,
-                 stream=None, timing=False, autotune=False, octree_leaf=800, esp_variant=-1):
+                 stream=None, timing=False, autotune=False, octree_leaf=800, esp_variant=-1, fp32x2=True):
         o = pcm_options()
         _lib.pcm_default_options(ctypes.byref(o))
         o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
@@ -201,6 +203,7 @@ class Context:
         o.autotune = 1 if autotune else 0
         o.octree_leaf = int(octree_leaf)
         o.esp_variant = int(esp_variant)
+        o.fp32x2 = 1 if fp32x2 else 0
         h = ctypes.c_void_p()
         self._check(_lib.pcm_create(ctypes.byref(h), ctypes.byref(o)), "pcm_create")
         self._h = h
@@ -349,7 +352,7 @@ class Batch:
 
     def __init__(self, nmol, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
                  precond="auto", jacobi_below=1000, precision="mixed", max_iter=5000, device=0, seed=0,
-                 stream=None, autotune=True):
+                 stream=None, autotune=True, fp32x2=True):
         o = pcm_options()
         _lib.pcm_default_options(ctypes.byref(o))
         o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
@@ -357,6 +360,7 @@ class Batch:
         o.precision = {"fp64": PCM_FP64, "mixed": PCM_MIXED}[precision]
         o.max_iter, o.device, o.seed, o.stream = max_iter, device, seed, stream
         o.autotune = 1 if autotune else 0
+        o.fp32x2 = 1 if fp32x2 else 0
         h = ctypes.c_void_p()
         st = _lib.pcm_batch_create(ctypes.byref(h), ctypes.byref(o), int(nmol))
         if st != PCM_OK:

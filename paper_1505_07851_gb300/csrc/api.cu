@@ -129,6 +129,7 @@ int pcm_default_options(pcm_options *o)
     o->stream = nullptr;
     o->octree_leaf = 800;
     o->esp_variant = -1;
+    o->fp32x2 = 1;
     return PCM_OK;
 }
 
@@ -141,7 +142,8 @@ int pcm_create(pcm_ctx **out, const pcm_options *opt)
     else pcm_default_options(&o);
     if (!(o.eps > 1.0) || !(o.zeta > 0.0) || o.rbj_block < 1 || o.max_iter < 1 || o.switch_drop < 0.0 ||
         o.schwarz < 0.0 || (o.precision != PCM_FP64 && o.precision != PCM_MIXED) || o.precond < 0 || o.precond > 4 ||
-        (o.precond == PCM_PRECOND_OCTREE && o.octree_leaf < 1) || o.esp_variant < -1 || o.esp_variant > 2) {
+        (o.precond == PCM_PRECOND_OCTREE && o.octree_leaf < 1) || o.esp_variant < -1 || o.esp_variant > 2 ||
+        (o.fp32x2 != 0 && o.fp32x2 != 1)) {
         set_last_error("invalid pcm_options");
         return PCM_ERR_ARG;
     }

@@ -48,6 +48,9 @@ __host__ __device__ inline void cart_xyz(int l, int c, int &lx, int &ly, int &lz
 //   R^(n)_{t+1,u,v} = t R^(n+1)_{t-1,u,v} + X R^(n+1)_{t,u,v}   (and y, z).
 // Fully unrolled for compile-time L so every array stays in registers.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double hmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float hmadd(float a, float b, float c) { return fmaf(a, b, c); }
+
 template <int L, typename T>
 __device__ __forceinline__ void hermite_R(T X, T Y, T Z, const T (&Rn)[L + 1], T (&R)[nherm(L)])
 {
@@ -73,13 +76,13 @@ __device__ __forceinline__ void hermite_R(T X, T Y, T Z, const T (&Rn)[L + 1], T
                         val = Rn[n];
                     } else if (t > 0) {
                         val = X * buf[hidx(t - 1, u, v)];
-                        if (t > 1) val += T(t - 1) * buf[hidx(t - 2, u, v)];
+                        if (t > 1) val = hmadd(T(t - 1), buf[hidx(t - 2, u, v)], val);
                     } else if (u > 0) {
                         val = Y * buf[hidx(t, u - 1, v)];
-                        if (u > 1) val += T(u - 1) * buf[hidx(t, u - 2, v)];
+                        if (u > 1) val = hmadd(T(u - 1), buf[hidx(t, u - 2, v)], val);
                     } else {
                         val = Z * buf[hidx(t, u, v - 1)];
-                        if (v > 1) val += T(v - 1) * buf[hidx(t, u, v - 2)];
+                        if (v > 1) val = hmadd(T(v - 1), buf[hidx(t, u, v - 2)], val);
                     }
                     nb[hidx(t, u, v)] = val;
                 }

@@ -852,7 +852,8 @@ static int fock_tune(pcm_ctx *c, int k, int L, const double *dq)
 {
     PairClass &pc = c->cls[k];
     const int bucket = tune_bucket(pc.npair);
-    if (tune_get(c->device, TUNE_FOCK_NPT, L, bucket) >= 0) return PCM_OK;
+    const int kind = c->opt.fp32x2 ? TUNE_FOCK_NPT : TUNE_FOCK_NPT_SCALAR;
+    if (tune_get(c->device, kind, L, bucket) >= 0) return PCM_OK;
     float ms[2] = {0.f, 0.f};
     cudaEvent_t e0, e1;
     PCM_CUDA(cudaEventCreate(&e0));
@@ -872,7 +873,7 @@ static int fock_tune(pcm_ctx *c, int k, int L, const double *dq)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != PCM_OK) return st;
-    tune_set(c->device, TUNE_FOCK_NPT, L, bucket, ms[1] < ms[0] ? 2 : 1, ms[0], ms[1]);
+    tune_set(c->device, kind, L, bucket, ms[1] < ms[0] ? 2 : 1, ms[0], ms[1]);
     return PCM_OK;
 }
 

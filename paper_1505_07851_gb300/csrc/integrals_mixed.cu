@@ -21,6 +21,7 @@
 #include "boys.cuh"
 #include "common.cuh"
 #include "context.h"
+#include "f2.cuh"
 #include "tune.h"
 
 namespace pcm {
@@ -163,10 +164,11 @@ __device__ __forceinline__ void boys_df(float Th, float Tl, const float *__restr
 
 constexpr int MESP_NT = 128;
 constexpr int MESP_TP = 32;
-// points per thread: more independent work for the light classes
-// points per thread: the autotuner picks 4 or 2 per class (default: 4 for
-// the light classes, which have more independent work per pair)
-constexpr int esp_default_ppt(int L) { return L <= 1 ? 4 : 2; }
+// points per thread: the autotuner picks 4 or 2 per class.  Default: 2 for
+// the packed kernels (at 4 the register count cuts the resident warps by a
+// third, measured slower for every class), else 4 for the light classes
+// (more independent work per pair) and 2 for the others.
+constexpr int esp_default_ppt(int L, bool packed) { return packed ? 2 : (L <= 1 ? 4 : 2); }
 
 // Per tile of TP pairs, shared memory holds per pair float4 (xh, yh, zh, rho_hi),
 // float4 (xl, yl, zl, rho_lo), rho_lo/rho_hi and NH float2 (hi, lo) of U D_h.
@@ -323,6 +325,137 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int jbeg, in
     }
 }
 
+// The cross-atom pairs (plain FP32 distance and T) with two pairs per
+// instruction: pairs 2i and 2i+1 of a tile occupy the two lanes of every
+// packed value, the thread's points are duplicated into both lanes, and the
+// Kahan sums run per lane (even and odd pairs) until the lanes are added in
+// FP64 at the end.  Each lane's arithmetic is that of esp_kernel_f32's plain
+// path.  Shared memory per pair of pairs: float4 (xh, yh), (zh, rho_hi),
+// (xl, yl), (zl, rho_lo), float2 rho_lo/rho_hi and NH float4 (hi, lo) of U D_h,
+// each lane-interleaved.
+template <int L, int PPT>
+__global__ void __launch_bounds__(MESP_NT) esp_kernel_f32x2(int nesp, int jbeg, int jend, int seglen,
+                                                            const float *__restrict__ eX,
+                                                            const float *__restrict__ eC,
+                                                            const int *__restrict__ blk_off,
+                                                            const int *__restrict__ blk_cls,
+                                                            const float *__restrict__ ph,
+                                                            const float *__restrict__ pl,
+                                                            const float *__restrict__ boys, int M,
+                                                            double *__restrict__ part)
+{
+    constexpr int NH = nherm(L);
+    constexpr int F = 3 + 2 * NH;
+    constexpr int TP2 = MESP_TP / 2;
+    __shared__ float4 sXY[TP2], sZR[TP2], sXYl[TP2], sZRl[TP2], sD[NH][TP2];
+    __shared__ float2 sDr[TP2];
+    const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
+    const float *C = eC + (size_t)blk_cls[blockIdx.x] * F * nesp;
+    const int j0 = jbeg + blockIdx.y * seglen;
+    const int j1 = min(jend, j0 + seglen);
+
+    // the points, negated and duplicated into both lanes
+    f2 nxh[PPT], nyh[PPT], nzh[PPT], nxl[PPT], nyl[PPT], nzl[PPT];
+    f2 a32[PPT], k32[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int k = min(k0 + (int)threadIdx.x + q * MESP_NT, k1 - 1);
+        nxh[q] = f2(-ph[k]);
+        nyh[q] = f2(-ph[(size_t)M + k]);
+        nzh[q] = f2(-ph[2 * (size_t)M + k]);
+        nxl[q] = f2(-pl[k]);
+        nyl[q] = f2(-pl[(size_t)M + k]);
+        nzl[q] = f2(-pl[2 * (size_t)M + k]);
+        a32[q] = k32[q] = f2(0.f);
+    }
+    for (int jt = j0; jt < j1; jt += MESP_TP) {
+        const int nt = min(MESP_TP, j1 - jt);
+        __syncthreads();
+        // pair jj goes to slot jj / 2, lane jj % 2; an odd tile's last slot
+        // gets a dummy pair (rho = 1, D = 0) that contributes zero
+        for (int jj = threadIdx.x; jj < MESP_TP; jj += MESP_NT) {
+            const bool v = jj < nt;
+            const size_t j = jt + jj;
+            const int s = jj >> 1, l = jj & 1;
+            float *xy = reinterpret_cast<float *>(&sXY[s]), *zr = reinterpret_cast<float *>(&sZR[s]);
+            float *xyl = reinterpret_cast<float *>(&sXYl[s]), *zrl = reinterpret_cast<float *>(&sZRl[s]);
+            xy[l] = v ? eX[j] : 0.f;
+            xy[2 + l] = v ? eX[(size_t)nesp + j] : 0.f;
+            zr[l] = v ? eX[2 * (size_t)nesp + j] : 0.f;
+            zr[2 + l] = v ? C[j] : 1.f;
+            xyl[l] = v ? eX[3 * (size_t)nesp + j] : 0.f;
+            xyl[2 + l] = v ? eX[4 * (size_t)nesp + j] : 0.f;
+            zrl[l] = v ? eX[5 * (size_t)nesp + j] : 0.f;
+            zrl[2 + l] = v ? C[(size_t)nesp + j] : 0.f;
+            reinterpret_cast<float *>(&sDr[s])[l] = v ? C[2 * (size_t)nesp + j] : 0.f;
+        }
+        for (int t = threadIdx.x; t < NH * MESP_TP; t += MESP_NT) {
+            const int h = t / MESP_TP, jj = t % MESP_TP;
+            const bool v = jj < nt;
+            float *d = reinterpret_cast<float *>(&sD[h][jj >> 1]);
+            d[jj & 1] = v ? C[(size_t)(3 + h) * nesp + jt + jj] : 0.f;
+            d[2 + (jj & 1)] = v ? C[(size_t)(3 + NH + h) * nesp + jt + jj] : 0.f;
+        }
+        __syncthreads();
+        const int np = (nt + 1) >> 1;
+        for (int s = 0; s < np; ++s) {
+            const float4 xy = sXY[s], zr = sZR[s], xyl = sXYl[s], zrl = sZRl[s];
+            const f2 Ax(xy.x, xy.y), Ay(xy.z, xy.w), Az(zr.x, zr.y), rh(zr.z, zr.w);
+            const f2 Bx(xyl.x, xyl.y), By(xyl.z, xyl.w), Bz(zrl.x, zrl.y), rl(zrl.z, zrl.w);
+            f2 m2r, ndr[L + 1];
+            if constexpr (L > 0) {
+                const float2 dr = sDr[s];
+                m2r = rh * f2(-2.f);
+#pragma unroll
+                for (int n = 1; n <= L; ++n) ndr[n] = f2((float)n) * f2(dr.x, dr.y);
+            }
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                const f2 X = (Ax + nxh[q]) + (Bx + nxl[q]);
+                const f2 Y = (Ay + nyh[q]) + (By + nyl[q]);
+                const f2 Z = (Az + nzh[q]) + (Bz + nzl[q]);
+                const f2 R2 = fma2(X, X, fma2(Y, Y, Z * Z));
+                const f2 T = fma2(rh, R2, rl * R2);
+                f2 Fb[L + 1];
+                boys_eval2<L>(T, boys, Fb);
+                f2 dot;
+                if constexpr (L == 0) {
+                    const float4 D = sD[0][s];
+                    dot = fma2(f2(D.x, D.y), Fb[0], f2(D.z, D.w) * Fb[0]);
+                } else {
+                    f2 Rn[L + 1];
+                    f2 f(1.f);
+#pragma unroll
+                    for (int n = 0; n <= L; ++n) {
+                        const f2 v = f * Fb[n];
+                        Rn[n] = (n == 0) ? v : fma2(v, ndr[n], v);
+                        f = f * m2r;
+                    }
+                    f2 R[NH];
+                    hermite_R<L, f2>(X, Y, Z, Rn, R);
+                    dot = f2(0.f);
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) {
+                        const float4 D = sD[h][s];
+                        dot = fma2(f2(D.x, D.y), R[h], fma2(f2(D.z, D.w), R[h], dot));
+                    }
+                }
+                const f2 y = dot - k32[q];
+                const f2 t = a32[q] + y;
+                k32[q] = (t - a32[q]) - y;
+                a32[q] = t;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int k = k0 + threadIdx.x + q * MESP_NT;
+        if (k < k1)
+            part[(size_t)blockIdx.y * M + k] =
+                ((double)a32[q].v.x - (double)k32[q].v.x) + ((double)a32[q].v.y - (double)k32[q].v.y);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Fock: NPT primitive pairs per thread (the point data staged in shared memory
 // serve them all); per class rho and U in FP64 (hi/lo for rho), per point tile
@@ -337,7 +470,7 @@ constexpr int fock_default_npt(int L) { return L <= 1 ? 2 : 1; }
 // choice when it has one for this context's GPU, else the default
 int fock_mixed_pairs_per_thread(pcm_ctx *c, int L, long long npair)
 {
-    const int t = c->opt.autotune ? tune_get(c->device, TUNE_FOCK_NPT, L, tune_bucket(npair)) : -1;
+    const int t = c->opt.autotune ? tune_get(c->device, c->opt.fp32x2 ? TUNE_FOCK_NPT : TUNE_FOCK_NPT_SCALAR, L, tune_bucket(npair)) : -1;
     return t > 0 ? t : fock_default_npt(L);
 }
 
@@ -457,6 +590,151 @@ __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double
         }
 }
 
+// The same contraction with two points per packed instruction: points 2i and
+// 2i+1 of a tile occupy the two lanes, the thread's pairs are duplicated into
+// both lanes, and each lane's tile sums are added in FP64 (times U) at the end
+// of the tile.  The points are staged negated and lane-interleaved: float4
+// (-xh, -yh), (-zh, q), (-xl, -yl) and float2 (-zl) per pair of points; past
+// the end of the range a point has q = 0 and contributes zero.
+template <int L, int NPT>
+__global__ void __launch_bounds__(MF_NT) fock_kernel_f32x2(int npair, const double *__restrict__ gp,
+                                                           const float *__restrict__ Phl, int ksplit,
+                                                           const float *__restrict__ ph, const float *__restrict__ pl,
+                                                           const double *__restrict__ q, int M, int ncls,
+                                                           const int *__restrict__ cls_off,
+                                                           const double *__restrict__ cls_zeta,
+                                                           const float *__restrict__ boys, double *__restrict__ W)
+{
+    constexpr int NH = nherm(L);
+    constexpr int TQ2 = MF_TQ / 2;
+    __shared__ float4 sXY[TQ2], sZQ[TQ2], sXYl[TQ2];
+    __shared__ float2 sZl[TQ2];
+    int r[NPT];
+    bool active[NPT];
+    f2 Pxh[NPT], Pyh[NPT], Pzh[NPT], Pxl[NPT], Pyl[NPT], Pzl[NPT];
+    double p[NPT];
+    double w64[NPT][NH];
+#pragma unroll
+    for (int i = 0; i < NPT; ++i) {
+        r[i] = (blockIdx.x * NPT + i) * MF_NT + threadIdx.x;
+        active[i] = r[i] < npair;
+        const int rr = active[i] ? r[i] : 0;
+        Pxh[i] = f2(Phl[rr]);
+        Pyh[i] = f2(Phl[(size_t)npair + rr]);
+        Pzh[i] = f2(Phl[2 * (size_t)npair + rr]);
+        Pxl[i] = f2(Phl[3 * (size_t)npair + rr]);
+        Pyl[i] = f2(Phl[4 * (size_t)npair + rr]);
+        Pzl[i] = f2(Phl[5 * (size_t)npair + rr]);
+        p[i] = gp[rr];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) w64[i][h] = 0.0;
+    }
+    const int ka = blockIdx.y * ksplit;
+    const int kb = min(M, ka + ksplit);
+    const int sl = threadIdx.x >> 1, ln = threadIdx.x & 1;
+    for (int ec = 0; ec < ncls; ++ec) {
+        const int a = max(ka, cls_off[ec]), b = min(kb, cls_off[ec + 1]);
+        if (a >= b) continue;
+        const double z2 = cls_zeta[ec] * cls_zeta[ec];
+        double U[NPT];
+        f2 rh[NPT], rl[NPT], ndr[NPT][L + 1], m2r[NPT];
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+            const double inv = 1.0 / (p[i] + z2);
+            const double rho = p[i] * z2 * inv;
+            U[i] = sqrt(z2 * inv);
+            const float h = (float)rho;
+            rh[i] = f2(h);
+            rl[i] = f2((float)(rho - (double)h));
+            const float dr = (float)((rho - (double)h) / (double)h);
+#pragma unroll
+            for (int n = 1; n <= L; ++n) ndr[i][n] = f2((float)n * dr);
+            m2r[i] = f2(-2.f * h);
+        }
+        // this thread's point of the first tile (negated coordinates)
+        float4 nH = make_float4(0.f, 0.f, 0.f, 0.f), nL = nH;
+        if (a + (int)threadIdx.x < b) {
+            const int k = a + threadIdx.x;
+            nH = make_float4(-ph[k], -ph[(size_t)M + k], -ph[2 * (size_t)M + k], (float)q[k]);
+            nL = make_float4(-pl[k], -pl[(size_t)M + k], -pl[2 * (size_t)M + k], 0.f);
+        }
+        for (int t0 = a; t0 < b; t0 += MF_TQ) {
+            const int nt = min(MF_TQ, b - t0);
+            __syncthreads();
+            {
+                float *xy = reinterpret_cast<float *>(&sXY[sl]), *zq = reinterpret_cast<float *>(&sZQ[sl]);
+                float *xyl = reinterpret_cast<float *>(&sXYl[sl]);
+                xy[ln] = nH.x;
+                xy[2 + ln] = nH.y;
+                zq[ln] = nH.z;
+                zq[2 + ln] = nH.w;
+                xyl[ln] = nL.x;
+                xyl[2 + ln] = nL.y;
+                reinterpret_cast<float *>(&sZl[sl])[ln] = nL.z;
+            }
+            __syncthreads();
+            // prefetch the next tile while this one is computed
+            if (t0 + MF_TQ + (int)threadIdx.x < b) {
+                const int k = t0 + MF_TQ + threadIdx.x;
+                nH = make_float4(-ph[k], -ph[(size_t)M + k], -ph[2 * (size_t)M + k], (float)q[k]);
+                nL = make_float4(-pl[k], -pl[(size_t)M + k], -pl[2 * (size_t)M + k], 0.f);
+            } else {
+                nH = make_float4(0.f, 0.f, 0.f, 0.f);
+                nL = nH;
+            }
+            f2 w32[NPT][NH];
+#pragma unroll
+            for (int i = 0; i < NPT; ++i)
+#pragma unroll
+                for (int h = 0; h < NH; ++h) w32[i][h] = f2(0.f);
+            const int np = (nt + 1) >> 1;
+            for (int s = 0; s < np; ++s) {
+                const float4 xy = sXY[s], zq = sZQ[s], xyl = sXYl[s];
+                const float2 zl = sZl[s];
+                const f2 Hx(xy.x, xy.y), Hy(xy.z, xy.w), Hz(zq.x, zq.y), Q(zq.z, zq.w);
+                const f2 Lx(xyl.x, xyl.y), Ly(xyl.z, xyl.w), Lz(zl.x, zl.y);
+#pragma unroll
+                for (int i = 0; i < NPT; ++i) {
+                    const f2 X = (Pxh[i] + Hx) + (Pxl[i] + Lx);
+                    const f2 Y = (Pyh[i] + Hy) + (Pyl[i] + Ly);
+                    const f2 Z = (Pzh[i] + Hz) + (Pzl[i] + Lz);
+                    const f2 R2 = fma2(X, X, fma2(Y, Y, Z * Z));
+                    const f2 T = fma2(rh[i], R2, rl[i] * R2);
+                    f2 Fb[L + 1];
+                    boys_eval2<L>(T, boys, Fb);
+                    if constexpr (L == 0) {
+                        w32[i][0] = fma2(Q, Fb[0], w32[i][0]);
+                    } else {
+                        f2 Rn[L + 1];
+                        f2 f = Q;
+#pragma unroll
+                        for (int n = 0; n <= L; ++n) {
+                            const f2 v = f * Fb[n];
+                            Rn[n] = (n == 0) ? v : fma2(v, ndr[i][n], v);
+                            f = f * m2r[i];
+                        }
+                        f2 R[NH];
+                        hermite_R<L, f2>(X, Y, Z, Rn, R);
+#pragma unroll
+                        for (int h = 0; h < NH; ++h) w32[i][h] += R[h];
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NPT; ++i)
+#pragma unroll
+                for (int h = 0; h < NH; ++h)
+                    w64[i][h] = fma(U[i], (double)w32[i][h].v.x + (double)w32[i][h].v.y, w64[i][h]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NPT; ++i)
+        if (active[i]) {
+#pragma unroll
+            for (int h = 0; h < NH; ++h) W[((size_t)blockIdx.y * NH + h) * npair + r[i]] = w64[i][h];
+        }
+}
+
 // ---------------------------------------------------------------------------
 // Point part of the integral gradient on the FP32 pipes (the FP64 statement
 // is esp_grad_kernel in integrals.cu): per point the three sums
@@ -478,7 +756,7 @@ __global__ void __launch_bounds__(MESP_NT) esp_grad_kernel_f32(int nesp, int seg
     constexpr int L1 = L + 1;
     constexpr int NH1 = nherm(L1);
     constexpr int F = 3 + 2 * NH;
-    constexpr int PPT = esp_default_ppt(L);
+    constexpr int PPT = esp_default_ppt(L, false);
     __shared__ float4 sA[MESP_TP], sB[MESP_TP];
     __shared__ float sR[MESP_TP];
     __shared__ float2 sD[NH][MESP_TP];
@@ -702,7 +980,7 @@ static void esp_plan(int n, int nblk, int *seglen, int *rows)
     *rows = (n + sl - 1) / sl;
 }
 
-template <int L, int PPT>
+template <int L, int PPT, bool PACKED>
 static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, const int *bcls, int nblk, double *part)
 {
     constexpr int NH = nherm(L);
@@ -728,9 +1006,13 @@ static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, co
     esp_plan(nx, nblk, &sl, &rows);
     if (rows > 0) {
         dim3 grid(nblk, rows);
-        esp_kernel_f32<L, false, PPT><<<grid, MESP_NT, 0, c->stream>>>(n, ns, n, sl, pc.eX32.p, pc.eC32.p, blk,
-                                                                        bcls,
-                                                                   c->p32.p, c->p32lo.p, c->boys32.p, c->M, part);
+        if constexpr (PACKED)
+            esp_kernel_f32x2<L, PPT><<<grid, MESP_NT, 0, c->stream>>>(n, ns, n, sl, pc.eX32.p, pc.eC32.p, blk, bcls,
+                                                                      c->p32.p, c->p32lo.p, c->boys32.p, c->M, part);
+        else
+            esp_kernel_f32<L, false, PPT><<<grid, MESP_NT, 0, c->stream>>>(n, ns, n, sl, pc.eX32.p, pc.eC32.p, blk,
+                                                                            bcls, c->p32.p, c->p32lo.p, c->boys32.p,
+                                                                            c->M, part);
         PCM_LAUNCHED(c);
     }
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[k], c->stream));
@@ -787,7 +1069,7 @@ static int esp_ms_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, const
 {
     constexpr int NH = nherm(L);
     constexpr int F = 3 + 2 * NH;
-    constexpr int PPT = esp_default_ppt(L);
+    constexpr int PPT = esp_default_ppt(L, false);
     const int n = pc.nesp;
     PCM_TRY(pc.eX32.alloc(6 * (size_t)n));
     PCM_TRY(pc.eC32.alloc((size_t)c->ncls * F * n));
@@ -819,12 +1101,14 @@ static int esp_ms_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, const
     return PCM_OK;
 }
 
-// layout v of the point blocks: PPT 4 (v = 0) or 2 (v = 1); v = 2: MS-driven
+// Variants of the FP32 ESP: pair-driven with 4 (v = 0) or 2 (v = 1) points per
+// thread (two pairs per packed instruction unless the context asks for scalar
+// FP32 instructions); MS-driven (v = 2).
 static int esp_launch_variant(pcm_ctx *c, int k, int v, DBuf<int> *blk, DBuf<int> *bcls, const int nb[2], double *part)
 {
     PairClass &pc = c->cls[k];
     if (v == 2) {
-        const int d = esp_default_ppt(CLASS_L[k]) == 4 ? 0 : 1;
+        const int d = esp_default_ppt(CLASS_L[k], false) == 4 ? 0 : 1;
         switch (CLASS_L[k]) {
         case 0: return esp_ms_launch<0>(c, pc, k, blk[d].p, bcls[d].p, nb[d], part);
         case 1: return esp_ms_launch<1>(c, pc, k, blk[d].p, bcls[d].p, nb[d], part);
@@ -834,8 +1118,11 @@ static int esp_launch_variant(pcm_ctx *c, int k, int v, DBuf<int> *blk, DBuf<int
     }
 #define PCM_ESPV(LL)                                                                                         \
     case LL:                                                                                                 \
-        return v == 0 ? esp_mixed_launch<LL, 4>(c, pc, k, blk[0].p, bcls[0].p, nb[0], part)                  \
-                      : esp_mixed_launch<LL, 2>(c, pc, k, blk[1].p, bcls[1].p, nb[1], part);
+        if (c->opt.fp32x2)                                                                                   \
+            return v == 0 ? esp_mixed_launch<LL, 4, true>(c, pc, k, blk[0].p, bcls[0].p, nb[0], part)        \
+                          : esp_mixed_launch<LL, 2, true>(c, pc, k, blk[1].p, bcls[1].p, nb[1], part);       \
+        return v == 0 ? esp_mixed_launch<LL, 4, false>(c, pc, k, blk[0].p, bcls[0].p, nb[0], part)           \
+                      : esp_mixed_launch<LL, 2, false>(c, pc, k, blk[1].p, bcls[1].p, nb[1], part);
     switch (CLASS_L[k]) {
         PCM_ESPV(0)
         PCM_ESPV(1)
@@ -859,7 +1146,7 @@ static int esp_rows(pcm_ctx *c, int k, int nblk)
 static int esp_rows_v(pcm_ctx *c, int k, int v, const int nb[2])
 {
     if (v < 2) return esp_rows(c, k, nb[v]);
-    const int d = esp_default_ppt(CLASS_L[k]) == 4 ? 0 : 1;
+    const int d = esp_default_ppt(CLASS_L[k], false) == 4 ? 0 : 1;
     int sl, r1, mrows, ns, ks;
     esp_plan(c->cls[k].nesp_same, nb[d], &sl, &r1);
     esp_ms_plan(c, c->cls[k].nesp - c->cls[k].nesp_same, &mrows, &ns, &ks);
@@ -873,7 +1160,8 @@ static int esp_tune(pcm_ctx *c, int k, DBuf<int> *blk, DBuf<int> *bcls, const in
 {
     const int L = CLASS_L[k];
     const int bucket = tune_bucket((long long)c->cls[k].nesp);
-    const int t = tune_get(c->device, TUNE_ESP_PPT, L, bucket);
+    const int kind = c->opt.fp32x2 ? TUNE_ESP_PPT : TUNE_ESP_PPT_SCALAR;
+    const int t = tune_get(c->device, kind, L, bucket);
     if (t >= 0) {
         *choice = t;
         return PCM_OK;
@@ -902,7 +1190,7 @@ static int esp_tune(pcm_ctx *c, int k, DBuf<int> *blk, DBuf<int> *bcls, const in
     for (int v = 1; v < nv; ++v)
         if (ms[v] < ms[best]) best = v;
     *choice = best;
-    tune_set(c->device, TUNE_ESP_PPT, L, bucket, best, ms[0], ms[1], ms[2]);
+    tune_set(c->device, kind, L, bucket, best, ms[0], ms[1], ms[2]);
     return PCM_OK;
 }
 
@@ -913,7 +1201,7 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
     DBuf<int> *blk = &c->si[4], *bcls = &c->si[6];  // blk[0..1], bcls[0..1]
     int var[6], rows[6], total = 0;
     for (int k = 0; k < 6; ++k) {
-        var[k] = esp_default_ppt(CLASS_L[k]) == 4 ? 0 : 1;
+        var[k] = esp_default_ppt(CLASS_L[k], c->opt.fp32x2) == 4 ? 0 : 1;
         if (c->opt.esp_variant >= 0) {
             if (c->opt.esp_variant < 2 || CLASS_L[k] <= 2) var[k] = c->opt.esp_variant;
         } else if (c->opt.autotune && c->cls[k].nesp > 0) {
@@ -943,13 +1231,23 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
 int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt)
 {
     PairClass &pc = c->cls[k];
+    // the packed kernel with two pairs per thread would spill for the dd class
+    if (c->opt.fp32x2 && CLASS_L[k] >= 4) npt = 1;
     const int per = MF_NT * npt;
     const int nb = (pc.npair + per - 1) / per;
     dim3 grid(nb, nsplit);
     switch (CLASS_L[k]) {
 #define PCM_FOCK_F32(LL)                                                                                           \
     case LL:                                                                                                       \
-        if (npt == 2)                                                                                              \
+        if (c->opt.fp32x2 && npt == 2)                                                                             \
+            fock_kernel_f32x2<LL, 2><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit,        \
+                                                                     c->p32.p, c->p32lo.p, dq, c->M, c->ncls,      \
+                                                                     c->cls_off.p, c->cls_zeta.p, c->boys32.p, W); \
+        else if (c->opt.fp32x2)                                                                                    \
+            fock_kernel_f32x2<LL, 1><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit,        \
+                                                                     c->p32.p, c->p32lo.p, dq, c->M, c->ncls,      \
+                                                                     c->cls_off.p, c->cls_zeta.p, c->boys32.p, W); \
+        else if (npt == 2)                                                                                         \
             fock_kernel_f32<LL, 2><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit, c->p32.p, \
                                                                    c->p32lo.p, dq, c->M, c->ncls, c->cls_off.p,    \
                                                                    c->cls_zeta.p, c->boys32.p, W);                 \

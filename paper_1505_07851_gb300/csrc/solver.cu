@@ -319,7 +319,7 @@ __global__ void residual_kernel(int M, const double *__restrict__ b, const doubl
 {
     double s = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
-        const double v = b[k] - y[k];
+        const double v = y ? b[k] - y[k] : b[k];
         r[k] = v;
         s = fma(v, v, s);
     }
@@ -968,14 +968,17 @@ static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double
 }
 
 // ||b - A x||_2 with the FP64 stored A; r receives the residual
+// r = b - A x (FP64) and |r|; x == nullptr stands for x = 0 (r = b, no GEMV)
 static int true_residual(pcm_ctx *c, const double *b, const double *x, double *r, double *norm)
 {
     const int M = c->M;
     const int gv = gemv_grid(c);
-    gemv_rp_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, x, c->vtmp.p, c->red.p);
-    PCM_LAUNCHED(c);
+    if (x) {
+        gemv_rp_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, x, c->vtmp.p, c->red.p);
+        PCM_LAUNCHED(c);
+    }
     const int nb = std::min(256, (M + 255) / 256);
-    residual_kernel<<<nb, 256, 0, c->stream>>>(M, b, c->vtmp.p, r, c->red.p);
+    residual_kernel<<<nb, 256, 0, c->stream>>>(M, b, x ? c->vtmp.p : nullptr, r, c->red.p);
     PCM_LAUNCHED(c);
     double h[256];
     PCM_CUDA(cudaMemcpyAsync(h, c->red.p, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1031,8 +1034,8 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
         PCM_TRY(c->vro.alloc(M));
         PCM_TRY(c->vd.alloc(M));
         if (!warm) PCM_CUDA(cudaMemsetAsync(dq, 0, M * sizeof(double), c->stream));
-        for (;;) {
-            PCM_TRY(true_residual(c, drhs, dq, c->vro.p, &rnorm));
+        for (bool zero = !warm;; zero = false) {
+            PCM_TRY(true_residual(c, drhs, zero ? nullptr : dq, c->vro.p, &rnorm));
             if (rnorm < delta) {
                 conv = 1;
                 break;

@@ -8,6 +8,9 @@ namespace pcm {
 enum TuneKind {
     TUNE_ESP_PPT = 0,    // FP32 ESP kernel: pair-driven with 4 (0) or 2 (1) points per thread, or MS-driven (2)
     TUNE_FOCK_NPT = 1,   // FP32 Fock kernel: primitive pairs per thread (1 or 2)
+    // the same choices for the kernels with scalar FP32 instructions (pcm_options.fp32x2 = 0)
+    TUNE_ESP_PPT_SCALAR = 2,
+    TUNE_FOCK_NPT_SCALAR = 3,
 };
 
 // size bucket of a kernel's work: floor(log2(n)) (pairs of the class)
