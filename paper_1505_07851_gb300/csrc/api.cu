@@ -206,6 +206,10 @@ int pcm_destroy(pcm_ctx *c)
             cudaEventDestroy(c->ev_a[i]);
             cudaEventDestroy(c->ev_b[i]);
         }
+    if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+    if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_side) cudaEventDestroy(c->ev_side);
     if (c->side) cudaStreamDestroy(c->side);

@@ -167,7 +167,13 @@ struct pcm_ctx {
     pcm::DBuf<double> scal;                // device scalars
     pcm::DBuf<int> iscal;                  // device ints (done flag, iteration count)
     pcm::DBuf<unsigned int> counter;       // last-block counters
-    double *h_pinned = nullptr;            // pinned host scratch for scalars
+    double *h_pinned = nullptr;            // pinned host scratch for scalars (32 doubles)
+    // the PCG iteration loop as a CUDA graph (conditional WHILE node), its key
+    // (what the captured launches read) and the private stream it is captured on
+    cudaGraph_t pcg_graph = nullptr;
+    cudaGraphExec_t pcg_exec = nullptr;
+    uintptr_t pcg_key[24] = {};
+    cudaStream_t cap_stream = nullptr;
 
     // integral scratch
     pcm::DBuf<double> esp_part;            // nseg x M partial potentials (x 3 for the gradient)

@@ -325,14 +325,20 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int jbeg, in
     }
 }
 
-// The cross-atom pairs (plain FP32 distance and T) with two pairs per
-// instruction: pairs 2i and 2i+1 of a tile occupy the two lanes of every
-// packed value, the thread's points are duplicated into both lanes, and the
-// Kahan sums run per lane (even and odd pairs) until the lanes are added in
-// FP64 at the end.  Each lane's arithmetic is that of esp_kernel_f32's plain
-// path.  Shared memory per pair of pairs: float4 (xh, yh), (zh, rho_hi),
-// (xl, yl), (zl, rho_lo), float2 rho_lo/rho_hi and NH float4 (hi, lo) of U D_h,
-// each lane-interleaved.
+// The cross-atom pairs with two pairs per instruction: pairs 2i and 2i+1 of
+// a tile occupy the two lanes of every packed value, the thread's points are
+// duplicated into both lanes, and the Kahan sums run per lane (even and odd
+// pairs) until the lanes are added in FP64 at the end.  Of the per-pair
+// constants, rho (in T and in (-2 rho)^n) and U D_000 carry their lo parts;
+// the higher Hermite coefficients U D_tuv enter as their FP32 roundings.
+// rho repeats exactly across the pairs of one element pair and exponent pair
+// (it depends on p and the class alone), so its rounding is shared by many
+// pairs and adds up in the energy: on the 1000-atom s/p/d cluster dropping
+// rho_lo moved the energy by 3.5e-7 Eh, dropping the lo part of U D_000 by
+// 1.2e-7 Eh on the 300-atom s/p/d cluster, while the lo parts of the higher
+// coefficients changed it by under 2e-9 Eh.  Shared memory per pair of pairs,
+// lane-interleaved: float4 (xh, yh), (zh, rho_hi), (xl, yl); float2 zl,
+// rho_lo, rho_lo / rho_hi, lo(U D_000) and NH float2 hi(U D_h).
 template <int L, int PPT>
 __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32x2(int nesp, int jbeg, int jend, int seglen,
                                                             const float *__restrict__ eX,
@@ -347,8 +353,8 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32x2(int nesp, int jbeg, 
     constexpr int NH = nherm(L);
     constexpr int F = 3 + 2 * NH;
     constexpr int TP2 = MESP_TP / 2;
-    __shared__ float4 sXY[TP2], sZR[TP2], sXYl[TP2], sZRl[TP2], sD[NH][TP2];
-    __shared__ float2 sDr[TP2];
+    __shared__ float4 sXY[TP2], sZR[TP2], sXYl[TP2];
+    __shared__ float2 sZl[TP2], sRl[TP2], sDr[TP2], sD0l[TP2], sD[NH][TP2];
     const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
     const float *C = eC + (size_t)blk_cls[blockIdx.x] * F * nesp;
     const int j0 = jbeg + blockIdx.y * seglen;
@@ -378,34 +384,35 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32x2(int nesp, int jbeg, 
             const size_t j = jt + jj;
             const int s = jj >> 1, l = jj & 1;
             float *xy = reinterpret_cast<float *>(&sXY[s]), *zr = reinterpret_cast<float *>(&sZR[s]);
-            float *xyl = reinterpret_cast<float *>(&sXYl[s]), *zrl = reinterpret_cast<float *>(&sZRl[s]);
+            float *xyl = reinterpret_cast<float *>(&sXYl[s]);
             xy[l] = v ? eX[j] : 0.f;
             xy[2 + l] = v ? eX[(size_t)nesp + j] : 0.f;
             zr[l] = v ? eX[2 * (size_t)nesp + j] : 0.f;
             zr[2 + l] = v ? C[j] : 1.f;
             xyl[l] = v ? eX[3 * (size_t)nesp + j] : 0.f;
             xyl[2 + l] = v ? eX[4 * (size_t)nesp + j] : 0.f;
-            zrl[l] = v ? eX[5 * (size_t)nesp + j] : 0.f;
-            zrl[2 + l] = v ? C[(size_t)nesp + j] : 0.f;
+            reinterpret_cast<float *>(&sZl[s])[l] = v ? eX[5 * (size_t)nesp + j] : 0.f;
+            reinterpret_cast<float *>(&sRl[s])[l] = v ? C[(size_t)nesp + j] : 0.f;
             reinterpret_cast<float *>(&sDr[s])[l] = v ? C[2 * (size_t)nesp + j] : 0.f;
+            reinterpret_cast<float *>(&sD0l[s])[l] = v ? C[(size_t)(3 + NH) * nesp + j] : 0.f;
         }
         for (int t = threadIdx.x; t < NH * MESP_TP; t += MESP_NT) {
             const int h = t / MESP_TP, jj = t % MESP_TP;
-            const bool v = jj < nt;
-            float *d = reinterpret_cast<float *>(&sD[h][jj >> 1]);
-            d[jj & 1] = v ? C[(size_t)(3 + h) * nesp + jt + jj] : 0.f;
-            d[2 + (jj & 1)] = v ? C[(size_t)(3 + NH + h) * nesp + jt + jj] : 0.f;
+            reinterpret_cast<float *>(&sD[h][jj >> 1])[jj & 1] = jj < nt ? C[(size_t)(3 + h) * nesp + jt + jj] : 0.f;
         }
         __syncthreads();
         const int np = (nt + 1) >> 1;
         for (int s = 0; s < np; ++s) {
-            const float4 xy = sXY[s], zr = sZR[s], xyl = sXYl[s], zrl = sZRl[s];
+            const float4 xy = sXY[s], zr = sZR[s], xyl = sXYl[s];
+            const float2 zl = sZl[s];
             const f2 Ax(xy.x, xy.y), Ay(xy.z, xy.w), Az(zr.x, zr.y), rh(zr.z, zr.w);
-            const f2 Bx(xyl.x, xyl.y), By(xyl.z, xyl.w), Bz(zrl.x, zrl.y), rl(zrl.z, zrl.w);
-            f2 m2r, ndr[L + 1];
+            const f2 Bx(xyl.x, xyl.y), By(xyl.z, xyl.w), Bz(zl.x, zl.y);
+            const float2 rlo = sRl[s], d0l = sD0l[s];
+            const f2 rl(rlo.x, rlo.y), D0l(d0l.x, d0l.y);
+            const f2 m2r = rh * f2(-2.f);
+            f2 ndr[L + 1];
             if constexpr (L > 0) {
                 const float2 dr = sDr[s];
-                m2r = rh * f2(-2.f);
 #pragma unroll
                 for (int n = 1; n <= L; ++n) ndr[n] = f2((float)n) * f2(dr.x, dr.y);
             }
@@ -420,24 +427,27 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32x2(int nesp, int jbeg, 
                 boys_eval2<L>(T, boys, Fb);
                 f2 dot;
                 if constexpr (L == 0) {
-                    const float4 D = sD[0][s];
-                    dot = fma2(f2(D.x, D.y), Fb[0], f2(D.z, D.w) * Fb[0]);
+                    const float2 D = sD[0][s];
+                    dot = fma2(f2(D.x, D.y), Fb[0], D0l * Fb[0]);
                 } else {
+                    // R^(n) = (-2 rho)^n F_n, rho = rho_hi (1 + rho_lo / rho_hi)
                     f2 Rn[L + 1];
-                    f2 f(1.f);
+                    Rn[0] = Fb[0];
+                    f2 f = m2r;
 #pragma unroll
-                    for (int n = 0; n <= L; ++n) {
+                    for (int n = 1; n <= L; ++n) {
                         const f2 v = f * Fb[n];
-                        Rn[n] = (n == 0) ? v : fma2(v, ndr[n], v);
-                        f = f * m2r;
+                        Rn[n] = fma2(v, ndr[n], v);
+                        if (n < L) f = f * m2r;
                     }
                     f2 R[NH];
                     hermite_R<L, f2>(X, Y, Z, Rn, R);
-                    dot = f2(0.f);
+                    const float2 D0 = sD[0][s];
+                    dot = fma2(f2(D0.x, D0.y), R[0], D0l * R[0]);
 #pragma unroll
-                    for (int h = 0; h < NH; ++h) {
-                        const float4 D = sD[h][s];
-                        dot = fma2(f2(D.x, D.y), R[h], fma2(f2(D.z, D.w), R[h], dot));
+                    for (int h = 1; h < NH; ++h) {
+                        const float2 D = sD[h][s];
+                        dot = fma2(f2(D.x, D.y), R[h], dot);
                     }
                 }
                 const f2 y = dot - k32[q];
@@ -593,7 +603,8 @@ __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double
 // The same contraction with two points per packed instruction: points 2i and
 // 2i+1 of a tile occupy the two lanes, the thread's pairs are duplicated into
 // both lanes, and each lane's tile sums are added in FP64 (times U) at the end
-// of the tile.  The points are staged negated and lane-interleaved: float4
+// of the tile.  rho carries its lo part (its rounding is shared by every pair
+// of the same exponents and adds up, as noted at esp_kernel_f32x2).  The points are staged negated and lane-interleaved: float4
 // (-xh, -yh), (-zh, q), (-xl, -yl) and float2 (-zl) per pair of points; past
 // the end of the range a point has q = 0 and contributes zero.
 template <int L, int NPT>
@@ -705,13 +716,14 @@ __global__ void __launch_bounds__(MF_NT) fock_kernel_f32x2(int npair, const doub
                     if constexpr (L == 0) {
                         w32[i][0] = fma2(Q, Fb[0], w32[i][0]);
                     } else {
+                        // q_k (-2 rho)^n F_n
                         f2 Rn[L + 1];
                         f2 f = Q;
 #pragma unroll
                         for (int n = 0; n <= L; ++n) {
                             const f2 v = f * Fb[n];
                             Rn[n] = (n == 0) ? v : fma2(v, ndr[i][n], v);
-                            f = f * m2r[i];
+                            if (n < L) f = f * m2r[i];
                         }
                         f2 R[NH];
                         hermite_R<L, f2>(X, Y, Z, Rn, R);
@@ -854,6 +866,138 @@ __global__ void __launch_bounds__(MESP_NT) esp_grad_kernel_f32(int nesp, int seg
     }
 }
 
+
+// The point part with two pairs per packed instruction (lanes as in
+// esp_kernel_f32x2, 2 points per thread); each lane's arithmetic is that of
+// esp_grad_kernel_f32: hi + lo distances, rho hi + lo, and U D_tuv as the
+// FP32 sum of its hi and lo parts.  Shared memory per pair of pairs,
+// lane-interleaved: float4 (xh, yh), (zh, rho_hi), (xl, yl); float2 zl, rho_lo,
+// rho_lo / rho_hi and NH float2 U D_tuv.
+template <int L>
+__global__ void __launch_bounds__(MESP_NT) esp_grad_kernel_f32x2(int nesp, int seglen, const float *__restrict__ eX,
+                                                                 const float *__restrict__ eC,
+                                                                 const int *__restrict__ blk_off,
+                                                                 const int *__restrict__ blk_cls,
+                                                                 const float *__restrict__ ph,
+                                                                 const float *__restrict__ pl,
+                                                                 const float *__restrict__ boys, int M,
+                                                                 double *__restrict__ part)
+{
+    constexpr int NH = nherm(L);
+    constexpr int L1 = L + 1;
+    constexpr int NH1 = nherm(L1);
+    constexpr int F = 3 + 2 * NH;
+    constexpr int PPT = 2;
+    constexpr int TP2 = MESP_TP / 2;
+    __shared__ float4 sXY[TP2], sZR[TP2], sXYl[TP2];
+    __shared__ float2 sZl[TP2], sRl[TP2], sDr[TP2], sD[NH][TP2];
+    const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
+    const float *C = eC + (size_t)blk_cls[blockIdx.x] * F * nesp;
+    const int j0 = blockIdx.y * seglen;
+    const int j1 = min(nesp, j0 + seglen);
+
+    f2 nxh[PPT], nyh[PPT], nzh[PPT], nxl[PPT], nyl[PPT], nzl[PPT];
+    f2 a32[3][PPT], k32[3][PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int k = min(k0 + (int)threadIdx.x + q * MESP_NT, k1 - 1);
+        nxh[q] = f2(-ph[k]);
+        nyh[q] = f2(-ph[(size_t)M + k]);
+        nzh[q] = f2(-ph[2 * (size_t)M + k]);
+        nxl[q] = f2(-pl[k]);
+        nyl[q] = f2(-pl[(size_t)M + k]);
+        nzl[q] = f2(-pl[2 * (size_t)M + k]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) a32[d][q] = k32[d][q] = f2(0.f);
+    }
+    for (int jt = j0; jt < j1; jt += MESP_TP) {
+        const int nt = min(MESP_TP, j1 - jt);
+        __syncthreads();
+        for (int jj = threadIdx.x; jj < MESP_TP; jj += MESP_NT) {
+            const bool v = jj < nt;
+            const size_t j = jt + jj;
+            const int s = jj >> 1, l = jj & 1;
+            float *xy = reinterpret_cast<float *>(&sXY[s]), *zr = reinterpret_cast<float *>(&sZR[s]);
+            float *xyl = reinterpret_cast<float *>(&sXYl[s]);
+            xy[l] = v ? eX[j] : 0.f;
+            xy[2 + l] = v ? eX[(size_t)nesp + j] : 0.f;
+            zr[l] = v ? eX[2 * (size_t)nesp + j] : 0.f;
+            zr[2 + l] = v ? C[j] : 1.f;
+            xyl[l] = v ? eX[3 * (size_t)nesp + j] : 0.f;
+            xyl[2 + l] = v ? eX[4 * (size_t)nesp + j] : 0.f;
+            reinterpret_cast<float *>(&sZl[s])[l] = v ? eX[5 * (size_t)nesp + j] : 0.f;
+            reinterpret_cast<float *>(&sRl[s])[l] = v ? C[(size_t)nesp + j] : 0.f;
+            reinterpret_cast<float *>(&sDr[s])[l] = v ? C[2 * (size_t)nesp + j] : 0.f;
+        }
+        for (int t = threadIdx.x; t < NH * MESP_TP; t += MESP_NT) {
+            const int h = t / MESP_TP, jj = t % MESP_TP;
+            reinterpret_cast<float *>(&sD[h][jj >> 1])[jj & 1] =
+                jj < nt ? C[(size_t)(3 + h) * nesp + jt + jj] + C[(size_t)(3 + NH + h) * nesp + jt + jj] : 0.f;
+        }
+        __syncthreads();
+        const int np = (nt + 1) >> 1;
+        for (int s = 0; s < np; ++s) {
+            const float4 xy = sXY[s], zr = sZR[s], xyl = sXYl[s];
+            const float2 zl = sZl[s], rlo = sRl[s], dr = sDr[s];
+            const f2 Ax(xy.x, xy.y), Ay(xy.z, xy.w), Az(zr.x, zr.y), rh(zr.z, zr.w);
+            const f2 Bx(xyl.x, xyl.y), By(xyl.z, xyl.w), Bz(zl.x, zl.y), rl(rlo.x, rlo.y);
+            const f2 m2r = rh * f2(-2.f);
+            f2 ndr[L1 + 1];
+#pragma unroll
+            for (int n = 1; n <= L1; ++n) ndr[n] = f2((float)n) * f2(dr.x, dr.y);
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                const f2 X = (Ax + nxh[q]) + (Bx + nxl[q]);
+                const f2 Y = (Ay + nyh[q]) + (By + nyl[q]);
+                const f2 Z = (Az + nzh[q]) + (Bz + nzl[q]);
+                const f2 R2 = fma2(X, X, fma2(Y, Y, Z * Z));
+                const f2 T = fma2(rh, R2, rl * R2);
+                f2 Fb[L1 + 1];
+                boys_eval2<L1>(T, boys, Fb);
+                f2 Rn[L1 + 1];
+                Rn[0] = Fb[0];
+                f2 f = m2r;
+#pragma unroll
+                for (int n = 1; n <= L1; ++n) {
+                    const f2 v = f * Fb[n];
+                    Rn[n] = fma2(v, ndr[n], v);
+                    if (n < L1) f = f * m2r;
+                }
+                f2 R[NH1];
+                hermite_R<L1, f2>(X, Y, Z, Rn, R);
+                f2 sd[3] = {f2(0.f), f2(0.f), f2(0.f)};
+#pragma unroll
+                for (int t = 0; t <= L; ++t)
+#pragma unroll
+                    for (int u = 0; u <= L - t; ++u)
+#pragma unroll
+                        for (int v = 0; v <= L - t - u; ++v) {
+                            const float2 Dv = sD[hidx(t, u, v)][s];
+                            const f2 Dt(Dv.x, Dv.y);
+                            sd[0] = fma2(Dt, R[hidx(t + 1, u, v)], sd[0]);
+                            sd[1] = fma2(Dt, R[hidx(t, u + 1, v)], sd[1]);
+                            sd[2] = fma2(Dt, R[hidx(t, u, v + 1)], sd[2]);
+                        }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const f2 y = sd[d] - k32[d][q];
+                    const f2 t = a32[d][q] + y;
+                    k32[d][q] = (t - a32[d][q]) - y;
+                    a32[d][q] = t;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int k = k0 + threadIdx.x + q * MESP_NT;
+        if (k < k1)
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                part[((size_t)blockIdx.y * 3 + d) * M + k] = ((double)a32[d][q].v.x - (double)k32[d][q].v.x) +
+                                                             ((double)a32[d][q].v.y - (double)k32[d][q].v.y);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // The "MS-driven" ESP of Section 4a (an autotuner candidate): one primitive
@@ -1283,8 +1427,12 @@ static int grad_point_mixed_class(pcm_ctx *c, PairClass &pc, const int *blk, con
                                                                      pc.eX32.p, pc.eC32.p);
     PCM_LAUNCHED(c);
     dim3 grid(nblk, rows);
-    esp_grad_kernel_f32<L><<<grid, MESP_NT, 0, c->stream>>>(n, sl, pc.eX32.p, pc.eC32.p, blk, bcls, c->p32.p,
-                                                             c->p32lo.p, c->boys32.p, c->M, part);
+    if (c->opt.fp32x2)
+        esp_grad_kernel_f32x2<L><<<grid, MESP_NT, 0, c->stream>>>(n, sl, pc.eX32.p, pc.eC32.p, blk, bcls, c->p32.p,
+                                                                   c->p32lo.p, c->boys32.p, c->M, part);
+    else
+        esp_grad_kernel_f32<L><<<grid, MESP_NT, 0, c->stream>>>(n, sl, pc.eX32.p, pc.eC32.p, blk, bcls, c->p32.p,
+                                                                 c->p32lo.p, c->boys32.p, c->M, part);
     PCM_LAUNCHED(c);
     return PCM_OK;
 }
@@ -1297,8 +1445,12 @@ int grad_point_mixed(pcm_ctx *c, int *total_rows)
     PCM_TRY(mixed_point_blocks(c, nb));
     DBuf<int> *blk = &c->si[4], *bcls = &c->si[6];
     int rows[6], sls[6], total = 0;
+    // point-block layout: 2 points per thread for the packed kernel, else the
+    // scalar kernel's 4 (L <= 1) or 2
+    int lay[6];
     for (int k = 0; k < 6; ++k) {
-        esp_plan(c->cls[k].nesp, nb[CLASS_L[k] <= 1 ? 0 : 1], &sls[k], &rows[k]);
+        lay[k] = (c->opt.fp32x2 || CLASS_L[k] > 1) ? 1 : 0;
+        esp_plan(c->cls[k].nesp, nb[lay[k]], &sls[k], &rows[k]);
         total += rows[k];
     }
     *total_rows = total;
@@ -1309,7 +1461,7 @@ int grad_point_mixed(pcm_ctx *c, int *total_rows)
         PairClass &pc = c->cls[k];
         if (rows[k] == 0) continue;
         double *part = c->esp_part.p + (size_t)base * 3 * c->M;
-        const int v = CLASS_L[k] <= 1 ? 0 : 1;
+        const int v = lay[k];
         switch (CLASS_L[k]) {
 #define PCM_GPM(LL)                                                                                      \
     case LL:                                                                                             \
@@ -1329,33 +1481,49 @@ int grad_point_mixed(pcm_ctx *c, int *total_rows)
 
 // W_tuv (t+u+v <= L+1) over the ESP pairs of class k on the FP32 pipes; the
 // pairs' split centres come from the point-part preparation (eX32)
+template <int LL>
+static void grad_w_launch(pcm_ctx *c, PairClass &pc, const double *dq, dim3 grid, int ksplit, double *W, int npt)
+{
+    const int n = pc.nesp;
+    const double *gp = pc.eP.p + 3 * (size_t)n;
+    if constexpr (LL <= 4) {
+        if (c->opt.fp32x2) {
+            if (npt == 2 && LL < 4)
+                fock_kernel_f32x2<LL, 2><<<grid, MF_NT, 0, c->stream>>>(n, gp, pc.eX32.p, ksplit, c->p32.p,
+                                                                         c->p32lo.p, dq, c->M, c->ncls,
+                                                                         c->cls_off.p, c->cls_zeta.p, c->boys32.p, W);
+            else
+                fock_kernel_f32x2<LL, 1><<<grid, MF_NT, 0, c->stream>>>(n, gp, pc.eX32.p, ksplit, c->p32.p,
+                                                                         c->p32lo.p, dq, c->M, c->ncls,
+                                                                         c->cls_off.p, c->cls_zeta.p, c->boys32.p, W);
+            return;
+        }
+    }
+    if (npt == 2)
+        fock_kernel_f32<LL, 2><<<grid, MF_NT, 0, c->stream>>>(n, gp, pc.eX32.p, ksplit, c->p32.p, c->p32lo.p, dq, c->M,
+                                                               c->ncls, c->cls_off.p, c->cls_zeta.p, c->boys32.p, W);
+    else
+        fock_kernel_f32<LL, 1><<<grid, MF_NT, 0, c->stream>>>(n, gp, pc.eX32.p, ksplit, c->p32.p, c->p32lo.p, dq, c->M,
+                                                               c->ncls, c->cls_off.p, c->cls_zeta.p, c->boys32.p, W);
+}
+
+// W accumulation of the integral gradient: the Fock contraction with R up to
+// L + 1 over the ESP pairs (packed two points per instruction up to L + 1 = 4;
+// one pair per thread from L + 1 = 4 on, where two would spill)
 int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt)
 {
     PairClass &pc = c->cls[k];
-    const int n = pc.nesp;
+    const int L1 = CLASS_L[k] + 1;
+    if (L1 >= 4) npt = 1;
     const int per = MF_NT * npt;
-    const int nb = (n + per - 1) / per;
+    const int nb = (pc.nesp + per - 1) / per;
     dim3 grid(nb, nsplit);
-    switch (CLASS_L[k] + 1) {
-#define PCM_GW(LL)                                                                                             \
-    case LL:                                                                                                   \
-        if (npt == 2)                                                                                          \
-            fock_kernel_f32<LL, 2><<<grid, MF_NT, 0, c->stream>>>(n, pc.eP.p + 3 * (size_t)n, pc.eX32.p,         \
-                                                                   ksplit, c->p32.p, c->p32lo.p, dq, c->M,     \
-                                                                   c->ncls, c->cls_off.p, c->cls_zeta.p,       \
-                                                                   c->boys32.p, W);                            \
-        else                                                                                                   \
-            fock_kernel_f32<LL, 1><<<grid, MF_NT, 0, c->stream>>>(n, pc.eP.p + 3 * (size_t)n, pc.eX32.p,         \
-                                                                   ksplit, c->p32.p, c->p32lo.p, dq, c->M,     \
-                                                                   c->ncls, c->cls_off.p, c->cls_zeta.p,       \
-                                                                   c->boys32.p, W);                            \
-        break;
-        PCM_GW(1)
-        PCM_GW(2)
-        PCM_GW(3)
-        PCM_GW(4)
-        PCM_GW(5)
-#undef PCM_GW
+    switch (L1) {
+    case 1: grad_w_launch<1>(c, pc, dq, grid, ksplit, W, npt); break;
+    case 2: grad_w_launch<2>(c, pc, dq, grid, ksplit, W, npt); break;
+    case 3: grad_w_launch<3>(c, pc, dq, grid, ksplit, W, npt); break;
+    case 4: grad_w_launch<4>(c, pc, dq, grid, ksplit, W, npt); break;
+    case 5: grad_w_launch<5>(c, pc, dq, grid, ksplit, W, npt); break;
     }
     PCM_LAUNCHED(c);
     return PCM_OK;

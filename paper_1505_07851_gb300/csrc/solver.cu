@@ -13,6 +13,7 @@
 // of iterations and look at the flag once per batch.
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -276,9 +277,18 @@ __global__ void pcg_update_rbj_kernel(int M, int l, const int *__restrict__ perm
     }
 }
 
-__global__ void pcg_dir_kernel(int M, const double *__restrict__ z, double *__restrict__ p,
-                               const double *__restrict__ scal, const int *__restrict__ iscal)
+// Inside the solver's CUDA graph the direction kernel also sets the loop
+// condition of the graph's WHILE node: continue while the stop flag is clear.
+__device__ __forceinline__ void pcg_set_condition(cudaGraphConditionalHandle h, int set_cond, const int *iscal)
 {
+    if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, iscal[I_DONE] ? 0u : 1u);
+}
+
+__global__ void pcg_dir_kernel(int M, const double *__restrict__ z, double *__restrict__ p,
+                               const double *__restrict__ scal, const int *__restrict__ iscal,
+                               cudaGraphConditionalHandle h, int set_cond)
+{
+    pcg_set_condition(h, set_cond, iscal);
     if (iscal[I_DONE]) return;
     const double beta = scal[S_BETA];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x)
@@ -287,8 +297,10 @@ __global__ void pcg_dir_kernel(int M, const double *__restrict__ z, double *__re
 
 // p = z + beta p, also as FP32 for the FP32 GEMV
 __global__ void pcg_dir32_kernel(int M, const double *__restrict__ z, double *__restrict__ p, float *__restrict__ p32,
-                                 const double *__restrict__ scal, const int *__restrict__ iscal)
+                                 const double *__restrict__ scal, const int *__restrict__ iscal,
+                                 cudaGraphConditionalHandle h, int set_cond)
 {
+    pcg_set_condition(h, set_cond, iscal);
     if (iscal[I_DONE]) return;
     const double beta = scal[S_BETA];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
@@ -882,19 +894,107 @@ int solver_prepare_full(pcm_ctx *c)
 // updated residual is below delta or max_iter steps; the FP64 stored A, or
 // with use32 the FP32 copy (FP32 GEMV).  Returns iterations, the stop flag
 // and the final residual norm.
+// One PCG iteration (gemv, update, dir) on stream st; set_cond: the direction
+// kernel sets the graph's loop condition h
+static void pcg_iteration(pcm_ctx *c, cudaStream_t st, double *x, bool use32, cudaGraphConditionalHandle h,
+                          int set_cond)
+{
+    const int M = c->M;
+    double *r = c->vr.p, *z = c->vz.p, *p = c->vp.p, *Ap = c->vAp.p;
+    float *p32 = c->vp32.p;
+    const int gv = gemv_grid(c);
+    const int ub = std::min(MAX_PART, (M + UP_NT - 1) / UP_NT);
+    const int eb = std::min(1024, (M + 255) / 256);
+    const double *dinv = (c->pc_kind == PCM_PRECOND_JACOBI) ? c->dinv.p : nullptr;
+    const bool rbj = c->pc_kind == PCM_PRECOND_RBJ || c->pc_kind == PCM_PRECOND_OCTREE;
+    const int *bstart = c->pc_kind == PCM_PRECOND_OCTREE ? c->rbj_bstart.p : nullptr;
+    const int rbj_nt = std::min(1024, RBJ_SPLIT * std::max(32, (c->rbj_l + 31) / 32 * 32));
+    const size_t rbj_smem = (size_t)c->rbj_l * sizeof(double);
+    if (use32)
+        pcg_gemv_rp_kernel<float><<<gv, GV_NT, 0, st>>>(M, c->lda, c->A32.p, p32, p, Ap, c->red.p, c->scal.p,
+                                                         c->iscal.p, c->counter.p);
+    else
+        pcg_gemv_rp_kernel<double><<<gv, GV_NT, 0, st>>>(M, c->lda, c->A.p, p, p, Ap, c->red.p, c->scal.p,
+                                                          c->iscal.p, c->counter.p);
+    if (rbj)
+        pcg_update_rbj_kernel<<<c->rbj_nblk, rbj_nt, rbj_smem, st>>>(M, c->rbj_l, c->rbj_perm.p, bstart,
+                                                                     c->rbj_inv.p, x, r, z, p, Ap, c->red.p,
+                                                                     c->scal.p, c->iscal.p, c->counter.p, 0);
+    else
+        pcg_update_diag_kernel<<<ub, UP_NT, 0, st>>>(M, dinv, x, r, z, p, Ap, c->red.p, c->scal.p, c->iscal.p,
+                                                     c->counter.p);
+    if (use32) pcg_dir32_kernel<<<eb, 256, 0, st>>>(M, z, p, p32, c->scal.p, c->iscal.p, h, set_cond);
+    else pcg_dir_kernel<<<eb, 256, 0, st>>>(M, z, p, c->scal.p, c->iscal.p, h, set_cond);
+}
+
+// The iteration loop as a CUDA graph: a conditional WHILE node whose body is
+// one iteration; the direction kernel clears the condition once the stop flag
+// is set (the test of Eq. 20, or the iteration cap in finish_update), so every
+// graph launch ends after at most max_iter + 1 bodies.  Rebuilt when anything
+// the captured launches read changes.
+static int pcg_graph(pcm_ctx *c, double *x, bool use32)
+{
+    const uintptr_t key[] = {(uintptr_t)use32, (uintptr_t)x, (uintptr_t)c->M, (uintptr_t)c->lda,
+                             (uintptr_t)(use32 ? (const void *)c->A32.p : (const void *)c->A.p),
+                             (uintptr_t)c->vr.p, (uintptr_t)c->vz.p, (uintptr_t)c->vp.p, (uintptr_t)c->vAp.p,
+                             (uintptr_t)c->vp32.p, (uintptr_t)c->red.p, (uintptr_t)c->scal.p, (uintptr_t)c->iscal.p,
+                             (uintptr_t)c->counter.p, (uintptr_t)c->pc_kind, (uintptr_t)c->dinv.p,
+                             (uintptr_t)c->rbj_perm.p, (uintptr_t)c->rbj_bstart.p, (uintptr_t)c->rbj_inv.p,
+                             (uintptr_t)c->rbj_l, (uintptr_t)c->rbj_nblk};
+    static_assert(sizeof(key) <= sizeof(c->pcg_key), "graph key too long");
+    if (c->pcg_exec && memcmp(key, c->pcg_key, sizeof(key)) == 0) return PCM_OK;
+    if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+    if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
+    c->pcg_exec = nullptr;
+    c->pcg_graph = nullptr;
+    memset(c->pcg_key, 0, sizeof(c->pcg_key));
+    if (!c->cap_stream) PCM_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    PCM_CUDA(cudaGraphCreate(&c->pcg_graph, 0));
+    cudaGraphConditionalHandle handle;
+    PCM_CUDA(cudaGraphConditionalHandleCreate(&handle, c->pcg_graph, 1, cudaGraphCondAssignDefault));
+    // the parameter struct has no default constructor: zeroed raw storage
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams *cp = reinterpret_cast<cudaGraphNodeParams *>(raw);
+    cp->type = cudaGraphNodeTypeConditional;
+    cp->conditional.handle = handle;
+    cp->conditional.type = cudaGraphCondTypeWhile;
+    cp->conditional.size = 1;
+    cudaGraphNode_t node;
+    PCM_CUDA(cudaGraphAddNode(&node, c->pcg_graph, nullptr, nullptr, 0, cp));
+    cudaGraph_t body = cp->conditional.phGraph_out[0];
+    PCM_CUDA(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    pcg_iteration(c, c->cap_stream, x, use32, handle, 1);
+    const cudaError_t e = cudaGetLastError();
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &captured);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        set_last_error("solver graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return PCM_ERR_CUDA;
+    }
+    PCM_CUDA(cudaGraphInstantiate(&c->pcg_exec, c->pcg_graph, 0));
+    memcpy(c->pcg_key, key, sizeof(key));
+    return PCM_OK;
+}
+
 static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double delta, int max_iter, bool use32,
                     int *iters, int *conv, double *rnorm)
 {
     const int M = c->M;
+    if (!c->h_pinned) PCM_CUDA(cudaMallocHost((void **)&c->h_pinned, 32 * sizeof(double)));
+    double *hs = c->h_pinned;
+    int *hi = reinterpret_cast<int *>(c->h_pinned + 16);
+    // the pinned scalars of the previous call were read after its final synchronisation
+    for (int i = 0; i < S_NSCAL; ++i) hs[i] = 0.0;
+    hs[S_DELTA] = delta;
+    hi[I_DONE] = 0;
+    hi[I_ITER] = 0;
+    hi[I_MAXIT] = max_iter;
+    hi[I_CONV] = 0;
     PCM_CUDA(cudaMemsetAsync(c->counter.p, 0, 4 * sizeof(unsigned int), c->stream));
-    {
-        double hs[S_NSCAL] = {0, 0, 0, 0, 0, delta, 0};
-        int hi[I_NINT] = {0, 0, max_iter, 0};
-        PCM_CUDA(cudaMemcpyAsync(c->scal.p, hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
-        PCM_CUDA(cudaMemcpyAsync(c->iscal.p, hi, sizeof(hi), cudaMemcpyHostToDevice, c->stream));
-        // hs, hi are read before the synchronisation below
-        PCM_CUDA(cudaStreamSynchronize(c->stream));
-    }
+    PCM_CUDA(cudaMemcpyAsync(c->scal.p, hs, S_NSCAL * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    PCM_CUDA(cudaMemcpyAsync(c->iscal.p, hi, I_NINT * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     double *r = c->vr.p, *z = c->vz.p, *p = c->vp.p, *Ap = c->vAp.p;
     float *p32 = c->vp32.p;
     const int gv = gemv_grid(c);
@@ -927,43 +1027,19 @@ static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double
     else copy_kernel<<<eb, 256, 0, c->stream>>>(M, z, p);
     PCM_LAUNCHED(c);
 
-    const int batch = 8;
-    int h_i[I_NINT] = {0, 0, 0, 0};
-    for (int done_it = 0;;) {
-        for (int b = 0; b < batch; ++b) {
-            if (use32)
-                pcg_gemv_rp_kernel<float><<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A32.p, p32, p, Ap, c->red.p,
-                                                                       c->scal.p, c->iscal.p, c->counter.p);
-            else
-                pcg_gemv_rp_kernel<double><<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, p, p, Ap, c->red.p,
-                                                                        c->scal.p, c->iscal.p, c->counter.p);
-            if (rbj)
-                pcg_update_rbj_kernel<<<c->rbj_nblk, rbj_nt, rbj_smem, c->stream>>>(
-                    M, c->rbj_l, c->rbj_perm.p, bstart, c->rbj_inv.p, x, r, z, p, Ap, c->red.p, c->scal.p, c->iscal.p,
-                    c->counter.p, 0);
-            else
-                pcg_update_diag_kernel<<<ub, UP_NT, 0, c->stream>>>(M, dinv, x, r, z, p, Ap, c->red.p, c->scal.p,
-                                                                    c->iscal.p, c->counter.p);
-            if (use32) pcg_dir32_kernel<<<eb, 256, 0, c->stream>>>(M, z, p, p32, c->scal.p, c->iscal.p);
-            else pcg_dir_kernel<<<eb, 256, 0, c->stream>>>(M, z, p, c->scal.p, c->iscal.p);
-            c->stats.launches += 3;
-        }
-        PCM_CUDA(cudaGetLastError());
-        PCM_CUDA(cudaMemcpyAsync(h_i, c->iscal.p, sizeof(h_i), cudaMemcpyDeviceToHost, c->stream));
-        PCM_CUDA(cudaStreamSynchronize(c->stream));
-        done_it += batch;
-        if (h_i[I_DONE]) break;
-        if (done_it > max_iter + 2 * batch) {  // the device cap ends the loop first
-            set_last_error("solver loop did not stop at its iteration cap");
-            return PCM_ERR_TIMEOUT;
-        }
-    }
-    double h_s[S_NSCAL];
-    PCM_CUDA(cudaMemcpyAsync(h_s, c->scal.p, sizeof(h_s), cudaMemcpyDeviceToHost, c->stream));
+    PCM_TRY(pcg_graph(c, x, use32));
+    PCM_CUDA(cudaGraphLaunch(c->pcg_exec, c->stream));
+    PCM_CUDA(cudaMemcpyAsync(hi, c->iscal.p, I_NINT * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PCM_CUDA(cudaMemcpyAsync(hs, c->scal.p, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
-    *iters = h_i[I_ITER];
-    *conv = h_i[I_CONV];
-    *rnorm = h_s[S_RNORM];
+    if (!hi[I_DONE]) {  // the graph's loop ends only with the flag set
+        set_last_error("solver loop ended without its stop flag");
+        return PCM_ERR_TIMEOUT;
+    }
+    *iters = hi[I_ITER];
+    *conv = hi[I_CONV];
+    *rnorm = hs[S_RNORM];
+    c->stats.launches += 3 * (long long)std::max(1, hi[I_ITER]);  // graph bodies run
     return PCM_OK;
 }
 
