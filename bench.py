@@ -79,13 +79,14 @@ def flops_per_interaction(L, kind):
 
 
 def flops_per_interaction_f32(L, kind):
-    """The FP32 kernels' operations: split-coordinate distance (9), R^2 (5),
-    T from split rho (3), Boys by 4-term Taylor (5 + 6 (L+1)), (-2 rho)^n
-    with the first-order rho_lo correction (4L + 1), Hermite recurrence, then
-    the split-D dot (4 nherm + 1) or the accumulation (nherm + 1)."""
+    """The packed FP32 kernels' own operations, compensation terms included
+    (the Kahan sum excepted): split-coordinate distance (9), R^2 (5), T from
+    split rho (3), Boys by 4-term Taylor (5 + 6 (L+1)), (-2 rho)^n with the
+    first-order rho_lo correction (4L + 1), Hermite recurrence, then the dot
+    with U D_000 split (2 nherm + 1) or the accumulation (nherm + 1)."""
     base = 9 + 5 + 3 + 5 + 6 * (L + 1) + (4 * L + 1 if L else 0) + _hermite_ops(L)
     if kind == "esp":
-        return base + (4 * _nherm(L) if L else 3) + 1
+        return base + 2 * _nherm(L) + 1
     return base + _nherm(L) + 1
 
 
@@ -93,7 +94,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/); a kernel missing here reports traffic null.
-NCU_TRAFFIC_BYTES = {"esp_kernel_f32<L=1> (ps)": 35.899648e6 + 15.616e3}
+NCU_TRAFFIC_BYTES = {"esp_kernel_f32<L=1> (ps)": 35.899648e6 + 15.616e3}  # scalar kernel (--scalar-fp32)
 
 CLASS_L = [0, 1, 2, 2, 3, 4]
 CLASS_NAME = ["ss", "ps", "pp", "ds", "dp", "dd"]
@@ -311,26 +312,34 @@ def _time_gradient(res, q, flush, stream, steps):
     return statistics.mean(ts), g.cpu().numpy(), ctx.stats()
 
 
-def _dominant(res, precision, steps):
+def _dominant(res, precision, steps, packed=True):
+    """The step's longest integral class: its algorithmic flops (the per-
+    interaction figures of flops_per_interaction, the same in both precisions)
+    over its CUDA-event time, against the pipe peak of its precision; the FP32
+    kernels' own operation count (with the hi + lo compensation terms) is
+    reported beside it."""
     s = res["stats"]
     M = s["M"]
-    fl = flops_per_interaction if precision == "fp64" else flops_per_interaction_f32
-    tag = "f64" if precision == "fp64" else "f32"
+    tag = "f64" if precision == "fp64" else ("f32x2" if packed else "f32")
     cand = []
     for k in range(6):
-        if res["esp_cls"][k] > 0:
-            cand.append(("esp_kernel_%s<L=%d> (%s)" % (tag, CLASS_L[k], CLASS_NAME[k]), res["esp_cls"][k] / steps,
-                         s["esp_class_pairs"][k] * M * fl(CLASS_L[k], "esp")))
-        if res["fock_cls"][k] > 0:
-            cand.append(("fock_kernel_%s<L=%d> (%s)" % (tag, CLASS_L[k], CLASS_NAME[k]), res["fock_cls"][k] / steps,
-                         s["fock_class_pairs"][k] * M * fl(CLASS_L[k], "fock")))
-    name, ms_k, flops_k = max(cand, key=lambda t: t[1])
+        for kind, ms in (("esp", res["esp_cls"][k]), ("fock", res["fock_cls"][k])):
+            if ms > 0:
+                n = s["%s_class_pairs" % kind][k] * M
+                cand.append(("%s_kernel_%s<L=%d> (%s)" % (kind, tag, CLASS_L[k], CLASS_NAME[k]), ms / steps,
+                             n * flops_per_interaction(CLASS_L[k], kind),
+                             n * flops_per_interaction_f32(CLASS_L[k], kind)))
+    name, ms_k, flops_k, ops_k = max(cand, key=lambda t: t[1])
     peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
     achieved = flops_k / (ms_k * 1e-3) / 1e12
     src = ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (nominal 1.25 TFLOP/s)" if precision == "fp64" else
            "FP32 pipe: 152 SMs x 128 FFMA/clk x 2070 MHz")
-    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "peak_source": src, "kernel_ms": ms_k}
+    out = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "peak_source": src, "kernel_ms": ms_k,
+           "flops": "algorithmic: flops_per_interaction x pair-point interactions"}
+    if precision != "fp64":
+        out["achieved_with_compensation_ops"] = ops_k / (ms_k * 1e-3) / 1e12
+    return out
 
 
 def run_ours(args):
@@ -363,7 +372,7 @@ def run_ours(args):
         other = _timed_steps(pcm, w, "fp64", args, dev, stream, flush, delta, max(1, args.steps // 2), 1)
 
     value, total_ms_max = replica_throughput(main["ints"], sum(main["times"]), world, dev)
-    roofline = _dominant(main, args.precision, args.steps)
+    roofline = _dominant(main, args.precision, args.steps, packed=not args.scalar_fp32)
     roofline["traffic"] = args.traffic if args.traffic is not None else NCU_TRAFFIC_BYTES.get(roofline["kernel"])
     s = main["stats"]
     ctx = main["ctx"]

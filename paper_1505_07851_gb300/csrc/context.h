@@ -133,6 +133,7 @@ struct pcm_ctx {
     int lda = 0;
     pcm::DBuf<double> A;
     pcm::DBuf<float> A32;                  // FP32 copy of A for the inner solves of PCM_MIXED
+    pcm::DBuf<float> A32lo;                // A - A32 in FP32: A32 + A32lo is the double-float A
     bool a32_ready = false;
     pcm::DBuf<double> dinv;                // 1 / A_kk
 
@@ -157,12 +158,14 @@ struct pcm_ctx {
     bool pc_ready = false;
     int rbj_l = 0, rbj_nblk = 0;
     pcm::DBuf<int> rbj_perm;               // M: block-ordered point indices
+    pcm::DBuf<int> rbj_T;                  // natom x points per sphere: candidate-index table of the RBJ set-up
     pcm::DBuf<double> rbj_inv;             // nblk x l x l inverses (padded)
     pcm::DBuf<int> rbj_bstart;             // octree: nblk + 1 block starts in rbj_perm (blocks of varying size)
 
     // solver work vectors and scalars
     pcm::DBuf<double> vx, vr, vz, vp, vAp, vrhs, vtmp, vro, vd;
     pcm::DBuf<float> vp32;
+    pcm::DBuf<float> vxs32;                // 2 x lda: FP32 hi and lo parts of a GEMV's input vector
     pcm::DBuf<double> red;                 // partial sums
     pcm::DBuf<double> scal;                // device scalars
     pcm::DBuf<int> iscal;                  // device ints (done flag, iteration count)

@@ -73,6 +73,35 @@ __device__ __forceinline__ double sum_partials(const double *part, int n)
     return t;
 }
 
+// the same for n interleaved pairs (part[2 i], part[2 i + 1]): both sums
+// valid in thread 0.  Every thread of the block takes a share of the loads, so
+// the partials are read in parallel rather than one after another.
+__device__ __forceinline__ void sum_partials2(const double *part, int n, double *a_out, double *b_out)
+{
+    __shared__ double sh[2][32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a += ((volatile const double *)part)[2 * i];
+        b += ((volatile const double *)part)[2 * i + 1];
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = a;
+        sh[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            x += sh[0][i];
+            y += sh[1][i];
+        }
+        *a_out = x;
+        *b_out = y;
+    }
+}
+
 // Ap = A p (FP64 or FP32 copy of A), p.Ap -> alpha
 template <typename TA>
 __global__ void __launch_bounds__(GV_NT) pcg_gemv_rp_kernel(int M, int lda, const TA *__restrict__ A,
@@ -159,12 +188,9 @@ __global__ void __launch_bounds__(UP_NT) pcg_update_diag_kernel(int M, const dou
         part[2 * blockIdx.x + 1] = b;
     }
     if (last_block(counter)) {
+        double a, b;
+        sum_partials2(part, gridDim.x, &a, &b);
         if (threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
-            for (unsigned int i = 0; i < gridDim.x; ++i) {
-                a += ((volatile double *)part)[2 * i];
-                b += ((volatile double *)part)[2 * i + 1];
-            }
             finish_update(a, b, scal, iscal);
             *counter = 0;
         }
@@ -255,12 +281,9 @@ __global__ void pcg_update_rbj_kernel(int M, int l, const int *__restrict__ perm
         part[2 * b + 1] = c;
     }
     if (last_block(counter)) {
+        double a, c;
+        sum_partials2(part, gridDim.x, &a, &c);
         if (threadIdx.x == 0) {
-            double a = 0.0, c = 0.0;
-            for (unsigned int i = 0; i < gridDim.x; ++i) {
-                a += ((volatile double *)part)[2 * i];
-                c += ((volatile double *)part)[2 * i + 1];
-            }
             if (init) {
                 scal[S_RZ] = c;
                 scal[S_RR] = a;
@@ -318,11 +341,70 @@ __global__ void copy32_kernel(int M, const double *__restrict__ a, double *__res
     }
 }
 
-// FP32 copy of the stored A for the inner solves of PCM_MIXED
-__global__ void a_to_f32_kernel(long long n, const double *__restrict__ A, float *__restrict__ A32)
+// FP32 copy of the stored A for the inner solves of PCM_MIXED, and the FP32
+// residual A - A32 (A = A32 + A32lo to ~2^-48) for the double-float GEMV
+__global__ void a_to_f32_kernel(long long n, const double *__restrict__ A, float *__restrict__ A32,
+                                float *__restrict__ A32lo)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        A32[i] = (float)A[i];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double a = A[i];
+        const float h = (float)a;
+        A32[i] = h;
+        A32lo[i] = (float)(a - (double)h);
+    }
+}
+
+static int a32_build(pcm_ctx *c, cudaStream_t st)
+{
+    PCM_TRY(c->A32.alloc((size_t)c->M * c->lda));
+    PCM_TRY(c->A32lo.alloc((size_t)c->M * c->lda));
+    const long long n = (long long)c->M * c->lda;
+    a_to_f32_kernel<<<4 * 152, 256, 0, st>>>(n, c->A.p, c->A32.p, c->A32lo.p);
+    PCM_LAUNCHED(c);
+    c->a32_ready = true;
+    return PCM_OK;
+}
+
+// x -> FP32 hi + lo parts for the double-float GEMV
+__global__ void split_x_kernel(int M, const double *__restrict__ x, float *__restrict__ xh, float *__restrict__ xl)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        const float h = (float)x[k];
+        xh[k] = h;
+        xl[k] = (float)(x[k] - (double)h);
+    }
+}
+
+// y = A x in double-float (PCM_MIXED), block partials of x.y
+__global__ void __launch_bounds__(GV_NT) gemv_df_kernel(int M, int lda, const float *__restrict__ Ahi,
+                                                        const float *__restrict__ Alo, const float *__restrict__ xh,
+                                                        const float *__restrict__ xl, const double *__restrict__ x,
+                                                        double *__restrict__ y, double *__restrict__ part)
+{
+    const double bsum = gemv_rowpair_df(blockIdx.x, M, lda, Ahi, Alo, xh, xl, x, y);
+    if (threadIdx.x == 0) part[blockIdx.x] = bsum;
+}
+
+// y = A x with the stored A: FP64, or double-float from A32 + A32lo when the
+// context is PCM_MIXED and they exist; block partials of x.y in part
+static int gemv_a(pcm_ctx *c, const double *x, double *y, double *part)
+{
+    const int M = c->M;
+    const int gv = std::max(1, (M + 1) / 2);
+    if (c->opt.precision == PCM_MIXED && c->a32_ready) {
+        // hi part at 0, lo part at lda (a multiple of 32 floats): both start on
+        // the 16-byte boundary the GEMV's float4 loads need
+        PCM_TRY(c->vxs32.alloc(2 * (size_t)c->lda));
+        float *xh = c->vxs32.p, *xl = c->vxs32.p + c->lda;
+        const int eb = std::min(1024, (M + 255) / 256);
+        split_x_kernel<<<eb, 256, 0, c->stream>>>(M, x, xh, xl);
+        PCM_LAUNCHED(c);
+        gemv_df_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A32.p, c->A32lo.p, xh, xl, x, y, part);
+    } else {
+        gemv_rp_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, x, y, part);
+    }
+    PCM_LAUNCHED(c);
+    return PCM_OK;
 }
 
 // r = b - y and per-block partial sums of r.r
@@ -397,12 +479,9 @@ __global__ void __launch_bounds__(UP_NT) pcg_init_diag_kernel(int M, const doubl
         part[2 * blockIdx.x + 1] = b;
     }
     if (last_block(counter)) {
+        double a, b;
+        sum_partials2(part, gridDim.x, &a, &b);
         if (threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
-            for (unsigned int i = 0; i < gridDim.x; ++i) {
-                a += ((volatile double *)part)[2 * i];
-                b += ((volatile double *)part)[2 * i + 1];
-            }
             scal[S_RZ] = b;
             scal[S_RR] = a;
             scal[S_RNORM] = sqrt(a);
@@ -477,19 +556,44 @@ __device__ __forceinline__ unsigned long long rbj_key64(double a) { return (unsi
 // coarse bin: top 11 bits of the FP32 value (monotone in |A|)
 __device__ __forceinline__ int rbj_bin(double a) { return (int)(__float_as_uint((float)fabs(a)) >> 20); }
 
+// The points are walked in their canonical order (the surface candidate index
+// I n + i: atom-major, the order of the points before they are grouped by
+// exponent class), so that the pivots and the ties of the selection, and with
+// them the blocks, do not depend on how the library stores the points.  pidx:
+// candidate index of each stored point; T: scratch of ncand ints.
 __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const double *__restrict__ A, int l,
-                                                          unsigned long long seed, int *__restrict__ U,
-                                                          int *__restrict__ U2, int *__restrict__ perm,
-                                                          int *__restrict__ status)
+                                                          unsigned long long seed, const int *__restrict__ pidx,
+                                                          long long ncand, int *__restrict__ T,
+                                                          int *__restrict__ U, int *__restrict__ U2,
+                                                          int *__restrict__ perm, int *__restrict__ status)
 {
     __shared__ unsigned int hist[RBJ_NBIN];
     __shared__ unsigned long long lkey[RBJ_LMAX];
-    __shared__ int lidx[RBJ_LMAX];
+    __shared__ int lidx[RBJ_LMAX];   // candidate index of each boundary-bin element
     __shared__ unsigned char lsel[RBJ_LMAX];
     __shared__ int sh_int[RBJ_NT / 32 + 1];
     __shared__ int s_nU, s_k, s_bin, s_need, s_nlist;
-    for (int i = threadIdx.x; i < M; i += RBJ_NT) U[i] = i;
-    if (threadIdx.x == 0) s_nU = M;
+    // U = the stored points in ascending candidate index: scatter into the
+    // candidate table, then compact it in order
+    for (long long t = threadIdx.x; t < ncand; t += RBJ_NT) T[t] = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < M; i += RBJ_NT) T[pidx[i]] = i;
+    __syncthreads();
+    {
+        int base = 0;
+        for (long long c0 = 0; c0 < ncand; c0 += RBJ_NT) {
+            const long long t = c0 + threadIdx.x;
+            const int v = t < ncand ? T[t] : -1;
+            int tot;
+            const int ex = rbj_block_scan(v >= 0 ? 1 : 0, sh_int, &tot);
+            if (v >= 0) U[base + ex] = v;
+            base += tot;
+        }
+        if (threadIdx.x == 0) {
+            s_nU = M;
+            if (base != M) *status = 2;
+        }
+    }
     __syncthreads();
     int out = 0;
     uint64_t draw = 0;
@@ -553,7 +657,7 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
                     const int p = atomicAdd(&s_nlist, 1);
                     if (p < RBJ_LMAX) {
                         lkey[p] = rbj_key64(row[j]);
-                        lidx[p] = j;
+                        lidx[p] = pidx[j];
                     }
                 }
             }
@@ -563,7 +667,8 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
                 if (threadIdx.x == 0) *status = 4;
                 return;
             }
-            // 4. exact rank in the boundary bin: larger key first, then lower index
+            // 4. exact rank in the boundary bin: larger key first, then lower
+            // candidate index
             const int need = s_need;
             for (int a = threadIdx.x; a < nl; a += RBJ_NT) {
                 const unsigned long long ka = lkey[a];
@@ -592,8 +697,9 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
                         if (bn > bstar) {
                             sel = 1;
                         } else if (bn == bstar) {
+                            const int cj = pidx[j];
                             for (int b = 0; b < nl; ++b)
-                                if (lidx[b] == j) {
+                                if (lidx[b] == cj) {
                                     sel = lsel[b];
                                     break;
                                 }
@@ -749,8 +855,10 @@ static int rbj_build(pcm_ctx *c, cudaStream_t s)
     PCM_TRY(c->rbj_U2.alloc(M));
     PCM_TRY(c->rbj_status.alloc(16));
     PCM_CUDA(cudaMemsetAsync(c->rbj_status.p, 0, 16 * sizeof(int), s));
-    rbj_perm_kernel<<<1, RBJ_NT, 0, s>>>(M, c->lda, c->A.p, l, c->opt.seed, c->rbj_U.p, c->rbj_U2.p, c->rbj_perm.p,
-                                         c->rbj_status.p);
+    const long long ncand = (long long)c->natom * c->npts_sphere;
+    PCM_TRY(c->rbj_T.alloc(ncand));
+    rbj_perm_kernel<<<1, RBJ_NT, 0, s>>>(M, c->lda, c->A.p, l, c->opt.seed, c->pindex.p, ncand, c->rbj_T.p,
+                                         c->rbj_U.p, c->rbj_U2.p, c->rbj_perm.p, c->rbj_status.p);
     PCM_LAUNCHED(c);
     PCM_TRY(c->rbj_inv.alloc((size_t)c->rbj_nblk * l * l));
     PCM_TRY(c->rbj_work.alloc((size_t)c->rbj_nblk * l * l));
@@ -783,13 +891,7 @@ int operator_build_async(pcm_ctx *c)
             c->side_rbj = true;
         }
         c->pc_ready = true;
-        if (c->opt.precision == PCM_MIXED) {
-            PCM_TRY(c->A32.alloc((size_t)c->M * c->lda));
-            const long long n = (long long)c->M * c->lda;
-            a_to_f32_kernel<<<4 * 152, 256, 0, c->side>>>(n, c->A.p, c->A32.p);
-            PCM_LAUNCHED(c);
-            c->a32_ready = true;
-        }
+        if (c->opt.precision == PCM_MIXED) PCM_TRY(a32_build(c, c->side));
     }
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[13], c->side));
     PCM_CUDA(cudaEventRecord(c->ev_side, c->side));
@@ -880,13 +982,7 @@ int solver_prepare(pcm_ctx *c)
 int solver_prepare_full(pcm_ctx *c)
 {
     PCM_TRY(solver_prepare(c));
-    if (c->opt.precision == PCM_MIXED && !c->a32_ready) {
-        PCM_TRY(c->A32.alloc((size_t)c->M * c->lda));
-        const long long n = (long long)c->M * c->lda;
-        a_to_f32_kernel<<<4 * 152, 256, 0, c->stream>>>(n, c->A.p, c->A32.p);
-        PCM_LAUNCHED(c);
-        c->a32_ready = true;
-    }
+    if (c->opt.precision == PCM_MIXED && !c->a32_ready) PCM_TRY(a32_build(c, c->stream));
     return PCM_OK;
 }
 
@@ -1048,11 +1144,7 @@ static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double
 static int true_residual(pcm_ctx *c, const double *b, const double *x, double *r, double *norm)
 {
     const int M = c->M;
-    const int gv = gemv_grid(c);
-    if (x) {
-        gemv_rp_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, x, c->vtmp.p, c->red.p);
-        PCM_LAUNCHED(c);
-    }
+    if (x) PCM_TRY(gemv_a(c, x, c->vtmp.p, c->red.p));
     const int nb = std::min(256, (M + 255) / 256);
     residual_kernel<<<nb, 256, 0, c->stream>>>(M, b, x ? c->vtmp.p : nullptr, r, c->red.p);
     PCM_LAUNCHED(c);
@@ -1100,13 +1192,7 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
         // it by ETA (or to delta / 2), and x accumulates the corrections
         constexpr double ETA = 1e-3;
         constexpr int MAX_REFINE = 12;
-        if (!c->a32_ready) {
-            PCM_TRY(c->A32.alloc((size_t)M * c->lda));
-            const long long n = (long long)M * c->lda;
-            a_to_f32_kernel<<<4 * 152, 256, 0, c->stream>>>(n, c->A.p, c->A32.p);
-            PCM_LAUNCHED(c);
-            c->a32_ready = true;
-        }
+        if (!c->a32_ready) PCM_TRY(a32_build(c, c->stream));
         PCM_TRY(c->vro.alloc(M));
         PCM_TRY(c->vd.alloc(M));
         if (!warm) PCM_CUDA(cudaMemsetAsync(dq, 0, M * sizeof(double), c->stream));
@@ -1176,8 +1262,7 @@ int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E)
     DBuf<double> &part2 = c->sd[1];
     const int nb = std::min(1024, (M + 255) / 256);
     PCM_TRY(part2.alloc(2 * nb));
-    gemv_rp_plain_kernel<<<gv, GV_NT, 0, c->stream>>>(M, c->lda, c->A.p, dq, c->vtmp.p, c->red.p);
-    PCM_LAUNCHED(c);
+    PCM_TRY(gemv_a(c, dq, c->vtmp.p, c->red.p));
     dot2_kernel<<<nb, 256, 0, c->stream>>>(M, c->Bz.p, dcv, dq, part2.p);
     PCM_LAUNCHED(c);
     std::vector<double> h1(gv), h2(2 * nb);

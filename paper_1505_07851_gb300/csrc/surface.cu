@@ -230,6 +230,151 @@ __global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, co
     }
 }
 
+// The same A for PCM_MIXED, evaluated in double-float arithmetic on the FP32
+// pipes (the FP64 pipe, 64 times slower on this GPU, bounds a_build_kernel):
+// with the points split as x = xh + xl (xh on a 2^-10 grid, so xh_k - xh_l is
+// exact), d = (xh_k - xh_l) + (xl_k - xl_l) as a hi + lo pair, R^2 = |d|^2 with
+// error-free products and sums, and 1/R from the FP32 reciprocal square root
+// refined by one Newton step in FP32 and one in double-float.  The off-diagonal
+// elements with zeta' R <= 6, where erf differs from 1 in FP64, and the
+// diagonal are evaluated in FP64 as in a_build_kernel.  1/R comes out to about
+// 3e-14 relative; the FP32 split of the coordinates limits the elements of the
+// nearest points to ~1e-10 relative.  Writes A (FP64, = hi + lo), A32 (hi) and
+// A32lo (lo), the matrices of the inner FP32 GEMV and of the double-float GEMV.
+__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void df_fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+__device__ __forceinline__ void df_rsqrt(float dxh, float dxl, float dyh, float dyl, float dzh, float dzl, float &ih,
+                                         float &il)
+{
+    // R^2 = sum_d (dh + dl)^2 = dh^2 + (2 dh dl + dl^2)
+    const float px = dxh * dxh, py = dyh * dyh, pz = dzh * dzh;
+    const float ex = fmaf(dxh, dxh, -px) + dxl * fmaf(2.f, dxh, dxl);
+    const float ey = fmaf(dyh, dyh, -py) + dyl * fmaf(2.f, dyh, dyl);
+    const float ez = fmaf(dzh, dzh, -pz) + dzl * fmaf(2.f, dzh, dzl);
+    float s1, t1, s2, t2;
+    df_two_sum(px, py, s1, t1);
+    df_two_sum(s1, pz, s2, t2);
+    float Sh, Sl;
+    df_fast_two_sum(s2, (t1 + t2) + ((ex + ey) + ez), Sh, Sl);
+    // FP32 Newton step on the hardware estimate, then one double-float step:
+    // r1 = r0 + r0 e / 2 with e = 1 - S r0^2 formed from the exact products
+    float r0 = rsqrtf(Sh);
+    r0 = fmaf(0.5f * r0, fmaf(-Sh * r0, r0, 1.f), r0);
+    const float th = Sh * r0;
+    const float tl = fmaf(Sh, r0, -th) + Sl * r0;
+    const float uh = th * r0;
+    const float ul = fmaf(th, r0, -uh) + tl * r0;
+    const float e = (1.f - uh) - ul;
+    df_fast_two_sum(r0, 0.5f * r0 * e, ih, il);
+}
+
+__global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, const float *__restrict__ pl,
+                                  const double *__restrict__ px, const double *__restrict__ py,
+                                  const double *__restrict__ pz, const double *__restrict__ pzeta,
+                                  const double *__restrict__ pS, const int *__restrict__ pcls, int ncls,
+                                  const double *__restrict__ cls_zeta, double *__restrict__ A,
+                                  float *__restrict__ A32, float *__restrict__ A32lo)
+{
+    __shared__ float zp_tab[16 * 16];
+    __shared__ double zp_tab64[16 * 16];
+    const bool tab = ncls <= 16;
+    if (tab)
+        for (int t = threadIdx.x; t < ncls * ncls; t += blockDim.x) {
+            const double a = cls_zeta[t / ncls], b = cls_zeta[t % ncls];
+            zp_tab64[t] = a * b / sqrt(a * a + b * b);
+            zp_tab[t] = (float)zp_tab64[t];
+        }
+    __syncthreads();
+    const int nt = (M + AT - 1) / AT;
+    long long t = blockIdx.x;
+    int bi = 0;
+    {
+        long long rem = t;
+        while (rem >= nt - bi) {
+            rem -= nt - bi;
+            ++bi;
+        }
+        t = rem;
+    }
+    const int bj = bi + (int)t;
+    __shared__ float2 tile[AT][AT + 1];
+    const int tx = threadIdx.x & (AT - 1);
+    const int ty = threadIdx.x / AT;  // 0 .. 7
+    const int l = bj * AT + tx;
+    float lxh = 0.f, lyh = 0.f, lzh = 0.f, lxl = 0.f, lyl = 0.f, lzl = 0.f;
+    double lzeta = 1.0;
+    int lcls = 0;
+    if (l < M) {
+        lxh = ph[l];
+        lyh = ph[(size_t)M + l];
+        lzh = ph[2 * (size_t)M + l];
+        lxl = pl[l];
+        lyl = pl[(size_t)M + l];
+        lzl = pl[2 * (size_t)M + l];
+        lzeta = pzeta[l];
+        lcls = pcls[l];
+    }
+    for (int r = ty; r < AT; r += 8) {
+        const int k = bi * AT + r;
+        float h = 0.f, lo = 0.f;
+        double v = 0.0;
+        if (k < M && l < M) {
+            if (k == l) {
+                v = pzeta[k] * 0.79788456080286535588 / pS[k];  // sqrt(2/pi)
+                h = (float)v;
+                lo = (float)(v - (double)h);
+            } else {
+                df_rsqrt(ph[k] - lxh, pl[k] - lxl, ph[(size_t)M + k] - lyh, pl[(size_t)M + k] - lyl,
+                         ph[2 * (size_t)M + k] - lzh, pl[2 * (size_t)M + k] - lzl, h, lo);
+                const float zp = tab ? zp_tab[pcls[k] * ncls + lcls]
+                                     : (float)(pzeta[k] * lzeta / sqrt(pzeta[k] * pzeta[k] + lzeta * lzeta));
+                // zeta' R in FP32 decides the branch with a margin: erf(6) rounds
+                // to 1 in FP64, and FP32 moves the threshold by ~1e-6
+                if (zp / h <= 6.001f) {
+                    const double dx = px[k] - px[l], dy = py[k] - py[l], dz = pz[k] - pz[l];
+                    const double d2 = dx * dx + dy * dy + dz * dz;
+                    const double inv = rsqrt(d2);
+                    const double zk = pzeta[k];
+                    const double zp64 = tab ? zp_tab64[pcls[k] * ncls + lcls]
+                                            : zk * lzeta / sqrt(zk * zk + lzeta * lzeta);
+                    const double a = zp64 * (d2 * inv);
+                    const double e = (a > 6.0) ? inv : erf(a) * inv;
+                    h = (float)e;
+                    lo = (float)(e - (double)h);
+                }
+                v = (double)h + (double)lo;
+            }
+            A[(size_t)k * lda + l] = v;
+            A32[(size_t)k * lda + l] = h;
+            A32lo[(size_t)k * lda + l] = lo;
+        }
+        tile[r][tx] = make_float2(h, lo);
+    }
+    if (bi == bj) return;
+    __syncthreads();
+    for (int r = ty; r < AT; r += 8) {
+        const int k = bj * AT + r;
+        const int ll = bi * AT + tx;
+        if (k < M && ll < M) {
+            const float2 e = tile[tx][r];
+            A[(size_t)k * lda + ll] = (double)e.x + (double)e.y;
+            A32[(size_t)k * lda + ll] = e.x;
+            A32lo[(size_t)k * lda + ll] = e.y;
+        }
+    }
+}
+
 __global__ void dinv_kernel(int M, int lda, const double *__restrict__ A, double *__restrict__ dinv)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,7 +491,8 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     return PCM_OK;
 }
 
-// Stored A in FP64 (Eq. 2, Eq. 3, Eq. 8) and 1/A_kk on stream s.
+// Stored A (Eq. 2, Eq. 3, Eq. 8) and 1/A_kk on stream s: FP64, or for
+// PCM_MIXED double-float with its FP32 hi and lo parts (A32, A32lo)
 int a_build(pcm_ctx *c, cudaStream_t s)
 {
     const int M = c->M;
@@ -355,8 +501,17 @@ int a_build(pcm_ctx *c, cudaStream_t s)
     {
         const long long nt = (M + AT - 1) / AT;
         const long long ntiles = nt * (nt + 1) / 2;
-        a_build_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p, c->pS.p,
-                                                       c->pcls.p, c->ncls, c->cls_zeta.p, c->A.p);
+        if (c->opt.precision == PCM_MIXED) {
+            PCM_TRY(c->A32.alloc((size_t)M * c->lda));
+            PCM_TRY(c->A32lo.alloc((size_t)M * c->lda));
+            a_build_df_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->p32.p, c->p32lo.p, c->px.p, c->py.p,
+                                                              c->pz.p, c->pzeta.p, c->pS.p, c->pcls.p, c->ncls,
+                                                              c->cls_zeta.p, c->A.p, c->A32.p, c->A32lo.p);
+            c->a32_ready = true;
+        } else {
+            a_build_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
+                                                           c->pS.p, c->pcls.p, c->ncls, c->cls_zeta.p, c->A.p);
+        }
         PCM_LAUNCHED(c);
     }
     PCM_TRY(c->dinv.alloc(M));

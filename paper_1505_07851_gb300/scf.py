@@ -27,11 +27,12 @@ def two_delta(prev_diis_error, delta_tight, s=1e4, switch=1e-3):
     return delta_tight
 
 
-def run_sequence(ctx, seq, scheme, delta_tight=1e-6, s=1e4, switch=1e-3, warm=True):
+def run_sequence(ctx, seq, scheme, delta_tight=1e-6, s=1e4, switch=1e-3, warm=True, keep_q=False):
     """Solve Eq. 1 along an SCF history on a Context whose surface and basis
     are set.  seq: [(P_n, e_n), ...] (NumPy arrays or CUDA tensors).
     Returns one record per iteration: the threshold used, the CG steps,
-    convergence, the energy of Eq. 13 and (with timing) the solve time."""
+    convergence, the energy of Eq. 13 and (with timing) the solve time;
+    with keep_q also a copy of the charges ("q", library point order)."""
     if scheme not in SCHEMES:
         raise ValueError("scheme must be one of %s" % (SCHEMES,))
     out = []
@@ -51,5 +52,7 @@ def run_sequence(ctx, seq, scheme, delta_tight=1e-6, s=1e4, switch=1e-3, warm=Tr
         out.append({"iteration": n, "diis_error": e, "delta": st["delta"], "cg_steps": st["iterations"],
                     "converged": bool(st["converged"]), "energy": E, "solve_ms": st["ms_solve"],
                     "refinements": st["refinements"]})
+        if keep_q:
+            out[-1]["q"] = q.clone() if hasattr(q, "clone") else q.copy()
         prev = e
     return out

@@ -2,7 +2,15 @@
 run with the oracle's PCG: per iteration the threshold, the CG steps (+-1:
 rounding changes the last step) and the energy; and the shape of the
 paper's comparison (the dynamic and 2-delta schemes need fewer CG steps in
-total than the fixed threshold, and the dynamic one spreads them evenly)."""
+total than the fixed threshold, and the dynamic one spreads them evenly).
+
+With warm starts each oracle solve starts from the library's previous
+charges: a solve stopped at ||r|| < delta leaves an iterate whose error is
+of the order of delta, the next solve reduces its residual by a similar
+factor, so a one-step difference in one solve changes the next solve's
+trajectory at its stopping point (the oracle's own sequence moves by a
+step under 1e-12 relative perturbations of c).  Compared from the same
+starting charges, each solve differs by rounding alone."""
 import numpy as np
 import pytest
 
@@ -14,7 +22,9 @@ pytestmark = pytest.mark.gpu
 DELTA_TIGHT = 1e-6
 
 
-def _oracle_sequence(w, seq, scheme, precond):
+def _oracle_sequence(w, seq, scheme, precond, starts=None):
+    """The sequence with the oracle's PCG; starts[n] (oracle point order) is
+    the initial guess of solve n, else the oracle's own previous charges."""
     s = oracle.surface(w.mol.xyz, w.mol.radius)
     eb = oracle.ExpandedBasis(w.basis, w.mol.xyz)
     f = oracle.f_factor()
@@ -22,7 +32,9 @@ def _oracle_sequence(w, seq, scheme, precond):
     Bz = oracle.bz(s, w.mol.xyz, w.mol.Z)
     pc = oracle.Preconditioner(A, precond, 100, 0)
     prev, x, out = None, None, []
-    for P, e in seq:
+    for n, (P, e) in enumerate(seq):
+        if starts is not None:
+            x = starts[n]
         c = oracle.esp(eb, P, s["r"], s["zeta"])
         if scheme == "fixed":
             delta = DELTA_TIGHT
@@ -48,10 +60,18 @@ def runs():
         M, _ = ctx.setup(w.mol, w.basis)
         _, idx = ctx.get_surface()
         for scheme in ("fixed", "2delta", "dynamic"):
-            res[scheme] = run_sequence(ctx, seq, scheme, delta_tight=DELTA_TIGHT)
+            res[scheme] = run_sequence(ctx, seq, scheme, delta_tight=DELTA_TIGHT, keep_q=True)
+    s = oracle.surface(w.mol.xyz, w.mol.radius)
+    pos = {int(k): i for i, k in enumerate(s["index"])}
+    perm = np.array([pos[int(k)] for k in idx])      # library point i -> oracle point perm[i]
     orc = {}
     for scheme in ("fixed", "2delta", "dynamic"):
-        s, orc[scheme] = _oracle_sequence(w, seq, scheme, "rbj")
+        starts = [None]
+        for r in res[scheme][:-1]:
+            q = np.empty(M)
+            q[perm] = r["q"]
+            starts.append(q)
+        _, orc[scheme] = _oracle_sequence(w, seq, scheme, "rbj", starts)
     return M, res, orc
 
 
