@@ -891,7 +891,7 @@ int operator_build_async(pcm_ctx *c)
             c->side_rbj = true;
         }
         c->pc_ready = true;
-        if (c->opt.precision == PCM_MIXED) PCM_TRY(a32_build(c, c->side));
+        if (c->opt.precision == PCM_MIXED && !c->a32_ready) PCM_TRY(a32_build(c, c->side));
     }
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[13], c->side));
     PCM_CUDA(cudaEventRecord(c->ev_side, c->side));

@@ -156,6 +156,21 @@ __global__ void bz_kernel(int M, int natom, const double *__restrict__ px, const
     if (active) Bz[k] = s;
 }
 
+// Tile (bi, bj), bi <= bj, of linear block t in the row-major upper triangle
+// of nt x nt tiles: row b starts at b nt - b (b - 1) / 2.  The row comes from
+// the quadratic's root and is then corrected to the exact integer answer.
+__device__ __forceinline__ void upper_tile(long long t, int nt, int &bi, int &bj)
+{
+    auto start = [nt](long long b) { return b * nt - b * (b - 1) / 2; };
+    const double q = 2.0 * nt + 1.0;
+    long long b = (long long)((q - sqrt(fmax(q * q - 8.0 * (double)t, 0.0))) * 0.5);
+    b = b < 0 ? 0 : (b > nt - 1 ? nt - 1 : b);
+    while (b > 0 && start(b) > t) --b;
+    while (b + 1 < nt && start(b + 1) <= t) ++b;
+    bi = (int)b;
+    bj = bi + (int)(t - start(b));
+}
+
 // Stored A in FP64 (Eq. 2, Eq. 3 read as zeta_k sqrt(2/pi) / S_k, Eq. 8).
 // Tiles (bi, bj) with bi <= bj are computed once and written to both halves.
 constexpr int AT = 32;
@@ -173,20 +188,9 @@ __global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, co
             zp_tab[t] = a * b / sqrt(a * a + b * b);
         }
     __syncthreads();
-    // map the linear block id onto the upper triangle of tiles
     const int nt = (M + AT - 1) / AT;
-    long long t = blockIdx.x;
-    int bi = 0;
-    {
-        // row bi holds nt - bi tiles
-        long long rem = t;
-        while (rem >= nt - bi) {
-            rem -= nt - bi;
-            ++bi;
-        }
-        t = rem;
-    }
-    const int bj = bi + (int)t;
+    int bi, bj;
+    upper_tile(blockIdx.x, nt, bi, bj);
     __shared__ double tile[AT][AT + 1];
     const int tx = threadIdx.x & (AT - 1);
     const int ty = threadIdx.x / AT;  // 0 .. 7
@@ -297,17 +301,8 @@ __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, 
         }
     __syncthreads();
     const int nt = (M + AT - 1) / AT;
-    long long t = blockIdx.x;
-    int bi = 0;
-    {
-        long long rem = t;
-        while (rem >= nt - bi) {
-            rem -= nt - bi;
-            ++bi;
-        }
-        t = rem;
-    }
-    const int bj = bi + (int)t;
+    int bi, bj;
+    upper_tile(blockIdx.x, nt, bi, bj);
     __shared__ float2 tile[AT][AT + 1];
     const int tx = threadIdx.x & (AT - 1);
     const int ty = threadIdx.x / AT;  // 0 .. 7
