@@ -94,7 +94,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/); a kernel missing here reports traffic null.
-NCU_TRAFFIC_BYTES = {"esp_kernel_f32<L=1> (ps)": 35.899648e6 + 15.616e3}  # scalar kernel (--scalar-fp32)
+NCU_TRAFFIC_BYTES = {"esp_kernel_f32<L=1> (ps)": 35.899648e6 + 15.616e3,      # scalar (--scalar-fp32)
+                     "esp_kernel_f32x2<L=1> (ps)": 27.160320e6 + 26.624e3,
+                     "fock_kernel_f32x2<L=1> (ps)": 6.007552e6 + 0.0}
 
 CLASS_L = [0, 1, 2, 2, 3, 4]
 CLASS_NAME = ["ss", "ps", "pp", "ds", "dp", "dd"]

@@ -374,33 +374,66 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32x2(int nesp, int jbeg, 
         nzl[q] = f2(-pl[2 * (size_t)M + k]);
         a32[q] = k32[q] = f2(0.f);
     }
+    // The next tile's pair data are read into registers while the current
+    // tile is computed: thread jj < MESP_TP holds pair jj's ten values, every
+    // thread NDPT of the tile's NH x MESP_TP coefficients.  Pair jj goes to
+    // slot jj / 2, lane jj % 2; an odd tile's last slot gets a dummy pair
+    // (rho = 1, D = 0) that contributes zero.
+    constexpr int NDPT = (NH * MESP_TP + MESP_NT - 1) / MESP_NT;
+    float pv[10], pd[NDPT];
+    auto fetch = [&](int jt) {
+        const int nt = min(MESP_TP, j1 - jt);
+        if (threadIdx.x < MESP_TP) {
+            const int jj = threadIdx.x;
+            const bool v = jj < nt;
+            const size_t j = jt + jj;
+            pv[0] = v ? eX[j] : 0.f;
+            pv[1] = v ? eX[(size_t)nesp + j] : 0.f;
+            pv[2] = v ? eX[2 * (size_t)nesp + j] : 0.f;
+            pv[3] = v ? C[j] : 1.f;
+            pv[4] = v ? eX[3 * (size_t)nesp + j] : 0.f;
+            pv[5] = v ? eX[4 * (size_t)nesp + j] : 0.f;
+            pv[6] = v ? eX[5 * (size_t)nesp + j] : 0.f;
+            pv[7] = v ? C[(size_t)nesp + j] : 0.f;
+            pv[8] = v ? C[2 * (size_t)nesp + j] : 0.f;
+            pv[9] = v ? C[(size_t)(3 + NH) * nesp + j] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < NDPT; ++i) {
+            const int t = threadIdx.x + i * MESP_NT;
+            const int h = t / MESP_TP, jj = t % MESP_TP;
+            pd[i] = (t < NH * MESP_TP && jj < nt) ? C[(size_t)(3 + h) * nesp + jt + jj] : 0.f;
+        }
+    };
+    fetch(j0);
     for (int jt = j0; jt < j1; jt += MESP_TP) {
         const int nt = min(MESP_TP, j1 - jt);
         __syncthreads();
-        // pair jj goes to slot jj / 2, lane jj % 2; an odd tile's last slot
-        // gets a dummy pair (rho = 1, D = 0) that contributes zero
-        for (int jj = threadIdx.x; jj < MESP_TP; jj += MESP_NT) {
-            const bool v = jj < nt;
-            const size_t j = jt + jj;
-            const int s = jj >> 1, l = jj & 1;
+        if (threadIdx.x < MESP_TP) {
+            const int jj = threadIdx.x, s = jj >> 1, l = jj & 1;
             float *xy = reinterpret_cast<float *>(&sXY[s]), *zr = reinterpret_cast<float *>(&sZR[s]);
             float *xyl = reinterpret_cast<float *>(&sXYl[s]);
-            xy[l] = v ? eX[j] : 0.f;
-            xy[2 + l] = v ? eX[(size_t)nesp + j] : 0.f;
-            zr[l] = v ? eX[2 * (size_t)nesp + j] : 0.f;
-            zr[2 + l] = v ? C[j] : 1.f;
-            xyl[l] = v ? eX[3 * (size_t)nesp + j] : 0.f;
-            xyl[2 + l] = v ? eX[4 * (size_t)nesp + j] : 0.f;
-            reinterpret_cast<float *>(&sZl[s])[l] = v ? eX[5 * (size_t)nesp + j] : 0.f;
-            reinterpret_cast<float *>(&sRl[s])[l] = v ? C[(size_t)nesp + j] : 0.f;
-            reinterpret_cast<float *>(&sDr[s])[l] = v ? C[2 * (size_t)nesp + j] : 0.f;
-            reinterpret_cast<float *>(&sD0l[s])[l] = v ? C[(size_t)(3 + NH) * nesp + j] : 0.f;
+            xy[l] = pv[0];
+            xy[2 + l] = pv[1];
+            zr[l] = pv[2];
+            zr[2 + l] = pv[3];
+            xyl[l] = pv[4];
+            xyl[2 + l] = pv[5];
+            reinterpret_cast<float *>(&sZl[s])[l] = pv[6];
+            reinterpret_cast<float *>(&sRl[s])[l] = pv[7];
+            reinterpret_cast<float *>(&sDr[s])[l] = pv[8];
+            reinterpret_cast<float *>(&sD0l[s])[l] = pv[9];
         }
-        for (int t = threadIdx.x; t < NH * MESP_TP; t += MESP_NT) {
-            const int h = t / MESP_TP, jj = t % MESP_TP;
-            reinterpret_cast<float *>(&sD[h][jj >> 1])[jj & 1] = jj < nt ? C[(size_t)(3 + h) * nesp + jt + jj] : 0.f;
+#pragma unroll
+        for (int i = 0; i < NDPT; ++i) {
+            const int t = threadIdx.x + i * MESP_NT;
+            if (t < NH * MESP_TP) {
+                const int h = t / MESP_TP, jj = t % MESP_TP;
+                reinterpret_cast<float *>(&sD[h][jj >> 1])[jj & 1] = pd[i];
+            }
         }
         __syncthreads();
+        if (jt + MESP_TP < j1) fetch(jt + MESP_TP);
         const int np = (nt + 1) >> 1;
         for (int s = 0; s < np; ++s) {
             const float4 xy = sXY[s], zr = sZR[s], xyl = sXYl[s];

@@ -62,8 +62,21 @@ __device__ __forceinline__ double block_sum_warps(double v /* lane-0 values */)
 __device__ __forceinline__ double sum_partials(const double *part, int n)
 {
     __shared__ double sh[32];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += ((volatile const double *)part)[i];
+    // four loads in flight per thread before their additions (each load is
+    // an L2 round trip; a single running sum would wait for each in turn)
+    const volatile double *v = part;
+    const int st = blockDim.x;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = threadIdx.x;
+    for (; j + 3 * st < n; j += 4 * st) {
+        const double a = v[j], b = v[j + st], c = v[j + 2 * st], d = v[j + 3 * st];
+        s0 += a;
+        s1 += b;
+        s2 += c;
+        s3 += d;
+    }
+    for (; j < n; j += st) s0 += v[j];
+    double s = (s0 + s1) + (s2 + s3);
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();

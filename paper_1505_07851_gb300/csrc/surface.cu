@@ -259,7 +259,7 @@ __device__ __forceinline__ void df_fast_two_sum(float a, float b, float &s, floa
 }
 
 __device__ __forceinline__ void df_rsqrt(float dxh, float dxl, float dyh, float dyl, float dzh, float dzl, float &ih,
-                                         float &il)
+                                         float &il, float &r2)
 {
     // R^2 = sum_d (dh + dl)^2 = dh^2 + (2 dh dl + dl^2)
     const float px = dxh * dxh, py = dyh * dyh, pz = dzh * dzh;
@@ -281,6 +281,7 @@ __device__ __forceinline__ void df_rsqrt(float dxh, float dxl, float dyh, float 
     const float ul = fmaf(th, r0, -uh) + tl * r0;
     const float e = (1.f - uh) - ul;
     df_fast_two_sum(r0, 0.5f * r0 * e, ih, il);
+    r2 = Sh;
 }
 
 __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, const float *__restrict__ pl,
@@ -304,6 +305,7 @@ __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, 
     int bi, bj;
     upper_tile(blockIdx.x, nt, bi, bj);
     __shared__ float2 tile[AT][AT + 1];
+    __shared__ double tile64[AT][AT + 1];
     const int tx = threadIdx.x & (AT - 1);
     const int ty = threadIdx.x / AT;  // 0 .. 7
     const int l = bj * AT + tx;
@@ -330,13 +332,14 @@ __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, 
                 h = (float)v;
                 lo = (float)(v - (double)h);
             } else {
+                float r2;
                 df_rsqrt(ph[k] - lxh, pl[k] - lxl, ph[(size_t)M + k] - lyh, pl[(size_t)M + k] - lyl,
-                         ph[2 * (size_t)M + k] - lzh, pl[2 * (size_t)M + k] - lzl, h, lo);
+                         ph[2 * (size_t)M + k] - lzh, pl[2 * (size_t)M + k] - lzl, h, lo, r2);
                 const float zp = tab ? zp_tab[pcls[k] * ncls + lcls]
                                      : (float)(pzeta[k] * lzeta / sqrt(pzeta[k] * pzeta[k] + lzeta * lzeta));
                 // zeta' R in FP32 decides the branch with a margin: erf(6) rounds
                 // to 1 in FP64, and FP32 moves the threshold by ~1e-6
-                if (zp / h <= 6.001f) {
+                if (zp * (r2 * h) <= 6.001f) {  // zeta' R, R = R^2 / R
                     const double dx = px[k] - px[l], dy = py[k] - py[l], dz = pz[k] - pz[l];
                     const double d2 = dx * dx + dy * dy + dz * dz;
                     const double inv = rsqrt(d2);
@@ -355,6 +358,7 @@ __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, 
             A32lo[(size_t)k * lda + l] = lo;
         }
         tile[r][tx] = make_float2(h, lo);
+        tile64[r][tx] = v;
     }
     if (bi == bj) return;
     __syncthreads();
@@ -363,7 +367,7 @@ __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, 
         const int ll = bi * AT + tx;
         if (k < M && ll < M) {
             const float2 e = tile[tx][r];
-            A[(size_t)k * lda + ll] = (double)e.x + (double)e.y;
+            A[(size_t)k * lda + ll] = tile64[tx][r];
             A32[(size_t)k * lda + ll] = e.x;
             A32lo[(size_t)k * lda + ll] = e.y;
         }

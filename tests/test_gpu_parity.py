@@ -133,6 +133,32 @@ def test_rbj_iterations_match_oracle(l, seed):
     assert np.linalg.norm(g["q"] - x[p]) <= 1e-6
 
 
+@pytest.mark.parametrize("l,seed", [(40, 3), (100, 7)])
+def test_rbj_residual_history_matches_oracle(l, seed):
+    """The RBJ blocks are the oracle's (pivots and ties follow the atom-major
+    point order, not the library's storage order), so the first CG steps
+    reproduce the oracle's residual norms to rounding: ||r_k|| after k = 1..6
+    steps, cold start, on a cluster of several elements (several exponent
+    classes, so storage and atom-major orders differ)."""
+    pcm = _pcm()
+    w = workloads.small_cluster(10, seed=31)
+    s = oracle.surface(w.mol.xyz, w.mol.radius)
+    A = oracle.a_matrix(s)
+    eb = oracle.ExpandedBasis(w.basis, w.mol.xyz)
+    c = oracle.esp(eb, w.P, s["r"], s["zeta"])
+    b = -oracle.f_factor() * (oracle.bz(s, w.mol.xyz, w.mol.Z) + c)
+    pc = oracle.Preconditioner(A, "rbj", l, seed)
+    assert len(set(s["zeta"].round(12))) > 1
+    for k in range(1, 7):
+        with pcm.Context(schwarz=0.0, precond="rbj", rbj_block=l, seed=seed, max_iter=k) as ctx:
+            ctx.setup(w.mol, w.basis)
+            ctx.esp(w.P)
+            q, st = ctx.solve(delta=1e-30)
+        _, it, ok, rn = oracle.pcg(A, b, 1e-30, pc, max_iter=k)
+        assert st["iterations"] == it == k
+        assert abs(st["rnorm"] - rn) <= 1e-8 * rn, (k, st["rnorm"], rn)
+
+
 def test_rbj_full_block_one_step():
     w = workloads.config(0)
     g = _run_gpu(w, delta=1e-8, precond="rbj", rbj_block=10 ** 6)
