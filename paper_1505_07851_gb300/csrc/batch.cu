@@ -41,6 +41,7 @@ struct BatchDev {
     // per molecule
     const double **A64;
     const float **A32;
+    const float **A32lo;   // PCM_MIXED: A - A32, for the double-float true residual
     const int **perm;
     const double **inv;
     const double **dinv;   // Jacobi (l == 1) when perm is null
@@ -67,12 +68,12 @@ struct pcm_batch {
     pcm::BatchDev dev{};
     // device tables
     pcm::DBuf<const double *> dA64, dinvp, ddinv;
-    pcm::DBuf<const float *> dA32;
+    pcm::DBuf<const float *> dA32, dA32lo;
     pcm::DBuf<const int *> dperm;
     pcm::DBuf<int> dlda, dM, doff, dl, dnblk, gb_mol, gb_rp, gb_start, rb_mol, rb_blk, rb_start, elem_mol;
     // vectors (Mtot) and per-molecule scalars
     pcm::DBuf<double> x, b, r, z, p, Ap, d, ro, y;
-    pcm::DBuf<float> p32;
+    pcm::DBuf<float> p32, xh32, xl32;  // FP32 copy of p; hi and lo parts of x for the residual
     pcm::DBuf<double> rz, pAp, alpha, beta, rr, tol, rnorm, gpart, rpart;
     pcm::DBuf<int> idone, iters, conv, maxit, gcount;
     // the inner loop as a graph
@@ -108,6 +109,34 @@ __global__ void __launch_bounds__(BG_NT) bgemv_kernel(BatchDev B, const TA *__re
     else A = B.A64[m];
     const double s = gemv_rowpair<TA>(B.gb_rp[blockIdx.x], B.M[m], B.lda[m], A, x + o, x64 + o, y + o);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// The same in double-float on the FP32 pipes (PCM_MIXED true residuals):
+// A = A32 + A32lo, x = xh + xl, as gemv_rowpair_df
+__global__ void __launch_bounds__(BG_NT) bgemv_df_kernel(BatchDev B, const float *__restrict__ xh,
+                                                         const float *__restrict__ xl, const double *__restrict__ x64,
+                                                         double *__restrict__ y, const int *__restrict__ idone,
+                                                         double *__restrict__ part)
+{
+    const int m = B.gb_mol[blockIdx.x];
+    if (idone[m]) {
+        if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
+        return;
+    }
+    const int o = B.off[m];
+    const double s = gemv_rowpair_df(B.gb_rp[blockIdx.x], B.M[m], B.lda[m], B.A32[m], B.A32lo[m], xh + o, xl + o,
+                                     x64 + o, y + o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// x -> FP32 hi and lo parts
+__global__ void bsplit_kernel(int n, const double *__restrict__ x, float *__restrict__ xh, float *__restrict__ xl)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const float h = (float)x[k];
+        xh[k] = h;
+        xl[k] = (float)(x[k] - (double)h);
+    }
 }
 
 // alpha_m = rz_m / (p.Ap)_m from the GEMV partials of molecule m (one warp per molecule)
@@ -324,7 +353,7 @@ static int batch_layout(pcm_batch *bt)
     if (bt->layout_ok) return PCM_OK;
     const int n = bt->nmol;
     std::vector<const double *> A64(n), inv(n), dinv(n);
-    std::vector<const float *> A32(n);
+    std::vector<const float *> A32(n), A32lo(n);
     std::vector<const int *> perm(n);
     std::vector<int> lda(n), M(n), off(n + 1), l(n), nblk(n), gbm, gbr, gbs(n + 1), rbm, rbb, rbs(n + 1);
     int o = 0;
@@ -333,6 +362,7 @@ static int batch_layout(pcm_batch *bt)
         pcm_ctx *c = bt->mol[m];
         A64[m] = c->A.p;
         A32[m] = c->A32.p;
+        A32lo[m] = c->A32lo.p;
         lda[m] = c->lda;
         M[m] = c->M;
         off[m] = o;
@@ -378,6 +408,7 @@ static int batch_layout(pcm_batch *bt)
     };
     PCM_TRY(up(bt->dA64, A64));
     PCM_TRY(up(bt->dA32, A32));
+    PCM_TRY(up(bt->dA32lo, A32lo));
     PCM_TRY(up(bt->dperm, perm));
     PCM_TRY(up(bt->dinvp, inv));
     PCM_TRY(up(bt->ddinv, dinv));
@@ -397,6 +428,7 @@ static int batch_layout(pcm_batch *bt)
     BatchDev &D = bt->dev;
     D.A64 = bt->dA64.p;
     D.A32 = bt->dA32.p;
+    D.A32lo = bt->dA32lo.p;
     D.perm = bt->dperm.p;
     D.inv = bt->dinvp.p;
     D.dinv = bt->ddinv.p;
@@ -417,8 +449,10 @@ static int batch_layout(pcm_batch *bt)
         PCM_TRY(v->alloc(Mt));
         PCM_CUDA(cudaMemsetAsync(v->p, 0, Mt * sizeof(double), bt->stream));
     }
-    PCM_TRY(bt->p32.alloc(Mt));
-    PCM_CUDA(cudaMemsetAsync(bt->p32.p, 0, Mt * sizeof(float), bt->stream));
+    for (DBuf<float> *v : {&bt->p32, &bt->xh32, &bt->xl32}) {
+        PCM_TRY(v->alloc(Mt));
+        PCM_CUDA(cudaMemsetAsync(v->p, 0, Mt * sizeof(float), bt->stream));
+    }
     for (DBuf<double> *v : {&bt->rz, &bt->pAp, &bt->alpha, &bt->beta, &bt->rr, &bt->tol, &bt->rnorm})
         PCM_TRY(v->alloc(n));
     for (DBuf<int> *v : {&bt->idone, &bt->iters, &bt->conv, &bt->maxit}) PCM_TRY(v->alloc(n));
@@ -535,8 +569,16 @@ static int batch_solve(pcm_batch *bt, double delta)
     for (int round = 0; round <= max_round; ++round) {
         // true residual of every molecule not yet done
         PCM_CUDA(cudaMemcpyAsync(bt->idone.p, done.data(), n * sizeof(int), cudaMemcpyHostToDevice, bt->stream));
-        bgemv_kernel<double><<<bt->ngb, BG_NT, 0, bt->stream>>>(D, bt->x.p, bt->x.p, bt->y.p, bt->idone.p,
-                                                                bt->gpart.p);
+        if (mixed) {
+            // double-float A x: the FP64 pipe would bound an FP64 GEMV below the HBM rate
+            const int sb = std::min(4096, (bt->Mtot + 255) / 256);
+            bsplit_kernel<<<sb, 256, 0, bt->stream>>>(bt->Mtot, bt->x.p, bt->xh32.p, bt->xl32.p);
+            bgemv_df_kernel<<<bt->ngb, BG_NT, 0, bt->stream>>>(D, bt->xh32.p, bt->xl32.p, bt->x.p, bt->y.p,
+                                                               bt->idone.p, bt->gpart.p);
+        } else {
+            bgemv_kernel<double><<<bt->ngb, BG_NT, 0, bt->stream>>>(D, bt->x.p, bt->x.p, bt->y.p, bt->idone.p,
+                                                                    bt->gpart.p);
+        }
         bresid_kernel<<<n, 1024, 0, bt->stream>>>(D, bt->b.p, bt->y.p, bt->ro.p, bt->rnorm.p);
         PCM_CUDA(cudaGetLastError());
         PCM_CUDA(cudaMemcpyAsync(rn.data(), bt->rnorm.p, n * sizeof(double), cudaMemcpyDeviceToHost, bt->stream));
