@@ -5,14 +5,19 @@
 // Error control.  FP32 rounding that is the same for every surface point
 // (a per-pair constant) would bias c_k for all k alike and add up in the
 // energy (dE = q^T dc); rounding that varies from point to point averages
-// out.  So every per-pair or per-(pair, class) constant is carried as an
-// FP32 hi + lo pair computed in FP64: the Hermite density D_tuv times U, rho
-// (T = rho_hi R^2 + rho_lo R^2, and (-2 rho)^n corrected to first order in
-// rho_lo / rho_hi), and sqrt(pi)/2 in the far-field Boys branch.  Coordinates
-// are split as hi (on a 2^-10 grid, so hi differences are exact) + lo, so
-// every distance is the FP32 rounding of the exact one.  Sums run in FP32
-// within a tile of 32 pairs (ESP, Kahan-compensated) or 128 points (Fock)
-// and in FP64 across tiles.
+// out, and so does a per-pair rounding whose sign varies from pair to pair.
+// So the per-pair or per-(pair, class) constants that repeat over many pairs
+// or dominate the sums are carried as FP32 hi + lo pairs computed in FP64:
+// rho (T = rho_hi R^2 + rho_lo R^2, and (-2 rho)^n corrected to first order
+// in rho_lo / rho_hi; rho depends only on p and the point class, so it
+// repeats over every pair of the same exponents), the Hermite density
+// U D_tuv (all components in the scalar and same-atom kernels, U D_000 in the
+// packed cross-atom kernel), and sqrt(pi)/2 in the far-field Boys branch.
+// Coordinates are split as hi (on a 2^-10 grid, so hi differences are exact)
+// + lo, so every distance is the FP32 rounding of the exact one.  ESP sums
+// are Kahan-compensated per interaction in FP32 over a pair segment and
+// added in FP64; Fock sums run in FP32 within a tile of 128 points (64 per
+// lane when packed) and in FP64 across tiles.
 #include <math.h>
 
 #include <algorithm>

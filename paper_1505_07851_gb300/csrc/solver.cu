@@ -1198,7 +1198,12 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
     int iters = 0, conv = 0, refinements = 0;
     double rnorm = 0.0;
     if (c->opt.precision != PCM_MIXED) {
-        PCM_TRY(pcg_core(c, drhs, dq, warm, delta, c->opt.max_iter, false, &iters, &conv, &rnorm));
+        // the iterate lives in a context buffer, so that the solver graph
+        // (which holds its address) is reused whatever output the caller passes
+        PCM_TRY(c->vd.alloc(M));
+        if (warm) PCM_CUDA(cudaMemcpyAsync(c->vd.p, dq, M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        PCM_TRY(pcg_core(c, drhs, c->vd.p, warm, delta, c->opt.max_iter, false, &iters, &conv, &rnorm));
+        PCM_CUDA(cudaMemcpyAsync(dq, c->vd.p, M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     } else {
         // FP64 iterative refinement around FP32-GEMV inner solves: the true
         // residual b - A x is formed with the FP64 A, each inner solve reduces
