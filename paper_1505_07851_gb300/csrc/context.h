@@ -123,6 +123,8 @@ struct pcm_ctx {
     std::vector<double> h_cls_zeta;        // exponent of each class (ascending)
     std::vector<int> h_cls_off;            // ncls + 1 offsets into the point list
     pcm::DBuf<double> cls_zeta;            // ncls
+    std::vector<double> h_zp_cls;          // ncls x ncls: zeta' of Eq. 8 for each pair of classes
+    pcm::DBuf<double> zp_cls;
     pcm::DBuf<int> cls_off;                // ncls + 1
     pcm::DBuf<double> px, py, pz, pzeta, pS, Bz;
     pcm::DBuf<int> pindex, pcls;

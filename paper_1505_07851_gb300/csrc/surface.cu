@@ -177,16 +177,14 @@ constexpr int AT = 32;
 __global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, const double *__restrict__ py,
                                const double *__restrict__ pz, const double *__restrict__ pzeta,
                                const double *__restrict__ pS, const int *__restrict__ pcls, int ncls,
-                               const double *__restrict__ cls_zeta, double *__restrict__ A)
+                               const double *__restrict__ zp_cls, double *__restrict__ A)
 {
-    // zeta'_kl of Eq. 8 depends only on the two exponent classes
+    // zeta'_kl of Eq. 8 depends only on the two exponent classes: zp_cls holds
+    // it for every class pair (up to 16 classes; more are computed per element)
     __shared__ double zp_tab[16 * 16];
     const bool tab = ncls <= 16;
     if (tab)
-        for (int t = threadIdx.x; t < ncls * ncls; t += blockDim.x) {
-            const double a = cls_zeta[t / ncls], b = cls_zeta[t % ncls];
-            zp_tab[t] = a * b / sqrt(a * a + b * b);
-        }
+        for (int t = threadIdx.x; t < ncls * ncls; t += blockDim.x) zp_tab[t] = zp_cls[t];
     __syncthreads();
     const int nt = (M + AT - 1) / AT;
     int bi, bj;
@@ -288,7 +286,7 @@ __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, 
                                   const double *__restrict__ px, const double *__restrict__ py,
                                   const double *__restrict__ pz, const double *__restrict__ pzeta,
                                   const double *__restrict__ pS, const int *__restrict__ pcls, int ncls,
-                                  const double *__restrict__ cls_zeta, double *__restrict__ A,
+                                  const double *__restrict__ zp_cls, double *__restrict__ A,
                                   float *__restrict__ A32, float *__restrict__ A32lo)
 {
     __shared__ float zp_tab[16 * 16];
@@ -296,9 +294,8 @@ __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, 
     const bool tab = ncls <= 16;
     if (tab)
         for (int t = threadIdx.x; t < ncls * ncls; t += blockDim.x) {
-            const double a = cls_zeta[t / ncls], b = cls_zeta[t % ncls];
-            zp_tab64[t] = a * b / sqrt(a * a + b * b);
-            zp_tab[t] = (float)zp_tab64[t];
+            zp_tab64[t] = zp_cls[t];
+            zp_tab[t] = (float)zp_cls[t];
         }
     __syncthreads();
     const int nt = (M + AT - 1) / AT;
@@ -498,6 +495,19 @@ int a_build(pcm_ctx *c, cudaStream_t s)
     c->lda = (M + 31) / 32 * 32;
     PCM_TRY(c->A.alloc((size_t)M * c->lda));
     {
+        // zeta'_kl = zeta_k zeta_l / sqrt(zeta_k^2 + zeta_l^2) (Eq. 8) for every
+        // pair of exponent classes, once on the host (IEEE division and square
+        // root, as on the device) instead of in every thread block
+        const int nc = c->ncls;
+        std::vector<double> &zp = c->h_zp_cls;  // kept in the context: the copy below reads it later
+        zp.assign((size_t)nc * nc, 0.0);
+        for (int a = 0; a < nc; ++a)
+            for (int b = 0; b < nc; ++b) {
+                const double za = c->h_cls_zeta[a], zb = c->h_cls_zeta[b];
+                zp[(size_t)a * nc + b] = za * zb / sqrt(za * za + zb * zb);
+            }
+        PCM_TRY(c->zp_cls.alloc(std::max<size_t>(1, zp.size())));
+        PCM_CUDA(cudaMemcpyAsync(c->zp_cls.p, zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         const long long nt = (M + AT - 1) / AT;
         const long long ntiles = nt * (nt + 1) / 2;
         if (c->opt.precision == PCM_MIXED) {
@@ -505,11 +515,11 @@ int a_build(pcm_ctx *c, cudaStream_t s)
             PCM_TRY(c->A32lo.alloc((size_t)M * c->lda));
             a_build_df_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->p32.p, c->p32lo.p, c->px.p, c->py.p,
                                                               c->pz.p, c->pzeta.p, c->pS.p, c->pcls.p, c->ncls,
-                                                              c->cls_zeta.p, c->A.p, c->A32.p, c->A32lo.p);
+                                                              c->zp_cls.p, c->A.p, c->A32.p, c->A32lo.p);
             c->a32_ready = true;
         } else {
             a_build_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
-                                                           c->pS.p, c->pcls.p, c->ncls, c->cls_zeta.p, c->A.p);
+                                                           c->pS.p, c->pcls.p, c->ncls, c->zp_cls.p, c->A.p);
         }
         PCM_LAUNCHED(c);
     }
