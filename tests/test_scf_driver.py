@@ -33,3 +33,54 @@ def test_scf_sequence_approaches_the_density():
     # seeded
     seq2 = workloads.scf_sequence(w, 12)
     assert all(np.array_equal(a[0], b[0]) for a, b in zip(seq, seq2))
+
+
+class _FakeContext:
+    """Stands in for pcm.Context on the host: records the calls run_sequence
+    makes and writes its 'solution' into the array it is given (as the C ABI
+    does for a warm start), so that aliasing would show."""
+
+    def __init__(self, M=5):
+        self.M = M
+        self.calls = []
+
+    def esp(self, P):
+        self.calls.append(("esp", float(np.sum(P))))
+
+    def solve(self, delta=-1.0, prev_diis_error=-1.0, q=None, warm=False, like=None):
+        d = delta if delta > 0 else (1.0 if prev_diis_error < 0 else
+                                     (1e-3 * prev_diis_error / 0.01) ** (1 / 1.07))
+        out = q if q is not None else np.zeros(self.M)
+        self.calls.append(("solve", d, warm, None if q is None else q.copy()))
+        out += 1.0                       # each solve moves the charges by one
+        return out, {"delta": d, "iterations": 3, "converged": 1, "ms_solve": 0.0, "refinements": 1}
+
+    def energy(self, q):
+        return float(np.sum(q))
+
+
+@pytest.mark.parametrize("scheme", ["fixed", "2delta", "dynamic"])
+def test_run_sequence_thresholds_and_warm_starts(scheme):
+    from paper_1505_07851_gb300.scf import run_sequence, two_delta
+    seq = [(np.full((2, 2), float(n)), 0.1 * 0.4 ** n) for n in range(5)]
+    ctx = _FakeContext()
+    res = run_sequence(ctx, seq, scheme, delta_tight=1e-6, keep_q=True)
+    solves = [c for c in ctx.calls if c[0] == "solve"]
+    assert len(res) == len(seq) == len(solves)
+    prev = None
+    for n, (r, s) in enumerate(zip(res, solves)):
+        if scheme == "fixed":
+            want = 1e-6
+        elif scheme == "2delta":
+            want = two_delta(prev, 1e-6)
+        else:
+            want = 1.0 if prev is None else (1e-3 * prev / 0.01) ** (1 / 1.07)
+        assert r["delta"] == pytest.approx(want, rel=1e-12)
+        # warm start from the previous charges after the first iteration
+        assert s[2] == (n > 0)
+        if n > 0:
+            assert np.array_equal(s[3], res[n - 1]["q"])
+        # the kept charges are copies: later in-place solves do not change them
+        assert np.all(r["q"] == n + 1)
+        assert r["energy"] == pytest.approx(ctx.M * (n + 1))
+        prev = seq[n][1]
