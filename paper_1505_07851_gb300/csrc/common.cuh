@@ -146,29 +146,29 @@ static_assert(cart_e(2, 1, 0) == 1 && cart_e(2, 1, 1) == 1 && cart_e(2, 4, 2) ==
 
 // Hermite expansion coefficients of one direction, sized for (LA, LB) and
 // fully unrolled (registers): same recurrences as hermite_E1D.
-template <int LA, int LB>
+template <int LA, int LB, typename T = double>
 struct E1T {
-    double e[LA + 1][LB + 1][LA + LB + 1];
+    T e[LA + 1][LB + 1][LA + LB + 1];
 };
 
-template <int LA, int LB>
-__device__ __forceinline__ void hermite_E1T(double PA, double PB, double inv2p, E1T<LA, LB> &E)
+template <int LA, int LB, typename T = double>
+__device__ __forceinline__ void hermite_E1T(T PA, T PB, T inv2p, E1T<LA, LB, T> &E)
 {
 #pragma unroll
     for (int i = 0; i <= LA; ++i)
 #pragma unroll
         for (int j = 0; j <= LB; ++j)
 #pragma unroll
-            for (int t = 0; t <= LA + LB; ++t) E.e[i][j][t] = 0.0;
-    E.e[0][0][0] = 1.0;
+            for (int t = 0; t <= LA + LB; ++t) E.e[i][j][t] = T(0);
+    E.e[0][0][0] = T(1);
 #pragma unroll
     for (int i = 0; i <= LA; ++i) {
         if (i > 0) {
 #pragma unroll
             for (int t = 0; t <= i; ++t) {
-                double v = PA * E.e[i - 1][0][t];
+                T v = PA * E.e[i - 1][0][t];
                 if (t > 0) v += inv2p * E.e[i - 1][0][t - 1];
-                if (t + 1 <= i - 1) v += (t + 1) * E.e[i - 1][0][t + 1];
+                if (t + 1 <= i - 1) v += T(t + 1) * E.e[i - 1][0][t + 1];
                 E.e[i][0][t] = v;
             }
         }
@@ -176,9 +176,9 @@ __device__ __forceinline__ void hermite_E1T(double PA, double PB, double inv2p, 
         for (int j = 1; j <= LB; ++j)
 #pragma unroll
             for (int t = 0; t <= i + j; ++t) {
-                double v = PB * E.e[i][j - 1][t];
+                T v = PB * E.e[i][j - 1][t];
                 if (t > 0) v += inv2p * E.e[i][j - 1][t - 1];
-                if (t + 1 <= i + j - 1) v += (t + 1) * E.e[i][j - 1][t + 1];
+                if (t + 1 <= i + j - 1) v += T(t + 1) * E.e[i][j - 1][t + 1];
                 E.e[i][j][t] = v;
             }
     }

@@ -44,7 +44,10 @@ __device__ inline double dfact_even(int T)
     return r;
 }
 
-template <int LA, int LB>
+// TS: arithmetic of the Schwarz bound (FP64, or FP32 for PCM_MIXED, where a
+// bound off by 1e-6 relative only moves pairs at the cutoff whose
+// contributions are of the cutoff's size); the pair data are FP64 either way.
+template <int LA, int LB, typename TS>
 __global__ void pair_screen_kernel(long long ncand, int nsp, const long long *__restrict__ sp_cand,
                                    const int *__restrict__ spA, const int *__restrict__ spB,
                                    const int *__restrict__ sh_atom, const int *__restrict__ sh_nprim,
@@ -98,17 +101,17 @@ __global__ void pair_screen_kernel(long long ncand, int nsp, const long long *__
     //             sum_{tuv,t'u'v'} E_tuv E_t'u'v' (-1)^(t'+u'+v') R_{t+t',u+u',v+v'}(p/2, 0),
     // R_{TUV}(alpha, 0) = (-2 alpha)^((T+U+V)/2) (T-1)!!(U-1)!!(V-1)!! / (T+U+V+1)
     // for even T, U, V and 0 otherwise.
-    E1T<LA, LB> Ex, Ey, Ez;
-    const double inv2p = 0.5 / p;
-    hermite_E1T<LA, LB>(P[0] - RA[0], P[0] - RB[0], inv2p, Ex);
-    hermite_E1T<LA, LB>(P[1] - RA[1], P[1] - RB[1], inv2p, Ey);
-    hermite_E1T<LA, LB>(P[2] - RA[2], P[2] - RB[2], inv2p, Ez);
+    E1T<LA, LB, TS> Ex, Ey, Ez;
+    const TS inv2p = TS(0.5 / p);
+    hermite_E1T<LA, LB, TS>(TS(P[0] - RA[0]), TS(P[0] - RB[0]), inv2p, Ex);
+    hermite_E1T<LA, LB, TS>(TS(P[1] - RA[1]), TS(P[1] - RB[1]), inv2p, Ey);
+    hermite_E1T<LA, LB, TS>(TS(P[2] - RA[2]), TS(P[2] - RB[2]), inv2p, Ez);
     constexpr int LL = LA + LB;
     // (-2 alpha)^n with alpha = p / 2
-    double pw[LL + 1];
-    pw[0] = 1.0;
+    TS pw[LL + 1];
+    pw[0] = TS(1);
 #pragma unroll
-    for (int n = 1; n <= LL; ++n) pw[n] = pw[n - 1] * (-p);
+    for (int n = 1; n <= LL; ++n) pw[n] = pw[n - 1] * TS(-p);
     double qmax = 0.0;
 #pragma unroll
     for (int ca = 0; ca < ncart(LA); ++ca)
@@ -116,20 +119,20 @@ __global__ void pair_screen_kernel(long long ncand, int nsp, const long long *__
         for (int cb = 0; cb < ncart(LB); ++cb) {
             const int ax = cart_e(LA, ca, 0), ay = cart_e(LA, ca, 1), az = cart_e(LA, ca, 2);
             const int bx = cart_e(LB, cb, 0), by = cart_e(LB, cb, 1), bz = cart_e(LB, cb, 2);
-            double Gx[2 * LL + 1], Gy[2 * LL + 1], Gz[2 * LL + 1];
+            TS Gx[2 * LL + 1], Gy[2 * LL + 1], Gz[2 * LL + 1];
 #pragma unroll
-            for (int t = 0; t <= 2 * LL; ++t) Gx[t] = Gy[t] = Gz[t] = 0.0;
+            for (int t = 0; t <= 2 * LL; ++t) Gx[t] = Gy[t] = Gz[t] = TS(0);
             // E_t vanishes for t > i + j, so the full loops add exact zeros there
 #pragma unroll
             for (int t = 0; t <= LL; ++t)
 #pragma unroll
                 for (int t2 = 0; t2 <= LL; ++t2) {
-                    const double sg = (t2 & 1) ? -1.0 : 1.0;
+                    const TS sg = (t2 & 1) ? TS(-1) : TS(1);
                     Gx[t + t2] += Ex.e[ax][bx][t] * Ex.e[ax][bx][t2] * sg;
                     Gy[t + t2] += Ey.e[ay][by][t] * Ey.e[ay][by][t2] * sg;
                     Gz[t + t2] += Ez.e[az][bz][t] * Ez.e[az][bz][t2] * sg;
                 }
-            double sum = 0.0;
+            TS sum = TS(0);
 #pragma unroll
             for (int T = 0; T <= 2 * LL; T += 2)
 #pragma unroll
@@ -137,10 +140,11 @@ __global__ void pair_screen_kernel(long long ncand, int nsp, const long long *__
 #pragma unroll
                     for (int V = 0; V <= 2 * LL - T - U; V += 2) {
                         const int n = (T + U + V) / 2;
-                        const double R = dfact_even(T) * dfact_even(U) * dfact_even(V) / (T + U + V + 1) * pw[n];
+                        const TS R = TS(dfact_even(T) * dfact_even(U) * dfact_even(V) / (T + U + V + 1)) * pw[n];
                         sum += Gx[T] * Gy[U] * Gz[V] * R;
                     }
-            const double eri = 2.0 * 17.493418327624862846 / (p * p * sqrt(2.0 * p)) * K * K * sum;  // 2 pi^(5/2) = 2 * 17.4934...
+            const double eri =
+                2.0 * 17.493418327624862846 / (p * p * sqrt(2.0 * p)) * K * K * (double)sum;  // 2 pi^(5/2) = 2 * 17.4934...
             const double f = comp_factor(LA, ca) * comp_factor(LB, cb);
             qmax = fmax(qmax, f * f * fabs(eri));
         }
@@ -210,9 +214,15 @@ static int screen_class(pcm_ctx *c, PairClass &pc)
     PCM_TRY(flag.alloc(n));
     PCM_TRY(pos.alloc(n + 1));
     if (n > 0) {
-        pair_screen_kernel<LA, LB><<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(
-            n, pc.nsp, pc.sp_cand.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_nprim.p, c->sh_off.p, c->exps.p,
-            c->cnorm.p, c->xyz.p, c->opt.schwarz, c_sp.p, c_i.p, c_j.p, c_P.p, c_p.p, c_pref.p, c_Q.p, flag.p);
+        const unsigned grid = (unsigned)((n + 127) / 128);
+        if (c->opt.precision == PCM_MIXED)
+            pair_screen_kernel<LA, LB, float><<<grid, 128, 0, c->stream>>>(
+                n, pc.nsp, pc.sp_cand.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_nprim.p, c->sh_off.p, c->exps.p,
+                c->cnorm.p, c->xyz.p, c->opt.schwarz, c_sp.p, c_i.p, c_j.p, c_P.p, c_p.p, c_pref.p, c_Q.p, flag.p);
+        else
+            pair_screen_kernel<LA, LB, double><<<grid, 128, 0, c->stream>>>(
+                n, pc.nsp, pc.sp_cand.p, pc.spA.p, pc.spB.p, c->sh_atom.p, c->sh_nprim.p, c->sh_off.p, c->exps.p,
+                c->cnorm.p, c->xyz.p, c->opt.schwarz, c_sp.p, c_i.p, c_j.p, c_P.p, c_p.p, c_pref.p, c_Q.p, flag.p);
         PCM_LAUNCHED(c);
     }
     DBuf<int> &idx = c->si[4];
