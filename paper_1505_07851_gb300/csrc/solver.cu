@@ -3,14 +3,17 @@
 // preconditioning (Section 4b-ii), and the energy of Eq. 13.
 //
 // A is stored in FP64 (row-major, leading dimension lda), and for PCM_MIXED
-// also as an FP32 copy.  Each PCG iteration is three kernels:
+// also as FP32 hi and lo parts (A32, A32lo).  Each PCG iteration is three
+// kernels:
 //   pcg_gemv_rp  Ap = A p, p.Ap                       -> alpha
 //   pcg_update   x += alpha p, r -= alpha Ap, z = C r, r.r, r.z -> beta, stop test
 //   pcg_dir      p = z + beta p
 // Scalars stay on the device; reductions use per-block partial sums added in
-// block order by the last block to finish (deterministic).  Every kernel
-// returns at once when the stop flag is set, so the host may enqueue a batch
-// of iterations and look at the flag once per batch.
+// a fixed order by the last block to finish (deterministic).  Every kernel
+// returns at once when the stop flag is set; the iterations run as a CUDA
+// graph whose WHILE node the direction kernel ends once the flag is set.
+// PCM_MIXED refines FP32-GEMV inner solves with true residuals formed in
+// double-float from A32 + A32lo.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
