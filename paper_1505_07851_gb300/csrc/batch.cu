@@ -1,7 +1,7 @@
 // Batched C-PCM: ESP, solve, Fock correction and energy for many molecules
 // of uneven size in one call.
 //
-// Each molecule keeps its own context (surface, stored A and its FP32 copy,
+// Each molecule keeps its own context (surface, stored A and its FP32 parts,
 // pair lists, RBJ preconditioner).  The integral stages run molecule after
 // molecule on the batch's stream (every launch fills the GPU).  The linear
 // solves of all molecules run in lockstep: every vector of the batch lives in
@@ -17,8 +17,8 @@
 // iteration.  Every molecule stops on its own test; converged molecules skip
 // their work.  The loop is bounded: bscalar clears the condition once the
 // iteration count reaches the cap.  PCM_MIXED wraps the FP32-GEMV loop in the
-// FP64 iterative refinement of the single-molecule solver (true residuals
-// with the FP64 matrices, inner tolerance max(eta |r|, delta / 2)).
+// iterative refinement of the single-molecule solver (true residuals in
+// double-float from A32 + A32lo, inner tolerance max(eta |r|, delta / 2)).
 #include <math.h>
 #include <string.h>
 
