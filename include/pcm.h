@@ -69,7 +69,8 @@ typedef enum pcm_status {
 
 /* precision modes */
 #define PCM_FP64 0              /* every step in FP64 */
-#define PCM_MIXED 1             /* FP32 integrals and inner solver, FP64 accumulation and refinement */
+#define PCM_MIXED 1             /* FP32 integrals and inner solver, FP64 accumulation, refinement with
+                                   double-float (FP32 hi + lo) true residuals; energy within 1e-6 Eh */
 
 /* preconditioners (Section 4b-ii) */
 #define PCM_PRECOND_AUTO 0      /* Jacobi below `jacobi_below` points, else RBJ */
@@ -107,7 +108,7 @@ typedef struct pcm_stats {
     int converged;              /* 1 if ||A q - rhs||_2 < delta was reached */
     double delta;               /* threshold used by the last solve */
     double rnorm;               /* final residual norm (recursively updated) */
-    int refinements;            /* outer FP64 refinement steps (PCM_MIXED) */
+    int refinements;            /* outer refinement steps (PCM_MIXED) */
     int M;                      /* surface points */
     int nbf;                    /* basis functions */
     long long pairs_candidate;  /* primitive pairs before screening */
@@ -120,7 +121,7 @@ typedef struct pcm_stats {
     double ms_esp_class[6];     /* with timing: main ESP kernel time per class (ms) */
     double ms_fock_class[6];    /* with timing: main Fock kernel time per class (ms) */
     double ms_solve;            /* with timing: device time of the last pcm_solve (ms) */
-    double ms_precond;          /* with timing: build of A, its preconditioner and FP32 copy on the context's
+    double ms_precond;          /* with timing: build of A, its preconditioner and FP32 parts on the context's
                                    second stream after the last pcm_build_surface (ms; it overlaps the basis
                                    set-up and the integrals) */
     long long launches;         /* kernels launched by this context since its creation */
@@ -212,8 +213,8 @@ int pcm_energy(pcm_ctx *ctx, const double *q, const double *c, double *E, int fl
  * PCM_PTR_DEVICE, PCM_ASYNC, and any of PCM_GRAD_B / PCM_GRAD_C / PCM_GRAD_A
  * to select terms (none of them: all three).  Primitive pairs are screened
  * as in pcm_esp (Eq. 18).  PCM_FP64: every step in FP64.  PCM_MIXED: the
- * integral kernels and the off-diagonal A term (once a solve has made the
- * FP32 copy of A) run on the FP32 pipes with FP64 accumulation across tiles;
+ * integral kernels and the off-diagonal A term (from the FP32 copy of A)
+ * run on the FP32 pipes with FP64 accumulation across tiles;
  * the nuclear B term, the switching term and every reduction stay FP64. */
 int pcm_gradient(pcm_ctx *ctx, const double *P, const double *q, double *grad, int flags);
 
@@ -221,13 +222,13 @@ int pcm_gradient(pcm_ctx *ctx, const double *P, const double *q, double *grad, i
  * Batches: many molecules of uneven size in one call.
  *
  * A batch holds one context per molecule (options as for pcm_create; every
- * molecule's A, its FP32 copy under PCM_MIXED, and its preconditioner stay
+ * molecule's A, its FP32 parts under PCM_MIXED, and its preconditioner stay
  * resident).  pcm_batch_run computes, for every molecule, the ESP (Eq. 5),
  * the solve of Eq. 1 to ||A q - rhs||_2 < delta (Eq. 20; fixed delta), the
  * Fock correction (Eq. 10) and the energy (Eq. 13).  The solves of all
  * molecules run in lockstep on the device: one launch per PCG step serves
  * every molecule, the iteration loop is a CUDA graph whose loop condition the
- * device sets (per-molecule convergence), and PCM_MIXED wraps it in FP64
+ * device sets (per-molecule convergence), and PCM_MIXED wraps it in
  * iterative refinement as in pcm_solve.
  * ---------------------------------------------------------------------- */
 typedef struct pcm_batch pcm_batch;
