@@ -2,21 +2,24 @@
 """Benchmark of the C-PCM / ISWIG hot path on one GB300 (or N, as replicas).
 
 One step is one pass of the whole path over one synthetic molecule:
-surface build (points, switching, stored A, Bz), basis and primitive-pair
-list with screening, ESP c, rhs, PCG solve (RBJ, threshold of Eq. 21 for a
-1e-6 Eh energy error), Fock correction dF and the Eq. 13 energy.
+surface build (points, switching, Bz and the solver's operator), basis and
+primitive-pair list with screening, ESP c, rhs, PCG solve (RBJ, threshold of
+Eq. 21 for a 1e-6 Eh energy error), Fock correction dF and the Eq. 13 energy.
 
 Metric: ESP + Fock equivalent Cartesian primitive integrals per second
 (kept primitive pairs x ncart(a) ncart(b) x M, summed over the ESP and the
 Fock call of a step) divided by the step time; the PCG solve time is
-reported beside it.  Workload: the 300-atom H:C:N:O:S = 50:31:9:9:1 cluster
-with 6-31G-like s/sp shells (nbf ~ 1.66k), 600 occupied orbitals, 110
-points per sphere at 1.2 x Bondi (M ~ 12k).  The timed path is PCM_MIXED
-(FP32 integrals, FP64 accumulation and solve) unless --precision fp64; the
-FP64 path is timed beside it, and the energy of the timed solve is compared
-with an FP64 solve at delta = 1e-10.
+reported beside it.  Default workload: the 1000-atom H:C:N:O:S =
+50:31:9:9:1 cluster with 6-31G*-like s/sp/d shells (nbf ~ 8.5k), 2000
+occupied orbitals, 110 points per sphere at 1.2 x Bondi (M ~ 46k).  The
+timed path is PCM_MIXED (FP32 integrals, FP64 accumulation, refinement with
+double-float residuals) unless --precision fp64; the PCM_FP64 step is timed
+beside it, and the energy of the timed solve is compared with an FP64 solve
+at delta = 1e-10.  The 300-atom s/sp cluster (nbf ~ 1.66k, M ~ 12k) is
+timed the same way as a sub-record.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload cluster1000_spd|cluster300_sp|cluster300_spd|water|batch]
 
 With N > 1 (torchrun) every rank runs its own conformation (seed offset by
 rank): independent problems, no data-path collective (weak scaling).
@@ -94,9 +97,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/); a kernel missing here reports traffic null.
-NCU_TRAFFIC_BYTES = {"esp_kernel_f32<L=1> (ps)": 35.899648e6 + 15.616e3,      # scalar (--scalar-fp32)
-                     "esp_kernel_f32x2<L=1> (ps)": 27.160320e6 + 26.624e3,
-                     "fock_kernel_f32x2<L=1> (ps)": 6.007552e6 + 0.0}
+NCU_TRAFFIC_BYTES = {}
 
 CLASS_L = [0, 1, 2, 2, 3, 4]
 CLASS_NAME = ["ss", "ps", "pp", "ds", "dp", "dd"]
@@ -206,13 +207,22 @@ def barrier(world):
         dist.barrier()
 
 
-def workload_for(config, rank):
+WORKLOADS = {"water": 0, "cluster300_sp": 1, "cluster1000_spd": 2, "cluster300_spd": 3}
+DEFAULT_WORKLOAD = "cluster1000_spd"
+# oracle points per sample: about 10-30 s of host work on 16 cores (cpu_baseline),
+# and a few seconds per step of the reference arm
+CPU_POINTS = {"water": 252, "cluster300_sp": 320, "cluster1000_spd": 16, "cluster300_spd": 96}
+REF_POINTS = {"water": 252, "cluster300_sp": 16, "cluster1000_spd": 2, "cluster300_spd": 8}
+
+
+def workload_for(name, rank):
+    i = WORKLOADS[name]
     if rank == 0:
-        return workloads.config(config)
-    w0 = workloads.config(config)
+        return workloads.config(i)
+    w0 = workloads.config(i)
     seed = w0.seed + 1000 * rank
     return workloads.cluster(w0.mol.natom, seed, workloads.GLOBULE_RADIUS_A[w0.mol.natom],
-                             d_shells=(config in (2, 3)), nocc=w0.nocc, name=w0.name + "_r%d" % rank)
+                             d_shells=name.endswith("_spd"), nocc=w0.nocc, name=w0.name + "_r%d" % rank)
 
 
 # --------------------------------------------------------------------------
@@ -344,6 +354,65 @@ def _dominant(res, precision, steps, packed=True):
     return out
 
 
+def _reference_energy(pcm, w, dev, stream):
+    """The FP64 path with a tight solve (delta = 1e-10), not timed."""
+    with pcm.Context(precision="fp64", device=dev.index, stream=stream.cuda_stream) as ref:
+        ref.setup(w.mol, w.basis)
+        ref.esp(w.P)
+        qr, _ = ref.solve(delta=1e-10)
+        return ref.energy(qr)
+
+
+def _measure(pcm, w, args, dev, stream, flush, delta, steps, warmup, fp64_steps):
+    """Time `steps` steps of the requested precision and, for PCM_MIXED,
+    `fp64_steps` PCM_FP64 steps of the same workload; energies against the
+    FP64 delta = 1e-10 solve."""
+    E_ref = _reference_energy(pcm, w, dev, stream)
+    main = _timed_steps(pcm, w, args.precision, args, dev, stream, flush, delta, steps, warmup)
+    torch_sync()
+    other = None
+    if args.precision == "mixed" and fp64_steps > 0:
+        other = _timed_steps(pcm, w, "fp64", args, dev, stream, flush, delta, fp64_steps, 1)
+    return E_ref, main, other
+
+
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def _fp64_record(other, E_ref, world):
+    n = len(other["times"])
+    return {"value": other["ints"] * world / (sum(other["times"]) * 1e-3), "unit": UNIT,
+            "ms_per_step": sum(other["times"]) / n, "steps": n,
+            "pcg_solve_ms": statistics.mean(other["solve_ms"]), "pcg_iterations": statistics.mean(other["iters"]),
+            "esp_kernel_ms": float(other["esp_cls"].sum() / n),
+            "fock_kernel_ms": float(other["fock_cls"].sum() / n),
+            "energy_err_Eh": abs(other["E"][-1] - E_ref), "phase_ms": other["phase_ms"],
+            "roofline": _dominant(other, "fp64", n)}
+
+
+def _small_record(pcm, args, dev, stream, flush, delta):
+    """The 300-atom s/sp cluster (nbf ~ 1.66k, M ~ 12k), timed as the main
+    workload: mixed steps, one FP64 step, energies against delta = 1e-10."""
+    w = workloads.config(WORKLOADS["cluster300_sp"])
+    E_ref, main, other = _measure(pcm, w, args, dev, stream, flush, delta, max(3, args.steps), 3, 1)
+    n = len(main["times"])
+    s = main["stats"]
+    rec = {"workload": w.name, "natom": w.mol.natom, "nbf": s["nbf"], "M": s["M"], "precision": args.precision,
+           "value": main["ints"] / (sum(main["times"]) * 1e-3), "unit": UNIT, "steps": n,
+           "ms_per_step": sum(main["times"]) / n, "pcg_solve_ms": statistics.mean(main["solve_ms"]),
+           "pcg_iterations": statistics.mean(main["iters"]), "energy_err_Eh": abs(main["E"][-1] - E_ref),
+           "phase_ms": main["phase_ms"], "roofline": _dominant(main, args.precision, n, packed=not args.scalar_fp32)}
+    if other is not None:
+        rec["fp64"] = _fp64_record(other, E_ref, 1)
+        rec["speedup_vs_fp64"] = rec["fp64"]["ms_per_step"] / rec["ms_per_step"]
+    main["ctx"].close()
+    if other is not None:
+        other["ctx"].close()
+    return rec
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_init("nccl")
@@ -351,18 +420,12 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     import paper_1505_07851_gb300 as pcm
 
-    w = workload_for(args.config, rank)
+    w = workload_for(args.workload, rank)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     delta = args.delta if args.delta else DELTA_1E6
     b = w.basis
-
-    # reference energy: FP64 path with a tight solve (not timed)
-    with pcm.Context(precision="fp64", device=local, stream=stream.cuda_stream) as ref:
-        ref.setup(w.mol, w.basis)
-        ref.esp(w.P)
-        qr, _ = ref.solve(delta=1e-10)
-        E_ref = ref.energy(qr)
+    E_ref = _reference_energy(pcm, w, dev, stream)
 
     barrier(world)
     with ClockSampler(local) as clk:
@@ -370,12 +433,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     other = None
-    if args.precision == "mixed" and not args.no_fp64:
-        other = _timed_steps(pcm, w, "fp64", args, dev, stream, flush, delta, max(1, args.steps // 2), 1)
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        other = _timed_steps(pcm, w, "fp64", args, dev, stream, flush, delta, args.fp64_steps, 1)
 
     value, total_ms_max = replica_throughput(main["ints"], sum(main["times"]), world, dev)
     roofline = _dominant(main, args.precision, args.steps, packed=not args.scalar_fp32)
-    roofline["traffic"] = args.traffic if args.traffic is not None else NCU_TRAFFIC_BYTES.get(roofline["kernel"])
+    roofline["traffic"] = args.traffic if args.traffic is not None else \
+        NCU_TRAFFIC_BYTES.get((w.name, roofline["kernel"]))
     s = main["stats"]
     ctx = main["ctx"]
 
@@ -404,7 +468,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(w, args.cpu_points)
+        cpu = cpu_baseline(w, args.cpu_points or CPU_POINTS.get(w.name, 16))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -423,12 +487,17 @@ def run_ours(args):
             "energy_err_Eh": abs(main["E"][-1] - E_ref),
             "esp_kernel_ms": float(main["esp_cls"].sum() / args.steps),
             "fock_kernel_ms": float(main["fock_cls"].sum() / args.steps),
+            "esp_class_ms": [float(x) / args.steps for x in main["esp_cls"]],
+            "fock_class_ms": [float(x) / args.steps for x in main["fock_cls"]],
             "integrals_per_step": main["ints"] / args.steps, "pairs_kept": s["pairs_kept"],
             "phase_ms": main["phase_ms"],
             "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": main["launches"],
             "autotune": pcm.autotune_table(),
             "cpu_baseline": cpu,
         }
+        if other is not None:
+            line["fp64"] = _fp64_record(other, E_ref, world)
+            line["speedup_vs_fp64"] = line["fp64"]["ms_per_step"] / line["ms_per_step"]
         if not args.no_grad:
             q = main["bufs"]["q"]
             g_ms, g_main, gst = _time_gradient(main, q, flush, stream, args.steps)
@@ -440,17 +509,24 @@ def run_ours(args):
                 grad.update(fp64_ms=g64_ms, speedup_vs_fp64=g64_ms / g_ms,
                             max_abs_diff_vs_fp64_Eh_per_bohr=float(np.max(np.abs(g_main - g64))))
             line["gradient"] = grad
+        if other is not None:
+            other["ctx"].close()
+            other = None
         if not args.no_precond:
-            # Section 4b-ii: CG steps and solve time per preconditioner (FP64, fixed delta = 1e-6)
+            # Section 4b-ii: CG steps and solve time per preconditioner (FP64, fixed delta = 1e-6) on the
+            # step's own right-hand side -f (Bz + c)
+            f = (78.39 - 1.0) / 78.39
+            Bz = torch.empty_like(main["bufs"]["c"])
+            ctx.esp(main["Pd"], out=main["bufs"]["c"], bz_out=Bz)
+            rhs = -f * (Bz + main["bufs"]["c"])
             pc = {}
             for name, kw in (("jacobi", {"precond": "jacobi"}), ("rbj-100", {"precond": "rbj", "rbj_block": 100}),
                              ("rbj-800", {"precond": "rbj", "rbj_block": 800}),
                              ("octree-800", {"precond": "octree", "octree_leaf": 800})):
                 with pcm.Context(precision="fp64", timing=True, device=dev.index, stream=stream.cuda_stream,
                                  **kw) as pctx:
-                    pctx.setup(w.mol, w.basis)
-                    pctx.esp(main["Pd"])
-                    _, pst = pctx.solve(delta=1e-6, like=main["Pd"])
+                    pctx.build_surface(w.mol.xyz, w.mol.Z, w.mol.radius, 110)
+                    _, pst = pctx.solve(rhs=rhs, delta=1e-6)
                     pc[name] = {"cg_steps": pst["iterations"], "converged": bool(pst["converged"]),
                                 "solve_ms_incl_setup": pst["ms_solve"], "setup_ms": pst["ms_precond"]}
             line["preconditioners"] = pc
@@ -467,20 +543,14 @@ def run_ours(args):
                               "final_energy_Eh": rec[-1]["energy"]}
             sc["workload"] = "%s, 14 iterations, DIIS error 0.1 x 0.4^n, warm start, delta_2 = 1e-6" % w.name
             line["scf_sequence"] = sc
-        if other is not None:
-            n = len(other["times"])
-            line["fp64"] = {"value": other["ints"] * world / (sum(other["times"]) * 1e-3), "unit": UNIT,
-                            "ms_per_step": sum(other["times"]) / n,
-                            "pcg_solve_ms": statistics.mean(other["solve_ms"]),
-                            "esp_kernel_ms": float(other["esp_cls"].sum() / n),
-                            "fock_kernel_ms": float(other["fock_cls"].sum() / n),
-                            "energy_err_Eh": abs(other["E"][-1] - E_ref), "phase_ms": other["phase_ms"],
-                            "roofline": _dominant(other, "fp64", n)}
-            line["speedup_vs_fp64"] = line["fp64"]["ms_per_step"] / line["ms_per_step"]
+        main["ctx"].close()
+        if not args.no_small and w.name != "cluster300_sp":
+            line["cluster300_sp"] = _small_record(pcm, args, dev, stream, flush, delta)
         print(json.dumps(line))
-    main["ctx"].close()
-    if other is not None:
-        other["ctx"].close()
+    else:
+        main["ctx"].close()
+        if other is not None:
+            other["ctx"].close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -518,13 +588,14 @@ def run_reference(args):
     rank, world, local = dist_init("gloo")
     if rank != 0:
         return
-    w = workloads.config(args.config)
+    w = workloads.config(WORKLOADS[args.workload])
+    npts = args.ref_points or REF_POINTS.get(w.name, 4)
     oracle, s, eb, idx_all, per_point = _oracle_sample(w, 10 ** 9)
     rng = np.random.default_rng(1)
     times = []
     ints = 0.0
     for it in range(args.warmup + args.steps):
-        idx = np.sort(rng.choice(len(s["zeta"]), size=args.ref_points, replace=False))
+        idx = np.sort(rng.choice(len(s["zeta"]), size=npts, replace=False))
         t0 = time.perf_counter()
         oracle.esp(eb, w.P, s["r"][idx], s["zeta"][idx])
         dt = time.perf_counter() - t0
@@ -535,7 +606,7 @@ def run_reference(args):
     value = ints / total
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     sample = ("oracle ESP at %d random surface points per step over all %d shell pairs (the full "
-              "step would need %d points)" % (args.ref_points, eb.nshell * (eb.nshell + 1) // 2, len(s["zeta"])))
+              "step would need %d points)" % (npts, eb.nshell * (eb.nshell + 1) // 2, len(s["zeta"])))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -652,18 +723,19 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="PCM_FP64 steps timed beside a mixed run (0: none)")
     ap.add_argument("--delta", type=float, default=None)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--cpu-points", type=int, default=32)
-    ap.add_argument("--ref-points", type=int, default=16)
+    ap.add_argument("--cpu-points", type=int, default=None, help="oracle points of the cpu_baseline sample")
+    ap.add_argument("--ref-points", type=int, default=None, help="oracle points per step of the reference arm")
     ap.add_argument("--traffic", type=float, default=None, help="DRAM bytes per launch of the dominant kernel (ncu)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the nuclear-gradient timing")
-    ap.add_argument("--nmol", type=int, default=64, help="conformations in the batch workload (--config 4)")
+    ap.add_argument("--no-small", action="store_true", help="skip the 300-atom sub-record")
+    ap.add_argument("--nmol", type=int, default=64, help="conformations in the batch workload")
     ap.add_argument("--ref-mols", type=int, default=4, help="batch members checked against the FP64 path")
     ap.add_argument("--no-scf", action="store_true", help="skip the SCF-sequence threshold comparison")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioner comparison")
@@ -675,7 +747,7 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.config == 4:
+    elif args.workload == "batch":
         run_batch(args)
     else:
         run_ours(args)

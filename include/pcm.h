@@ -66,6 +66,7 @@ typedef enum pcm_status {
 #define PCM_GRAD_B 8            /* pcm_gradient: include z^T (dB^T/dR) q */
 #define PCM_GRAD_C 16           /* pcm_gradient: include (d*c^T/dR) q (the integrals) */
 #define PCM_GRAD_A 32           /* pcm_gradient: include q^T (dA/dR) q / (2 f) (with switching) */
+#define PCM_TWO_DELTA 64        /* pcm_solve: delta is delta_2 of the 2-delta threshold scheme (Section 4b-i) */
 
 /* precision modes */
 #define PCM_FP64 0              /* every step in FP64 */
@@ -184,11 +185,24 @@ int pcm_esp(pcm_ctx *ctx, const double *P, double *c, double *Bz, int flags);
  * pcm_esp.  delta > 0: fixed threshold; delta <= 0: dynamic threshold of
  * Eq. 21 from prev_diis_error (delta = (1e-3 prev / 0.01)^(1/1.07) clamped
  * to [1e-10, 1]; prev_diis_error < 0 means first SCF step, delta = 1).
- * q: M outputs (and the initial guess with PCM_WARM).  st: optional stats.
+ * With PCM_TWO_DELTA, delta is delta_2 of the 2-delta scheme (see
+ * pcm_cg_threshold).  q: M outputs (and the initial guess with PCM_WARM).  st: optional stats.
  * Returns PCM_ERR_NOT_CONVERGED when max_iter is reached (q is the last
  * iterate). */
 int pcm_solve(pcm_ctx *ctx, const double *rhs, double delta, double prev_diis_error, double *q,
               pcm_stats *st, int flags);
+
+/* The CG threshold pcm_solve uses for (delta, prev_diis_error, flags), with
+ * no GPU work (host logic of Section 4b-i):
+ *   - PCM_TWO_DELTA in flags: the 2-delta scheme, delta = delta_2 > 0; the
+ *     threshold is 1e4 * delta_2 while prev_diis_error is negative (first SCF
+ *     step) or above 1e-3, then delta_2;
+ *   - else delta > 0: delta itself (fixed threshold);
+ *   - else: Eq. 21, (1e-3 prev_diis_error / 0.01)^(1/1.07) clamped to
+ *     [1e-10, 1]; 1 when prev_diis_error < 0.
+ * *out receives the threshold.  PCM_ERR_ARG for NaN inputs, a NULL out, or
+ * PCM_TWO_DELTA with delta <= 0. */
+int pcm_cg_threshold(double delta, double prev_diis_error, int flags, double *out);
 
 /* Solvation correction to the Fock matrix (Eq. 10, Eq. 16, Eq. 17):
  * dF_{mu nu} = -sum_k q_k (mu|J_k|nu).  q: M inputs; dF: nbf*nbf outputs,
@@ -284,20 +298,22 @@ int pcm_get_stats(pcm_ctx *ctx, pcm_stats *st);
  *   E = (Bz)^T q + c^T q + q^T A q / (2 f)
  *
  * All pointers are DEVICE pointers on the current CUDA device, owned by the
- * caller: A (M rows, leading dimension lda >= M, row-major, e.g. the matrix
- * of Eq. 2 and Eq. 3), Bz, c, q (M each) and the output E (one double).
- * f = (eps - 1) / (eps + k).  stream: cudaStream_t (NULL: legacy default
- * stream).  The work is only enqueued: E is valid once the stream reaches it.
+ * caller: A (M rows, leading dimension lda >= M, row-major: the stored
+ * interaction matrix of pcm_build_surface), Bz, c, q (M each) and the output
+ * E (one double).  f = (eps - 1) / (eps + k).  stream: cudaStream_t (NULL:
+ * legacy default stream).  The work is only enqueued: E is valid once the
+ * stream reaches it.
  *
- * Scratch (A q and per-block partial sums) lives in a fixed device array of
- * 536 KiB inside the library, held by every GPU that loads the library until
- * the process exits.  M above 65536 is rejected with PCM_ERR_ARG.  The first
- * call on a device looks up the array's device address (with that device
- * current) and may load the library's device code; make that first call
- * before any stream capture.  Every call shares the array: calls whose
+ * Scratch (the vector A q) lives in a fixed device array of 512 KiB inside
+ * the library, held by every GPU that loads the library until the process
+ * exits.  M above 65536 is rejected with PCM_ERR_ARG.  The first call on a
+ * device looks up the array's device address (with that device current)
+ * and may load the library's device code; make that first call before any
+ * stream capture.  The address is kept for the process: do not use the
+ * library across a device reset.  Every call shares the array: calls whose
  * kernels overlap on the GPU (other streams, other host threads) race and
- * give wrong results; serialise them.  Nothing in the array needs clearing
- * between calls. */
+ * give wrong results; serialise them.  Each call writes every element it
+ * reads, so nothing in the array needs clearing between calls. */
 int pcm_energy_noalloc(int M, const double *A, int lda, const double *Bz, const double *c,
                        const double *q, double f, double *E, void *stream);
 

@@ -44,6 +44,7 @@ PCM_WARM = 4
 PCM_GRAD_B = 8
 PCM_GRAD_C = 16
 PCM_GRAD_A = 32
+PCM_TWO_DELTA = 64
 PCM_FP64 = 0
 PCM_MIXED = 1
 PRECOND = {"auto": 0, "none": 1, "jacobi": 2, "rbj": 3, "octree": 4}
@@ -116,6 +117,7 @@ def _load():
         "pcm_get_stats": (i, [vp, ctypes.POINTER(pcm_stats)]),
         "pcm_autotune_table": (i, [vp, i]),
         "pcm_energy_noalloc": (i, [i, vp, i, vp, vp, vp, d, vp, vp]),
+        "pcm_cg_threshold": (i, [d, d, i, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -146,6 +148,18 @@ def _ptr(a, dtype):
     return arr.ctypes.data, 0, arr
 
 
+def cg_threshold(delta=-1.0, prev_diis_error=-1.0, two_delta=False):
+    """The CG threshold pcm_solve uses (pcm_cg_threshold): fixed delta > 0,
+    Eq. 21 from the previous DIIS error when delta <= 0, or the 2-delta
+    scheme with two_delta=True.  Host logic; needs no GPU."""
+    out = ctypes.c_double()
+    st = _lib.pcm_cg_threshold(float(delta), float(prev_diis_error), PCM_TWO_DELTA if two_delta else 0,
+                               ctypes.byref(out))
+    if st != PCM_OK:
+        raise PCMError(st, "pcm_cg_threshold", _lib.pcm_last_error().decode())
+    return out.value
+
+
 def autotune_table():
     """The autotuner's choices so far: list of dicts (device, kernel, L,
     bucket, choice, fp32x2, trial_us) with kernel "esp_variant" (pair-driven
@@ -170,17 +184,37 @@ def autotune_table():
 
 
 def energy_noalloc(A, Bz, c, q, f, E, stream=None):
-    """pcm_energy_noalloc on CUDA torch tensors: A (M, lda >= M) row-major,
-    Bz, c, q (M,), E (1,) output; nothing is allocated by the library.  The
-    result is ready once `stream` (default: torch's current stream) reaches it."""
+    """pcm_energy_noalloc on CUDA torch tensors: A (M, >= M) row-major with
+    unit column stride (its row stride is the leading dimension), Bz, c, q
+    (M,), E (>= 1,) output, all float64 on one device; nothing is allocated
+    by the library.  The call is made with that device current.  The result
+    is ready once `stream` (default: torch's current stream of that device)
+    reaches it."""
     import torch
-    for t in (A, Bz, c, q, E):
-        _ptr(t, np.float64)
-    if stream is None:
-        stream = torch.cuda.current_stream(A.device).cuda_stream
+    ts = (A, Bz, c, q, E)
     M = q.numel()
-    st = _lib.pcm_energy_noalloc(M, A.data_ptr(), A.stride(0), Bz.data_ptr(), c.data_ptr(), q.data_ptr(),
-                                 float(f), E.data_ptr(), stream)
+    if A.dim() != 2 or A.shape[0] < M or A.shape[1] < M or A.stride(1) != 1 or A.stride(0) < M:
+        raise ValueError("energy_noalloc: A must be 2-D with at least (M, M) = (%d, %d) elements, unit column "
+                         "stride and row stride >= M; got shape %s, strides %s" % (M, M, tuple(A.shape),
+                                                                                   A.stride()))
+    if Bz.numel() != M or c.numel() != M:
+        raise ValueError("energy_noalloc: Bz and c must have M = %d elements (got %d, %d)"
+                         % (M, Bz.numel(), c.numel()))
+    if E.numel() < 1:
+        raise ValueError("energy_noalloc: E must have at least one element")
+    for t in ts:
+        if not t.is_cuda or t.dtype != torch.float64:
+            raise TypeError("energy_noalloc: arguments must be float64 CUDA tensors")
+    for t in (Bz, c, q, E):
+        if not t.is_contiguous():
+            raise TypeError("energy_noalloc: Bz, c, q and E must be contiguous")
+    if any(t.device != A.device for t in ts):
+        raise ValueError("energy_noalloc: all tensors must be on one device (A is on %s)" % A.device)
+    with torch.cuda.device(A.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(A.device).cuda_stream
+        st = _lib.pcm_energy_noalloc(M, A.data_ptr(), A.stride(0), Bz.data_ptr(), c.data_ptr(), q.data_ptr(),
+                                     float(f), E.data_ptr(), stream)
     if st != PCM_OK:
         raise PCMError(st, "pcm_energy_noalloc", _lib.pcm_last_error().decode())
     return E
@@ -284,8 +318,10 @@ class Context:
         self._check(_lib.pcm_esp(self._h, pP, pc, pb, flags), "pcm_esp")
         return c
 
-    def solve(self, rhs=None, delta=-1.0, prev_diis_error=-1.0, q=None, warm=False, like=None):
-        """Returns (q, stats dict).  delta <= 0 selects the dynamic threshold of Eq. 21."""
+    def solve(self, rhs=None, delta=-1.0, prev_diis_error=-1.0, q=None, warm=False, like=None, two_delta=False):
+        """Returns (q, stats dict).  delta <= 0 selects the dynamic threshold of
+        Eq. 21; two_delta=True makes delta the delta_2 of the 2-delta scheme
+        (PCM_TWO_DELTA, Section 4b-i)."""
         pr, flr, keepr = _ptr(rhs, np.float64)
         if q is None:
             q = self._out(rhs if rhs is not None else like, (self.M,))
@@ -293,7 +329,7 @@ class Context:
         if rhs is not None and flr != flq:
             raise TypeError("rhs and q must live on the same side (host or device)")
         st = pcm_stats()
-        flags = flq | (PCM_WARM if warm else 0)
+        flags = flq | (PCM_WARM if warm else 0) | (PCM_TWO_DELTA if two_delta else 0)
         self._check(_lib.pcm_solve(self._h, pr, float(delta), float(prev_diis_error), pq, ctypes.byref(st),
                                    flags), "pcm_solve", ok=(PCM_OK, PCM_ERR_NOT_CONVERGED))
         return q, st.as_dict()

@@ -46,16 +46,33 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     cc = nvcc()
     extra = list(extra_flags or [])
 
+    # an object is rebuilt when its source, any header, this script or the
+    # flags changed since it was written (the flags are kept beside it)
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if not f.endswith(".cu")]
+    headers += [os.path.join(HERE, "..", "include", "pcm.h"), os.path.abspath(__file__)]
+    newest_header = max(os.path.getmtime(h) for h in headers)
+
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         cmd = [cc, *ARCH, *FLAGS, *extra, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
+        stamp = obj + ".cmd"
+        fresh = (not force and os.path.exists(obj) and os.path.exists(stamp)
+                 and open(stamp).read() == " ".join(cmd)
+                 and os.path.getmtime(obj) >= max(newest_header, os.path.getmtime(os.path.join(CSRC, src))))
+        if fresh:
+            return src, obj, None, cmd
         r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode == 0:
+            with open(stamp, "w") as fh:
+                fh.write(" ".join(cmd))
         return src, obj, r, cmd
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(compile_one, SOURCES))
     failed = False
     for src, obj, r, cmd in results:
+        if r is None:
+            continue
         if verbose or r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
         failed |= r.returncode != 0

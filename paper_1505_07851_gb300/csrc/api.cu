@@ -322,6 +322,36 @@ int pcm_esp(pcm_ctx *c, const double *P, double *cout, double *Bzout, int flags)
     return finish(c, flags);
 }
 
+int pcm_cg_threshold(double delta, double prev_diis_error, int flags, double *out)
+{
+    if (!out || std::isnan(delta) || std::isnan(prev_diis_error)) {
+        set_last_error("pcm_cg_threshold: NaN threshold or NULL output");
+        return PCM_ERR_ARG;
+    }
+    double d = delta;
+    if (flags & PCM_TWO_DELTA) {
+        // Section 4b-i: s * delta_2 (s = 1e4) until the previous SCF iteration's
+        // DIIS error has reached 1e-3, then delta_2
+        if (!(delta > 0.0)) {
+            set_last_error("pcm_cg_threshold: PCM_TWO_DELTA needs delta_2 > 0");
+            return PCM_ERR_ARG;
+        }
+        d = (prev_diis_error < 0.0 || prev_diis_error > 1e-3) ? 1e4 * delta : delta;
+    } else if (!(d > 0.0)) {
+        // Eq. 21 and the rule that follows it: the CG threshold that predicts an
+        // energy error of 1e-3 times the previous DIIS error; delta = 1 when
+        // there is no previous iteration
+        if (prev_diis_error < 0.0) {
+            d = 1.0;
+        } else {
+            d = pow(1e-3 * prev_diis_error / 0.01, 1.0 / 1.07);
+            d = fmin(1.0, fmax(1e-10, d));
+        }
+    }
+    *out = d;
+    return PCM_OK;
+}
+
 int pcm_solve(pcm_ctx *c, const double *rhs, double delta, double prev_diis_error, double *q, pcm_stats *st,
               int flags)
 {
@@ -337,18 +367,10 @@ int pcm_solve(pcm_ctx *c, const double *rhs, double delta, double prev_diis_erro
         set_last_error("pcm_solve: NaN threshold");
         return PCM_ERR_ARG;
     }
+    double d = 0.0;
+    PCM_TRY(pcm_cg_threshold(delta, prev_diis_error, flags, &d));
     DeviceGuard g(c->device);
     const int M = c->M;
-    // threshold: fixed, or Eq. 21 with the rule that follows it
-    double d = delta;
-    if (!(d > 0.0)) {
-        if (prev_diis_error < 0.0) {
-            d = 1.0;
-        } else {
-            d = pow(1e-3 * prev_diis_error / 0.01, 1.0 / 1.07);
-            d = fmin(1.0, fmax(1e-10, d));
-        }
-    }
     const double f = (c->opt.eps - 1.0) / (c->opt.eps + c->opt.k);
     const double *drhs;
     PCM_TRY(c->vrhs.alloc(M));

@@ -9,9 +9,13 @@
 // may synchronise the device in the middle of the caller's work.  Such a
 // caller keeps A, B z, c and q in its own buffers and passes them in.
 //
+// Two kernels: the first writes y = A q into the scratch array (one warp per
+// row), the second reads y back and forms q.y, Bz.q and c.q in one block in a
+// fixed order, so the result does not depend on the first kernel's grid.
+//
 // The scratch array is part of the library's device image: every GPU that
-// loads the library holds it ((65536 + 3 * 1024) doubles = 536 KiB) until the
-// process exits.  All calls share it; each call writes every value it later
+// loads the library holds it (65536 doubles = 512 KiB) until the process
+// exits.  All calls share it; each call writes every value of y it later
 // reads, so nothing has to be cleared between calls, but two calls whose
 // kernels overlap on the GPU (different streams, or another host thread)
 // race on it and give wrong results.
@@ -26,75 +30,70 @@
 namespace pcm {
 namespace noalloc {
 
-constexpr int MAX_M = 65536;          // largest number of surface points accepted
-constexpr int NT = 256;               // threads per block (8 warps, one row per warp at a time)
-constexpr int MAX_BLOCKS = 1024;      // partial-sum slots per quantity
+constexpr int MAX_M = 65536;          // largest number of surface points accepted (length of y)
+constexpr int NT = 256;               // threads per block of the row kernel (one row per warp at a time)
+constexpr int ROW_BLOCKS = 1024;      // most blocks of the row kernel (rows are grid-strided beyond)
+constexpr int DOT_NT = 1024;          // threads of the single dot-product block
 constexpr int MAX_DEVICES = 64;
 
-// scratch: y = A q (MAX_M doubles), then three rows of per-block partial sums
-static __device__ __align__(256) double g_scratch[MAX_M + 3 * MAX_BLOCKS];
+// scratch: y = A q
+static __device__ __align__(256) double g_scratch[MAX_M];
 
 static std::mutex g_mu;
 static double *g_scratch_addr[MAX_DEVICES];  // device address of g_scratch, per device
 
-// Block b: rows b*8+w, b*8+w+8*nb, ... of y = A q (one warp per row), and
-// partial sums of q.y, Bz.q and c.q over its rows and elements.
-__global__ void __launch_bounds__(NT) energy_partials_kernel(int M, int lda, const double *__restrict__ A,
-                                                             const double *__restrict__ Bz,
-                                                             const double *__restrict__ c,
-                                                             const double *__restrict__ q, double *__restrict__ scr)
+// y_row = sum_col A[row][col] q_col for rows b*8+w, b*8+w+8*nb, ... (warp w of block b)
+__global__ void __launch_bounds__(NT) energy_rows_kernel(int M, int lda, const double *__restrict__ A,
+                                                         const double *__restrict__ q, double *__restrict__ y)
 {
-    double *y = scr;
-    double *part = scr + MAX_M;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double qAq = 0.0, bzq = 0.0, cq = 0.0;
     for (int row = blockIdx.x * (NT / 32) + w; row < M; row += gridDim.x * (NT / 32)) {
         const double *a = A + (size_t)row * lda;
         double s = 0.0;
         for (int col = lane; col < M; col += 32) s = fma(a[col], q[col], s);
         s = warp_sum(s);
-        if (lane == 0) {
-            y[row] = s;
-            qAq = fma(q[row], s, qAq);
-        }
+        if (lane == 0) y[row] = s;
     }
-    for (int k = blockIdx.x * NT + threadIdx.x; k < M; k += gridDim.x * NT) {
-        bzq = fma(Bz[k], q[k], bzq);
-        cq = fma(c[k], q[k], cq);
+}
+
+// E = (Bz)^T q + c^T q + q^T y / (2 f): each thread sums a strided slice,
+// then warps and the block combine in a fixed order.
+__global__ void __launch_bounds__(DOT_NT) energy_dots_kernel(int M, const double *__restrict__ y,
+                                                             const double *__restrict__ Bz,
+                                                             const double *__restrict__ c,
+                                                             const double *__restrict__ q, double f,
+                                                             double *__restrict__ E)
+{
+    double qAq = 0.0, bzq = 0.0, cq = 0.0;
+    for (int k = threadIdx.x; k < M; k += DOT_NT) {
+        const double qk = q[k];
+        qAq = fma(qk, y[k], qAq);
+        bzq = fma(Bz[k], qk, bzq);
+        cq = fma(c[k], qk, cq);
     }
-    __shared__ double sh[3][NT / 32];
     qAq = warp_sum(qAq);
     bzq = warp_sum(bzq);
     cq = warp_sum(cq);
+    __shared__ double sh[3][DOT_NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
         sh[0][w] = qAq;
         sh[1][w] = bzq;
         sh[2][w] = cq;
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
-        double t = 0.0;
-        for (int i = 0; i < NT / 32; ++i) t += sh[threadIdx.x][i];
-        part[threadIdx.x * MAX_BLOCKS + blockIdx.x] = t;
+    if (threadIdx.x == 0) {
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < DOT_NT / 32; ++i)
+            for (int j = 0; j < 3; ++j) t[j] += sh[j][i];
+        *E = t[1] + t[2] + t[0] / (2.0 * f);
     }
-}
-
-// E = (Bz)^T q + c^T q + q^T A q / (2 f), partials added in block order.
-__global__ void energy_finish_kernel(int nb, const double *__restrict__ scr, double f, double *__restrict__ E)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double *part = scr + MAX_M;
-    double qAq = 0.0, bzq = 0.0, cq = 0.0;
-    for (int b = 0; b < nb; ++b) {
-        qAq += part[b];
-        bzq += part[MAX_BLOCKS + b];
-        cq += part[2 * MAX_BLOCKS + b];
-    }
-    *E = bzq + cq + qAq / (2.0 * f);
 }
 
 // Device address of g_scratch on the current device, looked up once per
-// device with that device current.
+// device with that device current.  The address is kept for the life of the
+// process: the library must not be used across a reset of the device
+// (cudaDeviceReset), after which its device image may be loaded elsewhere.
 static int scratch_address(double **out)
 {
     int dev = -1;
@@ -134,15 +133,15 @@ extern "C" int pcm_energy_noalloc(int M, const double *A, int lda, const double 
                             "use pcm_energy", M, MAX_M);
         return PCM_ERR_ARG;
     }
-    double *scr = nullptr;
-    int st = scratch_address(&scr);
+    double *y = nullptr;
+    int st = scratch_address(&y);
     if (st != PCM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int nb = std::min(MAX_BLOCKS, (M + NT / 32 - 1) / (NT / 32));
-    energy_partials_kernel<<<nb, NT, 0, s>>>(M, lda, A, Bz, c, q, scr);
+    const int nb = std::min(ROW_BLOCKS, (M + NT / 32 - 1) / (NT / 32));
+    energy_rows_kernel<<<nb, NT, 0, s>>>(M, lda, A, q, y);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-        energy_finish_kernel<<<1, 32, 0, s>>>(nb, scr, f, E);
+        energy_dots_kernel<<<1, DOT_NT, 0, s>>>(M, y, Bz, c, q, f, E);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

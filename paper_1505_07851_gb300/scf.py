@@ -6,9 +6,9 @@ the DIIS errors e_n it reports, Eq. 1 is solved at every iteration with the
 CG threshold of one of three schemes:
 
   fixed    delta_tight at every iteration;
-  2delta   the "2-delta switching threshold": s * delta_tight until the
-           previous iteration's DIIS error has reached `switch` (1e-3),
-           then delta_tight (s = 1e4 in the paper);
+  2delta   the "2-delta switching threshold": 1e4 * delta_tight until the
+           previous iteration's DIIS error has reached 1e-3, then delta_tight
+           (pcm_solve with PCM_TWO_DELTA);
   dynamic  Eq. 21 from the previous DIIS error, evaluated by pcm_solve
            (delta = 1 at the first iteration, when there is none);
 
@@ -19,15 +19,7 @@ from __future__ import annotations
 SCHEMES = ("fixed", "2delta", "dynamic")
 
 
-def two_delta(prev_diis_error, delta_tight, s=1e4, switch=1e-3):
-    """Threshold of the 2-delta scheme for an iteration whose predecessor
-    reported `prev_diis_error` (None or negative: first iteration)."""
-    if prev_diis_error is None or prev_diis_error < 0 or prev_diis_error > switch:
-        return s * delta_tight
-    return delta_tight
-
-
-def run_sequence(ctx, seq, scheme, delta_tight=1e-6, s=1e4, switch=1e-3, warm=True, keep_q=False):
+def run_sequence(ctx, seq, scheme, delta_tight=1e-6, warm=True, keep_q=False):
     """Solve Eq. 1 along an SCF history on a Context whose surface and basis
     are set.  seq: [(P_n, e_n), ...] (NumPy arrays or CUDA tensors).
     Returns one record per iteration: the threshold used, the CG steps,
@@ -43,11 +35,12 @@ def run_sequence(ctx, seq, scheme, delta_tight=1e-6, s=1e4, switch=1e-3, warm=Tr
         if scheme == "fixed":
             delta, pe = delta_tight, -1.0
         elif scheme == "2delta":
-            delta, pe = two_delta(prev, delta_tight, s, switch), -1.0
+            delta, pe = delta_tight, prev
         else:
             delta, pe = -1.0, prev
         start = warm and q is not None
-        q, st = ctx.solve(delta=delta, prev_diis_error=pe, q=q if start else None, warm=start, like=P)
+        q, st = ctx.solve(delta=delta, prev_diis_error=pe, q=q if start else None, warm=start, like=P,
+                          two_delta=(scheme == "2delta"))
         E = ctx.energy(q)
         out.append({"iteration": n, "diis_error": e, "delta": st["delta"], "cg_steps": st["iterations"],
                     "converged": bool(st["converged"]), "energy": E, "solve_ms": st["ms_solve"],

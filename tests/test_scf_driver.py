@@ -6,15 +6,27 @@ import pytest
 import workloads
 
 
-def test_two_delta_rule():
-    from paper_1505_07851_gb300.scf import two_delta
-    # loose threshold s * delta_2 until the previous DIIS error reaches 1e-3
-    assert two_delta(None, 1e-6) == pytest.approx(1e-2)
-    assert two_delta(-1.0, 1e-6) == pytest.approx(1e-2)
-    assert two_delta(5e-3, 1e-6) == pytest.approx(1e-2)
-    assert two_delta(1e-3, 1e-6) == 1e-6
-    assert two_delta(2e-7, 1e-5) == 1e-5
-    assert two_delta(5e-3, 1e-7, s=1e3) == pytest.approx(1e-4)
+def test_threshold_rules_through_the_c_abi():
+    """pcm_cg_threshold is the rule pcm_solve applies (host logic, no GPU)."""
+    import paper_1505_07851_gb300 as pcm
+    th = pcm.cg_threshold
+    # 2-delta (Section 4b-i): 1e4 * delta_2 until the previous DIIS error reaches 1e-3
+    assert th(1e-6, -1.0, two_delta=True) == pytest.approx(1e-2)
+    assert th(1e-6, 5e-3, two_delta=True) == pytest.approx(1e-2)
+    assert th(1e-6, 1e-3, two_delta=True) == 1e-6
+    assert th(1e-5, 2e-7, two_delta=True) == 1e-5
+    # fixed
+    assert th(3e-7, 0.5) == 3e-7
+    # Eq. 21: Err(delta) = 0.01 delta^1.07 equals 1e-3 of the previous DIIS error
+    for e in (1e-1, 1e-3, 1e-5):
+        d = th(-1.0, e)
+        assert 0.01 * d ** 1.07 == pytest.approx(1e-3 * e, rel=1e-12)
+    assert th(-1.0, -1.0) == 1.0                  # first SCF step
+    assert th(0.0, 1e3) == 1.0                    # clamped above
+    assert th(-1.0, 1e-20) == 1e-10               # clamped below
+    for bad in ((float("nan"), 1.0, False), (1e-6, float("nan"), False), (0.0, 1e-2, True)):
+        with pytest.raises(pcm.PCMError):
+            th(bad[0], bad[1], two_delta=bad[2])
 
 
 def test_scf_sequence_approaches_the_density():
@@ -47,9 +59,9 @@ class _FakeContext:
     def esp(self, P):
         self.calls.append(("esp", float(np.sum(P))))
 
-    def solve(self, delta=-1.0, prev_diis_error=-1.0, q=None, warm=False, like=None):
-        d = delta if delta > 0 else (1.0 if prev_diis_error < 0 else
-                                     (1e-3 * prev_diis_error / 0.01) ** (1 / 1.07))
+    def solve(self, delta=-1.0, prev_diis_error=-1.0, q=None, warm=False, like=None, two_delta=False):
+        import paper_1505_07851_gb300 as pcm
+        d = pcm.cg_threshold(delta, prev_diis_error, two_delta)
         out = q if q is not None else np.zeros(self.M)
         self.calls.append(("solve", d, warm, None if q is None else q.copy()))
         out += 1.0                       # each solve moves the charges by one
@@ -61,7 +73,7 @@ class _FakeContext:
 
 @pytest.mark.parametrize("scheme", ["fixed", "2delta", "dynamic"])
 def test_run_sequence_thresholds_and_warm_starts(scheme):
-    from paper_1505_07851_gb300.scf import run_sequence, two_delta
+    from paper_1505_07851_gb300.scf import run_sequence
     seq = [(np.full((2, 2), float(n)), 0.1 * 0.4 ** n) for n in range(5)]
     ctx = _FakeContext()
     res = run_sequence(ctx, seq, scheme, delta_tight=1e-6, keep_q=True)
@@ -72,7 +84,7 @@ def test_run_sequence_thresholds_and_warm_starts(scheme):
         if scheme == "fixed":
             want = 1e-6
         elif scheme == "2delta":
-            want = two_delta(prev, 1e-6)
+            want = 1e-2 if (prev is None or prev > 1e-3) else 1e-6
         else:
             want = 1.0 if prev is None else (1e-3 * prev / 0.01) ** (1 / 1.07)
         assert r["delta"] == pytest.approx(want, rel=1e-12)
