@@ -90,6 +90,8 @@ struct PairClass {
     int nesp_same = 0;                     // the first nesp_same ESP pairs join primitives on one atom
     DBuf<double> eP, eD;                   // eP: 4 x nesp (Px, Py, Pz, p); eD: nherm x nesp
     DBuf<float> eX32, eC32;                // PCM_MIXED ESP: 6 x nesp split centres; ncls x (3 + 2 nherm) x nesp constants
+    DBuf<float> tfar, tnear;               // PCM_MIXED packed ESP: per 32-pair tile far block, near block per class
+    DBuf<float> fnear;                     // PCM_MIXED packed Fock: near constants per (class, pair)
     DBuf<float> Pxyz32;                    // 6 x npair: hi (3) and lo (3) FP32 parts of the centre (Fock, PCM_MIXED)
     DBuf<int> elist;                       // nesp: ESP pair -> kept pair index (valid after each ESP preparation)
     // shell pairs by atom for the gradient: entry 2 s + side (side 0: atom of A, 1: atom of B)
@@ -198,6 +200,13 @@ struct pcm_ctx {
     pcm::DBuf<int> si[8];
     pcm::DBuf<unsigned char> su8[2];
 
+    pcm::DBuf<int> dev_err;                // device error flag (a bounded wait in a kernel gave up)
+    // packed Fock: tiles of 128 points of one class (class and first point per tile), the per-call tile data
+    int fk_ntile = 0;
+    std::vector<int> h_fk_cls, h_fk_k0;
+    pcm::DBuf<int> fk_cls, fk_k0;
+    pcm::DBuf<float> fk_tiles;
+
     pcm_stats stats;
     cudaEvent_t ev_a[14], ev_b[14];         // timing events: 0-5 ESP classes, 6-11 Fock classes, 12 solve, 13 precond
     bool have_events = false;
@@ -224,6 +233,16 @@ int fock_compute(pcm_ctx *c, const double *dq, double *ddF);
 // PCM_MIXED (integrals_mixed.cu)
 int points_split(pcm_ctx *c);
 int esp_compute_mixed(pcm_ctx *c, double *dc);
+// packed FP32x2 ESP with the far-field path (esp_packed.cu): pairs [jbeg, jend) of class pc
+int esp_packed(pcm_ctx *c, PairClass &pc, int L, int ppt, int jbeg, int jend, const int *blk, const int *bcls,
+               int nblk, double *part);
+// packed FP32x2 Fock with the far-field path (fock_packed.cu)
+int fock_point_tiles_map(pcm_ctx *c);
+int fock_packed(pcm_ctx *c, int L, int npt, int npair, const double *gp, const float *Phl, DBuf<float> &nbuf,
+                const double *dq, int nsplit, double *W);
+// the device error flag: allocated and cleared on first use; check after a synchronisation
+int device_error_flag(pcm_ctx *c);
+int check_device_error(pcm_ctx *c, const char *where);
 int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt);
 int fock_mixed_pairs_per_thread(pcm_ctx *c, int L, long long npair);
 int grad_point_mixed(pcm_ctx *c, int *total_rows);

@@ -62,7 +62,7 @@ int points_split(pcm_ctx *c)
     point_split_kernel<<<(c->M + 127) / 128, 128, 0, c->stream>>>(c->M, c->px.p, c->py.p, c->pz.p, c->p32.p,
                                                                   c->p32lo.p);
     PCM_LAUNCHED(c);
-    return PCM_OK;
+    return fock_point_tiles_map(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -72,14 +72,14 @@ int points_split(pcm_ctx *c)
 //   eC[e][3 + h][j] = hi(U D_h), eC[e][3 + NH + h][j] = lo(U D_h)
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void esp_mixed_prep_kernel(int nesp, int ncls, const double *__restrict__ cls_zeta,
+__global__ void esp_mixed_prep_kernel(int nesp, int jend, int ncls, const double *__restrict__ cls_zeta,
                                       const double *__restrict__ eP, const double *__restrict__ eD,
                                       float *__restrict__ eX, float *__restrict__ eC)
 {
     constexpr int NH = nherm(L);
     constexpr int F = 3 + 2 * NH;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nesp) return;
+    if (j >= jend) return;
     for (int d = 0; d < 3; ++d) split_coord(eP[(size_t)d * nesp + j], eX[(size_t)d * nesp + j], eX[(size_t)(3 + d) * nesp + j]);
     const double p = eP[3 * (size_t)nesp + j];
     for (int e = 0; e < ncls; ++e) {
@@ -330,180 +330,6 @@ __global__ void __launch_bounds__(MESP_NT) esp_kernel_f32(int nesp, int jbeg, in
     }
 }
 
-// The cross-atom pairs with two pairs per instruction: pairs 2i and 2i+1 of
-// a tile occupy the two lanes of every packed value, the thread's points are
-// duplicated into both lanes, and the Kahan sums run per lane (even and odd
-// pairs) until the lanes are added in FP64 at the end.  Of the per-pair
-// constants, rho (in T and in (-2 rho)^n) and U D_000 carry their lo parts;
-// the higher Hermite coefficients U D_tuv enter as their FP32 roundings.
-// rho repeats exactly across the pairs of one element pair and exponent pair
-// (it depends on p and the class alone), so its rounding is shared by many
-// pairs and adds up in the energy: on the 1000-atom s/p/d cluster dropping
-// rho_lo moved the energy by 3.5e-7 Eh, dropping the lo part of U D_000 by
-// 1.2e-7 Eh on the 300-atom s/p/d cluster, while the lo parts of the higher
-// coefficients changed it by under 2e-9 Eh.  Shared memory per pair of pairs,
-// lane-interleaved: float4 (xh, yh), (zh, rho_hi), (xl, yl); float2 zl,
-// rho_lo, rho_lo / rho_hi, lo(U D_000) and NH float2 hi(U D_h).
-template <int L, int PPT>
-__global__ void __launch_bounds__(MESP_NT) esp_kernel_f32x2(int nesp, int jbeg, int jend, int seglen,
-                                                            const float *__restrict__ eX,
-                                                            const float *__restrict__ eC,
-                                                            const int *__restrict__ blk_off,
-                                                            const int *__restrict__ blk_cls,
-                                                            const float *__restrict__ ph,
-                                                            const float *__restrict__ pl,
-                                                            const float *__restrict__ boys, int M,
-                                                            double *__restrict__ part)
-{
-    constexpr int NH = nherm(L);
-    constexpr int F = 3 + 2 * NH;
-    constexpr int TP2 = MESP_TP / 2;
-    __shared__ float4 sXY[TP2], sZR[TP2], sXYl[TP2];
-    __shared__ float2 sZl[TP2], sRl[TP2], sDr[TP2], sD0l[TP2], sD[NH][TP2];
-    const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
-    const float *C = eC + (size_t)blk_cls[blockIdx.x] * F * nesp;
-    const int j0 = jbeg + blockIdx.y * seglen;
-    const int j1 = min(jend, j0 + seglen);
-
-    // the points, negated and duplicated into both lanes
-    f2 nxh[PPT], nyh[PPT], nzh[PPT], nxl[PPT], nyl[PPT], nzl[PPT];
-    f2 a32[PPT], k32[PPT];
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        const int k = min(k0 + (int)threadIdx.x + q * MESP_NT, k1 - 1);
-        nxh[q] = f2(-ph[k]);
-        nyh[q] = f2(-ph[(size_t)M + k]);
-        nzh[q] = f2(-ph[2 * (size_t)M + k]);
-        nxl[q] = f2(-pl[k]);
-        nyl[q] = f2(-pl[(size_t)M + k]);
-        nzl[q] = f2(-pl[2 * (size_t)M + k]);
-        a32[q] = k32[q] = f2(0.f);
-    }
-    // The next tile's pair data are read into registers while the current
-    // tile is computed: thread jj < MESP_TP holds pair jj's ten values, every
-    // thread NDPT of the tile's NH x MESP_TP coefficients.  Pair jj goes to
-    // slot jj / 2, lane jj % 2; an odd tile's last slot gets a dummy pair
-    // (rho = 1, D = 0) that contributes zero.
-    constexpr int NDPT = (NH * MESP_TP + MESP_NT - 1) / MESP_NT;
-    float pv[10], pd[NDPT];
-    auto fetch = [&](int jt) {
-        const int nt = min(MESP_TP, j1 - jt);
-        if (threadIdx.x < MESP_TP) {
-            const int jj = threadIdx.x;
-            const bool v = jj < nt;
-            const size_t j = jt + jj;
-            pv[0] = v ? eX[j] : 0.f;
-            pv[1] = v ? eX[(size_t)nesp + j] : 0.f;
-            pv[2] = v ? eX[2 * (size_t)nesp + j] : 0.f;
-            pv[3] = v ? C[j] : 1.f;
-            pv[4] = v ? eX[3 * (size_t)nesp + j] : 0.f;
-            pv[5] = v ? eX[4 * (size_t)nesp + j] : 0.f;
-            pv[6] = v ? eX[5 * (size_t)nesp + j] : 0.f;
-            pv[7] = v ? C[(size_t)nesp + j] : 0.f;
-            pv[8] = v ? C[2 * (size_t)nesp + j] : 0.f;
-            pv[9] = v ? C[(size_t)(3 + NH) * nesp + j] : 0.f;
-        }
-#pragma unroll
-        for (int i = 0; i < NDPT; ++i) {
-            const int t = threadIdx.x + i * MESP_NT;
-            const int h = t / MESP_TP, jj = t % MESP_TP;
-            pd[i] = (t < NH * MESP_TP && jj < nt) ? C[(size_t)(3 + h) * nesp + jt + jj] : 0.f;
-        }
-    };
-    fetch(j0);
-    for (int jt = j0; jt < j1; jt += MESP_TP) {
-        const int nt = min(MESP_TP, j1 - jt);
-        __syncthreads();
-        if (threadIdx.x < MESP_TP) {
-            const int jj = threadIdx.x, s = jj >> 1, l = jj & 1;
-            float *xy = reinterpret_cast<float *>(&sXY[s]), *zr = reinterpret_cast<float *>(&sZR[s]);
-            float *xyl = reinterpret_cast<float *>(&sXYl[s]);
-            xy[l] = pv[0];
-            xy[2 + l] = pv[1];
-            zr[l] = pv[2];
-            zr[2 + l] = pv[3];
-            xyl[l] = pv[4];
-            xyl[2 + l] = pv[5];
-            reinterpret_cast<float *>(&sZl[s])[l] = pv[6];
-            reinterpret_cast<float *>(&sRl[s])[l] = pv[7];
-            reinterpret_cast<float *>(&sDr[s])[l] = pv[8];
-            reinterpret_cast<float *>(&sD0l[s])[l] = pv[9];
-        }
-#pragma unroll
-        for (int i = 0; i < NDPT; ++i) {
-            const int t = threadIdx.x + i * MESP_NT;
-            if (t < NH * MESP_TP) {
-                const int h = t / MESP_TP, jj = t % MESP_TP;
-                reinterpret_cast<float *>(&sD[h][jj >> 1])[jj & 1] = pd[i];
-            }
-        }
-        __syncthreads();
-        if (jt + MESP_TP < j1) fetch(jt + MESP_TP);
-        const int np = (nt + 1) >> 1;
-        for (int s = 0; s < np; ++s) {
-            const float4 xy = sXY[s], zr = sZR[s], xyl = sXYl[s];
-            const float2 zl = sZl[s];
-            const f2 Ax(xy.x, xy.y), Ay(xy.z, xy.w), Az(zr.x, zr.y), rh(zr.z, zr.w);
-            const f2 Bx(xyl.x, xyl.y), By(xyl.z, xyl.w), Bz(zl.x, zl.y);
-            const float2 rlo = sRl[s], d0l = sD0l[s];
-            const f2 rl(rlo.x, rlo.y), D0l(d0l.x, d0l.y);
-            const f2 m2r = rh * f2(-2.f);
-            f2 ndr[L + 1];
-            if constexpr (L > 0) {
-                const float2 dr = sDr[s];
-#pragma unroll
-                for (int n = 1; n <= L; ++n) ndr[n] = f2((float)n) * f2(dr.x, dr.y);
-            }
-#pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                const f2 X = (Ax + nxh[q]) + (Bx + nxl[q]);
-                const f2 Y = (Ay + nyh[q]) + (By + nyl[q]);
-                const f2 Z = (Az + nzh[q]) + (Bz + nzl[q]);
-                const f2 R2 = fma2(X, X, fma2(Y, Y, Z * Z));
-                const f2 T = fma2(rh, R2, rl * R2);
-                f2 Fb[L + 1];
-                boys_eval2<L>(T, boys, Fb);
-                f2 dot;
-                if constexpr (L == 0) {
-                    const float2 D = sD[0][s];
-                    dot = fma2(f2(D.x, D.y), Fb[0], D0l * Fb[0]);
-                } else {
-                    // R^(n) = (-2 rho)^n F_n, rho = rho_hi (1 + rho_lo / rho_hi)
-                    f2 Rn[L + 1];
-                    Rn[0] = Fb[0];
-                    f2 f = m2r;
-#pragma unroll
-                    for (int n = 1; n <= L; ++n) {
-                        const f2 v = f * Fb[n];
-                        Rn[n] = fma2(v, ndr[n], v);
-                        if (n < L) f = f * m2r;
-                    }
-                    f2 R[NH];
-                    hermite_R<L, f2>(X, Y, Z, Rn, R);
-                    const float2 D0 = sD[0][s];
-                    dot = fma2(f2(D0.x, D0.y), R[0], D0l * R[0]);
-#pragma unroll
-                    for (int h = 1; h < NH; ++h) {
-                        const float2 D = sD[h][s];
-                        dot = fma2(f2(D.x, D.y), R[h], dot);
-                    }
-                }
-                const f2 y = dot - k32[q];
-                const f2 t = a32[q] + y;
-                k32[q] = (t - a32[q]) - y;
-                a32[q] = t;
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-        const int k = k0 + threadIdx.x + q * MESP_NT;
-        if (k < k1)
-            part[(size_t)blockIdx.y * M + k] =
-                ((double)a32[q].v.x - (double)k32[q].v.x) + ((double)a32[q].v.y - (double)k32[q].v.y);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Fock: NPT primitive pairs per thread (the point data staged in shared memory
 // serve them all); per class rho and U in FP64 (hi/lo for rho), per point tile
@@ -628,153 +454,6 @@ __global__ void __launch_bounds__(MF_NT) fock_kernel_f32(int npair, const double
             for (int i = 0; i < NPT; ++i)
 #pragma unroll
                 for (int h = 0; h < NH; ++h) w64[i][h] = fma(U[i], (double)w32[i][h], w64[i][h]);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < NPT; ++i)
-        if (active[i]) {
-#pragma unroll
-            for (int h = 0; h < NH; ++h) W[((size_t)blockIdx.y * NH + h) * npair + r[i]] = w64[i][h];
-        }
-}
-
-// The same contraction with two points per packed instruction: points 2i and
-// 2i+1 of a tile occupy the two lanes, the thread's pairs are duplicated into
-// both lanes, and each lane's tile sums are added in FP64 (times U) at the end
-// of the tile.  rho carries its lo part (its rounding is shared by every pair
-// of the same exponents and adds up, as noted at esp_kernel_f32x2).  The points are staged negated and lane-interleaved: float4
-// (-xh, -yh), (-zh, q), (-xl, -yl) and float2 (-zl) per pair of points; past
-// the end of the range a point has q = 0 and contributes zero.
-template <int L, int NPT>
-__global__ void __launch_bounds__(MF_NT) fock_kernel_f32x2(int npair, const double *__restrict__ gp,
-                                                           const float *__restrict__ Phl, int ksplit,
-                                                           const float *__restrict__ ph, const float *__restrict__ pl,
-                                                           const double *__restrict__ q, int M, int ncls,
-                                                           const int *__restrict__ cls_off,
-                                                           const double *__restrict__ cls_zeta,
-                                                           const float *__restrict__ boys, double *__restrict__ W)
-{
-    constexpr int NH = nherm(L);
-    constexpr int TQ2 = MF_TQ / 2;
-    __shared__ float4 sXY[TQ2], sZQ[TQ2], sXYl[TQ2];
-    __shared__ float2 sZl[TQ2];
-    int r[NPT];
-    bool active[NPT];
-    f2 Pxh[NPT], Pyh[NPT], Pzh[NPT], Pxl[NPT], Pyl[NPT], Pzl[NPT];
-    double p[NPT];
-    double w64[NPT][NH];
-#pragma unroll
-    for (int i = 0; i < NPT; ++i) {
-        r[i] = (blockIdx.x * NPT + i) * MF_NT + threadIdx.x;
-        active[i] = r[i] < npair;
-        const int rr = active[i] ? r[i] : 0;
-        Pxh[i] = f2(Phl[rr]);
-        Pyh[i] = f2(Phl[(size_t)npair + rr]);
-        Pzh[i] = f2(Phl[2 * (size_t)npair + rr]);
-        Pxl[i] = f2(Phl[3 * (size_t)npair + rr]);
-        Pyl[i] = f2(Phl[4 * (size_t)npair + rr]);
-        Pzl[i] = f2(Phl[5 * (size_t)npair + rr]);
-        p[i] = gp[rr];
-#pragma unroll
-        for (int h = 0; h < NH; ++h) w64[i][h] = 0.0;
-    }
-    const int ka = blockIdx.y * ksplit;
-    const int kb = min(M, ka + ksplit);
-    const int sl = threadIdx.x >> 1, ln = threadIdx.x & 1;
-    for (int ec = 0; ec < ncls; ++ec) {
-        const int a = max(ka, cls_off[ec]), b = min(kb, cls_off[ec + 1]);
-        if (a >= b) continue;
-        const double z2 = cls_zeta[ec] * cls_zeta[ec];
-        double U[NPT];
-        f2 rh[NPT], rl[NPT], ndr[NPT][L + 1], m2r[NPT];
-#pragma unroll
-        for (int i = 0; i < NPT; ++i) {
-            const double inv = 1.0 / (p[i] + z2);
-            const double rho = p[i] * z2 * inv;
-            U[i] = sqrt(z2 * inv);
-            const float h = (float)rho;
-            rh[i] = f2(h);
-            rl[i] = f2((float)(rho - (double)h));
-            const float dr = (float)((rho - (double)h) / (double)h);
-#pragma unroll
-            for (int n = 1; n <= L; ++n) ndr[i][n] = f2((float)n * dr);
-            m2r[i] = f2(-2.f * h);
-        }
-        // this thread's point of the first tile (negated coordinates)
-        float4 nH = make_float4(0.f, 0.f, 0.f, 0.f), nL = nH;
-        if (a + (int)threadIdx.x < b) {
-            const int k = a + threadIdx.x;
-            nH = make_float4(-ph[k], -ph[(size_t)M + k], -ph[2 * (size_t)M + k], (float)q[k]);
-            nL = make_float4(-pl[k], -pl[(size_t)M + k], -pl[2 * (size_t)M + k], 0.f);
-        }
-        for (int t0 = a; t0 < b; t0 += MF_TQ) {
-            const int nt = min(MF_TQ, b - t0);
-            __syncthreads();
-            {
-                float *xy = reinterpret_cast<float *>(&sXY[sl]), *zq = reinterpret_cast<float *>(&sZQ[sl]);
-                float *xyl = reinterpret_cast<float *>(&sXYl[sl]);
-                xy[ln] = nH.x;
-                xy[2 + ln] = nH.y;
-                zq[ln] = nH.z;
-                zq[2 + ln] = nH.w;
-                xyl[ln] = nL.x;
-                xyl[2 + ln] = nL.y;
-                reinterpret_cast<float *>(&sZl[sl])[ln] = nL.z;
-            }
-            __syncthreads();
-            // prefetch the next tile while this one is computed
-            if (t0 + MF_TQ + (int)threadIdx.x < b) {
-                const int k = t0 + MF_TQ + threadIdx.x;
-                nH = make_float4(-ph[k], -ph[(size_t)M + k], -ph[2 * (size_t)M + k], (float)q[k]);
-                nL = make_float4(-pl[k], -pl[(size_t)M + k], -pl[2 * (size_t)M + k], 0.f);
-            } else {
-                nH = make_float4(0.f, 0.f, 0.f, 0.f);
-                nL = nH;
-            }
-            f2 w32[NPT][NH];
-#pragma unroll
-            for (int i = 0; i < NPT; ++i)
-#pragma unroll
-                for (int h = 0; h < NH; ++h) w32[i][h] = f2(0.f);
-            const int np = (nt + 1) >> 1;
-            for (int s = 0; s < np; ++s) {
-                const float4 xy = sXY[s], zq = sZQ[s], xyl = sXYl[s];
-                const float2 zl = sZl[s];
-                const f2 Hx(xy.x, xy.y), Hy(xy.z, xy.w), Hz(zq.x, zq.y), Q(zq.z, zq.w);
-                const f2 Lx(xyl.x, xyl.y), Ly(xyl.z, xyl.w), Lz(zl.x, zl.y);
-#pragma unroll
-                for (int i = 0; i < NPT; ++i) {
-                    const f2 X = (Pxh[i] + Hx) + (Pxl[i] + Lx);
-                    const f2 Y = (Pyh[i] + Hy) + (Pyl[i] + Ly);
-                    const f2 Z = (Pzh[i] + Hz) + (Pzl[i] + Lz);
-                    const f2 R2 = fma2(X, X, fma2(Y, Y, Z * Z));
-                    const f2 T = fma2(rh[i], R2, rl[i] * R2);
-                    f2 Fb[L + 1];
-                    boys_eval2<L>(T, boys, Fb);
-                    if constexpr (L == 0) {
-                        w32[i][0] = fma2(Q, Fb[0], w32[i][0]);
-                    } else {
-                        // q_k (-2 rho)^n F_n
-                        f2 Rn[L + 1];
-                        f2 f = Q;
-#pragma unroll
-                        for (int n = 0; n <= L; ++n) {
-                            const f2 v = f * Fb[n];
-                            Rn[n] = (n == 0) ? v : fma2(v, ndr[i][n], v);
-                            if (n < L) f = f * m2r[i];
-                        }
-                        f2 R[NH];
-                        hermite_R<L, f2>(X, Y, Z, Rn, R);
-#pragma unroll
-                        for (int h = 0; h < NH; ++h) w32[i][h] += R[h];
-                    }
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < NPT; ++i)
-#pragma unroll
-                for (int h = 0; h < NH; ++h)
-                    w64[i][h] = fma(U[i], (double)w32[i][h].v.x + (double)w32[i][h].v.y, w64[i][h]);
         }
     }
 #pragma unroll
@@ -1168,14 +847,18 @@ static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, co
     constexpr int NH = nherm(L);
     constexpr int F = 3 + 2 * NH;
     const int n = pc.nesp;
+    // same-atom pairs [0, nesp_same) in double-float, the rest in FP32 (the
+    // packed kernel prepares its own tiles for those)
+    const int ns = pc.nesp_same, nx = n - ns;
+    const int nprep = PACKED ? ns : n;
     PCM_TRY(pc.eX32.alloc(6 * (size_t)n));
     PCM_TRY(pc.eC32.alloc((size_t)c->ncls * F * n));
-    esp_mixed_prep_kernel<L><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->ncls, c->cls_zeta.p, pc.eP.p, pc.eD.p,
-                                                                     pc.eX32.p, pc.eC32.p);
-    PCM_LAUNCHED(c);
+    if (nprep > 0) {
+        esp_mixed_prep_kernel<L><<<(nprep + 127) / 128, 128, 0, c->stream>>>(n, nprep, c->ncls, c->cls_zeta.p,
+                                                                             pc.eP.p, pc.eD.p, pc.eX32.p, pc.eC32.p);
+        PCM_LAUNCHED(c);
+    }
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[k], c->stream));
-    // same-atom pairs [0, nesp_same) in double-float, the rest in FP32
-    const int ns = pc.nesp_same, nx = n - ns;
     int sl, rows;
     esp_plan(ns, nblk, &sl, &rows);
     if (rows > 0) {
@@ -1188,14 +871,14 @@ static int esp_mixed_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, co
     esp_plan(nx, nblk, &sl, &rows);
     if (rows > 0) {
         dim3 grid(nblk, rows);
-        if constexpr (PACKED)
-            esp_kernel_f32x2<L, PPT><<<grid, MESP_NT, 0, c->stream>>>(n, ns, n, sl, pc.eX32.p, pc.eC32.p, blk, bcls,
-                                                                      c->p32.p, c->p32lo.p, c->boys32.p, c->M, part);
-        else
+        if constexpr (PACKED) {
+            PCM_TRY(esp_packed(c, pc, L, PPT, ns, n, blk, bcls, nblk, part));
+        } else {
             esp_kernel_f32<L, false, PPT><<<grid, MESP_NT, 0, c->stream>>>(n, ns, n, sl, pc.eX32.p, pc.eC32.p, blk,
                                                                             bcls, c->p32.p, c->p32lo.p, c->boys32.p,
                                                                             c->M, part);
-        PCM_LAUNCHED(c);
+            PCM_LAUNCHED(c);
+        }
     }
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[k], c->stream));
     return PCM_OK;
@@ -1255,7 +938,7 @@ static int esp_ms_launch(pcm_ctx *c, PairClass &pc, int k, const int *blk, const
     const int n = pc.nesp;
     PCM_TRY(pc.eX32.alloc(6 * (size_t)n));
     PCM_TRY(pc.eC32.alloc((size_t)c->ncls * F * n));
-    esp_mixed_prep_kernel<L><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->ncls, c->cls_zeta.p, pc.eP.p, pc.eD.p,
+    esp_mixed_prep_kernel<L><<<(n + 127) / 128, 128, 0, c->stream>>>(n, n, c->ncls, c->cls_zeta.p, pc.eP.p, pc.eD.p,
                                                                      pc.eX32.p, pc.eC32.p);
     PCM_LAUNCHED(c);
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[k], c->stream));
@@ -1407,29 +1090,22 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
     esp_reduce_mixed_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
     PCM_LAUNCHED(c);
     PCM_CUDA(cudaStreamSynchronize(c->stream));  // the class timers are read next
-    return PCM_OK;
+    return check_device_error(c, "pcm_esp");
 }
 
 int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt)
 {
     PairClass &pc = c->cls[k];
-    // the packed kernel with two pairs per thread would spill for the dd class
-    if (c->opt.fp32x2 && CLASS_L[k] >= 4) npt = 1;
+    // the packed kernel with two pairs per thread would spill for L >= 3
+    if (c->opt.fp32x2 && CLASS_L[k] >= 3) npt = 1;
     const int per = MF_NT * npt;
     const int nb = (pc.npair + per - 1) / per;
     dim3 grid(nb, nsplit);
+    if (c->opt.fp32x2) return fock_packed(c, CLASS_L[k], npt, pc.npair, pc.p.p, pc.Pxyz32.p, pc.fnear, dq, nsplit, W);
     switch (CLASS_L[k]) {
 #define PCM_FOCK_F32(LL)                                                                                           \
     case LL:                                                                                                       \
-        if (c->opt.fp32x2 && npt == 2)                                                                             \
-            fock_kernel_f32x2<LL, 2><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit,        \
-                                                                     c->p32.p, c->p32lo.p, dq, c->M, c->ncls,      \
-                                                                     c->cls_off.p, c->cls_zeta.p, c->boys32.p, W); \
-        else if (c->opt.fp32x2)                                                                                    \
-            fock_kernel_f32x2<LL, 1><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit,        \
-                                                                     c->p32.p, c->p32lo.p, dq, c->M, c->ncls,      \
-                                                                     c->cls_off.p, c->cls_zeta.p, c->boys32.p, W); \
-        else if (npt == 2)                                                                                         \
+        if (npt == 2)                                                                                              \
             fock_kernel_f32<LL, 2><<<grid, MF_NT, 0, c->stream>>>(pc.npair, pc.p.p, pc.Pxyz32.p, ksplit, c->p32.p, \
                                                                    c->p32lo.p, dq, c->M, c->ncls, c->cls_off.p,    \
                                                                    c->cls_zeta.p, c->boys32.p, W);                 \
@@ -1461,7 +1137,7 @@ static int grad_point_mixed_class(pcm_ctx *c, PairClass &pc, const int *blk, con
     const int n = pc.nesp;
     PCM_TRY(pc.eX32.alloc(6 * (size_t)n));
     PCM_TRY(pc.eC32.alloc((size_t)c->ncls * F * n));
-    esp_mixed_prep_kernel<L><<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->ncls, c->cls_zeta.p, pc.eP.p, pc.eD.p,
+    esp_mixed_prep_kernel<L><<<(n + 127) / 128, 128, 0, c->stream>>>(n, n, c->ncls, c->cls_zeta.p, pc.eP.p, pc.eD.p,
                                                                      pc.eX32.p, pc.eC32.p);
     PCM_LAUNCHED(c);
     dim3 grid(nblk, rows);
@@ -1524,19 +1200,6 @@ static void grad_w_launch(pcm_ctx *c, PairClass &pc, const double *dq, dim3 grid
 {
     const int n = pc.nesp;
     const double *gp = pc.eP.p + 3 * (size_t)n;
-    if constexpr (LL <= 4) {
-        if (c->opt.fp32x2) {
-            if (npt == 2 && LL < 4)
-                fock_kernel_f32x2<LL, 2><<<grid, MF_NT, 0, c->stream>>>(n, gp, pc.eX32.p, ksplit, c->p32.p,
-                                                                         c->p32lo.p, dq, c->M, c->ncls,
-                                                                         c->cls_off.p, c->cls_zeta.p, c->boys32.p, W);
-            else
-                fock_kernel_f32x2<LL, 1><<<grid, MF_NT, 0, c->stream>>>(n, gp, pc.eX32.p, ksplit, c->p32.p,
-                                                                         c->p32lo.p, dq, c->M, c->ncls,
-                                                                         c->cls_off.p, c->cls_zeta.p, c->boys32.p, W);
-            return;
-        }
-    }
     if (npt == 2)
         fock_kernel_f32<LL, 2><<<grid, MF_NT, 0, c->stream>>>(n, gp, pc.eX32.p, ksplit, c->p32.p, c->p32lo.p, dq, c->M,
                                                                c->ncls, c->cls_off.p, c->cls_zeta.p, c->boys32.p, W);
@@ -1546,8 +1209,8 @@ static void grad_w_launch(pcm_ctx *c, PairClass &pc, const double *dq, dim3 grid
 }
 
 // W accumulation of the integral gradient: the Fock contraction with R up to
-// L + 1 over the ESP pairs (packed two points per instruction up to L + 1 = 4;
-// one pair per thread from L + 1 = 4 on, where two would spill)
+// L + 1 over the ESP pairs (the packed far-field kernel of fock_packed.cu by
+// default; one pair per thread from L + 1 = 4 on)
 int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt)
 {
     PairClass &pc = c->cls[k];
@@ -1556,6 +1219,8 @@ int grad_w_mixed(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, do
     const int per = MF_NT * npt;
     const int nb = (pc.nesp + per - 1) / per;
     dim3 grid(nb, nsplit);
+    if (c->opt.fp32x2)
+        return fock_packed(c, L1, npt, pc.nesp, pc.eP.p + 3 * (size_t)pc.nesp, pc.eX32.p, pc.fnear, dq, nsplit, W);
     switch (L1) {
     case 1: grad_w_launch<1>(c, pc, dq, grid, ksplit, W, npt); break;
     case 2: grad_w_launch<2>(c, pc, dq, grid, ksplit, W, npt); break;

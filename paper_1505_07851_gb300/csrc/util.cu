@@ -216,3 +216,30 @@ int compact_flags(pcm_ctx *c, const unsigned char *flags, long long n, int *out,
 }
 
 }  // namespace pcm
+
+namespace pcm {
+
+int device_error_flag(pcm_ctx *c)
+{
+    if (c->dev_err.p) return PCM_OK;
+    PCM_TRY(c->dev_err.alloc(1));
+    PCM_CUDA(cudaMemsetAsync(c->dev_err.p, 0, sizeof(int), c->stream));
+    return PCM_OK;
+}
+
+// Read the device error flag after the stream has been synchronised: a kernel
+// whose bounded wait gave up set it (and returned without its results).
+int check_device_error(pcm_ctx *c, const char *where)
+{
+    if (!c->dev_err.p) return PCM_OK;
+    int h = 0;
+    PCM_CUDA(cudaMemcpy(&h, c->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        PCM_CUDA(cudaMemset(c->dev_err.p, 0, sizeof(int)));
+        set_last_error("%s: a bounded device wait gave up (a bulk copy into shared memory did not complete)", where);
+        return PCM_ERR_TIMEOUT;
+    }
+    return PCM_OK;
+}
+
+}  // namespace pcm

@@ -2,14 +2,18 @@
 configuration bench.py times (Schwarz screening 1e-12, RBJ-100, the Eq. 21
 threshold for a 1e-6 Eh energy error), against the oracle on sampled
 outputs it computes one by one, and against properties that hold at any
-size.  Tolerances: unscreened FP64 1e-10 relative (normwise); screened FP64
-1e-8 (screening drops pairs with Schwarz bound below 1e-12); mixed 1e-6;
+size.  Tolerances, element by element (tests/_parity.py): unscreened FP64
+rtol 1e-10 / atol 1e-12; screened FP64 rtol 1e-8 / atol 1e-10 (screening
+drops pairs with Schwarz bound below 1e-12); mixed rtol 1e-6 / atol 1e-7;
 energies 1e-6 Eh against the FP64 solve at delta = 1e-10."""
 import numpy as np
 import pytest
 
 import oracle
 import workloads
+from _parity import FP64, MIXED, check
+
+SCREENED = (1e-8, 1e-10)
 
 pytestmark = pytest.mark.gpu
 
@@ -49,12 +53,11 @@ def test_surface_size_and_order(full):
 def test_esp_sampled_against_oracle(full):
     rng = np.random.default_rng(11)
     s, p = full["surf"], full["perm"]
-    sample = rng.choice(len(p), 24, replace=False)
+    sample = rng.choice(len(p), 64, replace=False)
     ref = oracle.esp(full["eb"], full["w"].P, s["r"][p[sample]], s["zeta"][p[sample]])
-    scale = np.max(np.abs(ref))
-    for name, tol in (("noscreen", 1e-10), ("fp64", 1e-8), ("mixed", 1e-6)):
-        err = np.max(np.abs(full[name]["c"][sample] - ref)) / scale
-        assert err <= tol, (name, err)
+    scale = np.max(np.abs(full["noscreen"]["c"]))
+    for name, bars in (("noscreen", FP64), ("fp64", SCREENED), ("mixed", MIXED)):
+        check(full[name]["c"][sample], ref, bars, scale=scale, what="c " + name)
 
 
 def test_fock_sampled_against_oracle(full):
@@ -62,16 +65,17 @@ def test_fock_sampled_against_oracle(full):
     eb, s, p = full["eb"], full["surf"], full["perm"]
     pairs = [tuple(sorted(rng.choice(eb.nshell, 2, replace=False))) for _ in range(10)]
     pairs += [(a, a) for a in rng.choice(eb.nshell, 4, replace=False)]
-    for name, tol in (("noscreen", 1e-10), ("fp64", 1e-8), ("mixed", 1e-6)):
+    for name, bars in (("noscreen", FP64), ("fp64", SCREENED), ("mixed", MIXED)):
         g = full[name]
         q_o = np.empty_like(g["q"])
         q_o[p] = g["q"]
         blocks = oracle.fock_blocks(eb, q_o, s["r"], s["zeta"], pairs)
         scale = np.max(np.abs(g["dF"]))
-        for (a, b), blk in zip(pairs, blocks):
-            ia, ib = eb.sh_bf[a], eb.sh_bf[b]
-            got = g["dF"][ia:ia + blk.shape[0], ib:ib + blk.shape[1]]
-            assert np.max(np.abs(got - blk)) <= tol * scale, (name, a, b)
+        got = np.concatenate([g["dF"][eb.sh_bf[a]:eb.sh_bf[a] + blk.shape[0],
+                                      eb.sh_bf[b]:eb.sh_bf[b] + blk.shape[1]].ravel()
+                              for (a, b), blk in zip(pairs, blocks)])
+        ref = np.concatenate([blk.ravel() for blk in blocks])
+        check(got, ref, bars, scale=scale, what="dF " + name)
 
 
 def test_energy_at_the_eq21_threshold(full):
