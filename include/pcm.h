@@ -67,6 +67,7 @@ typedef enum pcm_status {
 #define PCM_GRAD_C 16           /* pcm_gradient: include (d*c^T/dR) q (the integrals) */
 #define PCM_GRAD_A 32           /* pcm_gradient: include q^T (dA/dR) q / (2 f) (with switching) */
 #define PCM_TWO_DELTA 64        /* pcm_solve: delta is delta_2 of the 2-delta threshold scheme (Section 4b-i) */
+#define PCM_APPLY_FP32 128      /* pcm_apply_a: the inner solver's FP32 matrix-free product (PCM_MIXED) */
 
 /* precision modes */
 #define PCM_FP64 0              /* every step in FP64 */
@@ -101,8 +102,16 @@ typedef struct pcm_options {
                                    4 points per thread, 1 with 2, 2 MS-driven (s and p classes; others default) */
     int fp32x2;                 /* PCM_MIXED: 1 (default) evaluates two primitive pairs (ESP) or two points (Fock)
                                    per packed FP32x2 instruction (FADD2/FMUL2/FFMA2; each lane rounded as the
-                                   scalar instruction); 0 scalar FP32 instructions (same arithmetic per lane) */
+                                   scalar instruction); 0 scalar FP32 instructions (the general form for every
+                                   interaction, no far-field path) */
+    int operator_mode;          /* PCM_MIXED operator A: PCM_OPERATOR_AUTO (default), _STORED or _FREE */
 } pcm_options;
+
+/* operator modes (PCM_MIXED; PCM_FP64 always stores A) */
+#define PCM_OPERATOR_AUTO 0     /* matrix-free above 24576 points or when the stored parts would take more than a
+                                   quarter of the free device memory, else stored */
+#define PCM_OPERATOR_STORED 1   /* A stored in FP64 and as FP32 hi + lo parts (16 bytes per element) */
+#define PCM_OPERATOR_FREE 2     /* no stored A: near pairs kept exactly, every other element 1/R recomputed */
 
 typedef struct pcm_stats {
     int iterations;             /* PCG iterations of the last solve */
@@ -128,6 +137,7 @@ typedef struct pcm_stats {
     long long launches;         /* kernels launched by this context since its creation */
     double integrals_grad;      /* equivalent Cartesian primitive integrals of the last pcm_gradient (two passes) */
     double ms_grad;             /* with timing: device time of the last pcm_gradient (ms) */
+    int operator_free;          /* 1 if the current surface's PCM_MIXED solver is matrix-free (no stored A) */
 } pcm_stats;
 
 typedef struct pcm_ctx pcm_ctx;
@@ -213,6 +223,17 @@ int pcm_fock(pcm_ctx *ctx, const double *q, double *dF, int flags);
  * E = (Bz)^T q + c^T q + q^T A q / (2 f).  q, c: M inputs (c may be NULL
  * for the last pcm_esp result).  E: one host double. */
 int pcm_energy(pcm_ctx *ctx, const double *q, const double *c, double *E, int flags);
+
+/* y = A x with the context's operator (Eq. 2, Eq. 3, Eq. 8) for its current
+ * surface: x, y are M-vectors in library point order.  PCM_FP64 multiplies
+ * by the stored FP64 A.  PCM_MIXED keeps no A: pairs with zeta' R below a
+ * cutoff (the diagonal included) are held with their FP64 values, every other
+ * element is 1/R recomputed per product; the default product is the one the
+ * solver forms true residuals and the energy with (double-float 1/R, FP64
+ * near pairs, about 1e-14 relative), PCM_APPLY_FP32 the inner solver's FP32
+ * product (about 1e-6 relative).  flags: PCM_PTR_DEVICE, PCM_ASYNC,
+ * PCM_APPLY_FP32 (PCM_ERR_UNSUPPORTED for a PCM_FP64 context). */
+int pcm_apply_a(pcm_ctx *ctx, const double *x, double *y, int flags);
 
 /* Nuclear gradient of the solvation energy at fixed density and charges
  * (Eq. 14; its integral term split as in Eq. 22), in hartree/bohr:

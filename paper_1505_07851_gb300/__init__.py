@@ -45,9 +45,11 @@ PCM_GRAD_B = 8
 PCM_GRAD_C = 16
 PCM_GRAD_A = 32
 PCM_TWO_DELTA = 64
+PCM_APPLY_FP32 = 128
 PCM_FP64 = 0
 PCM_MIXED = 1
 PRECOND = {"auto": 0, "none": 1, "jacobi": 2, "rbj": 3, "octree": 4}
+OPERATOR = {"auto": 0, "stored": 1, "free": 2}   # pcm_options.operator_mode (PCM_MIXED)
 
 
 class pcm_options(ctypes.Structure):
@@ -57,7 +59,7 @@ class pcm_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("device", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("octree_leaf", ctypes.c_int), ("esp_variant", ctypes.c_int),
-                ("fp32x2", ctypes.c_int)]
+                ("fp32x2", ctypes.c_int), ("operator_mode", ctypes.c_int)]
 
 
 class pcm_stats(ctypes.Structure):
@@ -69,7 +71,7 @@ class pcm_stats(ctypes.Structure):
                 ("esp_class_pairs", ctypes.c_longlong * 6), ("fock_class_pairs", ctypes.c_longlong * 6),
                 ("ms_esp_class", ctypes.c_double * 6), ("ms_fock_class", ctypes.c_double * 6),
                 ("ms_solve", ctypes.c_double), ("ms_precond", ctypes.c_double), ("launches", ctypes.c_longlong),
-                ("integrals_grad", ctypes.c_double), ("ms_grad", ctypes.c_double)]
+                ("integrals_grad", ctypes.c_double), ("ms_grad", ctypes.c_double), ("operator_free", ctypes.c_int)]
 
     def as_dict(self):
         out = {}
@@ -118,6 +120,7 @@ def _load():
         "pcm_autotune_table": (i, [vp, i]),
         "pcm_energy_noalloc": (i, [i, vp, i, vp, vp, vp, d, vp, vp]),
         "pcm_cg_threshold": (i, [d, d, i, ctypes.POINTER(d)]),
+        "pcm_apply_a": (i, [vp, vp, vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -225,7 +228,8 @@ class Context:
 
     def __init__(self, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
                  precond="auto", jacobi_below=1000, precision="fp64", max_iter=5000, device=0, seed=0,
-                 stream=None, timing=False, autotune=False, octree_leaf=800, esp_variant=-1, fp32x2=True):
+                 stream=None, timing=False, autotune=False, octree_leaf=800, esp_variant=-1, fp32x2=True,
+                 operator="auto"):
         o = pcm_options()
         _lib.pcm_default_options(ctypes.byref(o))
         o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
@@ -238,6 +242,7 @@ class Context:
         o.octree_leaf = int(octree_leaf)
         o.esp_variant = int(esp_variant)
         o.fp32x2 = 1 if fp32x2 else 0
+        o.operator_mode = OPERATOR[operator]
         h = ctypes.c_void_p()
         self._check(_lib.pcm_create(ctypes.byref(h), ctypes.byref(o)), "pcm_create")
         self._h = h
@@ -351,6 +356,17 @@ class Context:
         E = ctypes.c_double()
         self._check(_lib.pcm_energy(self._h, pq, pc, ctypes.byref(E), fl), "pcm_energy")
         return E.value
+
+    def apply_a(self, x, out=None, fp32=False):
+        """y = A x (pcm_apply_a): the solver's accurate product, or with fp32
+        the FP32 matrix-free product of the inner PCM_MIXED solver."""
+        px, fl, keep = _ptr(x, np.float64)
+        y = out if out is not None else self._out(x, (self.M,))
+        py, fly, keepy = _ptr(y, np.float64)
+        if fly != fl:
+            raise TypeError("x and y must live on the same side (host or device)")
+        self._check(_lib.pcm_apply_a(self._h, px, py, fl | (PCM_APPLY_FP32 if fp32 else 0)), "pcm_apply_a")
+        return y
 
     def gradient(self, q, P=None, out=None, terms="BCA", async_=False):
         """Nuclear gradient (natom, 3) of Eq. 13 at fixed P and q (Eq. 14):

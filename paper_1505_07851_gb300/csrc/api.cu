@@ -130,6 +130,7 @@ int pcm_default_options(pcm_options *o)
     o->octree_leaf = 800;
     o->esp_variant = -1;
     o->fp32x2 = 1;
+    o->operator_mode = PCM_OPERATOR_AUTO;
     return PCM_OK;
 }
 
@@ -143,7 +144,7 @@ int pcm_create(pcm_ctx **out, const pcm_options *opt)
     if (!(o.eps > 1.0) || !(o.zeta > 0.0) || o.rbj_block < 1 || o.max_iter < 1 || o.switch_drop < 0.0 ||
         o.schwarz < 0.0 || (o.precision != PCM_FP64 && o.precision != PCM_MIXED) || o.precond < 0 || o.precond > 4 ||
         (o.precond == PCM_PRECOND_OCTREE && o.octree_leaf < 1) || o.esp_variant < -1 || o.esp_variant > 2 ||
-        (o.fp32x2 != 0 && o.fp32x2 != 1)) {
+        (o.fp32x2 != 0 && o.fp32x2 != 1) || o.operator_mode < 0 || o.operator_mode > 2) {
         set_last_error("invalid pcm_options");
         return PCM_ERR_ARG;
     }
@@ -454,6 +455,31 @@ int pcm_energy(pcm_ctx *c, const double *q, const double *cv, double *E, int fla
     else dcv = c->c_last.p;
     PCM_TRY(energy_compute(c, dq, dcv, E));
     return PCM_OK;
+}
+
+int pcm_apply_a(pcm_ctx *c, const double *x, double *y, int flags)
+{
+    if (!c || !x || !y || c->M == 0) {
+        set_last_error("pcm_apply_a: bad arguments");
+        return PCM_ERR_ARG;
+    }
+    if ((flags & PCM_APPLY_FP32) && !matrix_free(c)) {
+        set_last_error("pcm_apply_a: the FP32 product is the matrix-free operator of PCM_MIXED contexts");
+        return PCM_ERR_UNSUPPORTED;
+    }
+    DeviceGuard g(c->device);
+    const double *dx;
+    DBuf<double> &stx = c->sd[3];
+    PCM_TRY(to_device(c, x, c->M, stx, &dx, flags));
+    double *dy = y;
+    if (!(flags & PCM_PTR_DEVICE)) {
+        PCM_TRY(c->vout.alloc(c->M));
+        dy = c->vout.p;
+    }
+    PCM_TRY(apply_a(c, dx, dy, (flags & PCM_APPLY_FP32) != 0));
+    if (!(flags & PCM_PTR_DEVICE))
+        PCM_CUDA(cudaMemcpyAsync(y, dy, c->M * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return finish(c, flags);
 }
 
 int pcm_gradient(pcm_ctx *c, const double *P, const double *q, double *grad, int flags)

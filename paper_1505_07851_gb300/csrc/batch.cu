@@ -691,6 +691,7 @@ int pcm_batch_create(pcm_batch **out, const pcm_options *opt, int nmol)
             cudaSetDevice(prev);
             return s;
         }
+        bt->mol[m]->store_a = true;   // the lockstep solver reads each molecule's stored A
     }
     cudaSetDevice(prev);
     *out = bt;

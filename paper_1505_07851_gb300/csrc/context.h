@@ -201,6 +201,18 @@ struct pcm_ctx {
     pcm::DBuf<unsigned char> su8[2];
 
     pcm::DBuf<int> dev_err;                // device error flag (a bounded wait in a kernel gave up)
+    // matrix-free A (PCM_MIXED): FP32 coordinates, near pairs (CSR, exact values), solver scratch
+    bool store_a = false;                  // keep the stored A and its FP32 parts instead (batch members)
+    bool mf_active = false;                // this surface's PCM_MIXED solver is matrix-free (set per surface)
+    float mf_rc2 = 0.f;
+    int mf_nnz = 0, mf_grid = 0;
+    size_t mf_grid_smem = 0;
+    pcm::DBuf<float4> mf_pts;
+    pcm::DBuf<int> mf_off, mf_cnt, mf_col, mf_out, mf_iperm;
+    pcm::DBuf<double> mf_val, mf_y64, mf_idot, mf_red, mf_rn;
+    pcm::DBuf<float> mf_val32, mf_p32, mf_ypart;
+    pcm::DBuf<float2> mf_xs;
+    pcm::DBuf<unsigned> mf_bar;
     // packed Fock: tiles of 128 points of one class (class and first point per tile), the per-call tile data
     int fk_ntile = 0;
     std::vector<int> h_fk_cls, h_fk_k0;
@@ -240,6 +252,16 @@ int esp_packed(pcm_ctx *c, PairClass &pc, int L, int ppt, int jbeg, int jend, co
 int fock_point_tiles_map(pcm_ctx *c);
 int fock_packed(pcm_ctx *c, int L, int npt, int npair, const double *gp, const float *Phl, DBuf<float> &nbuf,
                 const double *dq, int nsplit, double *W);
+// matrix-free A for PCM_MIXED (matfree.cu)
+struct AFree;
+AFree afree(pcm_ctx *c);
+int zeta_pairs(pcm_ctx *c, cudaStream_t s);
+int matfree_build(pcm_ctx *c, cudaStream_t s);
+int matfree_dfmv(pcm_ctx *c, const double *x, double *y, double *part, int *nparts);
+int matfree_mv32(pcm_ctx *c, const double *x, double *y);
+int matfree_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max_iter, int *iters, int *conv,
+                double *rnorm);
+inline bool matrix_free(const pcm_ctx *c) { return c->mf_active; }
 // the device error flag: allocated and cleared on first use; check after a synchronisation
 int device_error_flag(pcm_ctx *c);
 int check_device_error(pcm_ctx *c, const char *where);
@@ -257,6 +279,7 @@ void octree_partition(const std::vector<double> &x, const std::vector<double> &y
                       int leaf, std::vector<int> &perm, std::vector<int> &start);
 int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st);
 int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E);
+int apply_a(pcm_ctx *c, const double *x, double *y, bool fp32);
 // gradient (gradient.cu, integrals.cu)
 int esp_prepare_all(pcm_ctx *c, const double *dP);
 int grad_integrals(pcm_ctx *c, const double *dP, const double *dq, double *gk, double *gpair);

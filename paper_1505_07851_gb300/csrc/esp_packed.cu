@@ -22,8 +22,10 @@
 // grid) + lo so every distance is the FP32 rounding of the exact one; 1/R by
 // the hardware reciprocal square root and one Newton step; the dominant
 // coefficient (Q_0, the charge term; U D_000 in the general form) carries its
-// lo part; every interaction is added with Kahan compensation, per lane, and
-// the lanes are added in FP64 at the end.
+// lo part; every interaction is added with Kahan compensation, per lane (the
+// compensation keeps the small terms that a plain FP32 running sum would drop,
+// always towards a smaller magnitude for terms of one sign), and the lanes
+// are added in FP64 at the end.
 #include <math.h>
 
 #include <algorithm>
@@ -32,6 +34,7 @@
 #include "common.cuh"
 #include "context.h"
 #include "f2.cuh"
+#include "fastmath.cuh"
 #include "farfield.cuh"
 #include "pipeline.cuh"
 
@@ -138,7 +141,7 @@ __device__ __forceinline__ f2 far_value(f2 X, f2 Y, f2 Z, f2 R2, const float2 *_
     constexpr int NC = far_nterms(L);
     constexpr FarTerms FT = far_terms(L);
     // 1/R: hardware estimate and one Newton step, rs = r0 (1 + e/2), e = 1 - R^2 r0^2
-    const f2 r0(rsqrtf(R2.v.x), rsqrtf(R2.v.y));
+    const f2 r0(rsqrt_fast(R2.v.x), rsqrt_fast(R2.v.y));
     const f2 em = fma2(R2 * r0, r0, f2(-1.f));
     const f2 rs = fma2(r0 * f2(-0.5f), em, r0);
     const float2 g0 = sG[s], g0l = sG[PK_NS * NC + s];
@@ -238,9 +241,8 @@ __device__ __forceinline__ f2 near_value(f2 X, f2 Y, f2 Z, f2 R2, const float4 *
 // tiles [blockIdx.y * tps, ...) of the class's cross-atom pairs; partial sums
 // to part[blockIdx.y][k].
 // resident blocks per SM the register allocation aims for
-// resident blocks per SM the register allocation aims for (L = 1: four blocks
-// measured 2% faster than five, which spill)
-constexpr int pk_min_blocks(int L, int PPT) { return PPT == 4 ? 2 : (L == 0 ? 7 : (L == 1 ? 4 : (L == 2 ? 4 : 3))); }
+// resident blocks per SM the register allocation aims for (without spills)
+constexpr int pk_min_blocks(int L, int PPT) { return PPT == 4 ? 2 : (L == 0 ? 7 : (L == 1 ? 5 : (L == 2 ? 4 : 3))); }
 
 template <int L, int PPT>
 __global__ void __launch_bounds__(PK_NT, pk_min_blocks(L, PPT)) esp_kernel_f32x2(int ntile, int tps, const float *__restrict__ far,

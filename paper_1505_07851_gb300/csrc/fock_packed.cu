@@ -16,8 +16,8 @@
 // lane-interleaved (points 2s and 2s+1 of slot s in the two lanes), in global
 // memory exactly as in shared memory; one thread streams the tiles into a
 // ring of three buffers with bulk copies (pipeline.cuh).  Tile sums run in
-// FP32 per lane (64 points), are added across the lanes and into double-float
-// (FP32 hi + lo) accumulators after every tile.
+// FP32 per lane (64 points) and go into double-float (FP32 hi + lo)
+// accumulators after every tile.
 #include <math.h>
 
 #include <algorithm>
@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "context.h"
 #include "f2.cuh"
+#include "fastmath.cuh"
 #include "farfield.cuh"
 #include "pipeline.cuh"
 
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(FK_NT, fk_min_blocks(L, NPT))
 #pragma unroll
             for (int i = 0; i < NPT; ++i) {
                 // far form: q (-1)^n (2n-1)!! R^-(2n+1), 1/R with one Newton step
-                const f2 r0(rsqrtf(R2[i].v.x), rsqrtf(R2[i].v.y));
+                const f2 r0(rsqrt_fast(R2[i].v.x), rsqrt_fast(R2[i].v.y));
                 const f2 em = fma2(R2[i] * r0, r0, f2(-1.f));
                 const f2 rs = fma2(r0 * f2(-0.5f), em, r0);
                 f2 Rn[L + 1];
@@ -258,15 +259,16 @@ __global__ void __launch_bounds__(FK_NT, fk_min_blocks(L, NPT))
                 }
             }
         }
-        // fold the tile: both lanes, then into the double-float accumulators
+        // fold the tile: each lane into the double-float accumulators
 #pragma unroll
         for (int i = 0; i < NPT; ++i)
 #pragma unroll
             for (int h = 0; h < NH; ++h) {
-                float s, e2;
-                two_sum_f(ah[i][h], w32[i][h].v.x + w32[i][h].v.y, s, e2);
-                ah[i][h] = s;
-                al[i][h] += e2;
+                float s, e2, s2, e3;
+                two_sum_f(ah[i][h], w32[i][h].v.x, s, e2);
+                two_sum_f(s, w32[i][h].v.y, s2, e3);
+                ah[i][h] = s2;
+                al[i][h] += e2 + e3;
             }
         ring.release(j);
     }

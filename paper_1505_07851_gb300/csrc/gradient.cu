@@ -208,9 +208,11 @@ __global__ void __launch_bounds__(GAO_NT) grad_aoff_kernel(int M, int lda, const
     }
 }
 
-// The same on the FP32 pipes (PCM_MIXED) from the FP32 copy of A and the
-// hi/lo split coordinates (hi on a 2^-10 grid, so hi differences are exact);
-// per-thread FP32 sums, the block reduction in FP64.
+// The same on the FP32 pipes (PCM_MIXED) from the hi/lo split coordinates
+// (hi on a 2^-10 grid, so hi differences are exact), with A_kl from the FP32
+// copy of A when one is stored (A != null), else evaluated in FP32 (1/R, or
+// erf(zeta' R) / R where zeta' R <= 6); per-thread FP32 sums, the block
+// reduction in FP64.
 __global__ void __launch_bounds__(GAO_NT) grad_aoff_kernel_f32(int M, int lda, const float *__restrict__ A,
                                                                const float *__restrict__ ph,
                                                                const float *__restrict__ pl,
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(GAO_NT) grad_aoff_kernel_f32(int M, int lda, c
     __syncthreads();
     const float xh = ph[k], yh = ph[(size_t)M + k], zh = ph[2 * (size_t)M + k];
     const float xl = pl[k], yl = pl[(size_t)M + k], zl = pl[2 * (size_t)M + k];
-    const float *row = A + (size_t)k * lda;
+    const float *row = A ? A + (size_t)k * lda : nullptr;
     float a[3] = {0.f, 0.f, 0.f};
     for (int l = threadIdx.x; l < M; l += GAO_NT) {
         if (l == k) continue;
@@ -240,7 +242,6 @@ __global__ void __launch_bounds__(GAO_NT) grad_aoff_kernel_f32(int M, int lda, c
         const float dy = (yh - ph[(size_t)M + l]) + (yl - pl[(size_t)M + l]);
         const float dz = (zh - ph[2 * (size_t)M + l]) + (zl - pl[2 * (size_t)M + l]);
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float Akl = row[l];
         const int cl = pcls[l];
         float zp, zp2;
         if (ncls <= 16) {
@@ -253,6 +254,13 @@ __global__ void __launch_bounds__(GAO_NT) grad_aoff_kernel_f32(int M, int lda, c
             zp2 = (float)(z * z);
         }
         const float x2 = zp2 * d2;
+        float Akl;
+        if (row) {
+            Akl = row[l];
+        } else {
+            const float rs = rsqrtf(d2);
+            Akl = (x2 > 36.f) ? rs : erff(zp * (d2 * rs)) * rs;
+        }
         const float t = (x2 > 36.f) ? -Akl * Akl * Akl
                                     : (1.1283791670955126f * zp * __expf(-x2) - Akl) / d2;
         const float w = (float)q[l] * t;
@@ -317,8 +325,9 @@ int gradient_compute(pcm_ctx *c, const double *dP, const double *dq, int terms, 
     PCM_LAUNCHED(c);
     // off-diagonal A
     if (terms & PCM_GRAD_A) {
-        if (c->opt.precision == PCM_MIXED && c->a32_ready) {
-            grad_aoff_kernel_f32<<<M, GAO_NT, 0, c->stream>>>(M, c->lda, c->A32.p, c->p32.p, c->p32lo.p, c->pcls.p,
+        if (c->opt.precision == PCM_MIXED) {
+            const float *A32 = matrix_free(c) ? nullptr : c->A32.p;
+            grad_aoff_kernel_f32<<<M, GAO_NT, 0, c->stream>>>(M, c->lda, A32, c->p32.p, c->p32lo.p, c->pcls.p,
                                                               c->ncls, c->cls_zeta.p, dq, 1.0 / f, c->g_pt.p);
         } else {
             grad_aoff_kernel<<<M, GAO_NT, 0, c->stream>>>(M, c->lda, c->A.p, c->px.p, c->py.p, c->pz.p, c->pcls.p,

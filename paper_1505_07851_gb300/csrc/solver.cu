@@ -23,6 +23,8 @@
 
 #include "common.cuh"
 #include "context.h"
+#include "aelem.cuh"
+#include "rbj_apply.cuh"
 #include "gemv.cuh"
 
 namespace pcm {
@@ -213,69 +215,6 @@ __global__ void __launch_bounds__(UP_NT) pcg_update_diag_kernel(int M, const dou
     }
 }
 
-constexpr int RBJ_SPLIT = 4;   // threads per row in the block-Jacobi apply
-
-// Randomized block-Jacobi apply for RBJ block b: its indices are
-// perm[b*l .. b*l + nb) and its inverse is inv[b] (l x l, symmetric).  Unless
-// init, first x += alpha p and r -= alpha Ap on the block's indices; then
-// z = Minv r there.  Returns the block's r.r and r.z in thread 0.
-__device__ __forceinline__ void rbj_apply_block(int M, int l, int b, const int *__restrict__ perm,
-                                                const int *__restrict__ bstart, const double *__restrict__ inv,
-                                                double *__restrict__ x, double *__restrict__ r,
-                                                double *__restrict__ z, const double *__restrict__ p,
-                                                const double *__restrict__ Ap, double alpha, int init, double *srb,
-                                                double *rr_out, double *rz_out)
-{
-    const int base = bstart ? bstart[b] : b * l;
-    const int nb = bstart ? bstart[b + 1] - base : min(l, M - base);
-    double rr = 0.0, rz = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        const int k = perm[base + i];
-        double rk = r[k];
-        if (!init) {
-            x[k] = fma(alpha, p[k], x[k]);
-            rk = fma(-alpha, Ap[k], rk);
-            r[k] = rk;
-        }
-        srb[i] = rk;
-    }
-    __syncthreads();
-    const double *Mi = inv + (size_t)b * l * l;
-    // z_i = sum_j Minv_ji r_j (Minv symmetric): RBJ_SPLIT threads share a row,
-    // each summing every RBJ_SPLIT-th column, combined by shuffles
-    const int sub = threadIdx.x % RBJ_SPLIT;
-    for (int i0 = threadIdx.x / RBJ_SPLIT; i0 < ((nb + 31) / 32) * 32; i0 += blockDim.x / RBJ_SPLIT) {
-        const int i = i0;
-        double s = 0.0;
-        if (i < nb)
-            for (int j = sub; j < nb; j += RBJ_SPLIT) s = fma(Mi[(size_t)j * l + i], srb[j], s);
-#pragma unroll
-        for (int o = RBJ_SPLIT / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (sub == 0 && i < nb) {
-            z[perm[base + i]] = s;
-            rr = fma(srb[i], srb[i], rr);
-            rz = fma(srb[i], s, rz);
-        }
-    }
-    __shared__ double sh[2][32];
-    rr = warp_sum(rr);
-    rz = warp_sum(rz);
-    if ((threadIdx.x & 31) == 0) {
-        sh[0][threadIdx.x >> 5] = rr;
-        sh[1][threadIdx.x >> 5] = rz;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, c = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            a += sh[0][i];
-            c += sh[1][i];
-        }
-        *rr_out = a;
-        *rz_out = c;
-    }
-}
-
 // Randomized block-Jacobi update, one block per RBJ block; the last block
 // to finish sums the partials.  With init (initialisation) x and r are left
 // unchanged.
@@ -403,10 +342,12 @@ __global__ void __launch_bounds__(GV_NT) gemv_df_kernel(int M, int lda, const fl
 
 // y = A x with the stored A: FP64, or double-float from A32 + A32lo when the
 // context is PCM_MIXED and they exist; block partials of x.y in part
-static int gemv_a(pcm_ctx *c, const double *x, double *y, double *part)
+static int gemv_a(pcm_ctx *c, const double *x, double *y, double *part, int *np)
 {
     const int M = c->M;
     const int gv = std::max(1, (M + 1) / 2);
+    if (np) *np = gv;
+    if (matrix_free(c)) return matfree_dfmv(c, x, y, part, np);
     if (c->opt.precision == PCM_MIXED && c->a32_ready) {
         // hi part at 0, lo part at lda (a multiple of 32 floats): both start on
         // the 16-byte boundary the GEMV's float4 loads need
@@ -421,6 +362,17 @@ static int gemv_a(pcm_ctx *c, const double *x, double *y, double *part)
     }
     PCM_LAUNCHED(c);
     return PCM_OK;
+}
+
+// y = A x for pcm_apply_a: the solver's accurate product (FP64 stored A, or
+// double-float from A32 + A32lo or matrix-free), or with fp32 the inner
+// solver's FP32 matrix-free product
+int apply_a(pcm_ctx *c, const double *x, double *y, bool fp32)
+{
+    PCM_TRY(join_side(c));
+    if (fp32) return matfree_mv32(c, x, y);
+    PCM_TRY(c->red.alloc(2 * (size_t)std::max(MAX_PART, std::max(1, (c->M + 1) / 2))));
+    return gemv_a(c, x, y, c->red.p, nullptr);
 }
 
 // r = b - y and per-block partial sums of r.r
@@ -567,17 +519,14 @@ __device__ __forceinline__ int rbj_block_scan(int v, int *sh /* RBJ_NT/32 + 1 */
 constexpr int RBJ_NBIN = 2048;   // histogram of the top 11 bits of the FP32 key
 constexpr int RBJ_LMAX = 3072;   // boundary-bin elements resolved exactly in shared memory
 
-// key of |A_kj| for ordering: FP64 bits (|A| >= 0, so bit order = value order)
-__device__ __forceinline__ unsigned long long rbj_key64(double a) { return (unsigned long long)__double_as_longlong(fabs(a)); }
-// coarse bin: top 11 bits of the FP32 value (monotone in |A|)
-__device__ __forceinline__ int rbj_bin(double a) { return (int)(__float_as_uint((float)fabs(a)) >> 20); }
 
 // The points are walked in their canonical order (the surface candidate index
 // I n + i: atom-major, the order of the points before they are grouped by
 // exponent class), so that the pivots and the ties of the selection, and with
 // them the blocks, do not depend on how the library stores the points.  pidx:
 // candidate index of each stored point; T: scratch of ncand ints.
-__global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const double *__restrict__ A, int l,
+template <typename AE>
+__global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, AE acc, int l,
                                                           unsigned long long seed, const int *__restrict__ pidx,
                                                           long long ncand, int *__restrict__ T,
                                                           int *__restrict__ U, int *__restrict__ U2,
@@ -633,12 +582,11 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
         __syncthreads();
         const int k = s_k;
         const int nsel = min(l - 1, nU - 1);
-        const double *row = A + (size_t)k * lda;
         if (nsel > 0) {
             // 1. coarse histogram
             for (int i = threadIdx.x; i < nU; i += RBJ_NT) {
                 const int j = U[i];
-                if (j != k) atomicAdd(&hist[rbj_bin(row[j])], 1u);
+                if (j != k) atomicAdd(&hist[acc.bin(k, j)], 1u);
             }
             __syncthreads();
             // 2. bin holding the nsel-th largest key: warp 0 scans from the top, 64 bins per lane
@@ -669,10 +617,10 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
             const int bstar = s_bin;
             for (int i = threadIdx.x; i < nU; i += RBJ_NT) {
                 const int j = U[i];
-                if (j != k && rbj_bin(row[j]) == bstar) {
+                if (j != k && acc.bin(k, j) == bstar) {
                     const int p = atomicAdd(&s_nlist, 1);
                     if (p < RBJ_LMAX) {
-                        lkey[p] = rbj_key64(row[j]);
+                        lkey[p] = rbj_key64(acc.exact(k, j));
                         lidx[p] = pidx[j];
                     }
                 }
@@ -709,7 +657,7 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
                 j = U[i];
                 if (j != k) {
                     if (nsel > 0) {
-                        const int bn = rbj_bin(row[j]);
+                        const int bn = acc.bin(k, j);
                         if (bn > bstar) {
                             sel = 1;
                         } else if (bn == bstar) {
@@ -744,7 +692,8 @@ __global__ void __launch_bounds__(RBJ_NT) rbj_perm_kernel(int M, int lda, const 
 
 // In-place Cholesky of one l x l block (lower), then the inverse by solving
 // L L^T X = I column by column.  One thread block per RBJ block.
-__global__ void rbj_invert_kernel(int M, int lda, const double *__restrict__ A, int l, const int *__restrict__ perm,
+template <typename AE>
+__global__ void rbj_invert_kernel(int M, AE acc, int l, const int *__restrict__ perm,
                                   const int *__restrict__ bstart, double *__restrict__ work, double *__restrict__ inv,
                                   int *__restrict__ status)
 {
@@ -756,7 +705,7 @@ __global__ void rbj_invert_kernel(int M, int lda, const double *__restrict__ A, 
     double *X = inv + (size_t)b * l * l;
     for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
         const int i = t / nb, j = t % nb;
-        W[(size_t)i * l + j] = A[(size_t)perm[base + i] * lda + perm[base + j]];
+        W[(size_t)i * l + j] = acc.exact(perm[base + i], perm[base + j]);
     }
     __syncthreads();
     __shared__ double dkk;
@@ -873,14 +822,23 @@ static int rbj_build(pcm_ctx *c, cudaStream_t s)
     PCM_CUDA(cudaMemsetAsync(c->rbj_status.p, 0, 16 * sizeof(int), s));
     const long long ncand = (long long)c->natom * c->npts_sphere;
     PCM_TRY(c->rbj_T.alloc(ncand));
-    rbj_perm_kernel<<<1, RBJ_NT, 0, s>>>(M, c->lda, c->A.p, l, c->opt.seed, c->pindex.p, ncand, c->rbj_T.p,
-                                         c->rbj_U.p, c->rbj_U2.p, c->rbj_perm.p, c->rbj_status.p);
+    if (matrix_free(c))
+        rbj_perm_kernel<AFree><<<1, RBJ_NT, 0, s>>>(M, afree(c), l, c->opt.seed, c->pindex.p, ncand, c->rbj_T.p,
+                                                    c->rbj_U.p, c->rbj_U2.p, c->rbj_perm.p, c->rbj_status.p);
+    else
+        rbj_perm_kernel<AStored><<<1, RBJ_NT, 0, s>>>(M, AStored{c->A.p, c->lda}, l, c->opt.seed, c->pindex.p, ncand,
+                                                      c->rbj_T.p, c->rbj_U.p, c->rbj_U2.p, c->rbj_perm.p,
+                                                      c->rbj_status.p);
     PCM_LAUNCHED(c);
     PCM_TRY(c->rbj_inv.alloc((size_t)c->rbj_nblk * l * l));
     PCM_TRY(c->rbj_work.alloc((size_t)c->rbj_nblk * l * l));
     const int nt = std::min(1024, std::max(32, (l + 31) / 32 * 32));
-    rbj_invert_kernel<<<c->rbj_nblk, nt, 0, s>>>(M, c->lda, c->A.p, l, c->rbj_perm.p, nullptr, c->rbj_work.p,
-                                                 c->rbj_inv.p, c->rbj_status.p);
+    if (matrix_free(c))
+        rbj_invert_kernel<AFree><<<c->rbj_nblk, nt, 0, s>>>(M, afree(c), l, c->rbj_perm.p, nullptr, c->rbj_work.p,
+                                                            c->rbj_inv.p, c->rbj_status.p);
+    else
+        rbj_invert_kernel<AStored><<<c->rbj_nblk, nt, 0, s>>>(M, AStored{c->A.p, c->lda}, l, c->rbj_perm.p, nullptr,
+                                                              c->rbj_work.p, c->rbj_inv.p, c->rbj_status.p);
     PCM_LAUNCHED(c);
     return PCM_OK;
 }
@@ -897,7 +855,10 @@ int operator_build_async(pcm_ctx *c)
     PCM_CUDA(cudaEventRecord(c->ev_fork, c->stream));
     PCM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[13], c->side));
-    PCM_TRY(a_build(c, c->side));
+    if (matrix_free(c))
+        PCM_TRY(matfree_build(c, c->side));
+    else
+        PCM_TRY(a_build(c, c->side));
     const int kind = precond_kind(c);
     c->side_rbj = false;
     if (kind != PCM_PRECOND_OCTREE) {   // the octree partition needs the points on the host: built at the solve
@@ -907,7 +868,7 @@ int operator_build_async(pcm_ctx *c)
             c->side_rbj = true;
         }
         c->pc_ready = true;
-        if (c->opt.precision == PCM_MIXED && !c->a32_ready) PCM_TRY(a32_build(c, c->side));
+        if (c->opt.precision == PCM_MIXED && !matrix_free(c) && !c->a32_ready) PCM_TRY(a32_build(c, c->side));
     }
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[13], c->side));
     PCM_CUDA(cudaEventRecord(c->ev_side, c->side));
@@ -970,9 +931,15 @@ int solver_prepare(pcm_ctx *c)
         PCM_TRY(c->rbj_status.alloc(16));
         PCM_CUDA(cudaMemsetAsync(c->rbj_status.p, 0, sizeof(int), c->stream));
         const int nt = std::min(1024, std::max(32, (lmax + 31) / 32 * 32));
-        rbj_invert_kernel<<<c->rbj_nblk, nt, 0, c->stream>>>(M, c->lda, c->A.p, lmax, c->rbj_perm.p,
-                                                             c->rbj_bstart.p, c->rbj_work.p, c->rbj_inv.p,
-                                                             c->rbj_status.p);
+        if (matrix_free(c))
+            rbj_invert_kernel<AFree><<<c->rbj_nblk, nt, 0, c->stream>>>(M, afree(c), lmax, c->rbj_perm.p,
+                                                                        c->rbj_bstart.p, c->rbj_work.p, c->rbj_inv.p,
+                                                                        c->rbj_status.p);
+        else
+            rbj_invert_kernel<AStored><<<c->rbj_nblk, nt, 0, c->stream>>>(M, AStored{c->A.p, c->lda}, lmax,
+                                                                          c->rbj_perm.p, c->rbj_bstart.p,
+                                                                          c->rbj_work.p, c->rbj_inv.p,
+                                                                          c->rbj_status.p);
         PCM_LAUNCHED(c);
         int st = 0;
         PCM_CUDA(cudaMemcpyAsync(&st, c->rbj_status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -998,7 +965,7 @@ int solver_prepare(pcm_ctx *c)
 int solver_prepare_full(pcm_ctx *c)
 {
     PCM_TRY(solver_prepare(c));
-    if (c->opt.precision == PCM_MIXED && !c->a32_ready) PCM_TRY(a32_build(c, c->stream));
+    if (c->opt.precision == PCM_MIXED && !matrix_free(c) && !c->a32_ready) PCM_TRY(a32_build(c, c->stream));
     return PCM_OK;
 }
 
@@ -1160,7 +1127,7 @@ static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double
 static int true_residual(pcm_ctx *c, const double *b, const double *x, double *r, double *norm)
 {
     const int M = c->M;
-    if (x) PCM_TRY(gemv_a(c, x, c->vtmp.p, c->red.p));
+    if (x) PCM_TRY(gemv_a(c, x, c->vtmp.p, c->red.p, nullptr));
     const int nb = std::min(256, (M + 255) / 256);
     residual_kernel<<<nb, 256, 0, c->stream>>>(M, b, x ? c->vtmp.p : nullptr, r, c->red.p);
     PCM_LAUNCHED(c);
@@ -1208,12 +1175,15 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
         PCM_TRY(pcg_core(c, drhs, c->vd.p, warm, delta, c->opt.max_iter, false, &iters, &conv, &rnorm));
         PCM_CUDA(cudaMemcpyAsync(dq, c->vd.p, M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     } else {
-        // FP64 iterative refinement around FP32-GEMV inner solves: the true
-        // residual b - A x is formed with the FP64 A, each inner solve reduces
-        // it by ETA (or to delta / 2), and x accumulates the corrections
-        constexpr double ETA = 1e-3;
+        // FP64 iterative refinement around FP32 inner solves: the true
+        // residual b - A x is formed in double-float, each inner solve reduces
+        // it by ETA (or to delta / 2), and x accumulates the corrections.  The
+        // matrix-free inner solve goes further per refinement (its FP32
+        // operator is accurate to ~1e-7, and every refinement restarts CG and
+        // costs a double-float product)
+        const double ETA = matrix_free(c) ? 1e-6 : 1e-3;
         constexpr int MAX_REFINE = 12;
-        if (!c->a32_ready) PCM_TRY(a32_build(c, c->stream));
+        if (!matrix_free(c) && !c->a32_ready) PCM_TRY(a32_build(c, c->stream));
         PCM_TRY(c->vro.alloc(M));
         PCM_TRY(c->vd.alloc(M));
         if (!warm) PCM_CUDA(cudaMemsetAsync(dq, 0, M * sizeof(double), c->stream));
@@ -1227,8 +1197,12 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
             int it_in = 0, conv_in = 0;
             double rn_in = 0.0;
             const double tol = std::max(ETA * rnorm, 0.5 * delta);
-            PCM_TRY(pcg_core(c, c->vro.p, c->vd.p, false, tol, std::max(1, c->opt.max_iter - iters), true, &it_in,
-                             &conv_in, &rn_in));
+            if (matrix_free(c))
+                PCM_TRY(matfree_pcg(c, c->vro.p, c->vd.p, tol, std::max(1, c->opt.max_iter - iters), &it_in, &conv_in,
+                                    &rn_in));
+            else
+                PCM_TRY(pcg_core(c, c->vro.p, c->vd.p, false, tol, std::max(1, c->opt.max_iter - iters), true,
+                                 &it_in, &conv_in, &rn_in));
             iters += it_in;
             ++refinements;
             const int eb = std::min(1024, (M + 255) / 256);
@@ -1283,15 +1257,16 @@ int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E)
     DBuf<double> &part2 = c->sd[1];
     const int nb = std::min(1024, (M + 255) / 256);
     PCM_TRY(part2.alloc(2 * nb));
-    PCM_TRY(gemv_a(c, dq, c->vtmp.p, c->red.p));
+    int np = gv;
+    PCM_TRY(gemv_a(c, dq, c->vtmp.p, c->red.p, &np));
     dot2_kernel<<<nb, 256, 0, c->stream>>>(M, c->Bz.p, dcv, dq, part2.p);
     PCM_LAUNCHED(c);
-    std::vector<double> h1(gv), h2(2 * nb);
-    PCM_CUDA(cudaMemcpyAsync(h1.data(), c->red.p, gv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double> h1(np), h2(2 * nb);
+    PCM_CUDA(cudaMemcpyAsync(h1.data(), c->red.p, np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaMemcpyAsync(h2.data(), part2.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
     double qAq = 0.0, bzq = 0.0, cq = 0.0;
-    for (int i = 0; i < gv; ++i) qAq += h1[i];
+    for (int i = 0; i < np; ++i) qAq += h1[i];
     for (int i = 0; i < nb; ++i) {
         bzq += h2[2 * i];
         cq += h2[2 * i + 1];

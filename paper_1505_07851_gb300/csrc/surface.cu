@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "context.h"
 
 namespace pcm {
@@ -243,45 +244,6 @@ __global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, co
 // 3e-14 relative; the FP32 split of the coordinates limits the elements of the
 // nearest points to ~1e-10 relative.  Writes A (FP64, = hi + lo), A32 (hi) and
 // A32lo (lo), the matrices of the inner FP32 GEMV and of the double-float GEMV.
-__device__ __forceinline__ void df_two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ void df_fast_two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    e = b - (s - a);
-}
-
-__device__ __forceinline__ void df_rsqrt(float dxh, float dxl, float dyh, float dyl, float dzh, float dzl, float &ih,
-                                         float &il, float &r2)
-{
-    // R^2 = sum_d (dh + dl)^2 = dh^2 + (2 dh dl + dl^2)
-    const float px = dxh * dxh, py = dyh * dyh, pz = dzh * dzh;
-    const float ex = fmaf(dxh, dxh, -px) + dxl * fmaf(2.f, dxh, dxl);
-    const float ey = fmaf(dyh, dyh, -py) + dyl * fmaf(2.f, dyh, dyl);
-    const float ez = fmaf(dzh, dzh, -pz) + dzl * fmaf(2.f, dzh, dzl);
-    float s1, t1, s2, t2;
-    df_two_sum(px, py, s1, t1);
-    df_two_sum(s1, pz, s2, t2);
-    float Sh, Sl;
-    df_fast_two_sum(s2, (t1 + t2) + ((ex + ey) + ez), Sh, Sl);
-    // FP32 Newton step on the hardware estimate, then one double-float step:
-    // r1 = r0 + r0 e / 2 with e = 1 - S r0^2 formed from the exact products
-    float r0 = rsqrtf(Sh);
-    r0 = fmaf(0.5f * r0, fmaf(-Sh * r0, r0, 1.f), r0);
-    const float th = Sh * r0;
-    const float tl = fmaf(Sh, r0, -th) + Sl * r0;
-    const float uh = th * r0;
-    const float ul = fmaf(th, r0, -uh) + tl * r0;
-    const float e = (1.f - uh) - ul;
-    df_fast_two_sum(r0, 0.5f * r0 * e, ih, il);
-    r2 = Sh;
-}
-
 __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, const float *__restrict__ pl,
                                   const double *__restrict__ px, const double *__restrict__ py,
                                   const double *__restrict__ pz, const double *__restrict__ pzeta,
@@ -478,6 +440,21 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
 
     PCM_TRY(points_split(c));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
+    // PCM_MIXED operator for this surface: matrix-free for large surfaces (its
+    // FP32 product outruns the stored FP32 GEMV there) or when the stored parts
+    // would crowd the device; stored otherwise, and always for batch members
+    c->mf_active = false;
+    if (c->opt.precision == PCM_MIXED && !c->store_a) {
+        if (c->opt.operator_mode == PCM_OPERATOR_FREE) {
+            c->mf_active = true;
+        } else if (c->opt.operator_mode == PCM_OPERATOR_AUTO) {
+            size_t fr = 0, tot = 0;
+            const double need = 16.0 * (double)c->M * (double)((c->M + 31) / 32 * 32);
+            const bool tight = cudaMemGetInfo(&fr, &tot) == cudaSuccess && need > 0.25 * (double)fr;
+            c->mf_active = c->M > 24576 || tight;
+        }
+    }
+    c->stats.operator_free = c->mf_active ? 1 : 0;
     c->pc_ready = false;
     c->a32_ready = false;
     c->have_c = false;
@@ -495,19 +472,7 @@ int a_build(pcm_ctx *c, cudaStream_t s)
     c->lda = (M + 31) / 32 * 32;
     PCM_TRY(c->A.alloc((size_t)M * c->lda));
     {
-        // zeta'_kl = zeta_k zeta_l / sqrt(zeta_k^2 + zeta_l^2) (Eq. 8) for every
-        // pair of exponent classes, once on the host (IEEE division and square
-        // root, as on the device) instead of in every thread block
-        const int nc = c->ncls;
-        std::vector<double> &zp = c->h_zp_cls;  // kept in the context: the copy below reads it later
-        zp.assign((size_t)nc * nc, 0.0);
-        for (int a = 0; a < nc; ++a)
-            for (int b = 0; b < nc; ++b) {
-                const double za = c->h_cls_zeta[a], zb = c->h_cls_zeta[b];
-                zp[(size_t)a * nc + b] = za * zb / sqrt(za * za + zb * zb);
-            }
-        PCM_TRY(c->zp_cls.alloc(std::max<size_t>(1, zp.size())));
-        PCM_CUDA(cudaMemcpyAsync(c->zp_cls.p, zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        PCM_TRY(zeta_pairs(c, s));
         const long long nt = (M + AT - 1) / AT;
         const long long ntiles = nt * (nt + 1) / 2;
         if (c->opt.precision == PCM_MIXED) {

@@ -1,5 +1,5 @@
 """PCM_MIXED (FP32 integrals, FP64 accumulation) against the oracle on every
-case, and against the FP64 GPU path (itself checked against the oracle at
+case with both operators (stored A, matrix-free), and against the FP64 GPU path (itself checked against the oracle at
 1e-10) with and without screening.  Bars: every element of c and dF within
 1e-6 of itself plus 1e-7 of the largest element (tests/_parity.py), and
 1e-6 Eh on the energy (the Eq. 21 target)."""
@@ -13,9 +13,9 @@ from _parity import MIXED, check
 pytestmark = pytest.mark.gpu
 
 
-def _run(w, precision, schwarz=0.0, delta=1e-10):
+def _run(w, precision, schwarz=0.0, delta=1e-10, operator="auto"):
     import paper_1505_07851_gb300 as pcm
-    with pcm.Context(precision=precision, schwarz=schwarz) as ctx:
+    with pcm.Context(precision=precision, schwarz=schwarz, operator=operator) as ctx:
         ctx.setup(w.mol, w.basis)
         c = ctx.esp(w.P)
         q, st = ctx.solve(delta=delta)
@@ -54,9 +54,10 @@ def test_mixed_matches_fp64(name, schwarz):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_mixed_against_oracle_directly(name):
+@pytest.mark.parametrize("operator", ["stored", "free"])
+def test_mixed_against_oracle_directly(name, operator):
     w = CASES[name]()
-    b = _run(w, "mixed")
+    b = _run(w, "mixed", operator=operator)
     o = oracle.run(w, delta=1e-10)
     pos = {int(k): i for i, k in enumerate(o["surf"]["index"])}
     p = np.array([pos[int(k)] for k in b["idx"]])

@@ -24,7 +24,7 @@ def _rank_main(rank, world, port, out):
     import torch.distributed as dist
     r, w, _ = bench.dist_init("gloo")
     assert (r, w) == (rank, world)
-    wl = bench.workload_for(1, rank)
+    wl = bench.workload_for("cluster300_sp", rank)
     # rank r claims (r + 1) units in (r + 1) * 10 ms
     value, ms_max = bench.replica_throughput(float(rank + 1), 10.0 * (rank + 1), w, "cpu")
     bench.barrier(w)
