@@ -546,6 +546,9 @@ def run_ours(args):
         main["ctx"].close()
         if not args.no_small and w.name != "cluster300_sp":
             line["cluster300_sp"] = _small_record(pcm, args, dev, stream, flush, delta)
+        if not args.no_batch:
+            line["batch"] = measure_batch(pcm, args, dev, stream, flush, delta, steps=2, warmup=1,
+                                          operator=args.batch_operator)
         print(json.dumps(line))
     else:
         main["ctx"].close()
@@ -617,39 +620,66 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_batch(args):
-    """The batch workload: conformations of 150-600 atoms (s/sp shells, M
-    about 6k-24k each), ESP + lockstep PCG + Fock + energy for all of them per
-    step (pcm_batch_run, PCM_MIXED), inputs resident on the device."""
+def _single_pass(pcm, w, precision, dev, stream, flush, delta):
+    """One molecule through single-molecule calls (surface and basis set up
+    and one warm pass untimed): the CUDA-event time of ESP + solve + Fock +
+    energy, with L2 flushed before it.  Returns (ms, energy)."""
     import torch
-    rank, world, local = dist_init("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    import paper_1505_07851_gb300 as pcm
+    with pcm.Context(precision=precision, device=dev.index, stream=stream.cuda_stream) as ctx:
+        M, nbf = ctx.setup(w.mol, w.basis)
+        Pd = torch.tensor(w.P, dtype=torch.float64, device=dev)
+        c = torch.empty(M, dtype=torch.float64, device=dev)
+        q = torch.empty_like(c)
+        F = torch.empty((nbf, nbf), dtype=torch.float64, device=dev)
+
+        def once():
+            ctx.esp(Pd, out=c)
+            ctx.solve(delta=delta, q=q)
+            ctx.fock(q, out=F)
+            return ctx.energy(q)
+        once()
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        E = once()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), E
+
+
+def measure_batch(pcm, args, dev, stream, flush, delta, rank=0, world=1, nmol=None, steps=None, warmup=None,
+                  operator="auto"):
+    """The batch of conformations (150-600 atoms, s/sp shells): ESP + solve +
+    Fock + energy for every molecule per step through pcm_batch_run (the
+    packed integral blocks of all molecules in one launch per angular class,
+    lockstep PCG), inputs resident on the device; beside it the same molecules
+    one at a time through single-molecule calls (mixed), and a sample in FP64
+    (time and energy error)."""
+    import torch
+    nmol = nmol or args.nmol
+    steps = steps or args.steps
+    warmup = args.warmup if warmup is None else warmup
     t0 = time.time()
-    confs = workloads.conformations(args.nmol, seed=150507851 + 4 + 1000 * rank, workers=os.cpu_count() or 1)
+    confs = workloads.conformations(nmol, seed=150507851 + 4 + 1000 * rank, workers=os.cpu_count() or 1)
     gen_s = time.time() - t0
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    delta = args.delta if args.delta else DELTA_1E6
-    b = pcm.Batch(len(confs), precision=args.precision, device=local, stream=stream.cuda_stream,
-                  fp32x2=not args.scalar_fp32)
+    b = pcm.Batch(len(confs), precision=args.precision, device=dev.index, stream=stream.cuda_stream,
+                  fp32x2=not args.scalar_fp32, operator=operator)
     t0 = time.time()
     for i, w in enumerate(confs):
         b.set_molecule(i, w.mol, w.basis)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     Pd = [torch.tensor(w.P, dtype=torch.float64, device=dev) for w in confs]
-    # outputs every step: the energies, and the Fock corrections on the device
     Fd = [torch.empty((w.basis.nbf, w.basis.nbf), dtype=torch.float64, device=dev) for w in confs]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.run(Pd, delta, dF_out=Fd)
     torch.cuda.synchronize()
     launches0 = b.stats()["launches"]
     times, ints = [], 0.0
-    barrier(world)
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+    with ClockSampler(dev.index) as clk:
+        for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -661,56 +691,85 @@ def run_batch(args):
             tot = b.stats()
             ints += tot["integrals_esp"] + tot["integrals_fock"]
     torch.cuda.synchronize()
-    barrier(world)
     tot = b.stats()
     launches = tot["launches"] - launches0
     per = [b.stats(i) for i in range(len(confs))]
-    value, ms_max = replica_throughput(ints, sum(times), world, dev)
-    solves = dist_sum(len(confs) * args.steps, world, dev) / (ms_max * 1e-3)
-    # end to end: host densities in, energies out
+    E = list(E)
     e2e = None
     if not args.no_e2e:
         Ph = [np.ascontiguousarray(w.P) for w in confs]
         Fh = [np.empty_like(P) for P in Ph]
         et = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             b.run(Ph, delta, dF_out=Fh)
             et.append(time.perf_counter() - t1)
-        e_val, e_ms = replica_throughput(ints * len(et) / args.steps, sum(et) * 1e3, world, dev)
-        e2e = {"value": e_val, "unit": UNIT, "h2d_bytes_per_step": int(sum(P.nbytes for P in Ph)),
-               "d2h_bytes_per_step": int(sum(F.nbytes for F in Fh)) + 8 * len(confs), "ms_per_step": e_ms / len(et)}
-    # per-conformation error against the FP64 single-molecule path (a sample)
-    errs = []
-    for i in range(min(args.ref_mols, len(confs))):
+        e2e = {"ms_per_step": 1e3 * statistics.mean(et), "h2d_bytes_per_step": int(sum(P.nbytes for P in Ph)),
+               "d2h_bytes_per_step": int(sum(F.nbytes for F in Fh)) + 8 * len(confs)}
+    b.close()
+    ms = sum(times) / len(times)
+    # the same molecules one at a time (PCM_MIXED single-molecule calls)
+    seq = [_single_pass(pcm, w, args.precision, dev, stream, flush, delta) for w in confs]
+    seq_ms = sum(t for t, _ in seq)
+    # a sample in FP64: time per molecule and the error of the batch energies
+    nref = min(args.ref_mols, len(confs))
+    fp64 = []
+    for i in range(nref):
         w = confs[i]
-        with pcm.Context(precision="fp64", device=local, stream=stream.cuda_stream) as ctx:
+        t64, _ = _single_pass(pcm, w, "fp64", dev, stream, flush, delta)
+        with pcm.Context(precision="fp64", device=dev.index, stream=stream.cuda_stream) as ctx:
             ctx.setup(w.mol, w.basis)
             ctx.esp(w.P)
-            q, _ = ctx.solve(delta=1e-10)
-            errs.append(abs(E[i] - ctx.energy(q)))
-    b.close()
+            qt, _ = ctx.solve(delta=1e-10)
+            fp64.append((t64, abs(E[i] - ctx.energy(qt))))
+    Ms = [p["M"] for p in per]
+    mixed_sample = sum(seq[i][0] for i in range(nref))
+    fp64_sample = sum(t for t, _ in fp64)
+    return {
+        "workload": "batch%d_conformations_150to600_sp" % len(confs), "nmol": len(confs),
+        "M_min": min(Ms), "M_max": max(Ms), "M_total": sum(Ms), "precision": args.precision, "delta": delta,
+        "operator": operator, "steps": len(times), "ms_per_step": ms, "solves_per_s": len(confs) / (ms * 1e-3),
+        "integrals_per_s": ints / (sum(times) * 1e-3), "gpu_launches_per_step": launches / len(times),
+        "pcg_iterations_max": max(p["iterations"] for p in per),
+        "pcg_iterations_mean": statistics.mean(p["iterations"] for p in per),
+        "all_converged": all(p["converged"] for p in per),
+        "sequential_mixed": {"ms_total": seq_ms, "solves_per_s": len(confs) / (seq_ms * 1e-3),
+                             "batched_speedup": seq_ms / ms,
+                             "what": "the same molecules one at a time: ESP + solve + Fock + energy through "
+                                     "single-molecule contexts (set-up untimed), L2 flushed before each"},
+        "fp64_sample": {"n": nref, "ms_total": fp64_sample, "mixed_ms_same_molecules": mixed_sample,
+                        "fp64_over_mixed": fp64_sample / mixed_sample if mixed_sample else None,
+                        "batch_energy_err_vs_fp64_Eh_max": max(e for _, e in fp64) if fp64 else None},
+        "l2": "flushed between timed steps (512 MB write, not timed)",
+        "setup_s": setup_s, "workload_generation_s": gen_s, "clocks": clk.summary(), "e2e": e2e,
+        "M_range_note": "150-600 atoms at the density of the 300-atom cluster give 6.4k-22k points; "
+                        "denser globules cannot place the atoms",
+    }
+
+
+def run_batch(args):
+    """The batch workload alone: one JSON line with the batch record."""
+    import torch
+    rank, world, local = dist_init("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1505_07851_gb300 as pcm
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    delta = args.delta if args.delta else DELTA_1E6
+    rec = measure_batch(pcm, args, dev, stream, flush, delta, rank, world, operator=args.batch_operator)
+    value, ms_max = replica_throughput(rec["integrals_per_s"] * rec["ms_per_step"] * 1e-3 * rec["steps"],
+                                       rec["ms_per_step"] * rec["steps"], world, dev)
     if rank == 0:
-        Ms = [p["M"] for p in per]
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64",
-            "data": "synthetic (seeded peptide-like clusters of 150-600 atoms)",
-            "config": {"workload": "batch%d_conformations_150to600_sp" % len(confs), "nmol": len(confs),
-                       "M_min": min(Ms), "M_max": max(Ms), "M_total": sum(Ms), "precision": args.precision,
-                       "delta": delta, "l2": "flushed between timed steps (512 MB write, not timed)",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "solves_per_s": solves,
-            "pcg_iterations_max": max(p["iterations"] for p in per),
-            "pcg_iterations_mean": statistics.mean(p["iterations"] for p in per),
-            "all_converged": all(p["converged"] for p in per),
-            "energy_err_vs_fp64_Eh": {"max": max(errs) if errs else None, "n": len(errs)},
-            "setup_s": setup_s, "workload_generation_s": gen_s, "autotune": pcm.autotune_table(),
-            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
-        }
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": rec["steps"],
+                "warmup": args.warmup, "ms_per_step": ms_max / rec["steps"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64",
+                "data": "synthetic (seeded peptide-like clusters of 150-600 atoms)",
+                "config": {"workload": rec["workload"], "nmol": rec["nmol"], "precision": args.precision,
+                           "parallelism": "replicas" if world > 1 else "single", "l2": rec["l2"]},
+                "batch": rec, "clocks": rec["clocks"], "e2e": None, "gpu_launches": rec["gpu_launches_per_step"]}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -736,6 +795,9 @@ def main():
     ap.add_argument("--no-grad", action="store_true", help="skip the nuclear-gradient timing")
     ap.add_argument("--no-small", action="store_true", help="skip the 300-atom sub-record")
     ap.add_argument("--nmol", type=int, default=64, help="conformations in the batch workload")
+    ap.add_argument("--batch-operator", default="auto", choices=["auto", "stored", "free"],
+                    help="operator of the batch members (auto: stored, lockstep solver)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch sub-record")
     ap.add_argument("--ref-mols", type=int, default=4, help="batch members checked against the FP64 path")
     ap.add_argument("--no-scf", action="store_true", help="skip the SCF-sequence threshold comparison")
     ap.add_argument("--no-precond", action="store_true", help="skip the preconditioner comparison")

@@ -404,7 +404,7 @@ class Batch:
 
     def __init__(self, nmol, eps=78.39, k=0.0, zeta=4.9, switch_drop=1e-8, schwarz=1e-12, rbj_block=100,
                  precond="auto", jacobi_below=1000, precision="mixed", max_iter=5000, device=0, seed=0,
-                 stream=None, autotune=True, fp32x2=True):
+                 stream=None, autotune=True, fp32x2=True, operator="auto"):
         o = pcm_options()
         _lib.pcm_default_options(ctypes.byref(o))
         o.eps, o.k, o.zeta, o.switch_drop, o.schwarz = eps, k, zeta, switch_drop, schwarz
@@ -413,6 +413,7 @@ class Batch:
         o.max_iter, o.device, o.seed, o.stream = max_iter, device, seed, stream
         o.autotune = 1 if autotune else 0
         o.fp32x2 = 1 if fp32x2 else 0
+        o.operator_mode = OPERATOR[operator]
         h = ctypes.c_void_p()
         st = _lib.pcm_batch_create(ctypes.byref(h), ctypes.byref(o), int(nmol))
         if st != PCM_OK:

@@ -80,6 +80,11 @@ struct pcm_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_mixed = false;
+    // the packed integral blocks of all molecules, one launch per class
+    pcm::JobSink sink;
+    pcm::DBuf<pcm::EspJob> dej;
+    pcm::DBuf<pcm::FockJob> dfj;
+    pcm::DBuf<int> derr;
     // results
     std::vector<pcm_stats> st;
     long long launches = 0;            // batch-level kernels (the molecules count their own)
@@ -691,7 +696,10 @@ int pcm_batch_create(pcm_batch **out, const pcm_options *opt, int nmol)
             cudaSetDevice(prev);
             return s;
         }
-        bt->mol[m]->store_a = true;   // the lockstep solver reads each molecule's stored A
+        // the lockstep solver reads each molecule's stored A; with
+        // PCM_OPERATOR_FREE the molecules keep none and are solved one after
+        // another by the matrix-free solver
+        bt->mol[m]->store_a = o.operator_mode != PCM_OPERATOR_FREE;
     }
     cudaSetDevice(prev);
     *out = bt;
@@ -777,6 +785,23 @@ int pcm_batch_run(pcm_batch *bt, const double *const *P, double delta, double *E
     PCM_TRY(batch_layout(bt));
     const double f = (bt->opt.eps - 1.0) / (bt->opt.eps + bt->opt.k);
     const bool dev = (flags & PCM_PTR_DEVICE) != 0;
+    // PCM_MIXED with the packed kernels: every molecule's packed ESP and Fock
+    // blocks are collected and run in one launch per angular class
+    const bool batched = bt->opt.precision == PCM_MIXED && bt->opt.fp32x2;
+    struct Undefer {
+        pcm_batch *bt;
+        ~Undefer()
+        {
+            for (pcm_ctx *c : bt->mol) c->jobs = nullptr;
+        }
+    } undefer{bt};
+    if (batched) {
+        bt->sink.clear();
+        if (!bt->derr.p) {
+            PCM_TRY(bt->derr.alloc(1));
+            PCM_CUDA(cudaMemsetAsync(bt->derr.p, 0, sizeof(int), bt->stream));
+        }
+    }
     // ESP of every molecule, and the right-hand sides
     for (int m = 0; m < bt->nmol; ++m) {
         pcm_ctx *c = bt->mol[m];
@@ -788,17 +813,45 @@ int pcm_batch_run(pcm_batch *bt, const double *const *P, double delta, double *E
             dP = c->dP.p;
         }
         PCM_TRY(c->c_last.alloc(c->M));
+        c->jobs = batched ? &bt->sink : nullptr;
         PCM_TRY(esp_compute(c, dP, c->c_last.p));
+        c->jobs = nullptr;
         c->have_c = true;
-        brhs_kernel<<<(c->M + 255) / 256, 256, 0, bt->stream>>>(c->M, f, c->Bz.p, c->c_last.p,
-                                                                 bt->b.p + bt->h_off[m]);
-        PCM_LAUNCHED(c);
         bt->st[m].integrals_esp = c->stats.integrals_esp;
         bt->st[m].pairs_esp = c->stats.pairs_esp;
     }
-    // every solve in lockstep
-    PCM_TRY(batch_solve(bt, delta));
+    if (batched) {
+        PCM_TRY(launch_jobs(bt->sink, bt->dej, bt->dfj, bt->mol[0]->boys32.p, bt->derr.p, bt->stream));
+        bt->launches += 10;
+        for (int m = 0; m < bt->nmol; ++m) PCM_TRY(esp_mixed_finish(bt->mol[m]));
+    }
+    for (int m = 0; m < bt->nmol; ++m) {
+        pcm_ctx *c = bt->mol[m];
+        brhs_kernel<<<(c->M + 255) / 256, 256, 0, bt->stream>>>(c->M, f, c->Bz.p, c->c_last.p,
+                                                                 bt->b.p + bt->h_off[m]);
+        PCM_LAUNCHED(c);
+    }
+    if (bt->opt.precision == PCM_MIXED && bt->opt.operator_mode == PCM_OPERATOR_FREE) {
+        // matrix-free molecules: each solve is one persistent inner solver per
+        // refinement, molecule after molecule
+        for (int m = 0; m < bt->nmol; ++m) {
+            pcm_ctx *c = bt->mol[m];
+            pcm_stats sm{};
+            const int st = solver_run(c, bt->b.p + bt->h_off[m], delta, bt->x.p + bt->h_off[m], false, &sm);
+            if (st != PCM_OK && st != PCM_ERR_NOT_CONVERGED) return st;
+            bt->st[m].iterations = sm.iterations;
+            bt->st[m].converged = sm.converged;
+            bt->st[m].rnorm = sm.rnorm;
+            bt->st[m].refinements = sm.refinements;
+            bt->st[m].delta = delta;
+        }
+    } else {
+        // every solve in lockstep
+        PCM_TRY(batch_solve(bt, delta));
+    }
     // Fock correction and energy of every molecule
+    std::vector<double *> ddFs(bt->nmol, nullptr);
+    if (batched) bt->sink.clear();
     for (int m = 0; m < bt->nmol; ++m) {
         pcm_ctx *c = bt->mol[m];
         const double *dq = bt->x.p + bt->h_off[m];
@@ -809,10 +862,25 @@ int pcm_batch_run(pcm_batch *bt, const double *const *P, double delta, double *E
                 PCM_TRY(c->dF.alloc(n2));
                 ddF = c->dF.p;
             }
+            ddFs[m] = ddF;
+            c->jobs = batched ? &bt->sink : nullptr;
             PCM_TRY(fock_compute(c, dq, ddF));
-            if (!dev)
-                PCM_CUDA(cudaMemcpyAsync(dF[m], ddF, n2 * sizeof(double), cudaMemcpyDeviceToHost, bt->stream));
+            c->jobs = nullptr;
             bt->st[m].integrals_fock = c->stats.integrals_fock;
+        }
+    }
+    if (batched) {
+        PCM_TRY(launch_jobs(bt->sink, bt->dej, bt->dfj, bt->mol[0]->boys32.p, bt->derr.p, bt->stream));
+        bt->launches += 10;
+        for (int m = 0; m < bt->nmol; ++m)
+            if (ddFs[m]) PCM_TRY(fock_mixed_finish(bt->mol[m], ddFs[m]));
+    }
+    for (int m = 0; m < bt->nmol; ++m) {
+        pcm_ctx *c = bt->mol[m];
+        const double *dq = bt->x.p + bt->h_off[m];
+        if (ddFs[m] && !dev) {
+            const size_t n2 = (size_t)c->nbf * c->nbf;
+            PCM_CUDA(cudaMemcpyAsync(dF[m], ddFs[m], n2 * sizeof(double), cudaMemcpyDeviceToHost, bt->stream));
         }
         PCM_TRY(energy_compute(c, dq, c->c_last.p, &E[m]));
         if (q && q[m])
@@ -820,6 +888,15 @@ int pcm_batch_run(pcm_batch *bt, const double *const *P, double delta, double *E
                                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, bt->stream));
     }
     PCM_CUDA(cudaStreamSynchronize(bt->stream));
+    if (batched) {
+        int h = 0;
+        PCM_CUDA(cudaMemcpy(&h, bt->derr.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h) {
+            PCM_CUDA(cudaMemset(bt->derr.p, 0, sizeof(int)));
+            set_last_error("pcm_batch_run: a bounded device wait gave up in a batched integral kernel");
+            return PCM_ERR_TIMEOUT;
+        }
+    }
     return PCM_OK;
 }
 

@@ -101,6 +101,36 @@ struct PairClass {
 
 struct pcm_ctx_impl;
 
+// Work of one thread block of the packed integral kernels, so that the blocks
+// of many molecules can run in one launch (batches).
+struct EspJob {
+    const float *far, *near, *ph, *pl;   // pair tiles (far block, near blocks per class), split point coordinates
+    double *part;                        // the block's row of partial sums (indexed by point)
+    int ntile, M, k0, k1, e, t0, nt, pad;  // tiles of the class, points, point range, class, tile range
+};
+
+struct FockJob {
+    const double *gp;                    // exponent sums of the pairs
+    const float *Phl, *nc, *tiles;       // split pair centres, near constants, point tiles
+    const int *tile_cls;                 // class of each point tile
+    double *W;                           // accumulators [nsplit][nherm][npair]
+    int npair, ntile, tps, bx, by, pad;  // pairs, point tiles, tiles per split, pair block, split
+};
+
+// Collects the blocks of the packed ESP (by L and points per thread: 2, 4)
+// and Fock (by L and pairs per thread: 1, 2) kernels instead of launching them.
+struct JobSink {
+    std::vector<EspJob> esp[5][2];
+    std::vector<FockJob> fock[6][2];
+    void clear()
+    {
+        for (auto &v : esp)
+            for (auto &w : v) w.clear();
+        for (auto &v : fock)
+            for (auto &w : v) w.clear();
+    }
+};
+
 }  // namespace pcm
 
 struct pcm_ctx {
@@ -201,6 +231,16 @@ struct pcm_ctx {
     pcm::DBuf<unsigned char> su8[2];
 
     pcm::DBuf<int> dev_err;                // device error flag (a bounded wait in a kernel gave up)
+    // deferred packed integral blocks (batches): while jobs is set, the packed
+    // kernels' blocks are appended there and the ESP reduction and Fock
+    // epilogues wait for esp_mixed_finish / fock_mixed_finish
+    pcm::JobSink *jobs = nullptr;
+    std::vector<int> h_pblk[2], h_pbcls[2];   // host copies of the PCM_MIXED point blocks (4 and 2 points per thread)
+    int esp_total_rows = 0;
+    double *esp_out = nullptr;
+    pcm::DBuf<double> fock_Wk[6];
+    int fock_nsplit_k[6] = {0, 0, 0, 0, 0, 0};
+    bool fock_pending[6] = {false, false, false, false, false, false};
     // matrix-free A (PCM_MIXED): FP32 coordinates, near pairs (CSR, exact values), solver scratch
     bool store_a = false;                  // keep the stored A and its FP32 parts instead (batch members)
     bool mf_active = false;                // this surface's PCM_MIXED solver is matrix-free (set per surface)
@@ -245,6 +285,11 @@ int fock_compute(pcm_ctx *c, const double *dq, double *ddF);
 // PCM_MIXED (integrals_mixed.cu)
 int points_split(pcm_ctx *c);
 int esp_compute_mixed(pcm_ctx *c, double *dc);
+// deferred blocks of a batch: launch every collected job, then finish each molecule
+int launch_jobs(JobSink &sink, DBuf<EspJob> &dej, DBuf<FockJob> &dfj, const float *boys, int *err, cudaStream_t s);
+int esp_mixed_finish(pcm_ctx *c);
+int esp_packed_jobs(int L, int ppt, const EspJob *jobs, int njob, const float *boys, int *err, cudaStream_t s);
+int fock_mixed_finish(pcm_ctx *c, double *ddF);
 // packed FP32x2 ESP with the far-field path (esp_packed.cu): pairs [jbeg, jend) of class pc
 int esp_packed(pcm_ctx *c, PairClass &pc, int L, int ppt, int jbeg, int jend, const int *blk, const int *bcls,
                int nblk, double *part);

@@ -29,6 +29,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "boys.cuh"
 #include "common.cuh"
@@ -237,30 +238,21 @@ __device__ __forceinline__ f2 near_value(f2 X, f2 Y, f2 Z, f2 R2, const float4 *
     }
 }
 
-// One block: a run of points of one class (blk_off, blk_cls) against the
-// tiles [blockIdx.y * tps, ...) of the class's cross-atom pairs; partial sums
-// to part[blockIdx.y][k].
-// resident blocks per SM the register allocation aims for
 // resident blocks per SM the register allocation aims for (without spills)
 constexpr int pk_min_blocks(int L, int PPT) { return PPT == 4 ? 2 : (L == 0 ? 7 : (L == 1 ? 5 : (L == 2 ? 4 : 3))); }
 
 template <int L, int PPT>
-__global__ void __launch_bounds__(PK_NT, pk_min_blocks(L, PPT)) esp_kernel_f32x2(int ntile, int tps, const float *__restrict__ far,
-                                                          const float *__restrict__ near,
-                                                          const int *__restrict__ blk_off,
-                                                          const int *__restrict__ blk_cls,
-                                                          const float *__restrict__ ph, const float *__restrict__ pl,
-                                                          const float *__restrict__ boys, int M,
-                                                          double *__restrict__ part, int *__restrict__ err)
+__device__ __forceinline__ void esp_block(const EspJob &jb, const float *__restrict__ boys, int *__restrict__ err)
 {
     using Ly = PkLayout<L>;
     constexpr int BUF = Ly::FAR + Ly::NEAR;
     constexpr int NSTAGE = 3;
     __shared__ __align__(16) TileRing<NSTAGE, BUF> ring;
-    const int k0 = blk_off[blockIdx.x], k1 = blk_off[blockIdx.x + 1];
-    const int e = blk_cls[blockIdx.x];
-    const int t0 = blockIdx.y * tps;
-    const int nt = max(0, min(ntile, t0 + tps) - t0);
+    const int k0 = jb.k0, k1 = jb.k1, e = jb.e, t0 = jb.t0, nt = jb.nt, ntile = jb.ntile, M = jb.M;
+    const float *__restrict__ far = jb.far;
+    const float *__restrict__ near = jb.near;
+    const float *__restrict__ ph = jb.ph;
+    const float *__restrict__ pl = jb.pl;
 
     if (threadIdx.x == 0) ring.init(PK_NT / 32);
     __syncthreads();
@@ -362,9 +354,42 @@ __global__ void __launch_bounds__(PK_NT, pk_min_blocks(L, PPT)) esp_kernel_f32x2
     for (int q = 0; q < PPT; ++q) {
         const int k = k0 + threadIdx.x + q * PK_NT;
         if (k < k1)
-            part[(size_t)blockIdx.y * M + k] =
-                ((double)a32[q].v.x - (double)k32[q].v.x) + ((double)a32[q].v.y - (double)k32[q].v.y);
+            jb.part[k] = ((double)a32[q].v.x - (double)k32[q].v.x) + ((double)a32[q].v.y - (double)k32[q].v.y);
     }
+}
+
+// One block: a run of points of one class (blk_off, blk_cls) against the
+// tiles [blockIdx.y * tps, ...) of the class's cross-atom pairs; partial sums
+// to part[blockIdx.y][k].
+template <int L, int PPT>
+__global__ void __launch_bounds__(PK_NT, pk_min_blocks(L, PPT))
+    esp_kernel_f32x2(int ntile, int tps, const float *__restrict__ far, const float *__restrict__ near,
+                     const int *__restrict__ blk_off, const int *__restrict__ blk_cls, const float *__restrict__ ph,
+                     const float *__restrict__ pl, const float *__restrict__ boys, int M, double *__restrict__ part,
+                     int *__restrict__ err)
+{
+    EspJob jb;
+    jb.far = far;
+    jb.near = near;
+    jb.ph = ph;
+    jb.pl = pl;
+    jb.part = part + (size_t)blockIdx.y * M;
+    jb.ntile = ntile;
+    jb.M = M;
+    jb.k0 = blk_off[blockIdx.x];
+    jb.k1 = blk_off[blockIdx.x + 1];
+    jb.e = blk_cls[blockIdx.x];
+    jb.t0 = blockIdx.y * tps;
+    jb.nt = max(0, min(ntile, jb.t0 + tps) - jb.t0);
+    esp_block<L, PPT>(jb, boys, err);
+}
+
+// The same for a table of blocks of many molecules (one launch per class)
+template <int L, int PPT>
+__global__ void __launch_bounds__(PK_NT, pk_min_blocks(L, PPT))
+    esp_jobs_kernel(const EspJob *__restrict__ jobs, const float *__restrict__ boys, int *__restrict__ err)
+{
+    esp_block<L, PPT>(jobs[blockIdx.x], boys, err);
 }
 
 // segments of ntile tiles for nblk point blocks: enough CTAs to fill the GPU
@@ -403,6 +428,34 @@ static int esp_packed_launch(pcm_ctx *c, PairClass &pc, int jbeg, int jend, cons
     PCM_LAUNCHED(c);
     int tps, rows;
     pk_plan(ntile, nblk, &tps, &rows);
+    if (c->jobs) {
+        // a batch: the blocks join one launch per class with the other molecules'
+        const std::vector<int> &hoff = c->h_pblk[PPT == 4 ? 0 : 1], &hcls = c->h_pbcls[PPT == 4 ? 0 : 1];
+        if ((int)hcls.size() != nblk) {
+            set_last_error("batched ESP: point blocks do not match");
+            return PCM_ERR_ARG;
+        }
+        auto &v = c->jobs->esp[L][PPT == 4 ? 1 : 0];
+        for (int y = 0; y < rows; ++y)
+            for (int x = 0; x < nblk; ++x) {
+                EspJob jb;
+                jb.far = pc.tfar.p;
+                jb.near = pc.tnear.p;
+                jb.ph = c->p32.p;
+                jb.pl = c->p32lo.p;
+                jb.part = part + (size_t)y * c->M;
+                jb.ntile = ntile;
+                jb.M = c->M;
+                jb.k0 = hoff[x];
+                jb.k1 = hoff[x + 1];
+                jb.e = hcls[x];
+                jb.t0 = y * tps;
+                jb.nt = std::max(0, std::min(ntile, jb.t0 + tps) - jb.t0);
+                jb.pad = 0;
+                v.push_back(jb);
+            }
+        return PCM_OK;
+    }
     dim3 grid(nblk, rows);
     esp_kernel_f32x2<L, PPT><<<grid, PK_NT, 0, c->stream>>>(ntile, tps, pc.tfar.p, pc.tnear.p, blk, bcls, c->p32.p,
                                                            c->p32lo.p, c->boys32.p, c->M, part, c->dev_err.p);
@@ -426,6 +479,27 @@ int esp_packed(pcm_ctx *c, PairClass &pc, int L, int ppt, int jbeg, int jend, co
     }
 #undef PCM_PK
     return PCM_ERR_ARG;
+}
+
+// the packed ESP blocks of a batch (job table on the device), one launch
+int esp_packed_jobs(int L, int ppt, const EspJob *jobs, int njob, const float *boys, int *err, cudaStream_t s)
+{
+#define PCM_PKJ(LL)                                                                                  \
+    case LL:                                                                                         \
+        if (ppt == 4) esp_jobs_kernel<LL, 4><<<njob, PK_NT, 0, s>>>(jobs, boys, err);               \
+        else esp_jobs_kernel<LL, 2><<<njob, PK_NT, 0, s>>>(jobs, boys, err);                        \
+        break;
+    switch (L) {
+        PCM_PKJ(0)
+        PCM_PKJ(1)
+        PCM_PKJ(2)
+        PCM_PKJ(3)
+        PCM_PKJ(4)
+    default: return PCM_ERR_ARG;
+    }
+#undef PCM_PKJ
+    PCM_CUDA(cudaGetLastError());
+    return PCM_OK;
 }
 
 }  // namespace pcm

@@ -122,16 +122,16 @@ constexpr int fk_min_blocks(int L, int NPT)
 // Block x: pairs (x NPT + i) FK_NT + threadIdx.x, i < NPT; block y: the tiles
 // [y tps, (y + 1) tps).  W[y][h][pair] receives that split's sum.
 template <int L, int NPT>
-__global__ void __launch_bounds__(FK_NT, fk_min_blocks(L, NPT))
-    fock_kernel_f32x2(int npair, const double *__restrict__ gp, const float *__restrict__ Phl,
-                      const float *__restrict__ nc, int ntile, int tps, const float *__restrict__ tiles,
-                      const int *__restrict__ tile_cls, const float *__restrict__ boys, double *__restrict__ W,
-                      int *__restrict__ err)
+__device__ __forceinline__ void fock_block(int bx, int by, int npair, const double *__restrict__ gp,
+                                           const float *__restrict__ Phl, const float *__restrict__ nc, int ntile,
+                                           int tps, const float *__restrict__ tiles,
+                                           const int *__restrict__ tile_cls, const float *__restrict__ boys,
+                                           double *__restrict__ W, int *__restrict__ err)
 {
     constexpr int NH = nherm(L);
     constexpr int NSTAGE = 3;
     __shared__ __align__(16) TileRing<NSTAGE, FK_TILE> ring;
-    const int t0 = blockIdx.y * tps;
+    const int t0 = by * tps;
     const int nt = max(0, min(ntile, t0 + tps) - t0);
     if (threadIdx.x == 0) ring.init(FK_NT / 32);
     __syncthreads();
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(FK_NT, fk_min_blocks(L, NPT))
     float ah[NPT][NH], al[NPT][NH];
 #pragma unroll
     for (int i = 0; i < NPT; ++i) {
-        r[i] = (blockIdx.x * NPT + i) * FK_NT + threadIdx.x;
+        r[i] = (bx * NPT + i) * FK_NT + threadIdx.x;
         const int rr = min(r[i], npair - 1);
         Pxh[i] = f2(Phl[rr]);
         Pyh[i] = f2(Phl[(size_t)npair + rr]);
@@ -285,8 +285,27 @@ __global__ void __launch_bounds__(FK_NT, fk_min_blocks(L, NPT))
             const double g = 0.88622692545275801365 / sqrt(gp[r[i]]);
 #pragma unroll
             for (int h = 0; h < NH; ++h)
-                W[((size_t)blockIdx.y * NH + h) * npair + r[i]] = g * ((double)ah[i][h] + (double)al[i][h]);
+                W[((size_t)by * NH + h) * npair + r[i]] = g * ((double)ah[i][h] + (double)al[i][h]);
         }
+}
+
+template <int L, int NPT>
+__global__ void __launch_bounds__(FK_NT, fk_min_blocks(L, NPT))
+    fock_kernel_f32x2(int npair, const double *__restrict__ gp, const float *__restrict__ Phl,
+                      const float *__restrict__ nc, int ntile, int tps, const float *__restrict__ tiles,
+                      const int *__restrict__ tile_cls, const float *__restrict__ boys, double *__restrict__ W,
+                      int *__restrict__ err)
+{
+    fock_block<L, NPT>(blockIdx.x, blockIdx.y, npair, gp, Phl, nc, ntile, tps, tiles, tile_cls, boys, W, err);
+}
+
+// The same for a table of blocks of many molecules (one launch per class)
+template <int L, int NPT>
+__global__ void __launch_bounds__(FK_NT, fk_min_blocks(L, NPT))
+    fock_jobs_kernel(const FockJob *__restrict__ jobs, const float *__restrict__ boys, int *__restrict__ err)
+{
+    const FockJob &j = jobs[blockIdx.x];
+    fock_block<L, NPT>(j.bx, j.by, j.npair, j.gp, j.Phl, j.nc, j.ntile, j.tps, j.tiles, j.tile_cls, boys, j.W, err);
 }
 
 template <int L, int NPT>
@@ -306,6 +325,28 @@ static int fock_packed_launch(pcm_ctx *c, int npair, const double *gp, const flo
     PCM_LAUNCHED(c);
     const int tps = std::max(1, (ntile + nsplit - 1) / nsplit);
     const int nb = (npair + FK_NT * NPT - 1) / (FK_NT * NPT);
+    if (c->jobs) {
+        // a batch: the blocks join one launch per class with the other molecules'
+        auto &v = c->jobs->fock[L][NPT == 2 ? 1 : 0];
+        for (int by = 0; by < nsplit; ++by)
+            for (int bx = 0; bx < nb; ++bx) {
+                FockJob fj;
+                fj.gp = gp;
+                fj.Phl = Phl;
+                fj.nc = nbuf.p;
+                fj.tiles = c->fk_tiles.p;
+                fj.tile_cls = c->fk_cls.p;
+                fj.W = W;
+                fj.npair = npair;
+                fj.ntile = ntile;
+                fj.tps = tps;
+                fj.bx = bx;
+                fj.by = by;
+                fj.pad = 0;
+                v.push_back(fj);
+            }
+        return PCM_OK;
+    }
     dim3 grid(nb, nsplit);
     fock_kernel_f32x2<L, NPT><<<grid, FK_NT, 0, c->stream>>>(npair, gp, Phl, nbuf.p, ntile, tps, c->fk_tiles.p,
                                                             c->fk_cls.p, c->boys32.p, W, c->dev_err.p);
@@ -333,6 +374,50 @@ int fock_packed(pcm_ctx *c, int L, int npt, int npair, const double *gp, const f
     case 5: return fock_packed_launch<5, 1>(c, npair, gp, Phl, nbuf, dq, nsplit, W);
     }
     return PCM_ERR_ARG;
+}
+
+// Launch every block collected from a batch's molecules: one launch per
+// (kernel, angular momentum, points or pairs per thread).  The job tables are
+// copied from the sink (kept by the caller until the stream has run them).
+int launch_jobs(JobSink &sink, DBuf<EspJob> &dej, DBuf<FockJob> &dfj, const float *boys, int *err, cudaStream_t s)
+{
+    size_t ne = 0, nf = 0;
+    for (auto &v : sink.esp)
+        for (auto &w : v) ne += w.size();
+    for (auto &v : sink.fock)
+        for (auto &w : v) nf += w.size();
+    if (ne) PCM_TRY(dej.alloc(ne));
+    if (nf) PCM_TRY(dfj.alloc(nf));
+    size_t o = 0;
+    for (int L = 0; L < 5; ++L)
+        for (int v = 0; v < 2; ++v) {
+            const auto &w = sink.esp[L][v];
+            if (w.empty()) continue;
+            PCM_CUDA(cudaMemcpyAsync(dej.p + o, w.data(), w.size() * sizeof(EspJob), cudaMemcpyHostToDevice, s));
+            PCM_TRY(esp_packed_jobs(L, v == 1 ? 4 : 2, dej.p + o, (int)w.size(), boys, err, s));
+            o += w.size();
+        }
+    o = 0;
+    for (int L = 0; L < 6; ++L)
+        for (int v = 0; v < 2; ++v) {
+            const auto &w = sink.fock[L][v];
+            if (w.empty()) continue;
+            PCM_CUDA(cudaMemcpyAsync(dfj.p + o, w.data(), w.size() * sizeof(FockJob), cudaMemcpyHostToDevice, s));
+            switch (L) {
+            case 0: v ? fock_jobs_kernel<0, 2><<<(unsigned)w.size(), FK_NT, 0, s>>>(dfj.p + o, boys, err)
+                      : fock_jobs_kernel<0, 1><<<(unsigned)w.size(), FK_NT, 0, s>>>(dfj.p + o, boys, err); break;
+            case 1: v ? fock_jobs_kernel<1, 2><<<(unsigned)w.size(), FK_NT, 0, s>>>(dfj.p + o, boys, err)
+                      : fock_jobs_kernel<1, 1><<<(unsigned)w.size(), FK_NT, 0, s>>>(dfj.p + o, boys, err); break;
+            case 2: v ? fock_jobs_kernel<2, 2><<<(unsigned)w.size(), FK_NT, 0, s>>>(dfj.p + o, boys, err)
+                      : fock_jobs_kernel<2, 1><<<(unsigned)w.size(), FK_NT, 0, s>>>(dfj.p + o, boys, err); break;
+            case 3: fock_jobs_kernel<3, 1><<<(unsigned)w.size(), FK_NT, 0, s>>>(dfj.p + o, boys, err); break;
+            case 4: fock_jobs_kernel<4, 1><<<(unsigned)w.size(), FK_NT, 0, s>>>(dfj.p + o, boys, err); break;
+            case 5: fock_jobs_kernel<5, 1><<<(unsigned)w.size(), FK_NT, 0, s>>>(dfj.p + o, boys, err); break;
+            }
+            PCM_CUDA(cudaGetLastError());
+            o += w.size();
+        }
+    return PCM_OK;
 }
 
 }  // namespace pcm

@@ -850,6 +850,12 @@ static void fock_split(pcm_ctx *c, int nb, int *nsplit, int *ks)
 // pairs per thread, each timed once; the faster is remembered.
 static int fock_tune(pcm_ctx *c, int k, int L, const double *dq)
 {
+    struct NoDefer {
+        pcm_ctx *c;
+        JobSink *j;
+        ~NoDefer() { c->jobs = j; }
+    } nd{c, c->jobs};
+    c->jobs = nullptr;   // the trials run now, whatever the caller collects
     PairClass &pc = c->cls[k];
     const int bucket = tune_bucket(pc.npair);
     const int kind = c->opt.fp32x2 ? TUNE_FOCK_NPT : TUNE_FOCK_NPT_SCALAR;
@@ -878,20 +884,62 @@ static int fock_tune(pcm_ctx *c, int k, int L, const double *dq)
 }
 
 template <int LA, int LB>
+static void fock_epilogue(pcm_ctx *c, PairClass &pc, int nsplit, const double *W, double *ddF)
+{
+    fock_epilogue_kernel<LA, LB><<<(pc.nsp + 127) / 128, 128, 0, c->stream>>>(
+        pc.nsp, pc.npair, nsplit, pc.spA.p, pc.spB.p, pc.sp_start.p, pc.ia.p, pc.ib.p, c->sh_atom.p, c->sh_off.p,
+        c->sh_bf.p, c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, W, c->nbf, ddF);
+}
+
+// the Fock epilogues a batch deferred until its packed blocks had run
+int fock_mixed_finish(pcm_ctx *c, double *ddF)
+{
+    for (int k = 0; k < 6; ++k) {
+        if (!c->fock_pending[k]) continue;
+        c->fock_pending[k] = false;
+        PairClass &pc = c->cls[k];
+        const double *W = c->fock_Wk[k].p;
+        const int ns = c->fock_nsplit_k[k];
+        switch (k) {
+        case 0: fock_epilogue<0, 0>(c, pc, ns, W, ddF); break;
+        case 1: fock_epilogue<1, 0>(c, pc, ns, W, ddF); break;
+        case 2: fock_epilogue<1, 1>(c, pc, ns, W, ddF); break;
+        case 3: fock_epilogue<2, 0>(c, pc, ns, W, ddF); break;
+        case 4: fock_epilogue<2, 1>(c, pc, ns, W, ddF); break;
+        case 5: fock_epilogue<2, 2>(c, pc, ns, W, ddF); break;
+        }
+        PCM_LAUNCHED(c);
+    }
+    return PCM_OK;
+}
+
+template <int LA, int LB>
 static int fock_class(pcm_ctx *c, PairClass &pc, const double *dq, double *ddF)
 {
     constexpr int L = LA + LB;
     constexpr int NH = nherm(L);
     if (pc.nsp == 0) return PCM_OK;
     int nsplit = 1;
+    const int kk = (int)(&pc - c->cls);
+    // a batch collects the packed blocks of every molecule and runs the
+    // epilogue afterwards (fock_mixed_finish), with one W per class
+    const bool defer = c->jobs && c->opt.precision == PCM_MIXED && c->opt.fp32x2;
     if (pc.npair > 0) {
         const bool mixed = c->opt.precision == PCM_MIXED;
-        const int k = (int)(&pc - c->cls);
+        const int k = kk;
         if (mixed && c->opt.autotune) PCM_TRY(fock_tune(c, k, L, dq));
         const int npt = mixed ? fock_mixed_pairs_per_thread(c, L, pc.npair) : 1;
         const int nb = (pc.npair + FOCK_NT * npt - 1) / (FOCK_NT * npt);
         int ks;
         fock_split(c, nb, &nsplit, &ks);
+        if (defer) {
+            PCM_TRY(c->fock_Wk[k].alloc((size_t)nsplit * NH * pc.npair));
+            PCM_TRY(fock_mixed_class(c, k, dq, nsplit, ks, c->fock_Wk[k].p, npt));
+            c->fock_nsplit_k[k] = nsplit;
+            c->fock_pending[k] = true;
+            c->stats.integrals_fock += (double)pc.npair * ncart(LA) * ncart(LB) * c->M;
+            return PCM_OK;
+        }
         PCM_TRY(c->fock_W.alloc((size_t)nsplit * NH * pc.npair));
         dim3 grid(nb, nsplit);
         if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[6 + k], c->stream));
@@ -906,9 +954,14 @@ static int fock_class(pcm_ctx *c, PairClass &pc, const double *dq, double *ddF)
         }
         if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[6 + k], c->stream));
     }
-    fock_epilogue_kernel<LA, LB><<<(pc.nsp + 127) / 128, 128, 0, c->stream>>>(
-        pc.nsp, pc.npair, nsplit, pc.spA.p, pc.spB.p, pc.sp_start.p, pc.ia.p, pc.ib.p, c->sh_atom.p, c->sh_off.p,
-        c->sh_bf.p, c->cnorm.p, c->xyz.p, pc.Px.p, pc.Py.p, pc.Pz.p, pc.p.p, pc.pref.p, c->fock_W.p, c->nbf, ddF);
+    if (defer) {
+        // no kept pairs: the epilogue writes the class's zero blocks
+        PCM_TRY(c->fock_Wk[kk].alloc(1));
+        c->fock_nsplit_k[kk] = nsplit;
+        c->fock_pending[kk] = true;
+        return PCM_OK;
+    }
+    fock_epilogue<LA, LB>(c, pc, nsplit, c->fock_W.p, ddF);
     PCM_LAUNCHED(c);
     c->stats.integrals_fock += (double)pc.npair * ncart(LA) * ncart(LB) * c->M;
     return PCM_OK;
@@ -923,6 +976,7 @@ int fock_compute(pcm_ctx *c, const double *dq, double *ddF)
     PCM_TRY((fock_class<2, 0>(c, c->cls[3], dq, ddF)));
     PCM_TRY((fock_class<2, 1>(c, c->cls[4], dq, ddF)));
     PCM_TRY((fock_class<2, 2>(c, c->cls[5], dq, ddF)));
+    if (c->jobs) return PCM_OK;
     if (c->have_events) PCM_CUDA(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < 6; ++k) {
         c->stats.fock_class_pairs[k] = c->cls[k].npair;

@@ -901,16 +901,18 @@ static int mixed_point_blocks(pcm_ctx *c, int nblk[2])
     }
     DBuf<int> *blk = &c->si[4], *bcls = &c->si[6];
     for (int v = 0; v < 2; ++v) {
+        // kept in the context: the copies below read them after this returns
+        // (the next call that rewrites them comes after a synchronisation)
+        c->h_pblk[v] = off[v];
+        c->h_pbcls[v] = bc[v];
         PCM_TRY(blk[v].alloc(off[v].size()));
         PCM_TRY(bcls[v].alloc(bc[v].size()));
-        PCM_CUDA(cudaMemcpyAsync(blk[v].p, off[v].data(), off[v].size() * sizeof(int), cudaMemcpyHostToDevice,
+        PCM_CUDA(cudaMemcpyAsync(blk[v].p, c->h_pblk[v].data(), off[v].size() * sizeof(int), cudaMemcpyHostToDevice,
                                  c->stream));
-        PCM_CUDA(cudaMemcpyAsync(bcls[v].p, bc[v].data(), bc[v].size() * sizeof(int), cudaMemcpyHostToDevice,
-                                 c->stream));
+        PCM_CUDA(cudaMemcpyAsync(bcls[v].p, c->h_pbcls[v].data(), bc[v].size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, c->stream));
         nblk[v] = (int)bc[v].size();
     }
-    // the host vectors are read by the copies above before they go out of scope
-    PCM_CUDA(cudaStreamSynchronize(c->stream));
     return PCM_OK;
 }
 
@@ -1023,6 +1025,12 @@ static int esp_rows_v(pcm_ctx *c, int k, int v, const int nb[2])
 // kernel family, angular momentum and size bucket.
 static int esp_tune(pcm_ctx *c, int k, DBuf<int> *blk, DBuf<int> *bcls, const int nb[2], int *choice)
 {
+    struct NoDefer {
+        pcm_ctx *c;
+        JobSink *j;
+        ~NoDefer() { c->jobs = j; }
+    } nd{c, c->jobs};
+    c->jobs = nullptr;   // the trials run now, whatever the caller collects
     const int L = CLASS_L[k];
     const int bucket = tune_bucket((long long)c->cls[k].nesp);
     const int kind = c->opt.fp32x2 ? TUNE_ESP_PPT : TUNE_ESP_PPT_SCALAR;
@@ -1076,7 +1084,10 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
         total += rows[k];
     }
     if (total == 0) {
+        c->esp_total_rows = 0;
+        c->esp_out = dc;
         PCM_CUDA(cudaMemsetAsync(dc, 0, c->M * sizeof(double), c->stream));
+        if (c->jobs) return PCM_OK;
         PCM_CUDA(cudaStreamSynchronize(c->stream));
         return PCM_OK;
     }
@@ -1087,10 +1098,22 @@ int esp_compute_mixed(pcm_ctx *c, double *dc)
         PCM_TRY(esp_launch_variant(c, k, var[k], blk, bcls, nb, c->esp_part.p + (size_t)base * c->M));
         base += rows[k];
     }
-    esp_reduce_mixed_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, total, c->esp_part.p, dc);
-    PCM_LAUNCHED(c);
+    c->esp_total_rows = total;
+    c->esp_out = dc;
+    if (c->jobs) return PCM_OK;   // the batch launches the packed blocks, then esp_mixed_finish
+    PCM_TRY(esp_mixed_finish(c));
     PCM_CUDA(cudaStreamSynchronize(c->stream));  // the class timers are read next
     return check_device_error(c, "pcm_esp");
+}
+
+// c = the sum of the partial rows (after the packed blocks have run)
+int esp_mixed_finish(pcm_ctx *c)
+{
+    if (c->esp_total_rows == 0) return PCM_OK;
+    esp_reduce_mixed_kernel<<<(c->M + 255) / 256, 256, 0, c->stream>>>(c->M, c->esp_total_rows, c->esp_part.p,
+                                                                       c->esp_out);
+    PCM_LAUNCHED(c);
+    return PCM_OK;
 }
 
 int fock_mixed_class(pcm_ctx *c, int k, const double *dq, int nsplit, int ksplit, double *W, int npt)

@@ -1,12 +1,16 @@
-"""Batched runs (pcm_batch_run: every solve in lockstep, the PCG loop as a
-device-driven CUDA graph) against the single-molecule path on the same
-inputs, and one molecule against the oracle.  Five clusters of uneven size
-(one below the Jacobi threshold, the others on RBJ)."""
+"""Batched runs (pcm_batch_run: the packed integral blocks of all molecules
+in one launch per angular class under PCM_MIXED, every solve in lockstep with
+the PCG loop as a device-driven CUDA graph, or with matrix-free members one
+persistent solver per molecule) against the single-molecule path on the same
+inputs, and three molecules against the oracle (energy, the charges against
+the LU solution, dF element by element).  Five clusters of uneven size (one below the Jacobi threshold, the
+others on RBJ)."""
 import numpy as np
 import pytest
 
 import oracle
 import workloads
+from _parity import FP64, MIXED, check
 
 pytestmark = pytest.mark.gpu
 
@@ -28,9 +32,9 @@ def _single(w, precision, delta):
         return dict(E=ctx.energy(q), q=q, dF=ctx.fock(q), it=st["iterations"], conv=st["converged"])
 
 
-def _batch(mols, precision, delta, device=False):
+def _batch(mols, precision, delta, device=False, operator="auto"):
     import paper_1505_07851_gb300 as pcm
-    with pcm.Batch(len(mols), precision=precision) as b:
+    with pcm.Batch(len(mols), precision=precision, operator=operator) as b:
         for i, w in enumerate(mols):
             b.set_molecule(i, w.mol, w.basis)
         Ps = [w.P for w in mols]
@@ -66,11 +70,28 @@ def test_mixed_batch_energy_error_vs_fp64(mols):
         assert np.max(np.abs(dF[i] - ref["dF"])) <= 1e-5 * np.max(np.abs(ref["dF"]))
 
 
-def test_batch_molecule_against_oracle(mols):
-    w = mols[2]
-    E, q, dF, st, tot = _batch(mols, "fp64", 1e-10)
-    o = oracle.run(w, delta=1e-10)
-    assert abs(E[2] - o["E_lu"]) <= 1e-9
+@pytest.mark.parametrize("precision,operator", [("fp64", "auto"), ("mixed", "auto"), ("mixed", "free")])
+def test_batch_molecules_against_oracle(mols, precision, operator):
+    import paper_1505_07851_gb300 as pcm
+    E, q, dF, st, tot = _batch(mols, precision, 1e-10, operator=operator)
+    bars = FP64 if precision == "fp64" else MIXED
+    for i in (0, 2, 4):
+        w = mols[i]
+        o = oracle.run(w, delta=1e-10)
+        assert st[i]["converged"]
+        assert abs(E[i] - o["E_lu"]) <= (1e-9 if precision == "fp64" else 1e-6), (i, E[i] - o["E_lu"])
+        with pcm.Context() as ctx:
+            ctx.build_surface(w.mol.xyz, w.mol.Z, w.mol.radius, 110)
+            _, idx = ctx.get_surface()
+        pos = {int(k): j for j, k in enumerate(o["surf"]["index"])}
+        perm = np.array([pos[int(k)] for k in idx])
+        q_o = np.empty_like(q[i])
+        q_o[perm] = q[i]
+        check(dF[i], oracle.fock(o["eb"], q_o, o["surf"]["r"], o["surf"]["zeta"]), bars, what="dF %d" % i)
+        # the batch's c stays inside it; its charges solve A q = -f (Bz + c) to the
+        # threshold, so they are compared with the LU solution of the oracle's system
+        lam_min = np.linalg.eigvalsh(o["A"])[0]
+        assert np.linalg.norm(q[i] - o["q_lu"][perm]) <= 10 * 1e-10 / lam_min + (0 if precision == "fp64" else 1e-5)
 
 
 def test_device_pointers_bit_identical(mols):
