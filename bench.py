@@ -81,18 +81,6 @@ def flops_per_interaction(L, kind):
     return base + 1 + _nherm(L)
 
 
-def flops_per_interaction_f32(L, kind):
-    """The packed FP32 kernels' own operations, compensation terms included
-    (the Kahan sum excepted): split-coordinate distance (9), R^2 (5), T from
-    split rho (3), Boys by 4-term Taylor (5 + 6 (L+1)), (-2 rho)^n with the
-    first-order rho_lo correction (4L + 1), Hermite recurrence, then the dot
-    with U D_000 split (2 nherm + 1) or the accumulation (nherm + 1)."""
-    base = 9 + 5 + 3 + 5 + 6 * (L + 1) + (4 * L + 1 if L else 0) + _hermite_ops(L)
-    if kind == "esp":
-        return base + 2 * _nherm(L) + 1
-    return base + _nherm(L) + 1
-
-
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
@@ -234,7 +222,7 @@ def _timed_steps(pcm, w, precision, args, dev, stream, flush, delta, steps, warm
     import torch
     ctx = pcm.Context(precision=precision, device=dev.index, stream=stream.cuda_stream, timing=True,
                       seed=args.seed, autotune=(precision == "mixed" and args.autotune),
-                      fp32x2=not args.scalar_fp32)
+                      fp32x2=not args.scalar_fp32, operator=args.operator)
     b = w.basis
     Pd = torch.tensor(w.P, dtype=torch.float64, device=dev)
     bufs = {}
@@ -324,12 +312,12 @@ def _time_gradient(res, q, flush, stream, steps):
     return statistics.mean(ts), g.cpu().numpy(), ctx.stats()
 
 
-def _dominant(res, precision, steps, packed=True):
+def _dominant(res, precision, steps, packed=True, measured=None):
     """The step's longest integral class: its algorithmic flops (the per-
-    interaction figures of flops_per_interaction, the same in both precisions)
-    over its CUDA-event time, against the pipe peak of its precision; the FP32
-    kernels' own operation count (with the hi + lo compensation terms) is
-    reported beside it."""
+    interaction figures of flops_per_interaction, the same in both precisions
+    and for near and far pairs) over its CUDA-event time, against the nominal
+    pipe peak of its precision (unit counts x maximum clock) and, when given,
+    the pipe rate pcm_pipe_peak measured on this GPU."""
     s = res["stats"]
     M = s["M"]
     tag = "f64" if precision == "fp64" else ("f32x2" if packed else "f32")
@@ -338,19 +326,30 @@ def _dominant(res, precision, steps, packed=True):
         for kind, ms in (("esp", res["esp_cls"][k]), ("fock", res["fock_cls"][k])):
             if ms > 0:
                 n = s["%s_class_pairs" % kind][k] * M
-                cand.append(("%s_kernel_%s<L=%d> (%s)" % (kind, tag, CLASS_L[k], CLASS_NAME[k]), ms / steps,
-                             n * flops_per_interaction(CLASS_L[k], kind),
-                             n * flops_per_interaction_f32(CLASS_L[k], kind)))
-    name, ms_k, flops_k, ops_k = max(cand, key=lambda t: t[1])
+                if precision == "fp64":
+                    label = "%s %s class: %s_kernel_f64<L=%d>" % (kind.upper(), CLASS_NAME[k], kind, CLASS_L[k])
+                else:
+                    rest = "same-atom pairs (esp_kernel_f32) + reduction" if kind == "esp" else "epilogue"
+                    label = ("%s %s class: %s_kernel_%s<L=%d> + %s"
+                             % (kind.upper(), CLASS_NAME[k], kind, tag, CLASS_L[k], rest))
+                cand.append((label, ms / steps, n * flops_per_interaction(CLASS_L[k], kind)))
+    name, ms_k, flops_k = max(cand, key=lambda t: t[1])
     peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
     achieved = flops_k / (ms_k * 1e-3) / 1e12
-    src = ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (nominal 1.25 TFLOP/s)" if precision == "fp64" else
-           "FP32 pipe: 152 SMs x 128 FFMA/clk x 2070 MHz")
+    src = ("nominal FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz" if precision == "fp64" else
+           "nominal FP32 pipe: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz")
     out = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
            "frac": achieved / peak, "peak_source": src, "kernel_ms": ms_k,
-           "flops": "algorithmic: flops_per_interaction x pair-point interactions"}
-    if precision != "fp64":
-        out["achieved_with_compensation_ops"] = ops_k / (ms_k * 1e-3) / 1e12
+           "flops": "algorithmic: flops_per_interaction (Hermite form with Boys F_0..F_L) x pair-point "
+                    "interactions; far pairs run a cheaper multipole form and count the same"}
+    out["classes"] = {lab.split(" class")[0]: {"ms": round(t, 3), "achieved": round(f / (t * 1e-3) / 1e12, 3),
+                                              "frac": round(f / (t * 1e-3) / 1e12 / peak, 3)}
+                      for lab, t, f in cand}
+    if measured:
+        key = "fp64" if precision == "fp64" else ("fp32x2" if packed else "fp32")
+        out["peak_measured"] = measured[key]
+        out["peak_measured_source"] = "pcm_pipe_peak(%s): independent FMA chains, CUDA events" % key
+        out["frac_of_measured"] = achieved / measured[key]
     return out
 
 
@@ -381,7 +380,7 @@ def torch_sync():
     torch.cuda.synchronize()
 
 
-def _fp64_record(other, E_ref, world):
+def _fp64_record(other, E_ref, world, pipe=None):
     n = len(other["times"])
     return {"value": other["ints"] * world / (sum(other["times"]) * 1e-3), "unit": UNIT,
             "ms_per_step": sum(other["times"]) / n, "steps": n,
@@ -389,10 +388,10 @@ def _fp64_record(other, E_ref, world):
             "esp_kernel_ms": float(other["esp_cls"].sum() / n),
             "fock_kernel_ms": float(other["fock_cls"].sum() / n),
             "energy_err_Eh": abs(other["E"][-1] - E_ref), "phase_ms": other["phase_ms"],
-            "roofline": _dominant(other, "fp64", n)}
+            "roofline": _dominant(other, "fp64", n, measured=pipe)}
 
 
-def _small_record(pcm, args, dev, stream, flush, delta):
+def _small_record(pcm, args, dev, stream, flush, delta, pipe=None):
     """The 300-atom s/sp cluster (nbf ~ 1.66k, M ~ 12k), timed as the main
     workload: mixed steps, one FP64 step, energies against delta = 1e-10."""
     w = workloads.config(WORKLOADS["cluster300_sp"])
@@ -403,9 +402,9 @@ def _small_record(pcm, args, dev, stream, flush, delta):
            "value": main["ints"] / (sum(main["times"]) * 1e-3), "unit": UNIT, "steps": n,
            "ms_per_step": sum(main["times"]) / n, "pcg_solve_ms": statistics.mean(main["solve_ms"]),
            "pcg_iterations": statistics.mean(main["iters"]), "energy_err_Eh": abs(main["E"][-1] - E_ref),
-           "phase_ms": main["phase_ms"], "roofline": _dominant(main, args.precision, n, packed=not args.scalar_fp32)}
+           "phase_ms": main["phase_ms"], "roofline": _dominant(main, args.precision, n, packed=not args.scalar_fp32, measured=pipe)}
     if other is not None:
-        rec["fp64"] = _fp64_record(other, E_ref, 1)
+        rec["fp64"] = _fp64_record(other, E_ref, 1, pipe)
         rec["speedup_vs_fp64"] = rec["fp64"]["ms_per_step"] / rec["ms_per_step"]
     main["ctx"].close()
     if other is not None:
@@ -437,7 +436,8 @@ def run_ours(args):
         other = _timed_steps(pcm, w, "fp64", args, dev, stream, flush, delta, args.fp64_steps, 1)
 
     value, total_ms_max = replica_throughput(main["ints"], sum(main["times"]), world, dev)
-    roofline = _dominant(main, args.precision, args.steps, packed=not args.scalar_fp32)
+    pipe = {k: pcm.pipe_peak(k, local) for k in ("fp32", "fp32x2", "fp64")}
+    roofline = _dominant(main, args.precision, args.steps, packed=not args.scalar_fp32, measured=pipe)
     roofline["traffic"] = args.traffic if args.traffic is not None else \
         NCU_TRAFFIC_BYTES.get((w.name, roofline["kernel"]))
     s = main["stats"]
@@ -491,12 +491,13 @@ def run_ours(args):
             "fock_class_ms": [float(x) / args.steps for x in main["fock_cls"]],
             "integrals_per_step": main["ints"] / args.steps, "pairs_kept": s["pairs_kept"],
             "phase_ms": main["phase_ms"],
-            "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": main["launches"],
+            "roofline": roofline, "pipe_peaks_measured_tflops": pipe,
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": main["launches"],
             "autotune": pcm.autotune_table(),
             "cpu_baseline": cpu,
         }
         if other is not None:
-            line["fp64"] = _fp64_record(other, E_ref, world)
+            line["fp64"] = _fp64_record(other, E_ref, world, pipe)
             line["speedup_vs_fp64"] = line["fp64"]["ms_per_step"] / line["ms_per_step"]
         if not args.no_grad:
             q = main["bufs"]["q"]
@@ -545,7 +546,7 @@ def run_ours(args):
             line["scf_sequence"] = sc
         main["ctx"].close()
         if not args.no_small and w.name != "cluster300_sp":
-            line["cluster300_sp"] = _small_record(pcm, args, dev, stream, flush, delta)
+            line["cluster300_sp"] = _small_record(pcm, args, dev, stream, flush, delta, pipe)
         if not args.no_batch:
             line["batch"] = measure_batch(pcm, args, dev, stream, flush, delta, steps=2, warmup=1,
                                           operator=args.batch_operator)
@@ -795,6 +796,8 @@ def main():
     ap.add_argument("--no-grad", action="store_true", help="skip the nuclear-gradient timing")
     ap.add_argument("--no-small", action="store_true", help="skip the 300-atom sub-record")
     ap.add_argument("--nmol", type=int, default=64, help="conformations in the batch workload")
+    ap.add_argument("--operator", default="auto", choices=["auto", "stored", "free"],
+                    help="PCM_MIXED operator of the single-molecule contexts (auto: matrix-free above 24576 points)")
     ap.add_argument("--batch-operator", default="auto", choices=["auto", "stored", "free"],
                     help="operator of the batch members (auto: stored, lockstep solver)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch sub-record")

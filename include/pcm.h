@@ -110,7 +110,7 @@ typedef struct pcm_options {
 /* operator modes (PCM_MIXED; PCM_FP64 always stores A) */
 #define PCM_OPERATOR_AUTO 0     /* matrix-free above 24576 points or when the stored parts would take more than a
                                    quarter of the free device memory, else stored */
-#define PCM_OPERATOR_STORED 1   /* A stored in FP64 and as FP32 hi + lo parts (16 bytes per element) */
+#define PCM_OPERATOR_STORED 1   /* A stored as FP32 hi + lo parts (8 bytes per element, no FP64 copy) */
 #define PCM_OPERATOR_FREE 2     /* no stored A: near pairs kept exactly, every other element 1/R recomputed */
 
 typedef struct pcm_stats {
@@ -226,13 +226,15 @@ int pcm_energy(pcm_ctx *ctx, const double *q, const double *c, double *E, int fl
 
 /* y = A x with the context's operator (Eq. 2, Eq. 3, Eq. 8) for its current
  * surface: x, y are M-vectors in library point order.  PCM_FP64 multiplies
- * by the stored FP64 A.  PCM_MIXED keeps no A: pairs with zeta' R below a
- * cutoff (the diagonal included) are held with their FP64 values, every other
- * element is 1/R recomputed per product; the default product is the one the
- * solver forms true residuals and the energy with (double-float 1/R, FP64
- * near pairs, about 1e-14 relative), PCM_APPLY_FP32 the inner solver's FP32
- * product (about 1e-6 relative).  flags: PCM_PTR_DEVICE, PCM_ASYNC,
- * PCM_APPLY_FP32 (PCM_ERR_UNSUPPORTED for a PCM_FP64 context). */
+ * by the stored FP64 A.  PCM_MIXED with a stored operator multiplies by
+ * A32 + A32lo in double-float (about 1e-14 relative).  PCM_MIXED with the
+ * matrix-free operator keeps no A: pairs with zeta' R below a cutoff (the
+ * diagonal included) are held with their FP64 values, every other element is
+ * 1/R recomputed per product; the default product is the one the solver forms
+ * true residuals and the energy with (double-float 1/R, FP64 near pairs,
+ * about 1e-14 relative), PCM_APPLY_FP32 the inner solver's FP32 product
+ * (about 1e-6 relative).  flags: PCM_PTR_DEVICE, PCM_ASYNC, PCM_APPLY_FP32
+ * (PCM_ERR_UNSUPPORTED unless the context is matrix-free). */
 int pcm_apply_a(pcm_ctx *ctx, const double *x, double *y, int flags);
 
 /* Nuclear gradient of the solvation energy at fixed density and charges
@@ -307,6 +309,13 @@ int pcm_autotune_table(int *entries, int max_entries);
 
 /* Statistics of the context's last calls. */
 int pcm_get_stats(pcm_ctx *ctx, pcm_stats *st);
+
+/* Measured FMA throughput of the device's FP32 (which = 0), FP64 (which = 1) or
+ * packed FP32x2 (which = 2, two lanes per instruction) pipe in TFLOP/s (an FMA
+ * counts two per lane), from independent FMA chains timed with
+ * CUDA events (the paper has no counterpart; a measurement aid for the roofline
+ * of the integral kernels).  Allocates and frees 16 bytes of device memory. */
+int pcm_pipe_peak(int device, int which, double *tflops);
 
 /* The energy of pcm_energy for callers that cannot allocate device memory
  * (the paper has no counterpart; this is a library service).  A program

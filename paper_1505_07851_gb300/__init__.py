@@ -121,6 +121,7 @@ def _load():
         "pcm_energy_noalloc": (i, [i, vp, i, vp, vp, vp, d, vp, vp]),
         "pcm_cg_threshold": (i, [d, d, i, ctypes.POINTER(d)]),
         "pcm_apply_a": (i, [vp, vp, vp, i]),
+        "pcm_pipe_peak": (i, [i, i, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -160,6 +161,16 @@ def cg_threshold(delta=-1.0, prev_diis_error=-1.0, two_delta=False):
                                ctypes.byref(out))
     if st != PCM_OK:
         raise PCMError(st, "pcm_cg_threshold", _lib.pcm_last_error().decode())
+    return out.value
+
+
+def pipe_peak(which="fp32", device=0):
+    """Measured FMA throughput (TFLOP/s) of the "fp32", "fp64" or packed "fp32x2"
+    pipe (pcm_pipe_peak)."""
+    out = ctypes.c_double()
+    st = _lib.pcm_pipe_peak(int(device), {"fp32": 0, "fp64": 1, "fp32x2": 2}[which], ctypes.byref(out))
+    if st != PCM_OK:
+        raise PCMError(st, "pcm_pipe_peak", _lib.pcm_last_error().decode())
     return out.value
 
 

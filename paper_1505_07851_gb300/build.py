@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpcm.so")
-SOURCES = ["api.cu", "util.cu", "surface.cu", "pairs.cu", "integrals.cu", "integrals_mixed.cu", "esp_packed.cu", "fock_packed.cu", "matfree.cu", "solver.cu", "gradient.cu", "batch.cu", "tune.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "util.cu", "surface.cu", "pairs.cu", "integrals.cu", "integrals_mixed.cu", "esp_packed.cu", "fock_packed.cu", "matfree.cu", "peaks.cu", "solver.cu", "gradient.cu", "batch.cu", "tune.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

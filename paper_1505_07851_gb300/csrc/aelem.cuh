@@ -3,6 +3,8 @@
 // the near-pair list of the matrix-free operator.
 //
 //   AStored  reads a stored FP64 A;
+//   AStoredDF reads the stored double-float A of PCM_MIXED as hi + lo (that
+//            mode keeps no FP64 copy);
 //   AFree    evaluates the element from the surface: exact() in FP64 exactly
 //            as the stored A is built, bin() the coarse ordering key of
 //            |A_kj| from an FP32 estimate (erf only where zeta' R < 6.5),
@@ -35,6 +37,17 @@ struct AStored {
     int lda;
     __device__ __forceinline__ double exact(int k, int j) const { return A[(size_t)k * lda + j]; }
     __device__ __forceinline__ int bin(int k, int j) const { return rbj_bin(A[(size_t)k * lda + j]); }
+};
+
+struct AStoredDF {
+    const float *hi, *lo;
+    int lda;
+    __device__ __forceinline__ double exact(int k, int j) const
+    {
+        const size_t i = (size_t)k * lda + j;
+        return (double)hi[i] + (double)lo[i];
+    }
+    __device__ __forceinline__ int bin(int k, int j) const { return rbj_bin(exact(k, j)); }
 };
 
 struct AFree {

@@ -168,7 +168,6 @@ struct pcm_ctx {
     pcm::DBuf<double> A;
     pcm::DBuf<float> A32;                  // FP32 copy of A for the inner solves of PCM_MIXED
     pcm::DBuf<float> A32lo;                // A - A32 in FP32: A32 + A32lo is the double-float A
-    bool a32_ready = false;
     pcm::DBuf<double> dinv;                // 1 / A_kk
 
     // basis (expanded: sp shells split into an s and a p shell)
@@ -198,7 +197,6 @@ struct pcm_ctx {
 
     // solver work vectors and scalars
     pcm::DBuf<double> vx, vr, vz, vp, vAp, vrhs, vtmp, vro, vd;
-    pcm::DBuf<float> vp32;
     pcm::DBuf<float> vxs32;                // 2 x lda: FP32 hi and lo parts of a GEMV's input vector
     pcm::DBuf<double> red;                 // partial sums
     pcm::DBuf<double> scal;                // device scalars
@@ -245,11 +243,12 @@ struct pcm_ctx {
     bool store_a = false;                  // keep the stored A and its FP32 parts instead (batch members)
     bool mf_active = false;                // this surface's PCM_MIXED solver is matrix-free (set per surface)
     float mf_rc2 = 0.f;
-    int mf_nnz = 0, mf_grid = 0;
-    size_t mf_grid_smem = 0;
+    int mf_nnz = 0;
+    int pg_grid[2] = {0, 0};      // persistent inner PCG: grid (matrix-free, stored)
+    size_t pg_smem[2] = {0, 0};
     pcm::DBuf<float4> mf_pts;
     pcm::DBuf<int> mf_off, mf_cnt, mf_col, mf_out, mf_iperm;
-    pcm::DBuf<double> mf_val, mf_y64, mf_idot, mf_red, mf_rn;
+    pcm::DBuf<double> mf_val, mf_y64, mf_idot, mf_red, mf_rn, st_yp64;
     pcm::DBuf<float> mf_val32, mf_p32, mf_ypart;
     pcm::DBuf<float2> mf_xs;
     pcm::DBuf<unsigned> mf_bar;
@@ -304,7 +303,7 @@ int zeta_pairs(pcm_ctx *c, cudaStream_t s);
 int matfree_build(pcm_ctx *c, cudaStream_t s);
 int matfree_dfmv(pcm_ctx *c, const double *x, double *y, double *part, int *nparts);
 int matfree_mv32(pcm_ctx *c, const double *x, double *y);
-int matfree_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max_iter, int *iters, int *conv,
+int persistent_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max_iter, int *iters, int *conv,
                 double *rnorm);
 inline bool matrix_free(const pcm_ctx *c) { return c->mf_active; }
 // the device error flag: allocated and cleared on first use; check after a synchronisation

@@ -13,11 +13,13 @@
 // far everywhere, so each element is counted exactly once.
 //
 // The inner PCG runs as one persistent cooperative kernel per inner solve:
-// per iteration the matrix-free product (work items of 512 rows x up to 1024
-// columns over all blocks, partial products per column chunk), the update and
+// per iteration the product (matrix-free: work items of 512 rows x up to 1024
+// columns over all blocks; stored FP32 A: one warp per row segment, streamed
+// from HBM; partial products per column chunk either way), the update and
 // preconditioner (Jacobi, or one randomized block-Jacobi block per thread
 // block), and the direction update, separated by grid-wide barriers whose
-// waits are bounded.
+// waits are bounded.  The stored-operator variant serves PCM_MIXED surfaces
+// small enough to keep A32 + A32lo.
 #include <math.h>
 
 #include <algorithm>
@@ -297,7 +299,10 @@ int matfree_dfmv(pcm_ctx *c, const double *x, double *y, double *part, int *npar
 // persistent inner PCG (cooperative launch: every block resident)
 // ---------------------------------------------------------------------------
 struct PcgArgs {
-    int M, S, nitems, ch;        // points, column chunks, work items of the product, chunk width
+    int M, S, nitems, ch;        // points, column chunks, work items of the product (stored: blocks), chunk width
+    const float *A32;            // stored FP32 A (row-major, leading dimension lda); null: matrix-free
+    int lda;
+    double *yp64;                // stored: S x M partial products (FP64) at block positions
     const float4 *pts;           // FP32 coordinates
     float *p32;                  // FP32 copy of the direction (the product's input)
     float rc2;
@@ -445,12 +450,64 @@ __device__ __forceinline__ void pcg_product(const PcgArgs &a, float4 (*sc)[2])
     }
 }
 
+// The product with the stored FP32 A: unit u = (row u / S, column chunk
+// u % S) per warp, the warps of the grid taking units in turn; each lane
+// streams 16-byte pieces of the row (four in flight) against the FP32
+// direction, read through L2 (other blocks wrote it).  The chunk's sum goes to
+// yp64 at the row's block position, p.Ap partial per block to idot[block].
+__device__ __forceinline__ void pcg_product_stored(const PcgArgs &a)
+{
+    __shared__ double red[MV_NT / 32];
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (MV_NT / 32);
+    const int M = a.M;
+    const long long nunits = (long long)M * a.S;
+    double d = 0.0;
+    for (long long u = blockIdx.x * (MV_NT / 32) + (threadIdx.x >> 5); u < nunits; u += nw) {
+        const int r = (int)(u / a.S), sg = (int)(u - (long long)r * a.S);
+        const int c0 = sg * a.ch, c1 = min(M, c0 + a.ch);
+        const float *row = a.A32 + (size_t)r * a.lda;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int col = c0 + 4 * lane;
+        for (; col + 387 < c1; col += 512) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(row + col);
+            const float4 a1 = *reinterpret_cast<const float4 *>(row + col + 128);
+            const float4 a2 = *reinterpret_cast<const float4 *>(row + col + 256);
+            const float4 a3 = *reinterpret_cast<const float4 *>(row + col + 384);
+            const float4 x0 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col));
+            const float4 x1 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col + 128));
+            const float4 x2 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col + 256));
+            const float4 x3 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col + 384));
+            s0 = fmaf(a0.x, x0.x, fmaf(a0.y, x0.y, fmaf(a0.z, x0.z, fmaf(a0.w, x0.w, s0))));
+            s1 = fmaf(a1.x, x1.x, fmaf(a1.y, x1.y, fmaf(a1.z, x1.z, fmaf(a1.w, x1.w, s1))));
+            s2 = fmaf(a2.x, x2.x, fmaf(a2.y, x2.y, fmaf(a2.z, x2.z, fmaf(a2.w, x2.w, s2))));
+            s3 = fmaf(a3.x, x3.x, fmaf(a3.y, x3.y, fmaf(a3.z, x3.z, fmaf(a3.w, x3.w, s3))));
+        }
+        for (; col + 3 < c1; col += 128) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(row + col);
+            const float4 x0 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col));
+            s0 = fmaf(a0.x, x0.x, fmaf(a0.y, x0.y, fmaf(a0.z, x0.z, fmaf(a0.w, x0.w, s0))));
+        }
+        for (int t = col; t < c1 && t < col + 4; ++t) s1 = fmaf(row[t], __ldcg(a.p32 + t), s1);
+        const float v = warp_sum((s0 + s1) + (s2 + s3));
+        if (lane == 0) {
+            a.yp64[(size_t)sg * M + (a.iperm ? a.iperm[r] : r)] = (double)v;
+            d = fma(__ldcg(a.p + r), (double)v, d);
+        }
+    }
+    d = block_sum<double, MV_NT>(d, red);
+    if (threadIdx.x == 0) a.idot[blockIdx.x] = d;
+}
+
 // A p at block position pos (the row at that place of the preconditioner's
 // order): the column chunks' partial products, added in a fixed order
 __device__ __forceinline__ double ap_pos(const PcgArgs &a, int pos)
 {
     double v = 0.0;
-    for (int s = 0; s < a.S; ++s) v += (double)__ldcg(a.ypart + (size_t)s * a.M + pos);
+    if (a.A32)
+        for (int s = 0; s < a.S; ++s) v += __ldcg(a.yp64 + (size_t)s * a.M + pos);
+    else
+        for (int s = 0; s < a.S; ++s) v += (double)__ldcg(a.ypart + (size_t)s * a.M + pos);
     return v;
 }
 
@@ -542,10 +599,11 @@ __device__ __forceinline__ void pcg_direction(const PcgArgs &a, double beta)
     }
 }
 
+template <bool STORED>
 __global__ void __launch_bounds__(MV_NT) pcg_persistent_kernel(PcgArgs a)
 {
     extern __shared__ double srb[];          // RBJ block: l entries
-    __shared__ float4 sc[MV_SUB][2];         // staged columns, lane-duplicated
+    __shared__ float4 sc[STORED ? 1 : MV_SUB][2];   // staged columns, lane-duplicated
     int *err = a.out + 2;
     const int nslot = a.rbj ? a.nblk : (int)gridDim.x;
     // initialisation: x = 0, r = b, z = C r
@@ -558,7 +616,10 @@ __global__ void __launch_bounds__(MV_NT) pcg_persistent_kernel(PcgArgs a)
         pcg_direction(a, 0.0);
         if (!grid_barrier(a.bar, err)) return;
         while (true) {
-            pcg_product(a, sc);
+            if constexpr (STORED)
+                pcg_product_stored(a);
+            else
+                pcg_product(a, sc);
             if (!grid_barrier(a.bar, err)) return;
             const double pAp = grid_sum(a.idot, a.nitems, 1, 0);
             pcg_update(a, rz / pAp, 0, srb);
@@ -603,36 +664,71 @@ static void mv_chunks(int M, int grid, int *S, int *ch)
     *S = (M + w - 1) / w;
 }
 
-// Inner PCG from x = 0 on A x = b with the matrix-free FP32 product and the
-// context's preconditioner, to ||r|| < delta (recursively updated residual)
-// or max_iter steps, in one cooperative launch.
-int matfree_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max_iter, int *iters, int *conv,
-                double *rnorm)
+// Column chunks of the stored-operator product for `grid` blocks of MV_NT/32
+// warps: S chunks per row (multiples of 128 columns), S from 1 to 16 chosen so
+// that the units (rows x chunks) spread most evenly over the warps.
+static void st_chunks(int M, int grid, int *S, int *ch)
+{
+    const double nw = (double)grid * (MV_NT / 32);
+    double best = -1.0;
+    int bs = 1, bw = (M + 127) / 128 * 128;
+    for (int s = 1; s <= 16; ++s) {
+        int w = (M + s - 1) / s;
+        w = (w + 127) / 128 * 128;
+        const int sa = (M + w - 1) / w;
+        const double units = (double)M * sa;
+        const double eff = units / (std::ceil(units / nw) * nw);
+        if (eff > best + 1e-9) {
+            best = eff;
+            bs = sa;
+            bw = w;
+        }
+    }
+    *S = bs;
+    *ch = bw;
+}
+
+// Inner PCG from x = 0 on A x = b with the FP32 product (matrix-free, or the
+// stored A32 of PCM_MIXED) and the context's preconditioner, to ||r|| < delta
+// (recursively updated residual) or max_iter steps, in one cooperative launch.
+int persistent_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max_iter, int *iters, int *conv,
+                   double *rnorm)
 {
     const int M = c->M;
+    const bool stored = !matrix_free(c);
     const int nrt = (M + MV_ROWS - 1) / MV_ROWS;
     const bool rbj = c->pc_kind == PCM_PRECOND_RBJ || c->pc_kind == PCM_PRECOND_OCTREE;
     const size_t smem = rbj ? (size_t)c->rbj_l * sizeof(double) : sizeof(double);
+    const void *kern = stored ? (const void *)pcg_persistent_kernel<true> : (const void *)pcg_persistent_kernel<false>;
+    const int v = stored ? 1 : 0;
     if (smem > 48 * 1024)
-        PCM_CUDA(cudaFuncSetAttribute(pcg_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (c->mf_grid == 0 || c->mf_grid_smem != smem) {
+        PCM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (c->pg_grid[v] == 0 || c->pg_smem[v] != smem) {
         int per = 0, nsm = 0;
-        PCM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_persistent_kernel, MV_NT, smem));
+        PCM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, MV_NT, smem));
         PCM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
         if (per < 1) {
-            set_last_error("matrix-free solver: the persistent kernel cannot be resident");
+            set_last_error("inner solver: the persistent kernel cannot be resident");
             return PCM_ERR_CUDA;
         }
-        c->mf_grid = per * nsm;
-        c->mf_grid_smem = smem;
+        c->pg_grid[v] = per * nsm;
+        c->pg_smem[v] = smem;
     }
-    const int grid = c->mf_grid;
+    const int grid = c->pg_grid[v];
     const int nslot = rbj ? c->rbj_nblk : grid;
     int S, ch;
-    mv_chunks(M, grid, &S, &ch);
+    if (stored)
+        st_chunks(M, grid, &S, &ch);
+    else
+        mv_chunks(M, grid, &S, &ch);
+    if (stored) {
+        PCM_TRY(c->st_yp64.alloc((size_t)S * M));
+        PCM_TRY(c->mf_idot.alloc((size_t)grid));
+    } else {
+        PCM_TRY(c->mf_ypart.alloc((size_t)S * M));
+        PCM_TRY(c->mf_idot.alloc((size_t)nrt * S));
+    }
     PCM_TRY(c->mf_p32.alloc(M));
-    PCM_TRY(c->mf_ypart.alloc((size_t)S * M));
-    PCM_TRY(c->mf_idot.alloc((size_t)nrt * S));
     PCM_TRY(c->vr.alloc(M));
     PCM_TRY(c->vz.alloc(M));
     PCM_TRY(c->vp.alloc(M));
@@ -652,14 +748,17 @@ int matfree_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max_it
     a.M = M;
     a.S = S;
     a.ch = ch;
-    a.nitems = nrt * S;
+    a.nitems = stored ? grid : nrt * S;
+    a.A32 = stored ? c->A32.p : nullptr;
+    a.lda = c->lda;
+    a.yp64 = stored ? c->st_yp64.p : nullptr;
     a.pts = c->mf_pts.p;
     a.p32 = c->mf_p32.p;
     a.rc2 = c->mf_rc2;
     a.off = c->mf_off.p;
     a.col = c->mf_col.p;
     a.val32 = c->mf_val32.p;
-    a.ypart = c->mf_ypart.p;
+    a.ypart = stored ? nullptr : c->mf_ypart.p;
     a.iperm = rbj ? c->mf_iperm.p : nullptr;
     a.idot = c->mf_idot.p;
     a.b = b;
@@ -682,8 +781,7 @@ int matfree_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max_it
     a.out = c->mf_out.p;
     a.rnorm = c->mf_rn.p;
     void *args[] = {&a};
-    PCM_CUDA(cudaLaunchCooperativeKernel((const void *)pcg_persistent_kernel, dim3(grid), dim3(MV_NT), args, smem,
-                                         c->stream));
+    PCM_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(MV_NT), args, smem, c->stream));
     PCM_LAUNCHED(c);
     int h[4];
     double rn = 0.0;
@@ -691,7 +789,7 @@ int matfree_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max_it
     PCM_CUDA(cudaMemcpyAsync(&rn, c->mf_rn.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaStreamSynchronize(c->stream));
     if (h[2]) {
-        set_last_error("matrix-free solver: a grid barrier wait gave up");
+        set_last_error("inner solver: a grid barrier wait gave up");
         return PCM_ERR_TIMEOUT;
     }
     *iters = h[0];

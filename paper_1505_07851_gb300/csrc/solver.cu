@@ -2,8 +2,9 @@
 // residual test of Eq. 20 (Section 4b), Jacobi or randomized block-Jacobi
 // preconditioning (Section 4b-ii), and the energy of Eq. 13.
 //
-// A is stored in FP64 (row-major, leading dimension lda), and for PCM_MIXED
-// also as FP32 hi and lo parts (A32, A32lo).  Each PCG iteration is three
+// A is stored in FP64 (row-major, leading dimension lda) for PCM_FP64, and
+// for PCM_MIXED as FP32 hi and lo parts only (A32, A32lo; no FP64 copy), or
+// not at all (the matrix-free operator).  Each PCG iteration is three
 // kernels:
 //   pcg_gemv_rp  Ap = A p, p.Ap                       -> alpha
 //   pcg_update   x += alpha p, r -= alpha Ap, z = C r, r.r, r.z -> beta, stop test
@@ -120,7 +121,7 @@ __device__ __forceinline__ void sum_partials2(const double *part, int n, double 
     }
 }
 
-// Ap = A p (FP64 or FP32 copy of A), p.Ap -> alpha
+// Ap = A p (FP64 A), p.Ap -> alpha
 template <typename TA>
 __global__ void __launch_bounds__(GV_NT) pcg_gemv_rp_kernel(int M, int lda, const TA *__restrict__ A,
                                                             const TA *__restrict__ px, const double *__restrict__ p,
@@ -273,53 +274,6 @@ __global__ void pcg_dir_kernel(int M, const double *__restrict__ z, double *__re
         p[k] = fma(beta, p[k], z[k]);
 }
 
-// p = z + beta p, also as FP32 for the FP32 GEMV
-__global__ void pcg_dir32_kernel(int M, const double *__restrict__ z, double *__restrict__ p, float *__restrict__ p32,
-                                 const double *__restrict__ scal, const int *__restrict__ iscal,
-                                 cudaGraphConditionalHandle h, int set_cond)
-{
-    pcg_set_condition(h, set_cond, iscal);
-    if (iscal[I_DONE]) return;
-    const double beta = scal[S_BETA];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
-        const double v = fma(beta, p[k], z[k]);
-        p[k] = v;
-        p32[k] = (float)v;
-    }
-}
-
-__global__ void copy32_kernel(int M, const double *__restrict__ a, double *__restrict__ b, float *__restrict__ b32)
-{
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
-        b[k] = a[k];
-        b32[k] = (float)a[k];
-    }
-}
-
-// FP32 copy of the stored A for the inner solves of PCM_MIXED, and the FP32
-// residual A - A32 (A = A32 + A32lo to ~2^-48) for the double-float GEMV
-__global__ void a_to_f32_kernel(long long n, const double *__restrict__ A, float *__restrict__ A32,
-                                float *__restrict__ A32lo)
-{
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double a = A[i];
-        const float h = (float)a;
-        A32[i] = h;
-        A32lo[i] = (float)(a - (double)h);
-    }
-}
-
-static int a32_build(pcm_ctx *c, cudaStream_t st)
-{
-    PCM_TRY(c->A32.alloc((size_t)c->M * c->lda));
-    PCM_TRY(c->A32lo.alloc((size_t)c->M * c->lda));
-    const long long n = (long long)c->M * c->lda;
-    a_to_f32_kernel<<<4 * 152, 256, 0, st>>>(n, c->A.p, c->A32.p, c->A32lo.p);
-    PCM_LAUNCHED(c);
-    c->a32_ready = true;
-    return PCM_OK;
-}
-
 // x -> FP32 hi + lo parts for the double-float GEMV
 __global__ void split_x_kernel(int M, const double *__restrict__ x, float *__restrict__ xh, float *__restrict__ xl)
 {
@@ -341,14 +295,14 @@ __global__ void __launch_bounds__(GV_NT) gemv_df_kernel(int M, int lda, const fl
 }
 
 // y = A x with the stored A: FP64, or double-float from A32 + A32lo when the
-// context is PCM_MIXED and they exist; block partials of x.y in part
+// context is PCM_MIXED; block partials of x.y in part
 static int gemv_a(pcm_ctx *c, const double *x, double *y, double *part, int *np)
 {
     const int M = c->M;
     const int gv = std::max(1, (M + 1) / 2);
     if (np) *np = gv;
     if (matrix_free(c)) return matfree_dfmv(c, x, y, part, np);
-    if (c->opt.precision == PCM_MIXED && c->a32_ready) {
+    if (c->opt.precision == PCM_MIXED) {
         // hi part at 0, lo part at lda (a multiple of 32 floats): both start on
         // the 16-byte boundary the GEMV's float4 loads need
         PCM_TRY(c->vxs32.alloc(2 * (size_t)c->lda));
@@ -807,6 +761,8 @@ static int rbj_status_error(int st)
     return PCM_ERR_CUDA;
 }
 
+static AStoredDF astored_df(pcm_ctx *c) { return AStoredDF{c->A32.p, c->A32lo.p, c->lda}; }
+
 // RBJ permutation and block inverses (Section 4b-ii) on stream s, with the
 // context's own RBJ scratch; the status lands in rbj_status[0]
 static int rbj_build(pcm_ctx *c, cudaStream_t s)
@@ -825,6 +781,10 @@ static int rbj_build(pcm_ctx *c, cudaStream_t s)
     if (matrix_free(c))
         rbj_perm_kernel<AFree><<<1, RBJ_NT, 0, s>>>(M, afree(c), l, c->opt.seed, c->pindex.p, ncand, c->rbj_T.p,
                                                     c->rbj_U.p, c->rbj_U2.p, c->rbj_perm.p, c->rbj_status.p);
+    else if (c->opt.precision == PCM_MIXED)
+        rbj_perm_kernel<AStoredDF><<<1, RBJ_NT, 0, s>>>(M, astored_df(c), l, c->opt.seed, c->pindex.p, ncand,
+                                                        c->rbj_T.p, c->rbj_U.p, c->rbj_U2.p, c->rbj_perm.p,
+                                                        c->rbj_status.p);
     else
         rbj_perm_kernel<AStored><<<1, RBJ_NT, 0, s>>>(M, AStored{c->A.p, c->lda}, l, c->opt.seed, c->pindex.p, ncand,
                                                       c->rbj_T.p, c->rbj_U.p, c->rbj_U2.p, c->rbj_perm.p,
@@ -836,6 +796,9 @@ static int rbj_build(pcm_ctx *c, cudaStream_t s)
     if (matrix_free(c))
         rbj_invert_kernel<AFree><<<c->rbj_nblk, nt, 0, s>>>(M, afree(c), l, c->rbj_perm.p, nullptr, c->rbj_work.p,
                                                             c->rbj_inv.p, c->rbj_status.p);
+    else if (c->opt.precision == PCM_MIXED)
+        rbj_invert_kernel<AStoredDF><<<c->rbj_nblk, nt, 0, s>>>(M, astored_df(c), l, c->rbj_perm.p, nullptr,
+                                                                c->rbj_work.p, c->rbj_inv.p, c->rbj_status.p);
     else
         rbj_invert_kernel<AStored><<<c->rbj_nblk, nt, 0, s>>>(M, AStored{c->A.p, c->lda}, l, c->rbj_perm.p, nullptr,
                                                               c->rbj_work.p, c->rbj_inv.p, c->rbj_status.p);
@@ -868,7 +831,6 @@ int operator_build_async(pcm_ctx *c)
             c->side_rbj = true;
         }
         c->pc_ready = true;
-        if (c->opt.precision == PCM_MIXED && !matrix_free(c) && !c->a32_ready) PCM_TRY(a32_build(c, c->side));
     }
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_b[13], c->side));
     PCM_CUDA(cudaEventRecord(c->ev_side, c->side));
@@ -935,6 +897,10 @@ int solver_prepare(pcm_ctx *c)
             rbj_invert_kernel<AFree><<<c->rbj_nblk, nt, 0, c->stream>>>(M, afree(c), lmax, c->rbj_perm.p,
                                                                         c->rbj_bstart.p, c->rbj_work.p, c->rbj_inv.p,
                                                                         c->rbj_status.p);
+        else if (c->opt.precision == PCM_MIXED)
+            rbj_invert_kernel<AStoredDF><<<c->rbj_nblk, nt, 0, c->stream>>>(M, astored_df(c), lmax, c->rbj_perm.p,
+                                                                            c->rbj_bstart.p, c->rbj_work.p,
+                                                                            c->rbj_inv.p, c->rbj_status.p);
         else
             rbj_invert_kernel<AStored><<<c->rbj_nblk, nt, 0, c->stream>>>(M, AStored{c->A.p, c->lda}, lmax,
                                                                           c->rbj_perm.p, c->rbj_bstart.p,
@@ -961,26 +927,19 @@ int solver_prepare(pcm_ctx *c)
 }
 
 // Everything a solve needs before its first iteration: the preconditioner
-// and, for PCM_MIXED, the FP32 copy of A.
+// (the stored parts of A come with the operator build).
 int solver_prepare_full(pcm_ctx *c)
 {
     PCM_TRY(solver_prepare(c));
-    if (c->opt.precision == PCM_MIXED && !matrix_free(c) && !c->a32_ready) PCM_TRY(a32_build(c, c->stream));
     return PCM_OK;
 }
 
-// Preconditioned CG on A x = b from x (warm) or 0 until the recursively
-// updated residual is below delta or max_iter steps; the FP64 stored A, or
-// with use32 the FP32 copy (FP32 GEMV).  Returns iterations, the stop flag
-// and the final residual norm.
-// One PCG iteration (gemv, update, dir) on stream st; set_cond: the direction
-// kernel sets the graph's loop condition h
-static void pcg_iteration(pcm_ctx *c, cudaStream_t st, double *x, bool use32, cudaGraphConditionalHandle h,
-                          int set_cond)
+// One PCG iteration of the FP64 solver (gemv, update, dir) on stream st;
+// set_cond: the direction kernel sets the graph's loop condition h
+static void pcg_iteration(pcm_ctx *c, cudaStream_t st, double *x, cudaGraphConditionalHandle h, int set_cond)
 {
     const int M = c->M;
     double *r = c->vr.p, *z = c->vz.p, *p = c->vp.p, *Ap = c->vAp.p;
-    float *p32 = c->vp32.p;
     const int gv = gemv_grid(c);
     const int ub = std::min(MAX_PART, (M + UP_NT - 1) / UP_NT);
     const int eb = std::min(1024, (M + 255) / 256);
@@ -989,12 +948,8 @@ static void pcg_iteration(pcm_ctx *c, cudaStream_t st, double *x, bool use32, cu
     const int *bstart = c->pc_kind == PCM_PRECOND_OCTREE ? c->rbj_bstart.p : nullptr;
     const int rbj_nt = std::min(1024, RBJ_SPLIT * std::max(32, (c->rbj_l + 31) / 32 * 32));
     const size_t rbj_smem = (size_t)c->rbj_l * sizeof(double);
-    if (use32)
-        pcg_gemv_rp_kernel<float><<<gv, GV_NT, 0, st>>>(M, c->lda, c->A32.p, p32, p, Ap, c->red.p, c->scal.p,
-                                                         c->iscal.p, c->counter.p);
-    else
-        pcg_gemv_rp_kernel<double><<<gv, GV_NT, 0, st>>>(M, c->lda, c->A.p, p, p, Ap, c->red.p, c->scal.p,
-                                                          c->iscal.p, c->counter.p);
+    pcg_gemv_rp_kernel<double><<<gv, GV_NT, 0, st>>>(M, c->lda, c->A.p, p, p, Ap, c->red.p, c->scal.p, c->iscal.p,
+                                                      c->counter.p);
     if (rbj)
         pcg_update_rbj_kernel<<<c->rbj_nblk, rbj_nt, rbj_smem, st>>>(M, c->rbj_l, c->rbj_perm.p, bstart,
                                                                      c->rbj_inv.p, x, r, z, p, Ap, c->red.p,
@@ -1002,8 +957,7 @@ static void pcg_iteration(pcm_ctx *c, cudaStream_t st, double *x, bool use32, cu
     else
         pcg_update_diag_kernel<<<ub, UP_NT, 0, st>>>(M, dinv, x, r, z, p, Ap, c->red.p, c->scal.p, c->iscal.p,
                                                      c->counter.p);
-    if (use32) pcg_dir32_kernel<<<eb, 256, 0, st>>>(M, z, p, p32, c->scal.p, c->iscal.p, h, set_cond);
-    else pcg_dir_kernel<<<eb, 256, 0, st>>>(M, z, p, c->scal.p, c->iscal.p, h, set_cond);
+    pcg_dir_kernel<<<eb, 256, 0, st>>>(M, z, p, c->scal.p, c->iscal.p, h, set_cond);
 }
 
 // The iteration loop as a CUDA graph: a conditional WHILE node whose body is
@@ -1011,12 +965,11 @@ static void pcg_iteration(pcm_ctx *c, cudaStream_t st, double *x, bool use32, cu
 // is set (the test of Eq. 20, or the iteration cap in finish_update), so every
 // graph launch ends after at most max_iter + 1 bodies.  Rebuilt when anything
 // the captured launches read changes.
-static int pcg_graph(pcm_ctx *c, double *x, bool use32)
+static int pcg_graph(pcm_ctx *c, double *x)
 {
-    const uintptr_t key[] = {(uintptr_t)use32, (uintptr_t)x, (uintptr_t)c->M, (uintptr_t)c->lda,
-                             (uintptr_t)(use32 ? (const void *)c->A32.p : (const void *)c->A.p),
+    const uintptr_t key[] = {(uintptr_t)x, (uintptr_t)c->M, (uintptr_t)c->lda, (uintptr_t)c->A.p,
                              (uintptr_t)c->vr.p, (uintptr_t)c->vz.p, (uintptr_t)c->vp.p, (uintptr_t)c->vAp.p,
-                             (uintptr_t)c->vp32.p, (uintptr_t)c->red.p, (uintptr_t)c->scal.p, (uintptr_t)c->iscal.p,
+                             (uintptr_t)c->red.p, (uintptr_t)c->scal.p, (uintptr_t)c->iscal.p,
                              (uintptr_t)c->counter.p, (uintptr_t)c->pc_kind, (uintptr_t)c->dinv.p,
                              (uintptr_t)c->rbj_perm.p, (uintptr_t)c->rbj_bstart.p, (uintptr_t)c->rbj_inv.p,
                              (uintptr_t)c->rbj_l, (uintptr_t)c->rbj_nblk};
@@ -1044,7 +997,7 @@ static int pcg_graph(pcm_ctx *c, double *x, bool use32)
     cudaGraph_t body = cp->conditional.phGraph_out[0];
     PCM_CUDA(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeThreadLocal));
-    pcg_iteration(c, c->cap_stream, x, use32, handle, 1);
+    pcg_iteration(c, c->cap_stream, x, handle, 1);
     const cudaError_t e = cudaGetLastError();
     cudaGraph_t captured = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &captured);
@@ -1057,8 +1010,11 @@ static int pcg_graph(pcm_ctx *c, double *x, bool use32)
     return PCM_OK;
 }
 
-static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double delta, int max_iter, bool use32,
-                    int *iters, int *conv, double *rnorm)
+// Preconditioned CG on A x = b with the FP64 stored A from x (warm) or 0
+// until the recursively updated residual is below delta or max_iter steps.
+// Returns iterations, the stop flag and the final residual norm.
+static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double delta, int max_iter, int *iters,
+                    int *conv, double *rnorm)
 {
     const int M = c->M;
     if (!c->h_pinned) PCM_CUDA(cudaMallocHost((void **)&c->h_pinned, 32 * sizeof(double)));
@@ -1075,7 +1031,6 @@ static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double
     PCM_CUDA(cudaMemcpyAsync(c->scal.p, hs, S_NSCAL * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     PCM_CUDA(cudaMemcpyAsync(c->iscal.p, hi, I_NINT * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     double *r = c->vr.p, *z = c->vz.p, *p = c->vp.p, *Ap = c->vAp.p;
-    float *p32 = c->vp32.p;
     const int gv = gemv_grid(c);
     const int ub = std::min(MAX_PART, (M + UP_NT - 1) / UP_NT);
     const int eb = std::min(1024, (M + 255) / 256);
@@ -1102,11 +1057,10 @@ static int pcg_core(pcm_ctx *c, const double *drhs, double *x, bool warm, double
                                                           c->counter.p);
     }
     PCM_LAUNCHED(c);
-    if (use32) copy32_kernel<<<eb, 256, 0, c->stream>>>(M, z, p, p32);
-    else copy_kernel<<<eb, 256, 0, c->stream>>>(M, z, p);
+    copy_kernel<<<eb, 256, 0, c->stream>>>(M, z, p);
     PCM_LAUNCHED(c);
 
-    PCM_TRY(pcg_graph(c, x, use32));
+    PCM_TRY(pcg_graph(c, x));
     PCM_CUDA(cudaGraphLaunch(c->pcg_exec, c->stream));
     PCM_CUDA(cudaMemcpyAsync(hi, c->iscal.p, I_NINT * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PCM_CUDA(cudaMemcpyAsync(hs, c->scal.p, S_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1160,7 +1114,6 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
     PCM_TRY(c->vp.alloc(M));
     PCM_TRY(c->vAp.alloc(M));
     PCM_TRY(c->vtmp.alloc(M));
-    PCM_TRY(c->vp32.alloc(M));
     PCM_TRY(c->red.alloc(2 * (size_t)std::max(std::max(MAX_PART, c->rbj_nblk), gemv_grid(c))));
     PCM_TRY(c->scal.alloc(S_NSCAL));
     PCM_TRY(c->counter.alloc(4));
@@ -1172,7 +1125,7 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
         // (which holds its address) is reused whatever output the caller passes
         PCM_TRY(c->vd.alloc(M));
         if (warm) PCM_CUDA(cudaMemcpyAsync(c->vd.p, dq, M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        PCM_TRY(pcg_core(c, drhs, c->vd.p, warm, delta, c->opt.max_iter, false, &iters, &conv, &rnorm));
+        PCM_TRY(pcg_core(c, drhs, c->vd.p, warm, delta, c->opt.max_iter, &iters, &conv, &rnorm));
         PCM_CUDA(cudaMemcpyAsync(dq, c->vd.p, M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     } else {
         // FP64 iterative refinement around FP32 inner solves: the true
@@ -1183,7 +1136,6 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
         // costs a double-float product)
         const double ETA = matrix_free(c) ? 1e-6 : 1e-3;
         constexpr int MAX_REFINE = 12;
-        if (!matrix_free(c) && !c->a32_ready) PCM_TRY(a32_build(c, c->stream));
         PCM_TRY(c->vro.alloc(M));
         PCM_TRY(c->vd.alloc(M));
         if (!warm) PCM_CUDA(cudaMemsetAsync(dq, 0, M * sizeof(double), c->stream));
@@ -1197,12 +1149,8 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
             int it_in = 0, conv_in = 0;
             double rn_in = 0.0;
             const double tol = std::max(ETA * rnorm, 0.5 * delta);
-            if (matrix_free(c))
-                PCM_TRY(matfree_pcg(c, c->vro.p, c->vd.p, tol, std::max(1, c->opt.max_iter - iters), &it_in, &conv_in,
-                                    &rn_in));
-            else
-                PCM_TRY(pcg_core(c, c->vro.p, c->vd.p, false, tol, std::max(1, c->opt.max_iter - iters), true,
-                                 &it_in, &conv_in, &rn_in));
+            PCM_TRY(persistent_pcg(c, c->vro.p, c->vd.p, tol, std::max(1, c->opt.max_iter - iters), &it_in, &conv_in,
+                                   &rn_in));
             iters += it_in;
             ++refinements;
             const int eb = std::min(1024, (M + 255) / 256);

@@ -242,8 +242,9 @@ __global__ void a_build_kernel(int M, int lda, const double *__restrict__ px, co
 // elements with zeta' R <= 6, where erf differs from 1 in FP64, and the
 // diagonal are evaluated in FP64 as in a_build_kernel.  1/R comes out to about
 // 3e-14 relative; the FP32 split of the coordinates limits the elements of the
-// nearest points to ~1e-10 relative.  Writes A (FP64, = hi + lo), A32 (hi) and
-// A32lo (lo), the matrices of the inner FP32 GEMV and of the double-float GEMV.
+// nearest points to ~1e-10 relative.  Writes A32 (hi) and A32lo (lo), the
+// matrices of the inner FP32 GEMV and of the double-float GEMV, and A (FP64,
+// = hi + lo) only when A is not null.
 __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, const float *__restrict__ pl,
                                   const double *__restrict__ px, const double *__restrict__ py,
                                   const double *__restrict__ pz, const double *__restrict__ pzeta,
@@ -312,7 +313,7 @@ __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, 
                 }
                 v = (double)h + (double)lo;
             }
-            A[(size_t)k * lda + l] = v;
+            if (A) A[(size_t)k * lda + l] = v;
             A32[(size_t)k * lda + l] = h;
             A32lo[(size_t)k * lda + l] = lo;
         }
@@ -326,7 +327,7 @@ __global__ void a_build_df_kernel(int M, int lda, const float *__restrict__ ph, 
         const int ll = bi * AT + tx;
         if (k < M && ll < M) {
             const float2 e = tile[tx][r];
-            A[(size_t)k * lda + ll] = tile64[tx][r];
+            if (A) A[(size_t)k * lda + ll] = tile64[tx][r];
             A32[(size_t)k * lda + ll] = e.x;
             A32lo[(size_t)k * lda + ll] = e.y;
         }
@@ -337,6 +338,16 @@ __global__ void dinv_kernel(int M, int lda, const double *__restrict__ A, double
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < M) dinv[k] = 1.0 / A[(size_t)k * lda + k];
+}
+
+__global__ void dinv_df_kernel(int M, int lda, const float *__restrict__ hi, const float *__restrict__ lo,
+                               double *__restrict__ dinv)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < M) {
+        const size_t i = (size_t)k * lda + k;
+        dinv[k] = 1.0 / ((double)hi[i] + (double)lo[i]);
+    }
 }
 
 int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, const double *radius, int n)
@@ -449,14 +460,13 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
             c->mf_active = true;
         } else if (c->opt.operator_mode == PCM_OPERATOR_AUTO) {
             size_t fr = 0, tot = 0;
-            const double need = 16.0 * (double)c->M * (double)((c->M + 31) / 32 * 32);
+            const double need = 8.0 * (double)c->M * (double)((c->M + 31) / 32 * 32);
             const bool tight = cudaMemGetInfo(&fr, &tot) == cudaSuccess && need > 0.25 * (double)fr;
             c->mf_active = c->M > 24576 || tight;
         }
     }
     c->stats.operator_free = c->mf_active ? 1 : 0;
     c->pc_ready = false;
-    c->a32_ready = false;
     c->have_c = false;
     // the stored A and what depends on it are built on the second stream when
     // first needed (pcm_esp starts it, so that it runs beside the integrals)
@@ -465,31 +475,32 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
 }
 
 // Stored A (Eq. 2, Eq. 3, Eq. 8) and 1/A_kk on stream s: FP64, or for
-// PCM_MIXED double-float with its FP32 hi and lo parts (A32, A32lo)
+// PCM_MIXED double-float only, as its FP32 hi and lo parts (A32, A32lo); the
+// RBJ set-up of that mode reads hi + lo
 int a_build(pcm_ctx *c, cudaStream_t s)
 {
     const int M = c->M;
     c->lda = (M + 31) / 32 * 32;
-    PCM_TRY(c->A.alloc((size_t)M * c->lda));
-    {
-        PCM_TRY(zeta_pairs(c, s));
-        const long long nt = (M + AT - 1) / AT;
-        const long long ntiles = nt * (nt + 1) / 2;
-        if (c->opt.precision == PCM_MIXED) {
-            PCM_TRY(c->A32.alloc((size_t)M * c->lda));
-            PCM_TRY(c->A32lo.alloc((size_t)M * c->lda));
-            a_build_df_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->p32.p, c->p32lo.p, c->px.p, c->py.p,
-                                                              c->pz.p, c->pzeta.p, c->pS.p, c->pcls.p, c->ncls,
-                                                              c->zp_cls.p, c->A.p, c->A32.p, c->A32lo.p);
-            c->a32_ready = true;
-        } else {
-            a_build_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p,
-                                                           c->pS.p, c->pcls.p, c->ncls, c->zp_cls.p, c->A.p);
-        }
-        PCM_LAUNCHED(c);
-    }
+    const bool mixed = c->opt.precision == PCM_MIXED;
+    PCM_TRY(zeta_pairs(c, s));
+    const long long nt = (M + AT - 1) / AT;
+    const long long ntiles = nt * (nt + 1) / 2;
     PCM_TRY(c->dinv.alloc(M));
-    dinv_kernel<<<(M + 127) / 128, 128, 0, s>>>(M, c->lda, c->A.p, c->dinv.p);
+    if (mixed) {
+        PCM_TRY(c->A32.alloc((size_t)M * c->lda));
+        PCM_TRY(c->A32lo.alloc((size_t)M * c->lda));
+        a_build_df_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->p32.p, c->p32lo.p, c->px.p, c->py.p,
+                                                          c->pz.p, c->pzeta.p, c->pS.p, c->pcls.p, c->ncls,
+                                                          c->zp_cls.p, nullptr, c->A32.p, c->A32lo.p);
+        PCM_LAUNCHED(c);
+        dinv_df_kernel<<<(M + 127) / 128, 128, 0, s>>>(M, c->lda, c->A32.p, c->A32lo.p, c->dinv.p);
+    } else {
+        PCM_TRY(c->A.alloc((size_t)M * c->lda));
+        a_build_kernel<<<(unsigned)ntiles, 256, 0, s>>>(M, c->lda, c->px.p, c->py.p, c->pz.p, c->pzeta.p, c->pS.p,
+                                                       c->pcls.p, c->ncls, c->zp_cls.p, c->A.p);
+        PCM_LAUNCHED(c);
+        dinv_kernel<<<(M + 127) / 128, 128, 0, s>>>(M, c->lda, c->A.p, c->dinv.p);
+    }
     PCM_LAUNCHED(c);
     return PCM_OK;
 }
