@@ -185,6 +185,10 @@ struct pcm_ctx {
     // last results
     pcm::DBuf<double> c_last;
     bool have_c = false;
+    // PCM_MIXED: the last solve's charges and A q = rhs - r from its final true
+    // residual, so that the energy of those charges needs no further product
+    pcm::DBuf<double> aq_q, aq_y;
+    bool aq_valid = false;
 
     // preconditioner
     int pc_kind = 0;                       // resolved PCM_PRECOND_*
@@ -248,7 +252,13 @@ struct pcm_ctx {
     size_t pg_smem[2] = {0, 0};
     pcm::DBuf<float4> mf_pts;
     pcm::DBuf<int> mf_off, mf_cnt, mf_col, mf_out, mf_iperm;
-    pcm::DBuf<double> mf_val, mf_y64, mf_idot, mf_red, mf_rn, st_yp64;
+    pcm::DBuf<double> mf_val, mf_y64, mf_idot, mf_red, mf_rn;
+    // stored-operator product of the persistent PCG: fixed-point accumulators,
+    // max |p| per product parity, max row sum of |A32| (built once per operator)
+    pcm::DBuf<unsigned long long> st_acc;
+    pcm::DBuf<unsigned> st_pmax;
+    pcm::DBuf<double> st_arow;
+    bool st_arow_ok = false;
     pcm::DBuf<float> mf_val32, mf_p32, mf_ypart;
     pcm::DBuf<float2> mf_xs;
     pcm::DBuf<unsigned> mf_bar;

@@ -14,8 +14,9 @@
 //
 // The inner PCG runs as one persistent cooperative kernel per inner solve:
 // per iteration the product (matrix-free: work items of 512 rows x up to 1024
-// columns over all blocks; stored FP32 A: one warp per row segment, streamed
-// from HBM; partial products per column chunk either way), the update and
+// columns over all blocks, partial products per column chunk; stored FP32 A:
+// the tiles of its upper triangle only, each streamed from HBM once and used
+// for both A_IJ p_J and A_IJ^T p_I, since A is symmetric), the update and
 // preconditioner (Jacobi, or one randomized block-Jacobi block per thread
 // block), and the direction update, separated by grid-wide barriers whose
 // waits are bounded.  The stored-operator variant serves PCM_MIXED surfaces
@@ -41,6 +42,9 @@ constexpr int MV_ROWS = 512;   // rows per work item (two per thread)
 constexpr int MV_CH = 1024;    // columns per work item
 constexpr int MV_SUB = 256;    // columns staged in shared memory at a time
 constexpr int NL_CH = 1024;    // columns staged per pass of the near-list build
+constexpr int ST_TB = 128;     // tile side of the symmetric stored-operator product
+constexpr int ST_RW = ST_TB / (MV_NT / 32);   // rows of a tile per warp (16)
+constexpr int FS_TB = 256;     // tile side of the symmetric matrix-free product
 
 __global__ void pts4_kernel(int M, const double *__restrict__ px, const double *__restrict__ py,
                             const double *__restrict__ pz, float4 *__restrict__ pts)
@@ -158,6 +162,7 @@ int zeta_pairs(pcm_ctx *c, cudaStream_t s)
 int matfree_build(pcm_ctx *c, cudaStream_t s)
 {
     const int M = c->M;
+    c->st_arow_ok = false;
     PCM_TRY(zeta_pairs(c, s));
     double zmin = 1e300;
     for (double z : c->h_zp_cls) zmin = std::min(zmin, z);
@@ -302,7 +307,11 @@ struct PcgArgs {
     int M, S, nitems, ch;        // points, column chunks, work items of the product (stored: blocks), chunk width
     const float *A32;            // stored FP32 A (row-major, leading dimension lda); null: matrix-free
     int lda;
-    double *yp64;                // stored: S x M partial products (FP64) at block positions
+    int ntb;                     // stored: tiles per side (ST_TB x ST_TB tiles)
+    unsigned long long *acc;     // stored: A p in fixed point (M), read and cleared by the update
+    unsigned *pmax;              // stored: [2] FP32 bits of max |p32| before each product (by its parity)
+    const double *arow;          // max over rows of sum_l |A32_kl| (stored) or of the near-list |values| (matrix-free)
+    double arow_add;             // matrix-free: M / rc, the bound of a row's far part
     const float4 *pts;           // FP32 coordinates
     float *p32;                  // FP32 copy of the direction (the product's input)
     float rc2;
@@ -450,49 +459,266 @@ __device__ __forceinline__ void pcg_product(const PcgArgs &a, float4 (*sc)[2])
     }
 }
 
-// The product with the stored FP32 A: unit u = (row u / S, column chunk
-// u % S) per warp, the warps of the grid taking units in turn; each lane
-// streams 16-byte pieces of the row (four in flight) against the FP32
-// direction, read through L2 (other blocks wrote it).  The chunk's sum goes to
-// yp64 at the row's block position, p.Ap partial per block to idot[block].
-__device__ __forceinline__ void pcg_product_stored(const PcgArgs &a)
+
+// Fixed-point scale of the symmetric products: every partial sum of a row of
+// A p is bounded by arow max|p32| < 2^e (arow: a bound on the row sums of |A|
+// as the product forms them), so sums of values v 2^(61 - e) rounded to
+// integers stay below 2^61 in magnitude, and integer addition makes the
+// result independent of the order in which the tiles add their parts.
+__device__ __forceinline__ double st_scale(const PcgArgs &a, int n, double *inv)
+{
+    const float pm = __uint_as_float(__ldcg(a.pmax + (n & 1)));
+    const double bound = (__ldcg(a.arow) + a.arow_add) * (double)pm;
+    if (!(bound > 0.0) || !isfinite(bound)) {
+        *inv = 1.0;
+        return 1.0;
+    }
+    int e = 0;
+    frexp(bound, &e);
+    *inv = ldexp(1.0, e - 61);
+    return ldexp(1.0, 61 - e);
+}
+
+__device__ __forceinline__ void st_add(unsigned long long *acc, float v, double scale)
+{
+    atomicAdd(acc, (unsigned long long)__double2ll_rn((double)v * scale));
+}
+
+// The matrix-free FP32 product over the tiles of the upper triangle (A
+// symmetric: each 1/R evaluated once serves A_ij p_j and A_ji p_i).  Blocks
+// take contiguous runs of the tiles (I <= J, FS_TB x FS_TB, row-major order).
+// In a tile, warp w takes columns J0 + 32 w + t (t < 32, staged in shared
+// memory, read as broadcasts) against all FS_TB rows, eight per lane (rows
+// I0 + 32 r + lane, two per packed FP32x2 word); the element is 1/R with R^2
+// clamped below at rc2 exactly as in the per-row product, near pairs and the
+// diagonal thus adding the constant that the near list takes back.  Row sums
+// are added across the warps in shared memory; the column sums of the 32
+// columns are reduced across the lanes by halving (31 shuffles per lane).
+// Diagonal tiles form row sums only (both triangles and the diagonal) and
+// add the near-pair corrections of their rows.  Sums enter the fixed-point
+// accumulators; block partials of p.Ap to idot[block].
+template <bool DIAG>
+__device__ __forceinline__ void fs_tile(const PcgArgs &a, int I0, int J0, double scale, float4 *scol,
+                                        float (*srow)[FS_TB], double &d)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int M = a.M;
+    const float rc2 = a.rc2;
+    __syncthreads();   // the previous tile's readers of scol / srow are done
+    {
+        const int j = J0 + threadIdx.x;
+        const float4 q = a.pts[min(j, M - 1)];
+        scol[threadIdx.x] = make_float4(q.x, q.y, q.z, j < M ? __ldcg(a.p32 + j) : 0.f);
+    }
+    f2 rx[4], ry[4], rz[4], rp[4], racc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i0 = I0 + 64 * q + lane, i1 = i0 + 32;
+        const float4 u0 = a.pts[min(i0, M - 1)], u1 = a.pts[min(i1, M - 1)];
+        rx[q] = f2(u0.x, u1.x);
+        ry[q] = f2(u0.y, u1.y);
+        rz[q] = f2(u0.z, u1.z);
+        rp[q] = f2(i0 < M ? __ldcg(a.p32 + i0) : 0.f, i1 < M ? __ldcg(a.p32 + i1) : 0.f);
+        racc[q] = f2(0.f);
+    }
+    __syncthreads();
+    float cp[32];
+    const float4 *col = scol + 32 * w;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        const float4 c = col[t];
+        const f2 cx(c.x), cy(c.y), cz(c.z), cw(c.w);
+        f2 ca(0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const f2 dx = rx[q] - cx, dy = ry[q] - cy, dz = rz[q] - cz;
+            const f2 r2 = fma2(dx, dx, fma2(dy, dy, dz * dz));
+            const f2 rs(rsqrt_fast(fmaxf(r2.v.x, rc2)), rsqrt_fast(fmaxf(r2.v.y, rc2)));
+            racc[q] = fma2(rs, cw, racc[q]);
+            if (!DIAG) ca = fma2(rs, rp[q], ca);
+        }
+        if (!DIAG) cp[t] = ca.v.x + ca.v.y;
+    }
+    // row parts of this warp's 32 columns
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        srow[w][64 * q + lane] = racc[q].v.x;
+        srow[w][64 * q + 32 + lane] = racc[q].v.y;
+    }
+    if (!DIAG) {
+        // column sums: halve the 32 partials across the lanes; lane l ends
+        // with the sum for column 32 w + l
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+            const bool up = (lane & h) != 0;
+#pragma unroll
+            for (int m = 0; m < h; ++m) {
+                const float send = up ? cp[m] : cp[m + h];
+                const float keep = up ? cp[m + h] : cp[m];
+                cp[m] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+            }
+        }
+        const int jc = J0 + 32 * w + lane;
+        if (jc < M) {
+            st_add(a.acc + jc, cp[0], scale);
+            d = fma(__ldcg(a.p + jc), (double)cp[0], d);
+        }
+    }
+    __syncthreads();
+    {
+        const int i = I0 + threadIdx.x;
+        float v = srow[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < MV_NT / 32; ++q) v += srow[q][threadIdx.x];
+        if (i < M) {
+            if (DIAG)
+                for (int e = a.off[i]; e < a.off[i + 1]; ++e) v = fmaf(a.val32[e], __ldcg(a.p32 + a.col[e]), v);
+            st_add(a.acc + i, v, scale);
+            d = fma(__ldcg(a.p + i), (double)v, d);
+        }
+    }
+}
+
+__device__ __forceinline__ void pcg_product_free_sym(const PcgArgs &a, int n)
 {
     __shared__ double red[MV_NT / 32];
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * (MV_NT / 32);
-    const int M = a.M;
-    const long long nunits = (long long)M * a.S;
+    __shared__ float4 scol[FS_TB];
+    __shared__ float srow[MV_NT / 32][FS_TB];
+    double inv;
+    const double scale = st_scale(a, n, &inv);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.pmax[(n + 1) & 1] = 0u;
+    const int ntb = a.ntb;
+    const long long ntiles = (long long)ntb * (ntb + 1) / 2;
+    const long long t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    int I = 0;
+    long long pos = t0;
+    while (I < ntb && pos >= ntb - I) {
+        pos -= ntb - I;
+        ++I;
+    }
     double d = 0.0;
-    for (long long u = blockIdx.x * (MV_NT / 32) + (threadIdx.x >> 5); u < nunits; u += nw) {
-        const int r = (int)(u / a.S), sg = (int)(u - (long long)r * a.S);
-        const int c0 = sg * a.ch, c1 = min(M, c0 + a.ch);
-        const float *row = a.A32 + (size_t)r * a.lda;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int col = c0 + 4 * lane;
-        for (; col + 387 < c1; col += 512) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(row + col);
-            const float4 a1 = *reinterpret_cast<const float4 *>(row + col + 128);
-            const float4 a2 = *reinterpret_cast<const float4 *>(row + col + 256);
-            const float4 a3 = *reinterpret_cast<const float4 *>(row + col + 384);
-            const float4 x0 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col));
-            const float4 x1 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col + 128));
-            const float4 x2 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col + 256));
-            const float4 x3 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col + 384));
-            s0 = fmaf(a0.x, x0.x, fmaf(a0.y, x0.y, fmaf(a0.z, x0.z, fmaf(a0.w, x0.w, s0))));
-            s1 = fmaf(a1.x, x1.x, fmaf(a1.y, x1.y, fmaf(a1.z, x1.z, fmaf(a1.w, x1.w, s1))));
-            s2 = fmaf(a2.x, x2.x, fmaf(a2.y, x2.y, fmaf(a2.z, x2.z, fmaf(a2.w, x2.w, s2))));
-            s3 = fmaf(a3.x, x3.x, fmaf(a3.y, x3.y, fmaf(a3.z, x3.z, fmaf(a3.w, x3.w, s3))));
+    for (long long t = t0; t < t1; ++t) {
+        const int J = I + (int)pos;
+        if (J == I)
+            fs_tile<true>(a, I * FS_TB, J * FS_TB, scale, scol, srow, d);
+        else
+            fs_tile<false>(a, I * FS_TB, J * FS_TB, scale, scol, srow, d);
+        if (++pos >= ntb - I) {
+            pos = 0;
+            ++I;
         }
-        for (; col + 3 < c1; col += 128) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(row + col);
-            const float4 x0 = __ldcg(reinterpret_cast<const float4 *>(a.p32 + col));
-            s0 = fmaf(a0.x, x0.x, fmaf(a0.y, x0.y, fmaf(a0.z, x0.z, fmaf(a0.w, x0.w, s0))));
+    }
+    d = block_sum<double, MV_NT>(d, red);
+    if (threadIdx.x == 0) a.idot[blockIdx.x] = d;
+}
+
+// The product with the stored FP32 A (A symmetric): tile t of the upper
+// triangle (I <= J, ST_TB x ST_TB) goes to block t mod grid.  Warp w takes
+// rows I0 + w + 8 m (m < 16), lane l columns J0 + 4 l .. + 3, all sixteen
+// 16-byte loads of the warp in flight at once.  Row sums (A_IJ p_J) are
+// reduced across the lanes; off-diagonal tiles also form column sums
+// (A_IJ^T p_I), reduced across the warps in shared memory.  Both are added to
+// the fixed-point accumulators; block partials of p.Ap to idot[block].
+__device__ __forceinline__ void pcg_product_stored(const PcgArgs &a, int n)
+{
+    __shared__ double red[MV_NT / 32];
+    __shared__ __align__(16) float cs[MV_NT / 32][ST_TB];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int M = a.M, ntb = a.ntb;
+    double inv;
+    const double scale = st_scale(a, n, &inv);
+    // the other parity's max |p| is cleared for the direction update before the next product
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.pmax[(n + 1) & 1] = 0u;
+    const long long ntiles = (long long)ntb * (ntb + 1) / 2;
+    // first tile of this block: row I of the triangle holds ntb - I tiles
+    int I = 0;
+    long long pos = blockIdx.x;
+    while (I < ntb && pos >= ntb - I) {
+        pos -= ntb - I;
+        ++I;
+    }
+    double d = 0.0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int J = I + (int)pos;
+        const int I0 = I * ST_TB, J0 = J * ST_TB;
+        const int c0 = J0 + 4 * lane;
+        const bool cok = c0 < M;
+        float4 a4[ST_RW];
+#pragma unroll
+        for (int m = 0; m < ST_RW; ++m) {
+            const int row = I0 + w + 8 * m;
+            a4[m] = (cok && row < M) ? *reinterpret_cast<const float4 *>(a.A32 + (size_t)row * a.lda + c0)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int t = col; t < c1 && t < col + 4; ++t) s1 = fmaf(row[t], __ldcg(a.p32 + t), s1);
-        const float v = warp_sum((s0 + s1) + (s2 + s3));
-        if (lane == 0) {
-            a.yp64[(size_t)sg * M + (a.iperm ? a.iperm[r] : r)] = (double)v;
-            d = fma(__ldcg(a.p + r), (double)v, d);
+        float4 pj = __ldcg(reinterpret_cast<const float4 *>(a.p32 + c0));
+        if (c0 + 3 >= M) {
+            // columns beyond M: zero both the direction and the (unwritten) matrix entries
+#pragma unroll
+            for (int m = 0; m < ST_RW; ++m) {
+                if (c0 + 1 >= M) a4[m].y = 0.f;
+                if (c0 + 2 >= M) a4[m].z = 0.f;
+                if (c0 + 3 >= M) a4[m].w = 0.f;
+            }
+            if (c0 >= M) pj.x = 0.f;
+            if (c0 + 1 >= M) pj.y = 0.f;
+            if (c0 + 2 >= M) pj.z = 0.f;
+            if (c0 + 3 >= M) pj.w = 0.f;
+        }
+        float rp[ST_RW];
+        float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < ST_RW; ++m) {
+            rp[m] = fmaf(a4[m].x, pj.x, fmaf(a4[m].y, pj.y, fmaf(a4[m].z, pj.z, a4[m].w * pj.w)));
+            const int row = I0 + w + 8 * m;
+            const float pi = row < M ? __ldcg(a.p32 + row) : 0.f;
+            ca.x = fmaf(a4[m].x, pi, ca.x);
+            ca.y = fmaf(a4[m].y, pi, ca.y);
+            ca.z = fmaf(a4[m].z, pi, ca.z);
+            ca.w = fmaf(a4[m].w, pi, ca.w);
+        }
+        // reduce the sixteen row partials across the lanes by halving: after
+        // the steps at 16, 8, 4, 2 and 1, lanes 2i and 2i + 1 hold the sum of
+        // row m = 8 b4 + 4 b3 + 2 b2 + b1 (b: the bits of the lane)
+#pragma unroll
+        for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int m = 0; m < h; ++m) {
+                const float send = up ? rp[m] : rp[m + h];
+                const float keep = up ? rp[m + h] : rp[m];
+                rp[m] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        const float rsum = rp[0] + __shfl_xor_sync(0xffffffffu, rp[0], 1);
+        {
+            const int m = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+            const int row = I0 + w + 8 * m;
+            if ((lane & 1) == 0 && row < M) {
+                st_add(a.acc + row, rsum, scale);
+                d = fma(__ldcg(a.p + row), (double)rsum, d);
+            }
+        }
+        if (I != J) {
+            // column sums: the warps' parts in shared memory, added in warp order
+            *reinterpret_cast<float4 *>(&cs[w][4 * lane]) = ca;
+            __syncthreads();
+            if (threadIdx.x < ST_TB) {
+                float v = cs[0][threadIdx.x];
+#pragma unroll
+                for (int q = 1; q < MV_NT / 32; ++q) v += cs[q][threadIdx.x];
+                const int col = J0 + threadIdx.x;
+                if (col < M) {
+                    st_add(a.acc + col, v, scale);
+                    d = fma(__ldcg(a.p + col), (double)v, d);
+                }
+            }
+            __syncthreads();
+        }
+        // next tile of this block
+        pos += gridDim.x;
+        while (I < ntb && pos >= ntb - I) {
+            pos -= ntb - I;
+            ++I;
         }
     }
     d = block_sum<double, MV_NT>(d, red);
@@ -504,16 +730,22 @@ __device__ __forceinline__ void pcg_product_stored(const PcgArgs &a)
 __device__ __forceinline__ double ap_pos(const PcgArgs &a, int pos)
 {
     double v = 0.0;
-    if (a.A32)
-        for (int s = 0; s < a.S; ++s) v += __ldcg(a.yp64 + (size_t)s * a.M + pos);
-    else
-        for (int s = 0; s < a.S; ++s) v += (double)__ldcg(a.ypart + (size_t)s * a.M + pos);
+    for (int s = 0; s < a.S; ++s) v += (double)__ldcg(a.ypart + (size_t)s * a.M + pos);
     return v;
+}
+
+// A p of point k from the stored product's accumulator, which is cleared for
+// the next product
+__device__ __forceinline__ double ap_acc(const PcgArgs &a, int k, double inv)
+{
+    const long long v = (long long)__ldcg(a.acc + k);
+    a.acc[k] = 0ull;
+    return (double)v * inv;
 }
 
 // update (init: only z = C r) on the rows this block owns; partials of r.r
 // and r.z to red[2 slot], red[2 slot + 1]
-__device__ __forceinline__ void pcg_update(const PcgArgs &a, double alpha, int init, double *srb)
+__device__ __forceinline__ void pcg_update(const PcgArgs &a, double alpha, int init, double *srb, double inv)
 {
     __shared__ double sh[2][MV_NT / 32];
     if (a.rbj) {
@@ -526,7 +758,7 @@ __device__ __forceinline__ void pcg_update(const PcgArgs &a, double alpha, int i
                     a.x[k] = 0.0;
                     a.r[k] = a.b[k];
                 } else {
-                    a.Ap[k] = ap_pos(a, base + i);
+                    a.Ap[k] = a.acc ? ap_acc(a, k, inv) : ap_pos(a, base + i);
                 }
             }
             __syncthreads();
@@ -548,7 +780,7 @@ __device__ __forceinline__ void pcg_update(const PcgArgs &a, double alpha, int i
                 rk = a.b[k];
             } else {
                 a.x[k] = fma(alpha, a.p[k], a.x[k]);
-                rk = fma(-alpha, ap_pos(a, k), a.r[k]);
+                rk = fma(-alpha, a.acc ? ap_acc(a, k, inv) : ap_pos(a, k), a.r[k]);
             }
             a.r[k] = rk;
             const double zk = a.dinv ? rk * a.dinv[k] : rk;
@@ -576,9 +808,11 @@ __device__ __forceinline__ void pcg_update(const PcgArgs &a, double alpha, int i
     }
 }
 
-// p = z + beta p on the owned rows (beta = 0: p = z), and its FP32 copy
-__device__ __forceinline__ void pcg_direction(const PcgArgs &a, double beta)
+// p = z + beta p on the owned rows (beta = 0: p = z), and its FP32 copy; for
+// the stored product also max |p32| (slot n & 1 for product n)
+__device__ __forceinline__ void pcg_direction(const PcgArgs &a, double beta, int n)
 {
+    float mx = 0.f;
     if (a.rbj) {
         for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) {
             const int base = a.bstart ? a.bstart[b] : b * a.l;
@@ -588,6 +822,7 @@ __device__ __forceinline__ void pcg_direction(const PcgArgs &a, double beta)
                 const double v = fma(beta, a.p[k], a.z[k]);
                 a.p[k] = v;
                 a.p32[k] = (float)v;
+                mx = fmaxf(mx, fabsf((float)v));
             }
         }
     } else {
@@ -595,7 +830,14 @@ __device__ __forceinline__ void pcg_direction(const PcgArgs &a, double beta)
             const double v = fma(beta, a.p[k], a.z[k]);
             a.p[k] = v;
             a.p32[k] = (float)v;
+            mx = fmaxf(mx, fabsf((float)v));
         }
+    }
+    if (a.acc) {
+        // non-negative floats order as their bit patterns
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(a.pmax + (n & 1), __float_as_uint(mx));
     }
 }
 
@@ -603,26 +845,27 @@ template <bool STORED>
 __global__ void __launch_bounds__(MV_NT) pcg_persistent_kernel(PcgArgs a)
 {
     extern __shared__ double srb[];          // RBJ block: l entries
-    __shared__ float4 sc[STORED ? 1 : MV_SUB][2];   // staged columns, lane-duplicated
     int *err = a.out + 2;
     const int nslot = a.rbj ? a.nblk : (int)gridDim.x;
     // initialisation: x = 0, r = b, z = C r
-    pcg_update(a, 0.0, 1, srb);
+    pcg_update(a, 0.0, 1, srb, 1.0);
     if (!grid_barrier(a.bar, err)) return;
     double rr = grid_sum(a.red, nslot, 2, 0);
     double rz = grid_sum(a.red, nslot, 2, 1);
     int it = 0, conv = sqrt(rr) < a.delta;
     if (!conv) {
-        pcg_direction(a, 0.0);
+        pcg_direction(a, 0.0, 0);
         if (!grid_barrier(a.bar, err)) return;
         while (true) {
+            double inv = 1.0;
+            st_scale(a, it, &inv);
             if constexpr (STORED)
-                pcg_product_stored(a);
+                pcg_product_stored(a, it);
             else
-                pcg_product(a, sc);
+                pcg_product_free_sym(a, it);
             if (!grid_barrier(a.bar, err)) return;
             const double pAp = grid_sum(a.idot, a.nitems, 1, 0);
-            pcg_update(a, rz / pAp, 0, srb);
+            pcg_update(a, rz / pAp, 0, srb, inv);
             if (!grid_barrier(a.bar, err)) return;
             rr = grid_sum(a.red, nslot, 2, 0);
             const double rz_new = grid_sum(a.red, nslot, 2, 1);
@@ -633,7 +876,7 @@ __global__ void __launch_bounds__(MV_NT) pcg_persistent_kernel(PcgArgs a)
                 break;
             }
             if (it >= a.max_iter) break;
-            pcg_direction(a, rz_new / rz);
+            pcg_direction(a, rz_new / rz, it);
             rz = rz_new;
             if (!grid_barrier(a.bar, err)) return;
         }
@@ -664,28 +907,37 @@ static void mv_chunks(int M, int grid, int *S, int *ch)
     *S = (M + w - 1) / w;
 }
 
-// Column chunks of the stored-operator product for `grid` blocks of MV_NT/32
-// warps: S chunks per row (multiples of 128 columns), S from 1 to 16 chosen so
-// that the units (rows x chunks) spread most evenly over the warps.
-static void st_chunks(int M, int grid, int *S, int *ch)
+// max over rows of sum_l |A32_kl| (FP64 row sums, one warp per row; the
+// maximum of non-negative doubles taken on their bit patterns), the bound
+// behind the fixed-point scale of the stored product
+__global__ void __launch_bounds__(MV_NT) arow_kernel(int M, int lda, const float *__restrict__ A32,
+                                                     unsigned long long *__restrict__ out)
 {
-    const double nw = (double)grid * (MV_NT / 32);
-    double best = -1.0;
-    int bs = 1, bw = (M + 127) / 128 * 128;
-    for (int s = 1; s <= 16; ++s) {
-        int w = (M + s - 1) / s;
-        w = (w + 127) / 128 * 128;
-        const int sa = (M + w - 1) / w;
-        const double units = (double)M * sa;
-        const double eff = units / (std::ceil(units / nw) * nw);
-        if (eff > best + 1e-9) {
-            best = eff;
-            bs = sa;
-            bw = w;
-        }
+    const int lane = threadIdx.x & 31;
+    double mx = 0.0;
+    for (int row = blockIdx.x * (MV_NT / 32) + (threadIdx.x >> 5); row < M; row += gridDim.x * (MV_NT / 32)) {
+        const float *r = A32 + (size_t)row * lda;
+        double s = 0.0;
+        for (int col = lane; col < M; col += 32) s += fabs((double)r[col]);
+        mx = fmax(mx, warp_sum(s));
     }
-    *S = bs;
-    *ch = bw;
+    if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+// max over rows of sum_e |val32_e| over the row's near pairs (one warp per
+// row), the near part of the matrix-free product's row-sum bound
+__global__ void __launch_bounds__(MV_NT) near_abs_kernel(int M, const int *__restrict__ off,
+                                                         const float *__restrict__ val32,
+                                                         unsigned long long *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    double mx = 0.0;
+    for (int row = blockIdx.x * (MV_NT / 32) + (threadIdx.x >> 5); row < M; row += gridDim.x * (MV_NT / 32)) {
+        double s = 0.0;
+        for (int e = off[row] + lane; e < off[row + 1]; e += 32) s += fabs((double)val32[e]);
+        mx = fmax(mx, warp_sum(s));
+    }
+    if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
 // Inner PCG from x = 0 on A x = b with the FP32 product (matrix-free, or the
@@ -696,7 +948,6 @@ int persistent_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max
 {
     const int M = c->M;
     const bool stored = !matrix_free(c);
-    const int nrt = (M + MV_ROWS - 1) / MV_ROWS;
     const bool rbj = c->pc_kind == PCM_PRECOND_RBJ || c->pc_kind == PCM_PRECOND_OCTREE;
     const size_t smem = rbj ? (size_t)c->rbj_l * sizeof(double) : sizeof(double);
     const void *kern = stored ? (const void *)pcg_persistent_kernel<true> : (const void *)pcg_persistent_kernel<false>;
@@ -716,19 +967,29 @@ int persistent_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max
     }
     const int grid = c->pg_grid[v];
     const int nslot = rbj ? c->rbj_nblk : grid;
-    int S, ch;
-    if (stored)
-        st_chunks(M, grid, &S, &ch);
-    else
-        mv_chunks(M, grid, &S, &ch);
-    if (stored) {
-        PCM_TRY(c->st_yp64.alloc((size_t)S * M));
-        PCM_TRY(c->mf_idot.alloc((size_t)grid));
-    } else {
-        PCM_TRY(c->mf_ypart.alloc((size_t)S * M));
-        PCM_TRY(c->mf_idot.alloc((size_t)nrt * S));
+    const int tb = stored ? ST_TB : FS_TB;
+    const int ntb = (M + tb - 1) / tb;
+    PCM_TRY(c->mf_idot.alloc((size_t)grid));
+    PCM_TRY(c->st_acc.alloc(M));
+    PCM_TRY(c->st_pmax.alloc(2));
+    PCM_TRY(c->st_arow.alloc(1));
+    if (!c->st_arow_ok) {
+        // the row-sum bound of the fixed-point scale, once per operator
+        PCM_CUDA(cudaMemsetAsync(c->st_arow.p, 0, sizeof(double), c->stream));
+        unsigned long long *o = reinterpret_cast<unsigned long long *>(c->st_arow.p);
+        if (stored)
+            arow_kernel<<<std::min(4096, (M + 7) / 8), MV_NT, 0, c->stream>>>(M, c->lda, c->A32.p, o);
+        else
+            near_abs_kernel<<<std::min(4096, (M + 7) / 8), MV_NT, 0, c->stream>>>(M, c->mf_off.p, c->mf_val32.p, o);
+        PCM_LAUNCHED(c);
+        c->st_arow_ok = true;
     }
-    PCM_TRY(c->mf_p32.alloc(M));
+    PCM_CUDA(cudaMemsetAsync(c->st_acc.p, 0, (size_t)M * sizeof(unsigned long long), c->stream));
+    PCM_CUDA(cudaMemsetAsync(c->st_pmax.p, 0, 2 * sizeof(unsigned), c->stream));
+    // the stored product reads the direction in whole tiles: zero padding to ntb tiles
+    const size_t np32 = (size_t)ntb * tb;
+    PCM_TRY(c->mf_p32.alloc(np32));
+    PCM_CUDA(cudaMemsetAsync(c->mf_p32.p, 0, np32 * sizeof(float), c->stream));
     PCM_TRY(c->vr.alloc(M));
     PCM_TRY(c->vz.alloc(M));
     PCM_TRY(c->vp.alloc(M));
@@ -746,19 +1007,23 @@ int persistent_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max
     PCM_CUDA(cudaMemsetAsync(c->mf_out.p, 0, 4 * sizeof(int), c->stream));
     PcgArgs a;
     a.M = M;
-    a.S = S;
-    a.ch = ch;
-    a.nitems = stored ? grid : nrt * S;
+    a.S = 0;
+    a.ch = 0;
+    a.nitems = grid;
     a.A32 = stored ? c->A32.p : nullptr;
     a.lda = c->lda;
-    a.yp64 = stored ? c->st_yp64.p : nullptr;
+    a.ntb = ntb;
+    a.acc = c->st_acc.p;
+    a.pmax = c->st_pmax.p;
+    a.arow = c->st_arow.p;
+    a.arow_add = stored ? 0.0 : (double)M / sqrt((double)c->mf_rc2);
     a.pts = c->mf_pts.p;
     a.p32 = c->mf_p32.p;
     a.rc2 = c->mf_rc2;
     a.off = c->mf_off.p;
     a.col = c->mf_col.p;
     a.val32 = c->mf_val32.p;
-    a.ypart = stored ? nullptr : c->mf_ypart.p;
+    a.ypart = nullptr;
     a.iperm = rbj ? c->mf_iperm.p : nullptr;
     a.idot = c->mf_idot.p;
     a.b = b;

@@ -1094,8 +1094,20 @@ static int true_residual(pcm_ctx *c, const double *b, const double *x, double *r
     return PCM_OK;
 }
 
+// the last solve's charges and A q = b - r (r: the final true residual b - A q)
+__global__ void aq_store_kernel(int M, const double *__restrict__ b, const double *__restrict__ r,
+                                const double *__restrict__ q, double *__restrict__ q_keep, double *__restrict__ y)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < M) {
+        q_keep[k] = q[k];
+        y[k] = b[k] - r[k];
+    }
+}
+
 int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool warm, pcm_stats *st)
 {
+    c->aq_valid = false;
     PCM_TRY(join_side(c));
     const bool fresh = !c->pc_ready;
     if (c->have_events) PCM_CUDA(cudaEventRecord(c->ev_a[13], c->stream));
@@ -1157,6 +1169,14 @@ int solver_run(pcm_ctx *c, const double *drhs, double delta, double *dq, bool wa
             axpy_kernel<<<eb, 256, 0, c->stream>>>(M, c->vd.p, dq);
             PCM_LAUNCHED(c);
         }
+        // every exit of the loop follows a true residual of the final x
+        if (std::isfinite(rnorm)) {
+            PCM_TRY(c->aq_q.alloc(M));
+            PCM_TRY(c->aq_y.alloc(M));
+            aq_store_kernel<<<(M + 255) / 256, 256, 0, c->stream>>>(M, drhs, c->vro.p, dq, c->aq_q.p, c->aq_y.p);
+            PCM_LAUNCHED(c);
+            c->aq_valid = true;
+        }
     }
     c->stats.iterations = iters;
     c->stats.converged = conv;
@@ -1195,10 +1215,68 @@ __global__ void dot2_kernel(int M, const double *__restrict__ a, const double *_
     }
 }
 
+// The energy's three dot products with A q taken from the last solve (qk, y)
+// when q is that solve's result: per block q.y, Bz.q, c.q and the number of
+// elements where q differs from qk (then the caller forms A q itself)
+__global__ void energy_kept_kernel(int M, const double *__restrict__ q, const double *__restrict__ qk,
+                                   const double *__restrict__ y, const double *__restrict__ Bz,
+                                   const double *__restrict__ cv, double *__restrict__ part)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, nd = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        const double v = q[k];
+        nd += v != qk[k] ? 1.0 : 0.0;
+        s0 = fma(v, y[k], s0);
+        s1 = fma(Bz[k], v, s1);
+        s2 = fma(cv[k], v, s2);
+    }
+    __shared__ double sh[4][32];
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    nd = warp_sum(nd);
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = s0;
+        sh[1][threadIdx.x >> 5] = s1;
+        sh[2][threadIdx.x >> 5] = s2;
+        sh[3][threadIdx.x >> 5] = nd;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[threadIdx.x][i];
+        part[4 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
 int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E)
 {
     PCM_TRY(join_side(c));
     const int M = c->M;
+    const double f = (c->opt.eps - 1.0) / (c->opt.eps + c->opt.k);
+    if (c->aq_valid) {
+        // q^T A q = q^T (b - r) with the last solve's final true residual, when
+        // q is that solve's result (checked element by element)
+        const int nb = std::min(1024, (M + 255) / 256);
+        DBuf<double> &part4 = c->sd[1];
+        PCM_TRY(part4.alloc(4 * (size_t)nb));
+        energy_kept_kernel<<<nb, 256, 0, c->stream>>>(M, dq, c->aq_q.p, c->aq_y.p, c->Bz.p, dcv, part4.p);
+        PCM_LAUNCHED(c);
+        std::vector<double> h(4 * (size_t)nb);
+        PCM_CUDA(cudaMemcpyAsync(h.data(), part4.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        PCM_CUDA(cudaStreamSynchronize(c->stream));
+        double qAq = 0.0, bzq = 0.0, cq = 0.0, nd = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            qAq += h[4 * i];
+            bzq += h[4 * i + 1];
+            cq += h[4 * i + 2];
+            nd += h[4 * i + 3];
+        }
+        if (nd == 0.0) {
+            *E = bzq + cq + qAq / (2.0 * f);
+            return PCM_OK;
+        }
+    }
     PCM_TRY(c->vtmp.alloc(M));
     const int gv = gemv_grid(c);
     PCM_TRY(c->red.alloc(2 * (size_t)std::max(MAX_PART, gv)));
@@ -1219,7 +1297,6 @@ int energy_compute(pcm_ctx *c, const double *dq, const double *dcv, double *E)
         bzq += h2[2 * i];
         cq += h2[2 * i + 1];
     }
-    const double f = (c->opt.eps - 1.0) / (c->opt.eps + c->opt.k);
     *E = bzq + cq + qAq / (2.0 * f);
     return PCM_OK;
 }

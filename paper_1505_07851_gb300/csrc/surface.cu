@@ -468,6 +468,7 @@ int surface_build(pcm_ctx *c, int natom, const double *xyz, const double *Z, con
     c->stats.operator_free = c->mf_active ? 1 : 0;
     c->pc_ready = false;
     c->have_c = false;
+    c->aq_valid = false;
     // the stored A and what depends on it are built on the second stream when
     // first needed (pcm_esp starts it, so that it runs beside the integrals)
     c->op_stale = true;
@@ -486,6 +487,7 @@ int a_build(pcm_ctx *c, cudaStream_t s)
     const long long nt = (M + AT - 1) / AT;
     const long long ntiles = nt * (nt + 1) / 2;
     PCM_TRY(c->dinv.alloc(M));
+    c->st_arow_ok = false;
     if (mixed) {
         PCM_TRY(c->A32.alloc((size_t)M * c->lda));
         PCM_TRY(c->A32lo.alloc((size_t)M * c->lda));

@@ -66,3 +66,51 @@ def test_mixed_against_oracle_directly(name, operator):
     q_o[p] = b["q"]
     check(b["dF"], oracle.fock(o["eb"], q_o, o["surf"]["r"], o["surf"]["zeta"]), MIXED, what="dF")
     assert abs(b["E"] - o["E_lu"]) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["cluster8_sp", "cluster20_spd"])
+@pytest.mark.parametrize("operator", ["stored", "free"])
+def test_mixed_solve_against_lu(name, operator):
+    """The refined PCM_MIXED solve of the oracle's own right-hand side (Eq. 1)
+    against the oracle's dense LU solution: the FP32 inner solves (the stored
+    operator's symmetric tile product, or the matrix-free product) inside the
+    double-float refinement reach the FP64 bound ||q - q_lu|| <= 10 delta /
+    lambda_min, as the FP64 solver does."""
+    import paper_1505_07851_gb300 as pcm
+    w = CASES[name]()
+    o = oracle.run(w, delta=1e-10)
+    with pcm.Context(precision="mixed", operator=operator) as ctx:
+        ctx.setup(w.mol, w.basis)
+        _, idx = ctx.get_surface()
+        pos = {int(k): i for i, k in enumerate(o["surf"]["index"])}
+        p = np.array([pos[int(k)] for k in idx])
+        q, st = ctx.solve(rhs=np.ascontiguousarray(o["rhs"][p]), delta=1e-10)
+    assert st["converged"] == 1 and st["rnorm"] < 1e-10
+    lam_min = np.linalg.eigvalsh(o["A"])[0]
+    assert np.linalg.norm(q - o["q_lu"][p]) <= 10 * 1e-10 / lam_min
+
+
+@pytest.mark.parametrize("operator", ["stored", "free"])
+def test_energy_from_last_residual_matches_product(operator):
+    """pcm_energy of the charges a PCM_MIXED solve just returned takes
+    q^T A q from that solve's final true residual (A q = rhs - r); a fresh
+    context, which has solved nothing, forms A q by the double-float product.
+    The two energies agree to rounding, and a changed q falls back to the
+    product."""
+    import paper_1505_07851_gb300 as pcm
+    w = CASES["cluster20_spd"]()
+    with pcm.Context(precision="mixed", operator=operator) as ctx:
+        ctx.setup(w.mol, w.basis)
+        c = ctx.esp(w.P)
+        q, _ = ctx.solve(delta=1e-8)
+        E_kept = ctx.energy(q)
+        q2 = q.copy()
+        q2[len(q2) // 2] *= 1.001
+        E_changed = ctx.energy(q2)
+    with pcm.Context(precision="mixed", operator=operator) as ctx:
+        ctx.setup(w.mol, w.basis)
+        E_prod = ctx.energy(q, c=c)
+        E_prod2 = ctx.energy(q2, c=c)
+    assert abs(E_kept - E_prod) <= 1e-12 * abs(E_prod), (E_kept, E_prod)
+    assert E_changed == E_prod2 or abs(E_changed - E_prod2) <= 1e-14 * abs(E_prod2)
+    assert E_changed != E_kept
