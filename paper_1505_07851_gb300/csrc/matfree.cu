@@ -198,59 +198,16 @@ int matfree_build(pcm_ctx *c, cudaStream_t s)
 
 // ---------------------------------------------------------------------------
 // y = A x in double-float: far pairs 1/R from the split coordinates (FP32 hi
-// on a 2^-10 grid + lo), float-float sums per work item of 256 rows x 2048
-// columns; then per row the column chunks and the near pairs (FP64) added in
-// a fixed order, with block partials of x.y
+// on a 2^-10 grid + lo), float-float sums over tiles of the upper triangle
+// (dfmv_sym_kernel); then per row the tile partials and the near pairs (FP64)
+// added in a fixed order, with block partials of x.y
 // ---------------------------------------------------------------------------
-constexpr int DF_CH = 2048;
-constexpr int DF_SUB = 512;
-
 __global__ void split_vec_kernel(int M, const double *__restrict__ x, float2 *__restrict__ xs)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < M) {
         const float h = (float)x[k];
         xs[k] = make_float2(h, (float)(x[k] - (double)h));
-    }
-}
-
-__global__ void __launch_bounds__(MV_NT) dfmv_items_kernel(int M, int S, int ch, const float4 *__restrict__ pts,
-                                                           const float *__restrict__ ph,
-                                                           const float *__restrict__ pl,
-                                                           const float2 *__restrict__ xs, float rc2,
-                                                           double *__restrict__ ypart)
-{
-    __shared__ float4 sP[DF_SUB], sH[DF_SUB], sL[DF_SUB];
-    const int nrt = (M + MV_NT - 1) / MV_NT;
-    for (int item = blockIdx.x; item < nrt * S; item += gridDim.x) {
-        const int rt = item / S, s = item % S;
-        const int k = rt * MV_NT + threadIdx.x;
-        const int kk = min(k, M - 1);
-        const float4 a = pts[kk];
-        const float xh = ph[kk], yh = ph[(size_t)M + kk], zh = ph[2 * (size_t)M + kk];
-        const float xl = pl[kk], yl = pl[(size_t)M + kk], zl = pl[2 * (size_t)M + kk];
-        float S_ = 0.f, C_ = 0.f;
-        const int c0 = s * ch, c1 = min(M, c0 + ch);
-        for (int b0 = c0; b0 < c1; b0 += DF_SUB) {
-            const int nc = min(DF_SUB, c1 - b0);
-            __syncthreads();
-            for (int t = threadIdx.x; t < nc; t += MV_NT) {
-                const int l = b0 + t;
-                const float2 x = xs[l];
-                sP[t] = pts[l];
-                sH[t] = make_float4(ph[l], ph[(size_t)M + l], ph[2 * (size_t)M + l], x.x);
-                sL[t] = make_float4(pl[l], pl[(size_t)M + l], pl[2 * (size_t)M + l], x.y);
-            }
-            __syncthreads();
-            for (int j = 0; j < nc; ++j) {
-                if (r2_test32(a, sP[j]) < rc2) continue;   // near pairs and the diagonal: the list
-                const float4 h = sH[j], lo = sL[j];
-                float ih, il, r2;
-                df_rsqrt(xh - h.x, xl - lo.x, yh - h.y, yl - lo.y, zh - h.z, zl - lo.z, ih, il, r2);
-                df_acc(S_, C_, ih, il, h.w, lo.w);
-            }
-        }
-        if (k < M) ypart[(size_t)s * M + k] = (double)S_ + (double)C_;
     }
 }
 
@@ -274,26 +231,122 @@ __global__ void __launch_bounds__(MV_NT) dfmv_reduce_kernel(int M, int S, const 
     if (threadIdx.x == 0) part[blockIdx.x] = d;
 }
 
+// The same product over the tiles of the upper triangle only (A symmetric:
+// each double-float 1/R serves A_ij x_j and A_ji x_i).  Tile t (I <= J,
+// DS_TB x DS_TB, row-major order) goes to block t mod grid; warp w takes rows
+// I0 + 32 w + lane, one per lane, against the tile's columns, which it visits
+// in groups of 32: at step s of a group, lane l takes column (l + s) mod 32,
+// so the 32 lanes touch 32 different columns and each column's float-float
+// sum (this warp's part, in shared memory) has one writer per step, in a
+// fixed order.  Near pairs and the diagonal (r2_test32 < rc2) contribute
+// nothing here.  Row sums go to ypart[J][row], column sums (the warps' parts
+// added in warp order) to ypart[I][column]: each row of y receives exactly
+// one partial per tile column block, summed by dfmv_reduce_kernel.
+constexpr int DS_TB = 256;
+
+__global__ void __launch_bounds__(MV_NT) dfmv_sym_kernel(int M, int ntb, const float4 *__restrict__ pts,
+                                                         const float *__restrict__ ph, const float *__restrict__ pl,
+                                                         const float2 *__restrict__ xs, float rc2,
+                                                         double *__restrict__ ypart)
+{
+    __shared__ float4 sP[DS_TB], sH[DS_TB], sL[DS_TB];
+    __shared__ float cS[MV_NT / 32][DS_TB], cC[MV_NT / 32][DS_TB];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long ntiles = (long long)ntb * (ntb + 1) / 2;
+    int I = 0;
+    long long pos = blockIdx.x;
+    while (I < ntb && pos >= ntb - I) {
+        pos -= ntb - I;
+        ++I;
+    }
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int J = I + (int)pos;
+        const int I0 = I * DS_TB, J0 = J * DS_TB;
+        const bool diag = I == J;
+        __syncthreads();
+        {
+            const int l = J0 + threadIdx.x;
+            const int ll = min(l, M - 1);
+            const float2 x = l < M ? xs[l] : make_float2(0.f, 0.f);
+            sP[threadIdx.x] = pts[ll];
+            sH[threadIdx.x] = make_float4(ph[ll], ph[(size_t)M + ll], ph[2 * (size_t)M + ll], x.x);
+            sL[threadIdx.x] = make_float4(pl[ll], pl[(size_t)M + ll], pl[2 * (size_t)M + ll], x.y);
+            if (!diag)
+                for (int q = 0; q < MV_NT / 32; ++q) {
+                    cS[q][threadIdx.x] = 0.f;
+                    cC[q][threadIdx.x] = 0.f;
+                }
+        }
+        const int k = I0 + 32 * w + lane;
+        const int kk = min(k, M - 1);
+        const float4 a = pts[kk];
+        const float xh = ph[kk], yh = ph[(size_t)M + kk], zh = ph[2 * (size_t)M + kk];
+        const float xl = pl[kk], yl = pl[(size_t)M + kk], zl = pl[2 * (size_t)M + kk];
+        const float2 xk = k < M ? xs[kk] : make_float2(0.f, 0.f);
+        __syncthreads();
+        float S_ = 0.f, C_ = 0.f;
+        for (int g = 0; g < DS_TB; g += 32) {
+#pragma unroll 4
+            for (int st = 0; st < 32; ++st) {
+                const int j = g + ((lane + st) & 31);
+                const float4 h = sH[j], lo = sL[j];
+                float ih, il, r2;
+                df_rsqrt(xh - h.x, xl - lo.x, yh - h.y, yl - lo.y, zh - h.z, zl - lo.z, ih, il, r2);
+                const bool far = r2_test32(a, sP[j]) >= rc2;
+                ih = far ? ih : 0.f;
+                il = far ? il : 0.f;
+                df_acc(S_, C_, ih, il, h.w, lo.w);
+                if (!diag) {
+                    float cs = cS[w][j], cc = cC[w][j];
+                    df_acc(cs, cc, ih, il, xk.x, xk.y);
+                    cS[w][j] = cs;
+                    cC[w][j] = cc;
+                }
+                __syncwarp();   // the next step's lane for this column reads it
+            }
+        }
+        if (k < M) ypart[(size_t)J * M + k] = (double)S_ + (double)C_;
+        if (!diag) {
+            __syncthreads();
+            const int l = J0 + threadIdx.x;
+            if (l < M) {
+                double v = 0.0;
+                for (int q = 0; q < MV_NT / 32; ++q) v += (double)cS[q][threadIdx.x] + (double)cC[q][threadIdx.x];
+                ypart[(size_t)I * M + l] = v;
+            }
+        }
+        pos += gridDim.x;
+        while (I < ntb && pos >= ntb - I) {
+            pos -= ntb - I;
+            ++I;
+        }
+    }
+}
+
 // y = A x (double-float far part, FP64 near part); part receives per-block
 // partials of x.y, *nparts their count
 int matfree_dfmv(pcm_ctx *c, const double *x, double *y, double *part, int *nparts)
 {
     const int M = c->M;
-    // chunks of at most DF_CH columns, at least four work items per SM
-    const int nrt_df = (M + MV_NT - 1) / MV_NT;
-    const int S = std::max((M + DF_CH - 1) / DF_CH, (4 * 152 + nrt_df - 1) / nrt_df);
-    const int ch = (M + S - 1) / S;
+    const int ntb = (M + DS_TB - 1) / DS_TB;
+    static int per = 0;
+    if (per == 0) {
+        PCM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dfmv_sym_kernel, MV_NT, 0));
+        per = std::max(per, 1);
+    }
+    int nsm = 0;
+    PCM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
     PCM_TRY(c->mf_xs.alloc(M));
-    PCM_TRY(c->mf_y64.alloc((size_t)S * M));
+    PCM_TRY(c->mf_y64.alloc((size_t)ntb * M));
     split_vec_kernel<<<(M + 255) / 256, 256, 0, c->stream>>>(M, x, c->mf_xs.p);
     PCM_LAUNCHED(c);
-    const int items = ((M + MV_NT - 1) / MV_NT) * S;
-    const int grid = std::min(items, 152 * 8);
-    dfmv_items_kernel<<<grid, MV_NT, 0, c->stream>>>(M, S, ch, c->mf_pts.p, c->p32.p, c->p32lo.p, c->mf_xs.p,
-                                                     c->mf_rc2, c->mf_y64.p);
+    const long long ntiles = (long long)ntb * (ntb + 1) / 2;
+    const int grid = (int)std::min<long long>(ntiles, (long long)per * nsm);
+    dfmv_sym_kernel<<<grid, MV_NT, 0, c->stream>>>(M, ntb, c->mf_pts.p, c->p32.p, c->p32lo.p, c->mf_xs.p, c->mf_rc2,
+                                                   c->mf_y64.p);
     PCM_LAUNCHED(c);
     const int nb = (M + MV_NT - 1) / MV_NT;
-    dfmv_reduce_kernel<<<nb, MV_NT, 0, c->stream>>>(M, S, c->mf_y64.p, c->mf_off.p, c->mf_col.p, c->mf_val.p, x, y,
+    dfmv_reduce_kernel<<<nb, MV_NT, 0, c->stream>>>(M, ntb, c->mf_y64.p, c->mf_off.p, c->mf_col.p, c->mf_val.p, x, y,
                                                     part);
     PCM_LAUNCHED(c);
     if (nparts) *nparts = nb;
@@ -486,42 +539,66 @@ __device__ __forceinline__ void st_add(unsigned long long *acc, float v, double 
 
 // The matrix-free FP32 product over the tiles of the upper triangle (A
 // symmetric: each 1/R evaluated once serves A_ij p_j and A_ji p_i).  Blocks
-// take contiguous runs of the tiles (I <= J, FS_TB x FS_TB, row-major order).
-// In a tile, warp w takes columns J0 + 32 w + t (t < 32, staged in shared
-// memory, read as broadcasts) against all FS_TB rows, eight per lane (rows
-// I0 + 32 r + lane, two per packed FP32x2 word); the element is 1/R with R^2
-// clamped below at rc2 exactly as in the per-row product, near pairs and the
-// diagonal thus adding the constant that the near list takes back.  Row sums
-// are added across the warps in shared memory; the column sums of the 32
-// columns are reduced across the lanes by halving (31 shuffles per lane).
-// Diagonal tiles form row sums only (both triangles and the diagonal) and
-// add the near-pair corrections of their rows.  Sums enter the fixed-point
-// accumulators; block partials of p.Ap to idot[block].
-template <bool DIAG>
-__device__ __forceinline__ void fs_tile(const PcgArgs &a, int I0, int J0, double scale, float4 *scol,
-                                        float (*srow)[FS_TB], double &d)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int M = a.M;
-    const float rc2 = a.rc2;
-    __syncthreads();   // the previous tile's readers of scol / srow are done
-    {
-        const int j = J0 + threadIdx.x;
-        const float4 q = a.pts[min(j, M - 1)];
-        scol[threadIdx.x] = make_float4(q.x, q.y, q.z, j < M ? __ldcg(a.p32 + j) : 0.f);
-    }
+// take contiguous runs of the tiles (I <= J, FS_TB x FS_TB, row-major order),
+// so a block stays on one tile row I for many tiles: the rows' coordinates
+// and their running sums stay in registers across the run and are flushed
+// once per row block.  In a tile, warp w takes columns J0 + 32 w + t (t < 32,
+// staged in shared memory, read as broadcasts) against all FS_TB rows, eight
+// per lane (rows I0 + 32 r + lane, two per packed FP32x2 word); the element is
+// 1/R with R^2 clamped below at rc2 exactly as in the per-row product, near
+// pairs and the diagonal thus adding the constant that the near list takes
+// back.  The 32 column partials of a lane are reduced across the lanes by
+// halving (31 shuffles); row sums are added across the warps in shared memory
+// at the flush.  Diagonal tiles form row sums only (both triangles and the
+// diagonal).  The near-pair corrections are one pass over the rows by the
+// whole grid.  Sums enter the fixed-point accumulators; block partials of
+// p.Ap to idot[block].
+struct FsRows {
     f2 rx[4], ry[4], rz[4], rp[4], racc[4];
+};
+
+__device__ __forceinline__ void fs_rows_load(const PcgArgs &a, int I0, FsRows &R)
+{
+    const int lane = threadIdx.x & 31, M = a.M;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i0 = I0 + 64 * q + lane, i1 = i0 + 32;
         const float4 u0 = a.pts[min(i0, M - 1)], u1 = a.pts[min(i1, M - 1)];
-        rx[q] = f2(u0.x, u1.x);
-        ry[q] = f2(u0.y, u1.y);
-        rz[q] = f2(u0.z, u1.z);
-        rp[q] = f2(i0 < M ? __ldcg(a.p32 + i0) : 0.f, i1 < M ? __ldcg(a.p32 + i1) : 0.f);
-        racc[q] = f2(0.f);
+        R.rx[q] = f2(u0.x, u1.x);
+        R.ry[q] = f2(u0.y, u1.y);
+        R.rz[q] = f2(u0.z, u1.z);
+        R.rp[q] = f2(i0 < M ? __ldcg(a.p32 + i0) : 0.f, i1 < M ? __ldcg(a.p32 + i1) : 0.f);
+        R.racc[q] = f2(0.f);
+    }
+}
+
+// the warps' row sums of row block I0, added in warp order, into the accumulators
+__device__ __forceinline__ void fs_rows_flush(const PcgArgs &a, int I0, const FsRows &R, float (*srow)[FS_TB],
+                                              double scale, double &d)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        srow[w][64 * q + lane] = R.racc[q].v.x;
+        srow[w][64 * q + 32 + lane] = R.racc[q].v.y;
     }
     __syncthreads();
+    const int i = I0 + threadIdx.x;
+    if (i < a.M) {
+        float v = srow[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < MV_NT / 32; ++q) v += srow[q][threadIdx.x];
+        st_add(a.acc + i, v, scale);
+        d = fma(__ldcg(a.p + i), (double)v, d);
+    }
+}
+
+template <bool DIAG>
+__device__ __forceinline__ void fs_tile(const PcgArgs &a, int J0, double scale, const float4 *scol, FsRows &R,
+                                        double &d)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float rc2 = a.rc2;
     float cp[32];
     const float4 *col = scol + 32 * w;
 #pragma unroll
@@ -531,19 +608,13 @@ __device__ __forceinline__ void fs_tile(const PcgArgs &a, int I0, int J0, double
         f2 ca(0.f);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const f2 dx = rx[q] - cx, dy = ry[q] - cy, dz = rz[q] - cz;
+            const f2 dx = R.rx[q] - cx, dy = R.ry[q] - cy, dz = R.rz[q] - cz;
             const f2 r2 = fma2(dx, dx, fma2(dy, dy, dz * dz));
             const f2 rs(rsqrt_fast(fmaxf(r2.v.x, rc2)), rsqrt_fast(fmaxf(r2.v.y, rc2)));
-            racc[q] = fma2(rs, cw, racc[q]);
-            if (!DIAG) ca = fma2(rs, rp[q], ca);
+            R.racc[q] = fma2(rs, cw, R.racc[q]);
+            if (!DIAG) ca = fma2(rs, R.rp[q], ca);
         }
         if (!DIAG) cp[t] = ca.v.x + ca.v.y;
-    }
-    // row parts of this warp's 32 columns
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        srow[w][64 * q + lane] = racc[q].v.x;
-        srow[w][64 * q + 32 + lane] = racc[q].v.y;
     }
     if (!DIAG) {
         // column sums: halve the 32 partials across the lanes; lane l ends
@@ -559,22 +630,9 @@ __device__ __forceinline__ void fs_tile(const PcgArgs &a, int I0, int J0, double
             }
         }
         const int jc = J0 + 32 * w + lane;
-        if (jc < M) {
+        if (jc < a.M) {
             st_add(a.acc + jc, cp[0], scale);
             d = fma(__ldcg(a.p + jc), (double)cp[0], d);
-        }
-    }
-    __syncthreads();
-    {
-        const int i = I0 + threadIdx.x;
-        float v = srow[0][threadIdx.x];
-#pragma unroll
-        for (int q = 1; q < MV_NT / 32; ++q) v += srow[q][threadIdx.x];
-        if (i < M) {
-            if (DIAG)
-                for (int e = a.off[i]; e < a.off[i + 1]; ++e) v = fmaf(a.val32[e], __ldcg(a.p32 + a.col[e]), v);
-            st_add(a.acc + i, v, scale);
-            d = fma(__ldcg(a.p + i), (double)v, d);
         }
     }
 }
@@ -587,6 +645,8 @@ __device__ __forceinline__ void pcg_product_free_sym(const PcgArgs &a, int n)
     double inv;
     const double scale = st_scale(a, n, &inv);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.pmax[(n + 1) & 1] = 0u;
+    const int M = a.M;
+    double d = 0.0;
     const int ntb = a.ntb;
     const long long ntiles = (long long)ntb * (ntb + 1) / 2;
     const long long t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
@@ -596,17 +656,55 @@ __device__ __forceinline__ void pcg_product_free_sym(const PcgArgs &a, int n)
         pos -= ntb - I;
         ++I;
     }
-    double d = 0.0;
+    FsRows R;
+    int cur = -1;
     for (long long t = t0; t < t1; ++t) {
         const int J = I + (int)pos;
+        if (I != cur) {
+            if (cur >= 0) fs_rows_flush(a, cur * FS_TB, R, srow, scale, d);
+            fs_rows_load(a, I * FS_TB, R);
+            cur = I;
+        }
+        __syncthreads();   // the previous tile's readers of scol (and the flush's of srow) are done
+        {
+            const int j = J * FS_TB + threadIdx.x;
+            const float4 q = a.pts[min(j, M - 1)];
+            scol[threadIdx.x] = make_float4(q.x, q.y, q.z, j < M ? __ldcg(a.p32 + j) : 0.f);
+        }
+        __syncthreads();
         if (J == I)
-            fs_tile<true>(a, I * FS_TB, J * FS_TB, scale, scol, srow, d);
+            fs_tile<true>(a, J * FS_TB, scale, scol, R, d);
         else
-            fs_tile<false>(a, I * FS_TB, J * FS_TB, scale, scol, srow, d);
+            fs_tile<false>(a, J * FS_TB, scale, scol, R, d);
         if (++pos >= ntb - I) {
             pos = 0;
             ++I;
         }
+    }
+    if (cur >= 0) {
+        __syncthreads();
+        fs_rows_flush(a, cur * FS_TB, R, srow, scale, d);
+    }
+    // near pairs and the diagonal: A_kl - rsqrt(rc2) for the constant the tiles
+    // add, one row per thread over the grid; the column indices and values of
+    // eight entries are loaded before their directions, so that the dependent
+    // loads overlap
+    for (int i = blockIdx.x * MV_NT + threadIdx.x; i < M; i += gridDim.x * MV_NT) {
+        float v = 0.f;
+        const int e0 = a.off[i], e1 = a.off[i + 1];
+        for (int e = e0; e < e1; e += 8) {
+            int cl[8];
+            float vl[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                cl[u] = e + u < e1 ? a.col[e + u] : 0;
+                vl[u] = e + u < e1 ? a.val32[e + u] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v = fmaf(vl[u], __ldcg(a.p32 + cl[u]), v);
+        }
+        st_add(a.acc + i, v, scale);
+        d = fma(__ldcg(a.p + i), (double)v, d);
     }
     d = block_sum<double, MV_NT>(d, red);
     if (threadIdx.x == 0) a.idot[blockIdx.x] = d;
