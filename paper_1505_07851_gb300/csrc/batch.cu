@@ -2,12 +2,18 @@
 // of uneven size in one call.
 //
 // Each molecule keeps its own context (surface, stored A and its FP32 parts,
-// pair lists, RBJ preconditioner).  The integral stages run molecule after
-// molecule on the batch's stream (every launch fills the GPU).  The linear
+// pair lists, RBJ preconditioner).  The integral stages prepare each
+// molecule's tiles on the batch's stream; in PCM_MIXED the packed ESP and Fock
+// blocks of all molecules then run in one launch per angular class (job
+// tables), the one-centre and epilogue kernels per molecule.  The linear
 // solves of all molecules run in lockstep: every vector of the batch lives in
 // one concatenated array (each molecule's slice starts on a 32-element
 // boundary), and one launch per step serves all molecules:
-//   bgemv      A p for every molecule (row pairs of all matrices, one table)
+//   bgemv      A p for every molecule (row pairs of all matrices, one table);
+//              PCM_MIXED: bsym over the 128 x 128 tiles of the upper triangle
+//              of every A32 (A is symmetric: each tile serves A_IJ p_J and
+//              A_IJ^T p_I, half the bytes of the row GEMV), partial sums per
+//              tile column block, then bsym_reduce adds them per row
 //   balpha     alpha_m = r.z / p.Ap per molecule (fixed-order partial sums)
 //   bupdate    x, r update and z = C r per RBJ block of every molecule
 //   bscalar    per-molecule stop test (Eq. 20) and beta; sets the loop condition
@@ -50,6 +56,12 @@ struct BatchDev {
     const int *gb_mol, *gb_rp, *gb_start;   // GEMV row-pair blocks; per-molecule ranges (nmol + 1)
     const int *rb_mol, *rb_blk, *rb_start;  // preconditioner blocks
     const int *elem_mol;                    // molecule of each (padded) element, -1 for padding
+    // PCM_MIXED symmetric products: tile blocks (molecule, I << 16 | J), the start of each
+    // molecule's partial slots (ceil(M / 128) slices of its padded length), reduction blocks
+    // (molecule, first row) with per-molecule ranges (nmol + 1)
+    const int *gt_mol, *gt_ij;
+    const long long *slot_off;
+    const int *rd_mol, *rd_row, *rd_start;
 };
 
 }  // namespace pcm
@@ -71,6 +83,10 @@ struct pcm_batch {
     pcm::DBuf<const float *> dA32, dA32lo;
     pcm::DBuf<const int *> dperm;
     pcm::DBuf<int> dlda, dM, doff, dl, dnblk, gb_mol, gb_rp, gb_start, rb_mol, rb_blk, rb_start, elem_mol;
+    pcm::DBuf<int> gt_mol, gt_ij, rd_mol, rd_row, rd_start;
+    pcm::DBuf<long long> slot_off;
+    pcm::DBuf<double> ypart;           // partial sums of the symmetric products
+    int ngt = 0, nrd = 0;
     // vectors (Mtot) and per-molecule scalars
     pcm::DBuf<double> x, b, r, z, p, Ap, d, ro, y;
     pcm::DBuf<float> p32, xh32, xl32;  // FP32 copy of p; hi and lo parts of x for the residual
@@ -116,25 +132,146 @@ __global__ void __launch_bounds__(BG_NT) bgemv_kernel(BatchDev B, const TA *__re
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// The same in double-float on the FP32 pipes (PCM_MIXED true residuals):
-// A = A32 + A32lo, x = xh + xl, as gemv_rowpair_df
-__global__ void __launch_bounds__(BG_NT) bgemv_df_kernel(BatchDev B, const float *__restrict__ xh,
-                                                         const float *__restrict__ xl, const double *__restrict__ x64,
-                                                         double *__restrict__ y, const int *__restrict__ idone,
-                                                         double *__restrict__ part)
+// y = A x over the tiles of the upper triangle of every molecule's A32 (DF:
+// double-float from A32 + A32lo and x = xh + xl, as gemv_rowpair_df; else FP32
+// from A32 and xh).  Block = tile (I, J) of molecule m: warp w takes rows
+// I0 + w + 8 i (i < 16), lane l columns J0 + 4 l .. + 3.  Row sums (reduced
+// across the lanes by halving) go to slot J of the rows, column sums of an
+// off-diagonal tile (reduced across the warps in shared memory) to slot I of
+// the columns; each (slot, row) is written by exactly one tile.
+constexpr int BT_TB = 128;
+template <bool DF>
+__global__ void __launch_bounds__(BG_NT) bsym_kernel(BatchDev B, const float *__restrict__ xh,
+                                                     const float *__restrict__ xl, const int *__restrict__ idone,
+                                                     double *__restrict__ ypart)
 {
-    const int m = B.gb_mol[blockIdx.x];
+    __shared__ double cs[BG_NT / 32][BT_TB];
+    const int m = B.gt_mol[blockIdx.x];
+    if (idone[m]) return;
+    const int ij = B.gt_ij[blockIdx.x], I = ij >> 16, J = ij & 0xffff;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int M = B.M[m], lda = B.lda[m], o = B.off[m], Mp = B.off[m + 1] - o;
+    const float *__restrict__ A = B.A32[m];
+    const float *__restrict__ Al = B.A32lo[m];
+    double *__restrict__ yp = ypart + B.slot_off[m];
+    const int I0 = I * BT_TB, J0 = J * BT_TB, c0 = J0 + 4 * lane;
+    const bool cok = c0 < M;   // then c0 + 3 < Mp <= lda: whole 16-byte loads stay in the slices
+    float xj[4] = {0.f, 0.f, 0.f, 0.f}, xjl[4] = {0.f, 0.f, 0.f, 0.f};
+    if (cok) {
+        const float4 v = *reinterpret_cast<const float4 *>(xh + o + c0);
+        xj[0] = v.x, xj[1] = v.y, xj[2] = v.z, xj[3] = v.w;
+        if (DF) {
+            const float4 u = *reinterpret_cast<const float4 *>(xl + o + c0);
+            xjl[0] = u.x, xjl[1] = u.y, xjl[2] = u.z, xjl[3] = u.w;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (c0 + t >= M) xj[t] = xjl[t] = 0.f;
+    }
+    double rp[16];
+    double cc[4] = {0.0, 0.0, 0.0, 0.0};
+    float cS[4] = {0.f, 0.f, 0.f, 0.f}, cC[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        float4 a4[8], l4[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int row = I0 + w + 8 * (8 * hh + i);
+            const bool ok = cok && row < M;
+            a4[i] = ok ? *reinterpret_cast<const float4 *>(A + (size_t)row * lda + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (DF)
+                l4[i] = ok ? *reinterpret_cast<const float4 *>(Al + (size_t)row * lda + c0)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int row = I0 + w + 8 * (8 * hh + i);
+            float a[4] = {a4[i].x, a4[i].y, a4[i].z, a4[i].w};
+            float al[4] = {0.f, 0.f, 0.f, 0.f};
+            if (DF) al[0] = l4[i].x, al[1] = l4[i].y, al[2] = l4[i].z, al[3] = l4[i].w;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (c0 + t >= M) a[t] = al[t] = 0.f;   // columns beyond M: unwritten entries
+            float xi = 0.f, xil = 0.f;
+            if (row < M) {
+                xi = xh[o + row];
+                if (DF) xil = xl[o + row];
+            }
+            if (DF) {
+                float S = 0.f, C = 0.f;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    df_acc(S, C, a[t], al[t], xj[t], xjl[t]);
+                    df_acc(cS[t], cC[t], a[t], al[t], xi, xil);
+                }
+                rp[8 * hh + i] = (double)S + (double)C;
+            } else {
+                rp[8 * hh + i] = (double)fmaf(a[0], xj[0], fmaf(a[1], xj[1], fmaf(a[2], xj[2], a[3] * xj[3])));
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cS[t] = fmaf(a[t], xi, cS[t]);
+            }
+        }
+    }
+    // rows: halve the sixteen partials across the lanes (row 8 b4 + 4 b3 + 2 b2 + b1 ends in lanes 2i, 2i + 1)
+#pragma unroll
+    for (int h = 8, off = 16; h >= 1; h >>= 1, off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double send = up ? rp[i] : rp[i + h];
+            const double keep = up ? rp[i + h] : rp[i];
+            rp[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    const double rsum = rp[0] + __shfl_xor_sync(0xffffffffu, rp[0], 1);
+    {
+        const int mm = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+        const int row = I0 + w + 8 * mm;
+        if ((lane & 1) == 0 && row < M) yp[(size_t)J * Mp + row] = rsum;
+    }
+    if (I != J) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) cc[t] = DF ? (double)cS[t] + (double)cC[t] : (double)cS[t];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) cs[w][4 * lane + t] = cc[t];
+        __syncthreads();
+        if (threadIdx.x < BT_TB) {
+            double v = cs[0][threadIdx.x];
+#pragma unroll
+            for (int q = 1; q < BG_NT / 32; ++q) v += cs[q][threadIdx.x];
+            const int col = J0 + threadIdx.x;
+            if (col < M) yp[(size_t)I * Mp + col] = v;
+        }
+    }
+}
+
+// y = the sum of a molecule's partial slots per row (fixed order), per-block
+// partials of x.y
+__global__ void __launch_bounds__(256) bsym_reduce_kernel(BatchDev B, const double *__restrict__ ypart,
+                                                          const double *__restrict__ x64, const int *__restrict__ idone,
+                                                          double *__restrict__ y, double *__restrict__ part)
+{
+    __shared__ double red[8];
+    const int m = B.rd_mol[blockIdx.x];
     if (idone[m]) {
         if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
         return;
     }
-    const int o = B.off[m];
-    const double s = gemv_rowpair_df(B.gb_rp[blockIdx.x], B.M[m], B.lda[m], B.A32[m], B.A32lo[m], xh + o, xl + o,
-                                     x64 + o, y + o);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    const int M = B.M[m], o = B.off[m], Mp = B.off[m + 1] - o;
+    const int ntb = (M + BT_TB - 1) / BT_TB;
+    const double *__restrict__ yp = ypart + B.slot_off[m];
+    const int k = B.rd_row[blockIdx.x] + threadIdx.x;
+    double d = 0.0;
+    if (k < M) {
+        double v = 0.0;
+        for (int s = 0; s < ntb; ++s) v += yp[(size_t)s * Mp + k];
+        y[o + k] = v;
+        d = x64[o + k] * v;
+    }
+    d = block_sum<double, 256>(d, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = d;
 }
 
-// x -> FP32 hi and lo parts
 __global__ void bsplit_kernel(int n, const double *__restrict__ x, float *__restrict__ xh, float *__restrict__ xl)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -145,14 +282,15 @@ __global__ void bsplit_kernel(int n, const double *__restrict__ x, float *__rest
 }
 
 // alpha_m = rz_m / (p.Ap)_m from the GEMV partials of molecule m (one warp per molecule)
-__global__ void balpha_kernel(int nmol, BatchDev B, const double *__restrict__ part, const int *__restrict__ idone,
-                              const double *__restrict__ rz, double *__restrict__ pAp, double *__restrict__ alpha)
+__global__ void balpha_kernel(int nmol, const int *__restrict__ start, const double *__restrict__ part,
+                              const int *__restrict__ idone, const double *__restrict__ rz, double *__restrict__ pAp,
+                              double *__restrict__ alpha)
 {
     const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (m >= nmol || idone[m]) return;
     double s = 0.0;
-    for (int i = B.gb_start[m] + lane; i < B.gb_start[m + 1]; i += 32) s += part[i];
+    for (int i = start[m] + lane; i < start[m + 1]; i += 32) s += part[i];
     s = warp_sum(s);
     if (lane == 0) {
         pAp[m] = s;
@@ -399,6 +537,31 @@ static int batch_layout(pcm_batch *bt)
     off[n] = o;
     gbs[n] = (int)gbm.size();
     rbs[n] = (int)rbm.size();
+    // PCM_MIXED: tiles of the upper triangles, partial slots, reduction blocks
+    std::vector<int> gtm, gtij, rdm, rdr, rds(n + 1);
+    std::vector<long long> soff(n + 1, 0);
+    const bool sym = bt->opt.precision == PCM_MIXED;
+    for (int m = 0; m < n && sym; ++m) {
+        const int ntb = (M[m] + BT_TB - 1) / BT_TB;
+        if (bt->mol[m]->A32.p)
+            for (int I = 0; I < ntb; ++I)
+                for (int J = I; J < ntb; ++J) {
+                    gtm.push_back(m);
+                    gtij.push_back((I << 16) | J);
+                }
+        soff[m + 1] = soff[m] + (long long)ntb * (off[m + 1] - off[m]);
+        rds[m] = (int)rdm.size();
+        for (int k = 0; k < M[m]; k += 256) {
+            rdm.push_back(m);
+            rdr.push_back(k);
+        }
+    }
+    rds[n] = (int)rdm.size();
+    bt->ngt = (int)gtm.size();
+    bt->nrd = (int)rdm.size();
+    if (sym && bt->ngt > 0) PCM_TRY(bt->ypart.alloc((size_t)std::max(1LL, soff[n])));
+    if (gtm.empty()) gtm.push_back(0), gtij.push_back(0);
+    if (rdm.empty()) rdm.push_back(0), rdr.push_back(0);
     bt->h_off = off;
     bt->Mtot = o;
     bt->ngb = (int)gbm.size();
@@ -429,6 +592,12 @@ static int batch_layout(pcm_batch *bt)
     PCM_TRY(up(bt->rb_blk, rbb));
     PCM_TRY(up(bt->rb_start, rbs));
     PCM_TRY(up(bt->elem_mol, em));
+    PCM_TRY(up(bt->gt_mol, gtm));
+    PCM_TRY(up(bt->gt_ij, gtij));
+    PCM_TRY(up(bt->slot_off, soff));
+    PCM_TRY(up(bt->rd_mol, rdm));
+    PCM_TRY(up(bt->rd_row, rdr));
+    PCM_TRY(up(bt->rd_start, rds));
     PCM_CUDA(cudaStreamSynchronize(bt->stream));  // the host vectors go out of scope
     BatchDev &D = bt->dev;
     D.A64 = bt->dA64.p;
@@ -449,6 +618,12 @@ static int batch_layout(pcm_batch *bt)
     D.rb_blk = bt->rb_blk.p;
     D.rb_start = bt->rb_start.p;
     D.elem_mol = bt->elem_mol.p;
+    D.gt_mol = bt->gt_mol.p;
+    D.gt_ij = bt->gt_ij.p;
+    D.slot_off = bt->slot_off.p;
+    D.rd_mol = bt->rd_mol.p;
+    D.rd_row = bt->rd_row.p;
+    D.rd_start = bt->rd_start.p;
     const size_t Mt = std::max(1, o);
     for (DBuf<double> *v : {&bt->x, &bt->b, &bt->r, &bt->z, &bt->p, &bt->Ap, &bt->d, &bt->ro, &bt->y}) {
         PCM_TRY(v->alloc(Mt));
@@ -462,7 +637,7 @@ static int batch_layout(pcm_batch *bt)
         PCM_TRY(v->alloc(n));
     for (DBuf<int> *v : {&bt->idone, &bt->iters, &bt->conv, &bt->maxit}) PCM_TRY(v->alloc(n));
     PCM_TRY(bt->gcount.alloc(1));
-    PCM_TRY(bt->gpart.alloc(std::max(1, bt->ngb)));
+    PCM_TRY(bt->gpart.alloc(std::max(1, std::max(bt->ngb, bt->nrd))));
     PCM_TRY(bt->rpart.alloc(2 * (size_t)std::max(1, bt->nrb)));
     if (bt->exec) {
         cudaGraphExecDestroy(bt->exec);
@@ -483,14 +658,18 @@ static void batch_iteration(pcm_batch *bt, bool use32, int cap, cudaGraphConditi
 {
     const int n = bt->nmol;
     const BatchDev &D = bt->dev;
-    if (use32)
-        bgemv_kernel<float><<<bt->ngb, BG_NT, 0, bt->stream>>>(D, bt->p32.p, bt->p.p, bt->Ap.p, bt->idone.p,
+    if (use32) {
+        if (bt->ngt > 0)
+            bsym_kernel<false><<<bt->ngt, BG_NT, 0, bt->stream>>>(D, bt->p32.p, nullptr, bt->idone.p, bt->ypart.p);
+        if (bt->nrd > 0)
+            bsym_reduce_kernel<<<bt->nrd, 256, 0, bt->stream>>>(D, bt->ypart.p, bt->p.p, bt->idone.p, bt->Ap.p,
                                                                bt->gpart.p);
-    else
+    } else {
         bgemv_kernel<double><<<bt->ngb, BG_NT, 0, bt->stream>>>(D, bt->p.p, bt->p.p, bt->Ap.p, bt->idone.p,
                                                                 bt->gpart.p);
-    balpha_kernel<<<(n + 7) / 8, 256, 0, bt->stream>>>(n, D, bt->gpart.p, bt->idone.p, bt->rz.p, bt->pAp.p,
-                                                       bt->alpha.p);
+    }
+    balpha_kernel<<<(n + 7) / 8, 256, 0, bt->stream>>>(n, use32 ? bt->rd_start.p : bt->gb_start.p, bt->gpart.p,
+                                                       bt->idone.p, bt->rz.p, bt->pAp.p, bt->alpha.p);
     bupdate_kernel<<<bt->nrb, rbj_threads(bt->rbj_l_max), bt->rbj_l_max * sizeof(double), bt->stream>>>(
         D, bt->d.p, bt->r.p, bt->z.p, bt->p.p, bt->Ap.p, bt->alpha.p, bt->idone.p, bt->rpart.p, 0);
     bscalar_kernel<<<1, BS_NT, 0, bt->stream>>>(n, D, bt->rpart.p, bt->idone.p, bt->iters.p, bt->conv.p,
@@ -578,8 +757,12 @@ static int batch_solve(pcm_batch *bt, double delta)
             // double-float A x: the FP64 pipe would bound an FP64 GEMV below the HBM rate
             const int sb = std::min(4096, (bt->Mtot + 255) / 256);
             bsplit_kernel<<<sb, 256, 0, bt->stream>>>(bt->Mtot, bt->x.p, bt->xh32.p, bt->xl32.p);
-            bgemv_df_kernel<<<bt->ngb, BG_NT, 0, bt->stream>>>(D, bt->xh32.p, bt->xl32.p, bt->x.p, bt->y.p,
-                                                               bt->idone.p, bt->gpart.p);
+            if (bt->ngt > 0)
+                bsym_kernel<true><<<bt->ngt, BG_NT, 0, bt->stream>>>(D, bt->xh32.p, bt->xl32.p, bt->idone.p,
+                                                                    bt->ypart.p);
+            if (bt->nrd > 0)
+                bsym_reduce_kernel<<<bt->nrd, 256, 0, bt->stream>>>(D, bt->ypart.p, bt->x.p, bt->idone.p, bt->y.p,
+                                                                   bt->gpart.p);
         } else {
             bgemv_kernel<double><<<bt->ngb, BG_NT, 0, bt->stream>>>(D, bt->x.p, bt->x.p, bt->y.p, bt->idone.p,
                                                                     bt->gpart.p);
@@ -848,6 +1031,20 @@ int pcm_batch_run(pcm_batch *bt, const double *const *P, double delta, double *E
     } else {
         // every solve in lockstep
         PCM_TRY(batch_solve(bt, delta));
+        if (bt->opt.precision == PCM_MIXED) {
+            // the refinement ends on a true residual of every molecule's final
+            // charges: y = A x is the energy's A q (as a single solve keeps it)
+            for (int m = 0; m < bt->nmol; ++m) {
+                pcm_ctx *c = bt->mol[m];
+                PCM_TRY(c->aq_q.alloc(c->M));
+                PCM_TRY(c->aq_y.alloc(c->M));
+                PCM_CUDA(cudaMemcpyAsync(c->aq_q.p, bt->x.p + bt->h_off[m], c->M * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, bt->stream));
+                PCM_CUDA(cudaMemcpyAsync(c->aq_y.p, bt->y.p + bt->h_off[m], c->M * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, bt->stream));
+                c->aq_valid = true;
+            }
+        }
     }
     // Fock correction and energy of every molecule
     std::vector<double *> ddFs(bt->nmol, nullptr);

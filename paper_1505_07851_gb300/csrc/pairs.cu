@@ -86,14 +86,16 @@ __global__ void pair_screen_kernel(long long ncand, int nsp, const long long *__
     const double a = exps[sh_off[A] + i], b = exps[sh_off[B] + j];
     const double *RA = xyz + 3 * sh_atom[A], *RB = xyz + 3 * sh_atom[B];
     const double p = a + b;
+    // one FP64 division per candidate (the FP64 pipe runs at 1/64 of FP32 here)
+    const double ip = 1.0 / p;
     double P[3], ab2 = 0.0;
     for (int d = 0; d < 3; ++d) {
-        P[d] = (a * RA[d] + b * RB[d]) / p;
+        P[d] = (a * RA[d] + b * RB[d]) * ip;
         const double t = RA[d] - RB[d];
         ab2 += t * t;
     }
-    const double K = exp(-a * b / p * ab2);
-    const double pref = 2.0 * PCM_PI / p * K;
+    const double K = exp(-a * b * ip * ab2);
+    const double pref = 2.0 * PCM_PI * ip * K;
 
     // Schwarz bound |c_i c_j| max_{ab} N_a N_b [ab|ab]^(1/2) from the
     // McMurchie-Davidson diagonal two-electron integral at zero separation
@@ -102,7 +104,9 @@ __global__ void pair_screen_kernel(long long ncand, int nsp, const long long *__
     // R_{TUV}(alpha, 0) = (-2 alpha)^((T+U+V)/2) (T-1)!!(U-1)!!(V-1)!! / (T+U+V+1)
     // for even T, U, V and 0 otherwise.
     E1T<LA, LB, TS> Ex, Ey, Ez;
-    const TS inv2p = TS(0.5 / p);
+    const TS inv2p = TS(0.5 * ip);
+    // 2 pi^(5/2) / (p^2 sqrt(2 p)) K^2 (2 pi^(5/2) = 2 * 17.4934...)
+    const double eri_pre = 2.0 * 17.493418327624862846 * ip * ip * sqrt(0.5 * ip) * K * K;
     hermite_E1T<LA, LB, TS>(TS(P[0] - RA[0]), TS(P[0] - RB[0]), inv2p, Ex);
     hermite_E1T<LA, LB, TS>(TS(P[1] - RA[1]), TS(P[1] - RB[1]), inv2p, Ey);
     hermite_E1T<LA, LB, TS>(TS(P[2] - RA[2]), TS(P[2] - RB[2]), inv2p, Ez);
@@ -143,12 +147,14 @@ __global__ void pair_screen_kernel(long long ncand, int nsp, const long long *__
                         const TS R = TS(dfact_even(T) * dfact_even(U) * dfact_even(V) / (T + U + V + 1)) * pw[n];
                         sum += Gx[T] * Gy[U] * Gz[V] * R;
                     }
-            const double eri =
-                2.0 * 17.493418327624862846 / (p * p * sqrt(2.0 * p)) * K * K * (double)sum;  // 2 pi^(5/2) = 2 * 17.4934...
+            const double eri = eri_pre * (double)sum;
             const double f = comp_factor(LA, ca) * comp_factor(LB, cb);
             qmax = fmax(qmax, f * f * fabs(eri));
         }
     const double Q = fabs(cnorm[sh_off[A] + i] * cnorm[sh_off[B] + j]) * sqrt(qmax);
+    const bool keep = thresh <= 0.0 || Q >= thresh;
+    flag[g] = keep ? 1 : 0;
+    if (!keep) return;   // only kept candidates are gathered
     o_sp[g] = s;
     o_i[g] = i;
     o_j[g] = j;
@@ -158,7 +164,6 @@ __global__ void pair_screen_kernel(long long ncand, int nsp, const long long *__
     o_p[g] = p;
     o_pref[g] = pref;
     o_Q[g] = Q;
-    flag[g] = (thresh <= 0.0 || Q >= thresh) ? 1 : 0;
 }
 
 __global__ void pair_gather_kernel(int n, const int *__restrict__ idx, const int *__restrict__ c_sp,

@@ -114,3 +114,22 @@ def test_energy_from_last_residual_matches_product(operator):
     assert abs(E_kept - E_prod) <= 1e-12 * abs(E_prod), (E_kept, E_prod)
     assert E_changed == E_prod2 or abs(E_changed - E_prod2) <= 1e-14 * abs(E_prod2)
     assert E_changed != E_kept
+
+
+@pytest.mark.parametrize("operator", ["stored", "free"])
+def test_mixed_solve_bitwise_reproducible(operator):
+    """The symmetric tile products add their row and column parts in 64-bit
+    fixed point and every other sum in a fixed order, so two solves of the
+    same system (in fresh contexts, with tiles arriving in whatever order the
+    hardware schedules them) return the same charges bit for bit."""
+    import paper_1505_07851_gb300 as pcm
+    w = CASES["cluster40_sp"]()
+    qs = []
+    for _ in range(2):
+        with pcm.Context(precision="mixed", operator=operator) as ctx:
+            ctx.setup(w.mol, w.basis)
+            ctx.esp(w.P)
+            q, st = ctx.solve(delta=1e-9)
+            qs.append((q, st["iterations"]))
+    assert qs[0][1] == qs[1][1]
+    assert np.array_equal(qs[0][0], qs[1][0])
