@@ -84,8 +84,14 @@ def flops_per_interaction(L, kind):
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernels (profiles/); a kernel missing here reports traffic null.
-NCU_TRAFFIC_BYTES = {}
+# kernels (profiles/); a kernel missing here reports traffic null.  The ESP ps
+# class of the 1000-atom cluster: its packed kernel esp_kernel_f32x2<1, 2>
+# read 105,000,704 and wrote 6,144,768 bytes in one launch (the class's
+# one-centre kernel and reduction add a few MB more).
+NCU_TRAFFIC_BYTES = {
+    ("cluster1000_spd", "ESP ps class: esp_kernel_f32x2<L=1> + same-atom pairs (esp_kernel_f32) + reduction"):
+        105000704 + 6144768,
+}
 
 CLASS_L = [0, 1, 2, 2, 3, 4]
 CLASS_NAME = ["ss", "ps", "pp", "ds", "dp", "dd"]

@@ -300,7 +300,10 @@ int pcm_batch_get_stats(pcm_batch *batch, int i, pcm_stats *st);
 /* The autotuner's choices so far in this process: up to max_entries records
  * of eight ints: device; kernel family (0: ESP variant, choice 0 pair-driven
  * with 4 points per thread, 1 with 2, 2 MS-driven (one pair per thread with
- * block reductions per point); 1: Fock pairs per thread, choice 1 or 2);
+ * block reductions per point); 1: Fock pairs per thread, choice 1 or 2;
+ * 2 and 3: the same with scalar FP32 instructions; 4: the ESP variant of
+ * batch members, choice 0 or 1 (their packed blocks run in one launch for
+ * all molecules));
  * angular momentum L; size bucket floor(log2(pairs)); the choice; the trial
  * times of variants 0, 1, 2 in microseconds (0: not tried; for the Fock
  * family variants 0 and 1 are 1 and 2 pairs per thread).  Returns the number

@@ -177,8 +177,10 @@ def pipe_peak(which="fp32", device=0):
 def autotune_table():
     """The autotuner's choices so far: list of dicts (device, kernel, L,
     bucket, choice, fp32x2, trial_us) with kernel "esp_variant" (pair-driven
-    with 4 or 2 points per thread, or MS-driven) or "fock_pairs_per_thread" (1 or 2);
-    trial_us the timed trial of each candidate in microseconds."""
+    with 4 or 2 points per thread, or MS-driven; "batch": the record of batch
+    members, whose packed blocks run in one launch for all molecules) or
+    "fock_pairs_per_thread" (1 or 2); trial_us the timed trial of each
+    candidate in microseconds."""
     n = _lib.pcm_autotune_table(None, 0)
     buf = (ctypes.c_int * (8 * max(1, n)))()
     n = _lib.pcm_autotune_table(buf, n)
@@ -186,11 +188,11 @@ def autotune_table():
     out = []
     for i in range(n):
         dev, kind, L, bucket, ch, t0, t1, t2 = buf[8 * i:8 * i + 8]
-        packed = kind in (0, 1)
-        if kind in (0, 2):
+        packed = kind in (0, 1, 4)
+        if kind in (0, 2, 4):
             trials = {names[v]: t for v, t in enumerate((t0, t1, t2)) if t > 0}
             out.append({"device": dev, "kernel": "esp_variant", "L": L, "bucket": bucket, "choice": names[ch],
-                        "fp32x2": packed, "trial_us": trials})
+                        "fp32x2": packed, "batch": kind == 4, "trial_us": trials})
         else:
             out.append({"device": dev, "kernel": "fock_pairs_per_thread", "L": L, "bucket": bucket, "choice": ch,
                         "fp32x2": packed, "trial_us": {1: t0, 2: t1}})

@@ -847,7 +847,8 @@ static void fock_split(pcm_ctx *c, int nb, int *nsplit, int *ks)
 }
 
 // The autotuner's trial for the FP32 Fock kernel of class k: one and two
-// pairs per thread, each timed once; the faster is remembered.
+// pairs per thread, each run once untimed and then timed once; the faster is
+// remembered.
 static int fock_tune(pcm_ctx *c, int k, int L, const double *dq)
 {
     struct NoDefer {
@@ -870,6 +871,13 @@ static int fock_tune(pcm_ctx *c, int k, int L, const double *dq)
         int nsplit, ks;
         fock_split(c, nb, &nsplit, &ks);
         st = c->fock_W.alloc((size_t)nsplit * nherm(L) * pc.npair);
+        if (st != PCM_OK) break;
+        // an untimed run first (first-use allocations and code loading)
+        st = fock_mixed_class(c, k, dq, nsplit, ks, c->fock_W.p, npt);
+        if (st == PCM_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            set_last_error("autotuner: a Fock trial failed");
+            st = PCM_ERR_CUDA;
+        }
         if (st != PCM_OK) break;
         cudaEventRecord(e0, c->stream);
         st = fock_mixed_class(c, k, dq, nsplit, ks, c->fock_W.p, npt);

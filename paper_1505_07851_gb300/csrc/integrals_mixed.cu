@@ -1020,11 +1020,14 @@ static int esp_rows_v(pcm_ctx *c, int k, int v, const int nb[2])
     return r1 + mrows;
 }
 
-// The autotuner's trial for class k: both layouts timed once with CUDA
-// events on the context's stream; the faster one is remembered for this GPU,
-// kernel family, angular momentum and size bucket.
+// The autotuner's trial for class k: every candidate run once untimed, then
+// once timed with CUDA events on the context's stream; the fastest is
+// remembered for this GPU, kernel family, angular momentum and size bucket.
 static int esp_tune(pcm_ctx *c, int k, DBuf<int> *blk, DBuf<int> *bcls, const int nb[2], int *choice)
 {
+    // a batch member: its packed blocks join one launch with every other
+    // molecule's, so only the packed layouts are candidates (their own record)
+    const bool batching = c->jobs != nullptr && c->opt.fp32x2;
     struct NoDefer {
         pcm_ctx *c;
         JobSink *j;
@@ -1033,17 +1036,21 @@ static int esp_tune(pcm_ctx *c, int k, DBuf<int> *blk, DBuf<int> *bcls, const in
     c->jobs = nullptr;   // the trials run now, whatever the caller collects
     const int L = CLASS_L[k];
     const int bucket = tune_bucket((long long)c->cls[k].nesp);
-    const int kind = c->opt.fp32x2 ? TUNE_ESP_PPT : TUNE_ESP_PPT_SCALAR;
+    const int kind = batching ? TUNE_ESP_PPT_BATCH : (c->opt.fp32x2 ? TUNE_ESP_PPT : TUNE_ESP_PPT_SCALAR);
     const int t = tune_get(c->device, kind, L, bucket);
     if (t >= 0) {
         *choice = t;
         return PCM_OK;
     }
-    // candidates: pair-driven with 4 or 2 points per thread; MS-driven for L <= 2
-    const int nv = L <= 2 ? 3 : 2;
+    // candidates: pair-driven with 4 or 2 points per thread; MS-driven for L <= 2 (not in batches)
+    const int nv = (L <= 2 && !batching) ? 3 : 2;
     int rmax = 1;
     for (int v = 0; v < nv; ++v) rmax = std::max(rmax, esp_rows_v(c, k, v, nb));
     PCM_TRY(c->esp_part.alloc((size_t)rmax * c->M));
+    // one untimed pass first: the first launch of a variant also allocates
+    // its tile buffers and loads its code, which is not what it costs per call
+    for (int v = 0; v < nv; ++v) PCM_TRY(esp_launch_variant(c, k, v, blk, bcls, nb, c->esp_part.p));
+    PCM_CUDA(cudaStreamSynchronize(c->stream));
     cudaEvent_t e[4];
     for (int i = 0; i <= nv; ++i) PCM_CUDA(cudaEventCreate(&e[i]));
     float ms[3] = {0.f, 0.f, 0.f};

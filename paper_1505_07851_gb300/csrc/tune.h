@@ -11,6 +11,9 @@ enum TuneKind {
     // the same choices for the kernels with scalar FP32 instructions (pcm_options.fp32x2 = 0)
     TUNE_ESP_PPT_SCALAR = 2,
     TUNE_FOCK_NPT_SCALAR = 3,
+    // the packed ESP blocks of a batch, which run in one launch for all molecules: pair-driven
+    // with 4 (0) or 2 (1) points per thread (the per-molecule MS-driven kernel has no batched form)
+    TUNE_ESP_PPT_BATCH = 4,
 };
 
 // size bucket of a kernel's work: floor(log2(n)) (pairs of the class)

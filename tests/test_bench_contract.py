@@ -49,3 +49,17 @@ def test_algorithmic_flop_counts():
         # the Fock accumulation adds each R_tuv once instead of an FMA with D
         assert bench.flops_per_interaction(L, "fock") == f - nherm[L] - 1
     assert bench.flops_per_interaction(0, "esp") == 32 and bench.flops_per_interaction(1, "esp") == 55
+
+
+def test_traffic_table_matches_the_roofline_label():
+    """The DRAM traffic recorded from an ncu capture is looked up by the label
+    the roofline gives its dominant class; a recorded entry must carry that
+    exact label, or the bench would report traffic null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    res = {"stats": {"M": 1000, "esp_class_pairs": [0, 10, 0, 0, 0, 0], "fock_class_pairs": [0] * 6},
+           "esp_cls": [0.0, 3.0, 0.0, 0.0, 0.0, 0.0], "fock_cls": [0.0] * 6}
+    roof = bench._dominant(res, "mixed", 1, packed=True)
+    assert ("cluster1000_spd", roof["kernel"]) in bench.NCU_TRAFFIC_BYTES
+    for (workload, label), traffic in bench.NCU_TRAFFIC_BYTES.items():
+        assert workload in bench.WORKLOADS and traffic > 0 and " class: " in label
