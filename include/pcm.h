@@ -67,7 +67,7 @@ typedef enum pcm_status {
 #define PCM_GRAD_C 16           /* pcm_gradient: include (d*c^T/dR) q (the integrals) */
 #define PCM_GRAD_A 32           /* pcm_gradient: include q^T (dA/dR) q / (2 f) (with switching) */
 #define PCM_TWO_DELTA 64        /* pcm_solve: delta is delta_2 of the 2-delta threshold scheme (Section 4b-i) */
-#define PCM_APPLY_FP32 128      /* pcm_apply_a: the inner solver's FP32 matrix-free product (PCM_MIXED) */
+#define PCM_APPLY_FP32 128      /* pcm_apply_a: the FP32 matrix-free product (PCM_MIXED; the inner solver's elements) */
 
 /* precision modes */
 #define PCM_FP64 0              /* every step in FP64 */
@@ -232,8 +232,12 @@ int pcm_energy(pcm_ctx *ctx, const double *q, const double *c, double *E, int fl
  * diagonal included) are held with their FP64 values, every other element is
  * 1/R recomputed per product; the default product is the one the solver forms
  * true residuals and the energy with (double-float 1/R, FP64 near pairs,
- * about 1e-14 relative), PCM_APPLY_FP32 the inner solver's FP32 product
- * (about 1e-6 relative).  flags: PCM_PTR_DEVICE, PCM_ASYNC, PCM_APPLY_FP32
+ * about 1e-14 relative), PCM_APPLY_FP32 an FP32 product with the inner
+ * solver's element formula (FP32 1/R with R^2 clamped at the near-pair
+ * radius, the near-pair list's FP32 corrections; rows summed per column
+ * chunk, whereas the inner solver sums the upper triangle's tiles in fixed
+ * point: the same elements, another order of the FP32 sums; about 1e-6
+ * relative).  flags: PCM_PTR_DEVICE, PCM_ASYNC, PCM_APPLY_FP32
  * (PCM_ERR_UNSUPPORTED unless the context is matrix-free). */
 int pcm_apply_a(pcm_ctx *ctx, const double *x, double *y, int flags);
 

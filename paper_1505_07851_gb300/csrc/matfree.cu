@@ -445,8 +445,10 @@ __device__ __forceinline__ double grid_sum(const double *v, int n, int stride, i
     return res;
 }
 
-// the product's work items: rows rt*512 + t and + 256 (two lanes), columns
-// [s*1024, ...); partial products to ypart[s], p.Ap partial to idot[item]
+// The per-row FP32 matrix-free product (pcm_apply_a with PCM_APPLY_FP32):
+// work items of rows rt*512 + t and + 256 (two lanes), columns [s*1024, ...);
+// partial products to ypart[s], p.Ap partial to idot[item].  The inner solver
+// evaluates the same elements over the upper triangle (pcg_product_free_sym).
 __device__ __forceinline__ void pcg_product(const PcgArgs &a, float4 (*sc)[2])
 {
     __shared__ double red[MV_NT / 32];
@@ -1161,8 +1163,9 @@ int persistent_pcg(pcm_ctx *c, const double *b, double *x, double delta, int max
     return PCM_OK;
 }
 
-// y = A x with the FP32 matrix-free product (for tests: the inner solver's
-// operator applied once), y in FP64
+// y = A x with the FP32 matrix-free elements of the inner solver, summed per
+// row over column chunks (pcg_product; pcm_apply_a with PCM_APPLY_FP32), y in
+// FP64
 __global__ void __launch_bounds__(MV_NT) mv32_reduce_kernel(int M, int S, const float *__restrict__ ypart,
                                                             double *__restrict__ y)
 {
